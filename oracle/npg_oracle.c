@@ -1,0 +1,822 @@
+/*
+ * Neu-PiG per-sequence optimization: plain, slow FP64 CPU oracle.
+ *
+ * TEST INFRASTRUCTURE. Only the test suite, the package's smoke check and the
+ * benchmark's CPU-baseline leg load this library. The product path (libnpg.so
+ * and its Python binding) never calls, links or includes anything here, and
+ * this file includes nothing from the product path.
+ *
+ * Every routine restates the paper's definitions directly, in the paper's
+ * order and notation, with no blocking, fusion or reordering:
+ *   Sec. 3.2  multi-resolution latent grids, trilinear lookup, Eq. 1 level mean
+ *   Sec. 3.3  input vector (Eq. 2), Fourier time encoding (Eq. 3), MLP (Eq. 4)
+ *   Sec. 3.4  quaternion offset + normalisation (Eq. 5), tanh translation
+ *             (Eq. 6), rigid transform (Eq. 7); supplementary rotation study:
+ *             exponential map
+ *   Sec. 3.5  total loss (Eq. 8), Sobolev preconditioner (Eq. 9), L_def
+ *             (Eq. 10), confidence weight (Eq. 11-12), L_iso (Eq. 13), Adam
+ *             with per-level learning rates (implementation details)
+ * The reverse-mode gradient is written by hand, step by step, in the reverse
+ * order of the forward pass. The preconditioner solves (I + lambda L) u = g
+ * twice by conjugate gradients in FP64.
+ *
+ * Readings where the paper is silent (each mirrored by the GPU library):
+ *   - nodes sit at -1 + 2k/(r-1) per axis; queries are clamped to [-1,1];
+ *     the cell index is min(floor(u), r-2); corner c = bx + 2 by + 4 bz;
+ *     node (ix,iy,iz) is stored at ((iz r + iy) r + ix), features innermost.
+ *   - the Chamfer distance is the plain bidirectional squared-L2 one:
+ *     cd = mean_i min_j |x_i - p_j|^2 + mean_j min_i |p_j - x_i|^2; nearest
+ *     neighbour ties go to the lowest index.
+ *   - the Laplacian is the combinatorial graph Laplacian of the 6-connected
+ *     node lattice (natural Neumann boundary), applied per feature channel.
+ *   - the preconditioned gradient replaces the raw gradient as Adam's input
+ *     for grid parameters; MLP parameters use the raw gradient.
+ *   - L_iso reference lengths are the current keyframe lengths, stop-grad;
+ *     d|u|/du at u = 0 is 0 and d|e|/de at e = 0 is 0.
+ *   - frames are 0-based here; t~ = t / (T-1) (t~ = 0 when T = 1); the
+ *     Fourier features are interleaved (sin_1, cos_1, ..., sin_M, cos_M).
+ *   - a zero-norm quaternion (1 + q_w = q_x = q_y = q_z = 0) maps to the
+ *     identity rotation with zero gradient.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAX_LEVELS 16
+
+typedef struct {
+  int L;                   /* number of position-grid levels                 */
+  int res[OR_MAX_LEVELS];  /* nodes per axis of level l (l = 0 is coarsest)  */
+  int F;                   /* features per position-grid node                */
+  int Fn;                  /* features per normal-grid node                  */
+  int rn;                  /* nodes per axis of the normal grid              */
+  int H;                   /* hidden width                                   */
+  int D;                   /* number of hidden layers                        */
+  int rot_mode;            /* 0: quaternion (Eq. 5), 1: exponential map      */
+  int n_freq;              /* Fourier frequencies M (Eq. 3)                  */
+  double slope;            /* LeakyReLU negative slope                       */
+  double alpha;            /* translation squashing factor (Eq. 6)           */
+  double w_iso;            /* isometry weight (Eq. 8)                        */
+} or_cfg;
+
+/* ------------------------------------------------------------------ sizes */
+
+int or_n_out(const or_cfg* c) { return c->rot_mode == 0 ? 7 : 6; }
+int or_k_in(const or_cfg* c) { return c->Fn + c->F + 2 * c->n_freq; }
+
+static long cube(long r) { return r * r * r; }
+
+/* Offset of level l's block in the flat grid vector; l == L is the normal grid. */
+long or_level_offset(const or_cfg* c, int l) {
+  long off = 0;
+  for (int k = 0; k < l && k < c->L; ++k) off += cube(c->res[k]) * c->F;
+  return off;
+}
+
+long or_grid_len(const or_cfg* c) {
+  return or_level_offset(c, c->L) + cube(c->rn) * c->Fn;
+}
+
+/* MLP layout: layer 0 W (H x K) row-major then b (H); hidden layers
+ * 1..D-1 W (H x H), b (H); output layer W (O x H), b (O). */
+long or_mlp_len(const or_cfg* c) {
+  long K = or_k_in(c), H = c->H, D = c->D, O = or_n_out(c);
+  return H * K + H + (D - 1) * (H * H + H) + O * H + O;
+}
+
+/* -------------------------------------------- Sec. 3.2: trilinear lookup */
+
+void or_trilinear(int r, const double* p, long* idx, double* w) {
+  long i0[3];
+  double f[3];
+  for (int a = 0; a < 3; ++a) {
+    double q = p[a];
+    if (q < -1.0) q = -1.0;
+    if (q > 1.0) q = 1.0;
+    double u = (q + 1.0) * 0.5 * (double)(r - 1);
+    long i = (long)floor(u);
+    if (i > r - 2) i = r - 2;
+    if (i < 0) i = 0;
+    i0[a] = i;
+    f[a] = u - (double)i;
+  }
+  for (int c = 0; c < 8; ++c) {
+    int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
+    idx[c] = ((i0[2] + bz) * r + (i0[1] + by)) * r + (i0[0] + bx);
+    w[c] = (bx ? f[0] : 1.0 - f[0]) * (by ? f[1] : 1.0 - f[1]) *
+           (bz ? f[2] : 1.0 - f[2]);
+  }
+}
+
+/* Sec. 3.2: z_p(x) = (1/L) sum_l z_p^l(x) (Eq. 1); z_n(n) from the normal grid.
+ * z is N x (Fn + F), ordered (z_n, z_p) as in the input vector of Eq. 2. */
+void or_encode(const or_cfg* c, int N, const double* x, const double* n,
+               const double* grid, double* z) {
+  int F = c->F, Fn = c->Fn, Z = Fn + F;
+  long idx[8];
+  double w[8];
+  for (int i = 0; i < N; ++i) {
+    double* zi = z + (long)i * Z;
+    for (int k = 0; k < Z; ++k) zi[k] = 0.0;
+    or_trilinear(c->rn, n + 3L * i, idx, w);
+    const double* gn = grid + or_level_offset(c, c->L);
+    for (int k = 0; k < 8; ++k)
+      for (int f = 0; f < Fn; ++f) zi[f] += w[k] * gn[idx[k] * Fn + f];
+    for (int l = 0; l < c->L; ++l) {
+      const double* gl = grid + or_level_offset(c, l);
+      or_trilinear(c->res[l], x + 3L * i, idx, w);
+      for (int k = 0; k < 8; ++k)
+        for (int f = 0; f < F; ++f)
+          zi[Fn + f] += w[k] * gl[idx[k] * F + f] / (double)c->L;
+    }
+  }
+}
+
+/* ------------------------------------- Sec. 3.3, Eq. 3: time embedding */
+
+void or_time_embedding(const or_cfg* c, int T, double* gamma) {
+  const double pi = 3.14159265358979323846;
+  int M = c->n_freq;
+  for (int t = 0; t < T; ++t) {
+    double tt = T > 1 ? (double)t / (double)(T - 1) : 0.0;
+    for (int j = 0; j < M; ++j) {
+      double nu = ldexp(1.0, j); /* nu_j = 2^(j-1) for 1-based j */
+      gamma[(long)t * 2 * M + 2 * j] = sin(pi * nu * tt);
+      gamma[(long)t * 2 * M + 2 * j + 1] = cos(pi * nu * tt);
+    }
+  }
+}
+
+/* ------------------------------------------ Sec. 3.3: the MLP psi (Eq. 4) */
+
+static double act(double s, double slope) { return s > 0.0 ? s : slope * s; }
+static double dact(double s, double slope) { return s > 0.0 ? 1.0 : slope; }
+
+/* One row: pre[k*H + j] and h[k*H + j] for hidden layer k, then o (O). */
+static void mlp_row(const or_cfg* c, const double* mlp, const double* y,
+                    double* pre, double* h, double* o) {
+  int K = or_k_in(c), H = c->H, D = c->D, O = or_n_out(c);
+  const double* W = mlp;
+  const double* b = W + (long)H * K;
+  for (int j = 0; j < H; ++j) {
+    double s = b[j];
+    for (int k = 0; k < K; ++k) s += W[(long)j * K + k] * y[k];
+    pre[j] = s;
+    h[j] = act(s, c->slope);
+  }
+  const double* p = b + H;
+  for (int layer = 1; layer < D; ++layer) {
+    W = p;
+    b = W + (long)H * H;
+    p = b + H;
+    const double* hin = h + (long)(layer - 1) * H;
+    for (int j = 0; j < H; ++j) {
+      double s = b[j];
+      for (int k = 0; k < H; ++k) s += W[(long)j * H + k] * hin[k];
+      pre[(long)layer * H + j] = s;
+      h[(long)layer * H + j] = act(s, c->slope);
+    }
+  }
+  W = p;
+  b = W + (long)O * H;
+  const double* hl = h + (long)(D - 1) * H;
+  for (int j = 0; j < O; ++j) {
+    double s = b[j];
+    for (int k = 0; k < H; ++k) s += W[(long)j * H + k] * hl[k];
+    o[j] = s;
+  }
+}
+
+void or_mlp_forward(const or_cfg* c, const double* mlp, int rows,
+                    const double* y, double* o) {
+  int H = c->H, D = c->D, K = or_k_in(c), O = or_n_out(c);
+  double* pre = (double*)malloc(sizeof(double) * H * D);
+  double* h = (double*)malloc(sizeof(double) * H * D);
+  for (int r = 0; r < rows; ++r)
+    mlp_row(c, mlp, y + (long)r * K, pre, h, o + (long)r * O);
+  free(pre);
+  free(h);
+}
+
+/* ---------------------------------------- Sec. 3.4: transformation mapping */
+
+static void quat_to_R(const double* q, double* R) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* Exponential map R = I + A K + B K^2, K = [w]x, A = sin t / t, B = (1-cos t)/t^2,
+ * with the Taylor series below t = 1e-2. Also returns A'/t and B'/t. */
+static void expmap_coeffs(double th, double* A, double* B, double* dA, double* dB) {
+  double t2 = th * th;
+  if (th < 1e-2) {
+    *A = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
+    *B = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+    *dA = -1.0 / 3.0 + t2 / 30.0 - t2 * t2 / 840.0;
+    *dB = -1.0 / 12.0 + t2 / 180.0 - t2 * t2 / 6720.0;
+  } else {
+    double s = sin(th), co = cos(th), omc = 2.0 * sin(0.5 * th) * sin(0.5 * th);
+    *A = s / th;
+    *B = omc / t2;
+    *dA = (th * co - s) / (t2 * th);
+    *dB = (th * s - 2.0 * omc) / (t2 * t2);
+  }
+}
+
+static void skew(const double* w, double* K) {
+  K[0] = 0; K[1] = -w[2]; K[2] = w[1];
+  K[3] = w[2]; K[4] = 0; K[5] = -w[0];
+  K[6] = -w[1]; K[7] = w[0]; K[8] = 0;
+}
+
+static void matmul3(const double* A, const double* B, double* C) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += A[i * 3 + k] * B[k * 3 + j];
+      C[i * 3 + j] = s;
+    }
+}
+
+static void expmap_R(const double* w, double* R) {
+  double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  double A, B, dA, dB, K[9], K2[9];
+  expmap_coeffs(th, &A, &B, &dA, &dB);
+  skew(w, K);
+  matmul3(K, K, K2);
+  for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + A * K[i] + B * K2[i];
+}
+
+/* Rotation matrix R (row-major) and translation d-hat from one output row o. */
+void or_rotation_translation(const or_cfg* c, const double* o, double* R, double* d) {
+  if (c->rot_mode == 0) {
+    double q[4] = {1.0 + o[0], o[1], o[2], o[3]};
+    double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (nq > 0.0) {
+      for (int k = 0; k < 4; ++k) q[k] /= nq;
+    } else {
+      q[0] = 1.0; q[1] = q[2] = q[3] = 0.0;
+    }
+    quat_to_R(q, R);
+    for (int a = 0; a < 3; ++a) d[a] = tanh(c->alpha * o[4 + a]);
+  } else {
+    expmap_R(o, R);
+    for (int a = 0; a < 3; ++a) d[a] = tanh(c->alpha * o[3 + a]);
+  }
+}
+
+/* Eq. 7: x-hat = R(q-hat) x + d-hat. */
+static void transform_row(const or_cfg* c, const double* o, const double* x, double* xh) {
+  double R[9], d[3];
+  or_rotation_translation(c, o, R, d);
+  for (int a = 0; a < 3; ++a)
+    xh[a] = R[a * 3 + 0] * x[0] + R[a * 3 + 1] * x[1] + R[a * 3 + 2] * x[2] + d[a];
+}
+
+/* Given g = dL/dx-hat of one row, write dL/do (length O). */
+static void transform_row_backward(const or_cfg* c, const double* o, const double* x,
+                                   const double* g, double* go) {
+  double G[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) G[a * 3 + b] = g[a] * x[b];
+  if (c->rot_mode == 0) {
+    double q[4] = {1.0 + o[0], o[1], o[2], o[3]};
+    double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    if (nq > 0.0) {
+      double w = q[0] / nq, X = q[1] / nq, Y = q[2] / nq, Z = q[3] / nq;
+      double gq[4];
+      gq[0] = 2 * (-Z * G[1] + Y * G[2] + Z * G[3] - X * G[5] - Y * G[6] + X * G[7]);
+      gq[1] = 2 * (Y * G[1] + Z * G[2] + Y * G[3] - 2 * X * G[4] - w * G[5] + Z * G[6] +
+                   w * G[7] - 2 * X * G[8]);
+      gq[2] = 2 * (-2 * Y * G[0] + X * G[1] + w * G[2] + X * G[3] + Z * G[5] - w * G[6] +
+                   Z * G[7] - 2 * Y * G[8]);
+      gq[3] = 2 * (-2 * Z * G[0] - w * G[1] + X * G[2] + w * G[3] - 2 * Z * G[4] + Y * G[5] +
+                   X * G[6] + Y * G[7]);
+      double qh[4] = {w, X, Y, Z};
+      double dot = 0;
+      for (int k = 0; k < 4; ++k) dot += qh[k] * gq[k];
+      for (int k = 0; k < 4; ++k) go[k] = (gq[k] - qh[k] * dot) / nq;
+    } else {
+      for (int k = 0; k < 4; ++k) go[k] = 0.0;
+    }
+    for (int a = 0; a < 3; ++a) {
+      double th = tanh(c->alpha * o[4 + a]);
+      go[4 + a] = g[a] * c->alpha * (1.0 - th * th);
+    }
+  } else {
+    const double* w = o;
+    double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double A, B, dA, dB, K[9], K2[9];
+    expmap_coeffs(th, &A, &B, &dA, &dB);
+    skew(w, K);
+    matmul3(K, K, K2);
+    for (int k = 0; k < 3; ++k) {
+      double e[3] = {0, 0, 0}, Ek[9], EK[9], KE[9];
+      e[k] = 1.0;
+      skew(e, Ek);
+      matmul3(Ek, K, EK);
+      matmul3(K, Ek, KE);
+      double s = 0;
+      for (int i = 0; i < 9; ++i) {
+        double dR = dA * w[k] * K[i] + A * Ek[i] + dB * w[k] * K2[i] + B * (EK[i] + KE[i]);
+        s += G[i] * dR;
+      }
+      go[k] = s;
+    }
+    for (int a = 0; a < 3; ++a) {
+      double t = tanh(c->alpha * o[3 + a]);
+      go[3 + a] = g[a] * c->alpha * (1.0 - t * t);
+    }
+  }
+}
+
+/* Full decode of all rows (i, t): y = (z_i, gamma_t) (Eq. 2), o = psi(y),
+ * x-hat[t][i] = R x_i + d (Eq. 5-7). xhat is T x N x 3. */
+void or_decode(const or_cfg* c, int N, int T, const double* x, const double* z,
+               const double* gamma, const double* mlp, double* xhat) {
+  int K = or_k_in(c), Z = c->Fn + c->F, G2 = 2 * c->n_freq, O = or_n_out(c);
+  int H = c->H, D = c->D;
+  double* y = (double*)malloc(sizeof(double) * K);
+  double* pre = (double*)malloc(sizeof(double) * H * D);
+  double* h = (double*)malloc(sizeof(double) * H * D);
+  double o[8];
+  for (int t = 0; t < T; ++t)
+    for (int i = 0; i < N; ++i) {
+      for (int k = 0; k < Z; ++k) y[k] = z[(long)i * Z + k];
+      for (int k = 0; k < G2; ++k) y[Z + k] = gamma[(long)t * G2 + k];
+      mlp_row(c, mlp, y, pre, h, o);
+      (void)O;
+      transform_row(c, o, x + 3L * i, xhat + ((long)t * N + i) * 3);
+    }
+  free(y);
+  free(pre);
+  free(h);
+}
+
+/* ------------------------------------------- Sec. 3.5: Chamfer distance */
+
+/* Brute-force nearest neighbour of each query among the candidates; ties go
+ * to the lowest index. decide_f32 != 0 takes the argmin decision in FP32 on
+ * the inputs rounded to float, with the distance formed as
+ * d = dx*dx; d = fma(dy, dy, d); d = fma(dz, dz, d). The returned distance is
+ * always the FP64 squared distance of the chosen pair. */
+void or_nn(int nq, const double* q, int nc, const double* cand, int decide_f32,
+           int32_t* idx, double* dist) {
+  for (int i = 0; i < nq; ++i) {
+    const double* a = q + 3L * i;
+    int best = -1;
+    if (decide_f32) {
+      float ax = (float)a[0], ay = (float)a[1], az = (float)a[2];
+      float bd = 0.0f;
+      for (int j = 0; j < nc; ++j) {
+        float dx = ax - (float)cand[3L * j];
+        float dy = ay - (float)cand[3L * j + 1];
+        float dz = az - (float)cand[3L * j + 2];
+        float d = dx * dx;
+        d = fmaf(dy, dy, d);
+        d = fmaf(dz, dz, d);
+        if (best < 0 || d < bd) { bd = d; best = j; }
+      }
+    } else {
+      double bd = 0.0;
+      for (int j = 0; j < nc; ++j) {
+        double dx = a[0] - cand[3L * j], dy = a[1] - cand[3L * j + 1], dz = a[2] - cand[3L * j + 2];
+        double d = dx * dx + dy * dy + dz * dz;
+        if (best < 0 || d < bd) { bd = d; best = j; }
+      }
+    }
+    idx[i] = best;
+    const double* b = cand + 3L * best;
+    double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    dist[i] = dx * dx + dy * dy + dz * dz;
+  }
+}
+
+/* Per frame t: cd_t = mean_i min_j |x-hat_i - p_j|^2 + mean_j min_i |p_j - x-hat_i|^2.
+ * off has T+1 entries; points of frame t are pts[off[t] .. off[t+1]).
+ * nn_x, d_x are T x N; nn_p, d_p follow the point order (off[T] entries). */
+void or_chamfer(int T, int N, const double* xhat, const int64_t* off, const double* pts,
+                int decide_f32, int32_t* nn_x, double* d_x, int32_t* nn_p, double* d_p,
+                double* cd) {
+  for (int t = 0; t < T; ++t) {
+    const double* X = xhat + (long)t * N * 3;
+    long M = off[t + 1] - off[t];
+    const double* P = pts + 3 * off[t];
+    or_nn(N, X, (int)M, P, decide_f32, nn_x + (long)t * N, d_x + (long)t * N);
+    or_nn((int)M, P, N, X, decide_f32, nn_p + off[t], d_p + off[t]);
+    double sx = 0, sp = 0;
+    for (int i = 0; i < N; ++i) sx += d_x[(long)t * N + i];
+    for (long j = 0; j < M; ++j) sp += d_p[off[t] + j];
+    cd[t] = sx / N + sp / (double)M;
+  }
+}
+
+/* ---------------------------------- Sec. 3.5, Eq. 11-12: confidence weight */
+
+/* w(t) = prod_{tau between t_key and t, inclusive} omega(tau)^delta,
+ * omega(tau) = 1 / (1 + max(0, cd_tau - cd_tkey)), delta = 1 - sqrt(e / e_max)
+ * with e / e_max clamped to [0, 1]. */
+void or_conf_weights(int T, const double* cd, int t_key, double e, double e_max, double* w) {
+  double eb = e_max > 0 ? e / e_max : 1.0;
+  if (eb < 0) eb = 0;
+  if (eb > 1) eb = 1;
+  double delta = 1.0 - sqrt(eb);
+  for (int t = 0; t < T; ++t) {
+    int lo = t < t_key ? t : t_key, hi = t < t_key ? t_key : t;
+    double prod = 1.0;
+    for (int tau = lo; tau <= hi; ++tau) {
+      double ex = cd[tau] - cd[t_key];
+      double om = 1.0 / (1.0 + (ex > 0 ? ex : 0.0));
+      prod *= pow(om, delta);
+    }
+    w[t] = prod;
+  }
+}
+
+/* ------------------------------------------------------ mesh edges */
+
+static int cmp_edge(const void* a, const void* b) {
+  const int32_t* x = (const int32_t*)a;
+  const int32_t* y = (const int32_t*)b;
+  if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
+  if (x[1] != y[1]) return x[1] < y[1] ? -1 : 1;
+  return 0;
+}
+
+/* Unique undirected edges (i < j), sorted; edges must hold 3 * F_tri pairs.
+ * Returns the number of edges. */
+long or_edges(int F_tri, const int32_t* faces, int32_t* edges) {
+  long n = 0;
+  for (int f = 0; f < F_tri; ++f)
+    for (int k = 0; k < 3; ++k) {
+      int32_t a = faces[3L * f + k], b = faces[3L * f + (k + 1) % 3];
+      if (a == b) continue;
+      edges[2 * n] = a < b ? a : b;
+      edges[2 * n + 1] = a < b ? b : a;
+      ++n;
+    }
+  qsort(edges, (size_t)n, 2 * sizeof(int32_t), cmp_edge);
+  long u = 0;
+  for (long k = 0; k < n; ++k)
+    if (u == 0 || cmp_edge(edges + 2 * k, edges + 2 * (u - 1)) != 0) {
+      edges[2 * u] = edges[2 * k];
+      edges[2 * u + 1] = edges[2 * k + 1];
+      ++u;
+    }
+  return u;
+}
+
+/* Edge lengths |x-hat_i - x-hat_j| of frame t (E entries). */
+void or_edge_lengths(int N, const double* xhat, int t, long E, const int32_t* edges,
+                     double* len) {
+  const double* X = xhat + (long)t * N * 3;
+  for (long e = 0; e < E; ++e) {
+    const double* a = X + 3L * edges[2 * e];
+    const double* b = X + 3L * edges[2 * e + 1];
+    double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    len[e] = sqrt(dx * dx + dy * dy + dz * dz);
+  }
+}
+
+/* Eq. 13 with the reference lengths given (their stop-grad values). */
+double or_iso(int T, int N, const double* xhat, long E, const int32_t* edges,
+              const double* lref) {
+  double s = 0;
+  double* len = (double*)malloc(sizeof(double) * (E > 0 ? E : 1));
+  for (int t = 0; t < T; ++t) {
+    or_edge_lengths(N, xhat, t, E, edges, len);
+    for (long e = 0; e < E; ++e) s += fabs(len[e] - lref[e]);
+  }
+  free(len);
+  return E > 0 ? s / ((double)T * (double)E) : 0.0;
+}
+
+/* ------------------------------ loss and hand-written reverse-mode gradient */
+
+/* L = L_def + w_iso L_iso (Eq. 8, 10, 13) with the stop-grad quantities held
+ * fixed: w_fixed (T confidence weights) and lref (E keyframe edge lengths).
+ * Writes dL/d grid and dL/d mlp when the pointers are non-null (they are
+ * overwritten, not accumulated). parts (nullable) receives {L_def, L_iso}.
+ * xhat_out (nullable, T x N x 3), cd_out (nullable, T). nn_x/nn_p (nullable)
+ * receive the nearest-neighbour indices. */
+double or_loss_grad(const or_cfg* c, int N, const double* x, const double* n, int T,
+                    const int64_t* off, const double* pts, long E, const int32_t* edges,
+                    const double* grid, const double* mlp, const double* w_fixed,
+                    const double* lref, int decide_f32, double* g_grid, double* g_mlp,
+                    double* xhat_out, double* cd_out, double* parts, int32_t* nn_x_out,
+                    int32_t* nn_p_out) {
+  int F = c->F, Fn = c->Fn, Z = Fn + F, G2 = 2 * c->n_freq, K = or_k_in(c);
+  int H = c->H, D = c->D, O = or_n_out(c);
+  long MT = off[T];
+  double* z = (double*)malloc(sizeof(double) * (size_t)N * Z);
+  double* gamma = (double*)malloc(sizeof(double) * (size_t)T * G2);
+  double* xhat = (double*)malloc(sizeof(double) * (size_t)T * N * 3);
+  or_encode(c, N, x, n, grid, z);
+  or_time_embedding(c, T, gamma);
+  or_decode(c, N, T, x, z, gamma, mlp, xhat);
+
+  int32_t* nn_x = (int32_t*)malloc(sizeof(int32_t) * (size_t)T * N);
+  double* d_x = (double*)malloc(sizeof(double) * (size_t)T * N);
+  int32_t* nn_p = (int32_t*)malloc(sizeof(int32_t) * (size_t)(MT > 0 ? MT : 1));
+  double* d_p = (double*)malloc(sizeof(double) * (size_t)(MT > 0 ? MT : 1));
+  double* cd = (double*)malloc(sizeof(double) * T);
+  or_chamfer(T, N, xhat, off, pts, decide_f32, nn_x, d_x, nn_p, d_p, cd);
+
+  /* Eq. 10 and Eq. 13 */
+  double Ldef = 0;
+  for (int t = 0; t < T; ++t) Ldef += w_fixed[t] * cd[t];
+  Ldef /= T;
+  double Liso = or_iso(T, N, xhat, E, edges, lref);
+  double Lval = Ldef + c->w_iso * Liso;
+  if (parts) { parts[0] = Ldef; parts[1] = Liso; }
+
+  if (g_grid || g_mlp) {
+    /* dL/dx-hat (T x N x 3) */
+    double* gx = (double*)calloc((size_t)T * N * 3, sizeof(double));
+    for (int t = 0; t < T; ++t) {
+      double ct = w_fixed[t] / T; /* dL/dcd_t */
+      long M = off[t + 1] - off[t];
+      const double* P = pts + 3 * off[t];
+      const double* X = xhat + (long)t * N * 3;
+      double* GX = gx + (long)t * N * 3;
+      for (int i = 0; i < N; ++i) {
+        const double* p = P + 3L * nn_x[(long)t * N + i];
+        for (int a = 0; a < 3; ++a) GX[3L * i + a] += ct * (2.0 / N) * (X[3L * i + a] - p[a]);
+      }
+      for (long j = 0; j < M; ++j) {
+        int i = nn_p[off[t] + j];
+        for (int a = 0; a < 3; ++a)
+          GX[3L * i + a] += ct * (2.0 / (double)M) * (X[3L * i + a] - P[3 * j + a]);
+      }
+      if (E > 0) {
+        double ci = c->w_iso / ((double)T * (double)E);
+        for (long e = 0; e < E; ++e) {
+          int a0 = edges[2 * e], b0 = edges[2 * e + 1];
+          double v[3];
+          for (int a = 0; a < 3; ++a) v[a] = X[3L * a0 + a] - X[3L * b0 + a];
+          double len = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+          double diff = len - lref[e];
+          double s = diff > 0 ? 1.0 : (diff < 0 ? -1.0 : 0.0);
+          if (len > 0 && s != 0) {
+            for (int a = 0; a < 3; ++a) {
+              GX[3L * a0 + a] += ci * s * v[a] / len;
+              GX[3L * b0 + a] -= ci * s * v[a] / len;
+            }
+          }
+        }
+      }
+    }
+
+    /* back through Eq. 7-5, the MLP (Eq. 4) and the input vector (Eq. 2) */
+    double* gm = (double*)calloc((size_t)or_mlp_len(c), sizeof(double));
+    double* gz = (double*)calloc((size_t)N * Z, sizeof(double));
+    double* y = (double*)malloc(sizeof(double) * K);
+    double* pre = (double*)malloc(sizeof(double) * H * D);
+    double* h = (double*)malloc(sizeof(double) * H * D);
+    double* dh = (double*)malloc(sizeof(double) * H);
+    double* dp = (double*)malloc(sizeof(double) * H);
+    double o[8], go[8];
+    for (int t = 0; t < T; ++t)
+      for (int i = 0; i < N; ++i) {
+        for (int k = 0; k < Z; ++k) y[k] = z[(long)i * Z + k];
+        for (int k = 0; k < G2; ++k) y[Z + k] = gamma[(long)t * G2 + k];
+        mlp_row(c, mlp, y, pre, h, o);
+        transform_row_backward(c, o, x + 3L * i, gx + ((long)t * N + i) * 3, go);
+        /* layer offsets in the flat parameter vector */
+        long offW0 = 0, offb0 = (long)H * K;
+        long offHid = offb0 + H; /* hidden layer k>=1 at offHid + (k-1)(H*H+H) */
+        long offWo = offHid + (long)(D - 1) * (H * H + H), offbo = offWo + (long)O * H;
+        /* output layer */
+        const double* hl = h + (long)(D - 1) * H;
+        for (int k = 0; k < H; ++k) dh[k] = 0.0;
+        for (int j = 0; j < O; ++j) {
+          gm[offbo + j] += go[j];
+          for (int k = 0; k < H; ++k) {
+            gm[offWo + (long)j * H + k] += go[j] * hl[k];
+            dh[k] += mlp[offWo + (long)j * H + k] * go[j];
+          }
+        }
+        /* hidden layers D-1 .. 1 */
+        for (int layer = D - 1; layer >= 1; --layer) {
+          long offW = offHid + (long)(layer - 1) * (H * H + H), offb = offW + (long)H * H;
+          const double* hin = h + (long)(layer - 1) * H;
+          for (int j = 0; j < H; ++j) dp[j] = dh[j] * dact(pre[(long)layer * H + j], c->slope);
+          for (int k = 0; k < H; ++k) dh[k] = 0.0;
+          for (int j = 0; j < H; ++j) {
+            gm[offb + j] += dp[j];
+            for (int k = 0; k < H; ++k) {
+              gm[offW + (long)j * H + k] += dp[j] * hin[k];
+              dh[k] += mlp[offW + (long)j * H + k] * dp[j];
+            }
+          }
+        }
+        /* first layer */
+        for (int j = 0; j < H; ++j) dp[j] = dh[j] * dact(pre[j], c->slope);
+        for (int j = 0; j < H; ++j) {
+          gm[offb0 + j] += dp[j];
+          for (int k = 0; k < K; ++k) gm[offW0 + (long)j * K + k] += dp[j] * y[k];
+          for (int k = 0; k < Z; ++k) gz[(long)i * Z + k] += mlp[offW0 + (long)j * K + k] * dp[j];
+        }
+      }
+    if (g_mlp) memcpy(g_mlp, gm, sizeof(double) * (size_t)or_mlp_len(c));
+
+    /* back through the trilinear lookups and the level mean (Eq. 1) */
+    if (g_grid) {
+      memset(g_grid, 0, sizeof(double) * (size_t)or_grid_len(c));
+      long idx[8];
+      double w[8];
+      for (int i = 0; i < N; ++i) {
+        const double* gzi = gz + (long)i * Z;
+        or_trilinear(c->rn, n + 3L * i, idx, w);
+        double* gn = g_grid + or_level_offset(c, c->L);
+        for (int k = 0; k < 8; ++k)
+          for (int f = 0; f < Fn; ++f) gn[idx[k] * Fn + f] += w[k] * gzi[f];
+        for (int l = 0; l < c->L; ++l) {
+          double* gl = g_grid + or_level_offset(c, l);
+          or_trilinear(c->res[l], x + 3L * i, idx, w);
+          for (int k = 0; k < 8; ++k)
+            for (int f = 0; f < F; ++f) gl[idx[k] * F + f] += w[k] * gzi[Fn + f] / (double)c->L;
+        }
+      }
+    }
+    free(gx); free(gm); free(gz); free(y); free(pre); free(h); free(dh); free(dp);
+  }
+
+  if (xhat_out) memcpy(xhat_out, xhat, sizeof(double) * (size_t)T * N * 3);
+  if (cd_out) memcpy(cd_out, cd, sizeof(double) * T);
+  if (nn_x_out) memcpy(nn_x_out, nn_x, sizeof(int32_t) * (size_t)T * N);
+  if (nn_p_out && MT > 0) memcpy(nn_p_out, nn_p, sizeof(int32_t) * (size_t)MT);
+  free(z); free(gamma); free(xhat); free(nn_x); free(d_x); free(nn_p); free(d_p); free(cd);
+  return Lval;
+}
+
+/* The loss as the method evaluates it at iteration e: the stop-grad inputs
+ * (w_conf from this forward pass's cd, Eq. 11-12, and the keyframe edge
+ * lengths of this forward pass, Eq. 13) are computed first, then held fixed.
+ * w_out (T) and lref_out (E) are nullable. */
+double or_loss_full(const or_cfg* c, int N, const double* x, const double* n, int T,
+                    const int64_t* off, const double* pts, long E, const int32_t* edges,
+                    int t_key, double e, double e_max, const double* grid, const double* mlp,
+                    int decide_f32, double* g_grid, double* g_mlp, double* xhat_out,
+                    double* cd_out, double* w_out, double* parts, int32_t* nn_x_out,
+                    int32_t* nn_p_out) {
+  int Z = c->Fn + c->F, G2 = 2 * c->n_freq;
+  long MT = off[T];
+  double* z = (double*)malloc(sizeof(double) * (size_t)N * Z);
+  double* gamma = (double*)malloc(sizeof(double) * (size_t)T * G2);
+  double* xhat = (double*)malloc(sizeof(double) * (size_t)T * N * 3);
+  or_encode(c, N, x, n, grid, z);
+  or_time_embedding(c, T, gamma);
+  or_decode(c, N, T, x, z, gamma, mlp, xhat);
+  int32_t* nn_x = (int32_t*)malloc(sizeof(int32_t) * (size_t)T * N);
+  double* d_x = (double*)malloc(sizeof(double) * (size_t)T * N);
+  int32_t* nn_p = (int32_t*)malloc(sizeof(int32_t) * (size_t)(MT > 0 ? MT : 1));
+  double* d_p = (double*)malloc(sizeof(double) * (size_t)(MT > 0 ? MT : 1));
+  double* cd = (double*)malloc(sizeof(double) * T);
+  double* w = (double*)malloc(sizeof(double) * T);
+  double* lref = (double*)malloc(sizeof(double) * (E > 0 ? E : 1));
+  or_chamfer(T, N, xhat, off, pts, decide_f32, nn_x, d_x, nn_p, d_p, cd);
+  or_conf_weights(T, cd, t_key, e, e_max, w);
+  or_edge_lengths(N, xhat, t_key, E, edges, lref);
+  double L = or_loss_grad(c, N, x, n, T, off, pts, E, edges, grid, mlp, w, lref, decide_f32,
+                          g_grid, g_mlp, xhat_out, cd_out, parts, nn_x_out, nn_p_out);
+  if (w_out) memcpy(w_out, w, sizeof(double) * T);
+  free(z); free(gamma); free(xhat); free(nn_x); free(d_x); free(nn_p); free(d_p);
+  free(cd); free(w); free(lref);
+  return L;
+}
+
+/* ------------------------------------------- Sec. 3.5, Eq. 9: preconditioner */
+
+/* y = (I + lambda L) u on an r^3 node lattice, one channel (stride F). */
+static void apply_A(int r, int F, int ch, double lambda, const double* u, double* y) {
+  for (long iz = 0; iz < r; ++iz)
+    for (long iy = 0; iy < r; ++iy)
+      for (long ix = 0; ix < r; ++ix) {
+        long k = (iz * r + iy) * r + ix;
+        double uk = u[k * F + ch];
+        double lap = 0.0;
+        if (ix > 0) lap += uk - u[(k - 1) * F + ch];
+        if (ix < r - 1) lap += uk - u[(k + 1) * F + ch];
+        if (iy > 0) lap += uk - u[(k - r) * F + ch];
+        if (iy < r - 1) lap += uk - u[(k + r) * F + ch];
+        if (iz > 0) lap += uk - u[(k - (long)r * r) * F + ch];
+        if (iz < r - 1) lap += uk - u[(k + (long)r * r) * F + ch];
+        y[k * F + ch] = uk + lambda * lap;
+      }
+}
+
+/* Solve (I + lambda L) u = b for channel ch by conjugate gradients. */
+static int cg_solve(int r, int F, int ch, double lambda, const double* b, double* u,
+                    double tol, int max_iter) {
+  long n = cube(r);
+  double* res = (double*)malloc(sizeof(double) * n * F);
+  double* p = (double*)malloc(sizeof(double) * n * F);
+  double* Ap = (double*)malloc(sizeof(double) * n * F);
+  double bb = 0;
+  for (long k = 0; k < n; ++k) {
+    u[k * F + ch] = 0.0;
+    res[k * F + ch] = b[k * F + ch];
+    p[k * F + ch] = b[k * F + ch];
+    bb += b[k * F + ch] * b[k * F + ch];
+  }
+  double rr = bb;
+  int it = 0;
+  while (rr > tol * tol * bb && it < max_iter) {
+    apply_A(r, F, ch, lambda, p, Ap);
+    double pAp = 0;
+    for (long k = 0; k < n; ++k) pAp += p[k * F + ch] * Ap[k * F + ch];
+    double al = rr / pAp;
+    double rr2 = 0;
+    for (long k = 0; k < n; ++k) {
+      u[k * F + ch] += al * p[k * F + ch];
+      res[k * F + ch] -= al * Ap[k * F + ch];
+      rr2 += res[k * F + ch] * res[k * F + ch];
+    }
+    double be = rr2 / rr;
+    for (long k = 0; k < n; ++k) p[k * F + ch] = res[k * F + ch] + be * p[k * F + ch];
+    rr = rr2;
+    ++it;
+  }
+  free(res);
+  free(p);
+  free(Ap);
+  return it;
+}
+
+/* out = (I + lambda L)^-2 g for every channel of one r^3 x F block.
+ * Returns the largest CG iteration count used. */
+int or_precondition(int r, int F, double lambda, const double* g, double* out, double tol,
+                    int max_iter) {
+  long n = cube(r);
+  double* tmp = (double*)malloc(sizeof(double) * n * F);
+  int worst = 0;
+  for (int ch = 0; ch < F; ++ch) {
+    int a = cg_solve(r, F, ch, lambda, g, tmp, tol, max_iter);
+    int b = cg_solve(r, F, ch, lambda, tmp, out, tol, max_iter);
+    if (a > worst) worst = a;
+    if (b > worst) worst = b;
+  }
+  free(tmp);
+  return worst;
+}
+
+/* ------------------------------------------------------------ Adam */
+
+/* Kingma & Ba, bias-corrected; step is 1-based. */
+void or_adam(long n, double* p, const double* g, double* m, double* v, double lr, double b1,
+             double b2, double eps, int step) {
+  double c1 = 1.0 - pow(b1, step), c2 = 1.0 - pow(b2, step);
+  for (long k = 0; k < n; ++k) {
+    m[k] = b1 * m[k] + (1.0 - b1) * g[k];
+    v[k] = b2 * v[k] + (1.0 - b2) * g[k] * g[k];
+    double mh = m[k] / c1, vh = v[k] / c2;
+    p[k] -= lr * mh / (sqrt(vh) + eps);
+  }
+}
+
+/* ------------------------------------------------- one whole iteration */
+
+/* One optimisation iteration e (0-based): loss and gradient at the current
+ * parameters, the preconditioner of Eq. 9 on every grid level (lambda[l],
+ * l = L for the normal grid), then Adam (lr_grid[l] per level, lr_mlp on the
+ * MLP) with step count e + 1. Parameters and moments are updated in place.
+ * g_grid_pc (nullable) receives the preconditioned grid gradient.
+ * Returns the loss before the update. */
+double or_iteration(const or_cfg* c, int N, const double* x, const double* n, int T,
+                    const int64_t* off, const double* pts, long E, const int32_t* edges,
+                    int t_key, int e, int e_max, double* grid, double* mlp, double* m_grid,
+                    double* v_grid, double* m_mlp, double* v_mlp, const double* lr_grid,
+                    double lr_mlp, const double* lambda, double b1, double b2, double eps,
+                    int decide_f32, double cg_tol, double* cd_out, double* g_grid_out,
+                    double* g_grid_pc, double* g_mlp_out) {
+  long GL = or_grid_len(c), ML = or_mlp_len(c);
+  double* gg = (double*)malloc(sizeof(double) * GL);
+  double* gp = (double*)malloc(sizeof(double) * GL);
+  double* gm = (double*)malloc(sizeof(double) * ML);
+  double L = or_loss_full(c, N, x, n, T, off, pts, E, edges, t_key, (double)e, (double)e_max,
+                          grid, mlp, decide_f32, gg, gm, NULL, cd_out, NULL, NULL, NULL, NULL);
+  for (int l = 0; l <= c->L; ++l) {
+    int r = l < c->L ? c->res[l] : c->rn;
+    int F = l < c->L ? c->F : c->Fn;
+    long o = or_level_offset(c, l);
+    or_precondition(r, F, lambda[l], gg + o, gp + o, cg_tol, 100000);
+  }
+  for (int l = 0; l <= c->L; ++l) {
+    int r = l < c->L ? c->res[l] : c->rn;
+    int F = l < c->L ? c->F : c->Fn;
+    long o = or_level_offset(c, l), len = cube(r) * F;
+    or_adam(len, grid + o, gp + o, m_grid + o, v_grid + o, lr_grid[l], b1, b2, eps, e + 1);
+  }
+  or_adam(ML, mlp, gm, m_mlp, v_mlp, lr_mlp, b1, b2, eps, e + 1);
+  if (g_grid_out) memcpy(g_grid_out, gg, sizeof(double) * GL);
+  if (g_grid_pc) memcpy(g_grid_pc, gp, sizeof(double) * GL);
+  if (g_mlp_out) memcpy(g_mlp_out, gm, sizeof(double) * ML);
+  free(gg);
+  free(gp);
+  free(gm);
+  return L;
+}

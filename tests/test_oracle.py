@@ -1,0 +1,387 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test pins one part of the oracle to a closed form, an invariant the paper
+states, a library routine computing the same textbook quantity, a hand-worked
+example (tests/golden/) or brute force / finite differences, so that a dropped
+term, a wrong sign or index or a transposed operand fails at least one test.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_22212_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def small_cfg(rot_mode=0, slope=0.01, F=2, L=2, res=(3, 5), H=8, D=2):
+    return O.make_cfg(L=L, res=res, F=F, Fn=2, rn=4, H=H, D=D, rot_mode=rot_mode, slope=slope)
+
+
+# ---------------------------------------------------------------- Sec. 3.2
+
+def test_trilinear_matches_scipy_regular_grid_interpolator():
+    """Sec. 3.2: trilinear lookup == scipy's linear RegularGridInterpolator."""
+    from scipy.interpolate import RegularGridInterpolator
+    rng = np.random.default_rng(1)
+    for r in (2, 3, 7, 16):
+        cfg = O.make_cfg(L=1, res=(r,), F=3, Fn=1, rn=2)
+        G = rng.normal(size=(r, r, r, 3))            # [iz, iy, ix, f]
+        gn = np.zeros(2 * 2 * 2 * 1)
+        grid = np.concatenate([G.ravel(), gn])
+        ax = np.linspace(-1, 1, r)
+        x = rng.uniform(-1, 1, size=(200, 3))
+        x[:5] = [[-1, -1, -1], [1, 1, 1], [1, -1, 1], [0, 0, 0], [-1, 1, 0.3]]
+        z = O.encode(cfg, x, np.zeros_like(x), grid)[:, 1:]
+        for f in range(3):
+            ip = RegularGridInterpolator((ax, ax, ax), G[..., f], method="linear")
+            ref = ip(x[:, ::-1])  # (z, y, x) order
+            np.testing.assert_allclose(z[:, f], ref, rtol=0, atol=1e-12)
+
+
+def test_trilinear_weights_partition_of_unity_and_node_values():
+    rng = np.random.default_rng(2)
+    for r in (2, 5, 9):
+        for _ in range(50):
+            p = rng.uniform(-1, 1, 3)
+            idx, w = O.trilinear(r, p)
+            assert abs(w.sum() - 1.0) < 1e-14
+            assert np.all(w >= -1e-15) and np.all(idx >= 0) and np.all(idx < r ** 3)
+        # at a node, the node's own weight is 1
+        k = (1, r - 1, 0)
+        p = np.array([-1 + 2 * k[0] / (r - 1), -1 + 2 * k[1] / (r - 1), -1 + 2 * k[2] / (r - 1)])
+        idx, w = O.trilinear(r, p)
+        node = (k[2] * r + k[1]) * r + k[0]
+        assert abs(w[list(idx).index(node)] - 1.0) < 1e-12 if node in idx else False
+
+
+def test_level_mean_reproduces_affine_field():
+    """Eq. 1: averaging L levels that all hold the same affine field gives it back."""
+    rng = np.random.default_rng(3)
+    res = (2, 4, 9)
+    F = 2
+    cfg = O.make_cfg(L=3, res=res, F=F, Fn=2, rn=4)
+    A = rng.normal(size=(F, 3))
+    b = rng.normal(size=F)
+    parts = []
+    for r in res:
+        ax = np.linspace(-1, 1, r)
+        Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+        P = np.stack([X, Y, Z], -1).reshape(-1, 3)
+        parts.append((P @ A.T + b).ravel())
+    An = rng.normal(size=(2, 3))
+    ax = np.linspace(-1, 1, 4)
+    Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+    P = np.stack([X, Y, Z], -1).reshape(-1, 3)
+    parts.append((P @ An.T).ravel())
+    grid = np.concatenate(parts)
+    assert len(grid) == O.grid_len(cfg)
+    x = rng.uniform(-1, 1, size=(100, 3))
+    n = rng.normal(size=(100, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    z = O.encode(cfg, x, n, grid)
+    np.testing.assert_allclose(z[:, 2:], x @ A.T + b, atol=1e-12)
+    np.testing.assert_allclose(z[:, :2], n @ An.T, atol=1e-12)
+
+
+# ---------------------------------------------------------------- Sec. 3.3
+
+def test_time_embedding_golden():
+    g = _gold("time_embedding.json")
+    cfg = small_cfg()
+    gam = O.time_embedding(cfg, g["T"])
+    for t, row in g["rows"].items():
+        np.testing.assert_allclose(gam[int(t)], row, atol=1e-15)
+    # T = 1 means t~ = 0
+    np.testing.assert_allclose(O.time_embedding(cfg, 1)[0], g["rows"]["0"], atol=0)
+
+
+@pytest.mark.parametrize("slope", [0.0, 0.01, 0.2])
+def test_mlp_matches_torch_nn(slope):
+    """Sec. 3.3, Eq. 4: the oracle MLP == a torch.nn FP64 stack with the same weights."""
+    torch = pytest.importorskip("torch")
+    cfg = O.make_cfg(L=1, res=(3,), F=4, H=16, D=3, slope=slope)
+    K, H, No = O.k_in(cfg), 16, O.n_out(cfg)
+    mlp = I.mlp_init(K, H, 3, No, seed=5, zero_last=False).astype(np.float64)
+    rng = np.random.default_rng(6)
+    y = rng.normal(size=(37, K))
+    o = O.mlp_forward(cfg, mlp, y)
+    layers = []
+    dims = [(H, K), (H, H), (H, H), (No, H)]
+    off = 0
+    for li, (fo, fi) in enumerate(dims):
+        lin = torch.nn.Linear(fi, fo).double()
+        with torch.no_grad():
+            lin.weight.copy_(torch.from_numpy(mlp[off:off + fo * fi].reshape(fo, fi)))
+            off += fo * fi
+            lin.bias.copy_(torch.from_numpy(mlp[off:off + fo]))
+            off += fo
+        layers.append(lin)
+        if li < 3:
+            layers.append(torch.nn.LeakyReLU(slope) if slope > 0 else torch.nn.ReLU())
+    assert off == len(mlp) == O.mlp_len(cfg)
+    ref = torch.nn.Sequential(*layers)(torch.from_numpy(y)).detach().numpy()
+    np.testing.assert_allclose(o, ref, rtol=1e-13, atol=1e-14)
+
+
+# ---------------------------------------------------------------- Sec. 3.4
+
+def test_quaternion_rotation_matches_scipy():
+    """Eq. 5-6: R((1+q_w, q_x, q_y, q_z)/norm) == scipy's quaternion rotation; d = tanh(0.1 d)."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(7)
+    cfg = small_cfg(rot_mode=0)
+    for _ in range(50):
+        o = rng.normal(scale=0.7, size=7)
+        R, d = O.rotation_translation(cfg, o)
+        q = np.array([1 + o[0], o[1], o[2], o[3]])
+        ref = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        np.testing.assert_allclose(R, ref, atol=1e-14)
+        np.testing.assert_allclose(R.T @ R, np.eye(3), atol=1e-14)
+        assert abs(np.linalg.det(R) - 1) < 1e-14
+        np.testing.assert_allclose(d, np.tanh(0.1 * o[4:]), atol=1e-16)
+    R, d = O.rotation_translation(cfg, np.array([0, 0, 0, 0, 10.0, -10.0, 0]))
+    np.testing.assert_array_equal(R, np.eye(3))
+    np.testing.assert_allclose(d, [0.7615941559557649, -0.7615941559557649, 0.0], atol=1e-16)
+    # 90 degrees about z maps e_x to e_y: q = (cos 45, 0, 0, sin 45)
+    c = np.sqrt(0.5)
+    R, _ = O.rotation_translation(cfg, np.array([c - 1, 0, 0, c, 0, 0, 0]))
+    np.testing.assert_allclose(R @ [1, 0, 0], [0, 1, 0], atol=1e-15)
+
+
+def test_expmap_rotation_matches_scipy_and_quaternion():
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(8)
+    ce = small_cfg(rot_mode=1)
+    cq = small_cfg(rot_mode=0)
+    for scale in (1e-7, 1e-3, 5e-3, 2e-2, 0.5, 2.0):
+        for _ in range(10):
+            w = rng.normal(size=3)
+            w *= scale / np.linalg.norm(w)
+            o = np.concatenate([w, rng.normal(size=3)])
+            R, d = O.rotation_translation(ce, o)
+            np.testing.assert_allclose(R, Rotation.from_rotvec(w).as_matrix(), atol=2e-15)
+            np.testing.assert_allclose(d, np.tanh(0.1 * o[3:]), atol=1e-16)
+            th = np.linalg.norm(w)
+            a = w / th
+            oq = np.array([np.cos(th / 2) - 1, *(np.sin(th / 2) * a), 0, 0, 0])
+            Rq, _ = O.rotation_translation(cq, oq)
+            np.testing.assert_allclose(R, Rq, atol=2e-15)
+
+
+def test_identity_at_initialisation():
+    """Sec. 3.1: zero grids and a zeroed last layer give x-hat == x exactly."""
+    seq = I.random_cloud_sequence(T=3)
+    for rot in (0, 1):
+        cfg = small_cfg(rot_mode=rot)
+        grid = np.zeros(O.grid_len(cfg))
+        mlp = I.mlp_init(O.k_in(cfg), cfg.H, cfg.D, O.n_out(cfg), seed=0)
+        z = O.encode(cfg, seq.x, seq.n, grid)
+        xh = O.decode(cfg, seq.x.astype(np.float64), z, O.time_embedding(cfg, 3), mlp)
+        for t in range(3):
+            np.testing.assert_array_equal(xh[t], seq.x.astype(np.float64))
+
+
+# ---------------------------------------------------------------- Sec. 3.5 Chamfer
+
+def test_nn_matches_kdtree_and_tie_rule():
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(9)
+    q = rng.uniform(-1, 1, size=(300, 3))
+    c = rng.uniform(-1, 1, size=(500, 3))
+    idx, d = O.nn(q, c)
+    dd, ii = cKDTree(c).query(q)
+    np.testing.assert_array_equal(idx, ii)
+    np.testing.assert_allclose(d, dd ** 2, rtol=1e-12)
+    # FP32 decision on float inputs: same answer except within float rounding
+    qf, cf = q.astype(np.float32).astype(np.float64), c.astype(np.float32).astype(np.float64)
+    i32, d32 = O.nn(qf, cf, decide_f32=True)
+    i64, d64 = O.nn(qf, cf, decide_f32=False)
+    bad = i32 != i64
+    assert np.all(np.abs(d32[bad] - d64[bad]) <= 1e-6)
+    # exact duplicates: the lowest index wins in both precisions
+    c2 = np.concatenate([c[:10], c[:10]])
+    for f32 in (False, True):
+        i2, _ = O.nn(c2[:10] + 1e-3, c2, decide_f32=f32)
+        assert np.all(i2 < 10)
+
+
+def test_chamfer_invariants():
+    rng = np.random.default_rng(10)
+    X = rng.uniform(-1, 1, size=(1, 50, 3))
+    off = np.array([0, 50])
+    assert O.chamfer(X, off, X[0])[4][0] == 0.0
+    P = rng.uniform(-1, 1, size=(70, 3))
+    cd = O.chamfer(X, np.array([0, 70]), P)[4][0]
+    cd_sw = O.chamfer(P[None], np.array([0, 50]), X[0])[4][0]
+    assert abs(cd - cd_sw) < 1e-14
+    perm = rng.permutation(70)
+    assert abs(O.chamfer(X, np.array([0, 70]), P[perm])[4][0] - cd) < 1e-14
+    s = np.array([0.3, -0.2, 0.1])
+    assert abs(O.chamfer(X + s, np.array([0, 70]), P + s)[4][0] - cd) < 1e-12
+    from scipy.spatial import cKDTree
+    ref = np.mean(cKDTree(P).query(X[0])[0] ** 2) + np.mean(cKDTree(X[0]).query(P)[0] ** 2)
+    assert abs(cd - ref) < 1e-13
+
+
+# ---------------------------------------------------------------- Sec. 3.5 weights, iso
+
+def test_confidence_weights_golden_and_invariants():
+    g = _gold("confidence_weights.json")
+    for case in g["cases"]:
+        w = O.conf_weights(np.array(g["cd"]), g["t_key"], case["e"], case["e_max"])
+        np.testing.assert_allclose(w, case["w"], rtol=1e-14)
+    rng = np.random.default_rng(11)
+    cd = rng.uniform(0, 1, size=9)
+    w = O.conf_weights(cd, 4, 3, 10)
+    assert w[4] == 1.0
+    assert np.all(np.diff(w[4:]) <= 0) and np.all(np.diff(w[:5]) >= 0)
+
+
+def test_iso_golden_and_rigid_invariance():
+    from scipy.spatial.transform import Rotation
+    g = _gold("isometry_edge.json")
+    xh = np.array(g["xhat"])
+    e = np.array(g["edges"], dtype=np.int32)
+    lref = O.edge_lengths(xh, g["t_key"], e)
+    assert abs(O.iso(xh, e, lref) - g["L_iso"]) < 1e-15
+    seq = I.random_cloud_sequence()
+    ed = O.edges(seq.faces)
+    assert len(ed) == 120  # icosphere subdiv 1: E = 3F/2
+    x = seq.x.astype(np.float64)
+    frames = np.stack([x @ Rotation.random(random_state=k).as_matrix().T + k * 0.1
+                       for k in range(4)])
+    lref = O.edge_lengths(frames, 2, ed)
+    assert O.iso(frames, ed, lref) < 1e-14
+
+
+# ---------------------------------------------------------------- gradient (FD)
+
+def _fd_problem(rot_mode, seed=0):
+    seq = I.random_cloud_sequence(T=3, M=[25, 31, 18], seed=seed)
+    cfg = small_cfg(rot_mode=rot_mode)
+    prob = O.Problem(cfg, seq.x, seq.n, seq.faces, seq.points, seq.offsets, seq.t_key)
+    rng = np.random.default_rng(seed + 100)
+    grid = rng.normal(scale=0.3, size=O.grid_len(cfg))
+    mlp = I.mlp_init(O.k_in(cfg), cfg.H, cfg.D, O.n_out(cfg), seed=seed,
+                     zero_last=False).astype(np.float64) * 1.5
+    return prob, grid, mlp
+
+
+@pytest.mark.parametrize("rot_mode", [0, 1])
+def test_gradient_matches_central_differences(rot_mode):
+    """Hand-written reverse mode == central FD of the same loss (FP64,
+    stop-grad inputs held fixed as Eq. 11-13 prescribe)."""
+    prob, grid, mlp = _fd_problem(rot_mode)
+    full = O.loss_full(prob, grid, mlp, e=3, e_max=10)
+    w = full["w"]
+    lref = O.edge_lengths(full["xhat"], prob.t_key, prob.edges)
+    L0, gg, gm, _ = O.loss_grad(prob, grid, mlp, w, lref)
+    assert abs(L0 - full["loss"]) < 1e-15
+    np.testing.assert_array_equal(gg, full["g_grid"])
+    eps = 1e-6
+    num_g = np.zeros_like(grid)
+    for k in range(len(grid)):
+        if gg[k] == 0.0:  # node not touched by any vertex: check a few only
+            if k % 17:
+                continue
+        gp, gmn = grid.copy(), grid.copy()
+        gp[k] += eps
+        gmn[k] -= eps
+        num_g[k] = (O.loss_grad(prob, gp, mlp, w, lref, want_grad=False)[0] -
+                    O.loss_grad(prob, gmn, mlp, w, lref, want_grad=False)[0]) / (2 * eps)
+    num_m = np.zeros_like(mlp)
+    for k in range(len(mlp)):
+        mp, mm = mlp.copy(), mlp.copy()
+        mp[k] += eps
+        mm[k] -= eps
+        num_m[k] = (O.loss_grad(prob, grid, mp, w, lref, want_grad=False)[0] -
+                    O.loss_grad(prob, grid, mm, w, lref, want_grad=False)[0]) / (2 * eps)
+    mask = (gg != 0) | (np.arange(len(grid)) % 17 == 0)
+    assert np.linalg.norm(gg[mask] - num_g[mask]) <= 1e-6 * np.linalg.norm(gg[mask])
+    assert np.linalg.norm(gm - num_m) <= 1e-6 * np.linalg.norm(gm)
+    assert np.linalg.norm(gg) > 0 and np.linalg.norm(gm) > 0
+
+
+# ---------------------------------------------------------------- Eq. 9
+
+def _lattice_laplacian(r):
+    import networkx as nx
+    G = nx.grid_graph(dim=[r, r, r])  # nodes (ix, iy, iz) in dim order given
+    order = sorted(G.nodes(), key=lambda p: (p[2], p[1], p[0]))
+    Lap = nx.laplacian_matrix(G, nodelist=order).toarray().astype(np.float64)
+    return Lap
+
+
+@pytest.mark.parametrize("r,lam", [(2, 0.4), (3, 0.6), (4, 2.0), (5, 0.4), (6, 6.8)])
+def test_preconditioner_matches_dense_solve(r, lam):
+    """Eq. 9: (I + lambda L)^-2 g by CG == a dense direct solve with the
+    lattice Laplacian built by networkx."""
+    F = 2
+    rng = np.random.default_rng(r)
+    g = rng.normal(size=r ** 3 * F)
+    out, its = O.precondition(r, F, lam, g)
+    Lap = _lattice_laplacian(r)
+    A = np.eye(r ** 3) + lam * Lap
+    for ch in range(F):
+        ref = np.linalg.solve(A @ A, g[ch::F])
+        np.testing.assert_allclose(out[ch::F], ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+
+
+def test_preconditioner_invariants():
+    r, F = 7, 3
+    rng = np.random.default_rng(12)
+    g = rng.normal(size=r ** 3 * F)
+    out, _ = O.precondition(r, F, 0.0, g)
+    np.testing.assert_allclose(out, g, atol=1e-14)
+    c = np.tile([1.5, -2.0, 0.25], r ** 3)
+    out, _ = O.precondition(r, F, 3.0, c)
+    np.testing.assert_allclose(out, c, atol=1e-11)
+    u, v = rng.normal(size=r ** 3), rng.normal(size=r ** 3)
+    Pu, _ = O.precondition(r, 1, 1.7, u)
+    Pv, _ = O.precondition(r, 1, 1.7, v)
+    assert abs(u @ Pv - v @ Pu) < 1e-10 * abs(u @ Pv)
+
+
+# ---------------------------------------------------------------- Adam
+
+def test_adam_matches_torch_and_first_step():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(13)
+    p0 = rng.normal(size=40)
+    grads = [rng.normal(size=40) for _ in range(6)]
+    p, m, v = p0.copy(), np.zeros(40), np.zeros(40)
+    tp = torch.tensor(p0.copy(), requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=0.01)
+    for s, g in enumerate(grads, start=1):
+        p, m, v = O.adam(p, g, m, v, lr=0.01, step=s)
+        tp.grad = torch.tensor(g)
+        opt.step()
+        if s == 1:
+            np.testing.assert_allclose(p, p0 - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-14)
+    np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+# ---------------------------------------------------------------- whole iteration
+
+def test_iteration_decreases_chamfer():
+    seq = I.sphere_blob(subdiv=2, T=4, M=300, seed=3)
+    cfg = O.make_cfg(L=2, res=(5, 9), F=2, H=16, D=2, slope=0.0)
+    prob = O.Problem(cfg, seq.x, seq.n, seq.faces, seq.points, seq.offsets, seq.t_key)
+    st = O.State(prob, np.zeros(O.grid_len(cfg)),
+                 I.mlp_init(O.k_in(cfg), 16, 2, O.n_out(cfg), seed=1))
+    lr = [0.005 * 2.5 ** l for l in range(cfg.L)] + [0.005]
+    lam = [0.4 * 1.5 ** l for l in range(cfg.L)] + [0.4]
+    # the weighted loss itself may rise as delta -> 0 lifts w_conf towards 1
+    # (Eq. 11); the unweighted Chamfer distance is what must fall
+    cds = [O.iteration(prob, st, 20, lr, 1e-3, lam)["cd"].mean() for _ in range(8)]
+    assert cds[-1] < cds[0]
+    assert st.e == 8
