@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""fwd+bwd+step vertex-frames/s of the Neu-PiG optimisation iteration on GB300.
+
+One step = one full iteration through the C ABI (npg_iteration): latent-grid
+lookup, time modulation, MLP decode + rigid transform for every vertex and
+frame, bidirectional Chamfer nearest neighbours, loss, hand-written backward,
+Sobolev preconditioner on every grid level and Adam.
+
+Workload (default "paper"): capsule figure remeshed to N = 40962 vertices,
+T = 100 frames of 20000 noisy points, 8-level grid 16 -> 256 with 4 features,
+MLP 3 x 64 LeakyReLU; synthetic, seeded. Its per-iteration working set (grid,
+gradient, moments: ~3 GB) is far larger than L2, so no L2 flush is needed
+between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
+                  [--graph|--no-graph] [--impl npg|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank optimises its own sequence
+(independent problems: weak scaling, no data-path collective); value counts
+the vertex-frames of all ranks over the slowest rank's time.
+--impl reference times the FP64 CPU oracle on the host cores instead, each
+step a bounded sample of the same workload extrapolated to a full iteration.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd+step vertex-frames/s at T=100, N=40962; batched BF16 vs plain FP32"
+UNIT = "vertex-frames/s"
+FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e-3  # SMs x FP32 lanes x FMA x max GHz -> TFLOP/s
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm=d["hbm_gbs"], bf16=d["bf16_tflops"], bf16_sus=d["bf16_tflops_sustained"],
+                    src="measured")
+    return dict(hbm=6800.0, bf16=1900.0, bf16_sus=1700.0, src="fallback")
+
+
+def workload(name, seed=0):
+    from paper_2602_22212_gb300 import inputs as I
+    p = I.preset(name)
+    seq = I.make_sequence(p, seed=seed)
+    return p, seq
+
+
+def make_cfg(npg, p, precision, graph, stream, e_max):
+    return npg.make_config(p["L"], p["res"], p["F"], p["H"], p["D"], slope=p["slope"],
+                           precision=npg.BF16_MLP if precision == "bf16" else npg.FP32,
+                           e_max=e_max, use_graph=graph, stream=stream)
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- algorithmic work
+
+def stage_work(p, N, T, MT, mlp_dims, G_nodes):
+    """Algorithmic bytes / FLOPs per launch of each stage (documented in the design doc)."""
+    H, D, K, Z, NO = mlp_dims
+    L, F = p["L"], p["F"]
+    rows = N * T
+    fwd_row = 2 * H * H * (D - 1) + 2 * NO * H
+    bwd_row = fwd_row + 2 * NO * H * 2 + (D - 1) * 4 * H * H + 2 * H * K + 2 * H * Z
+    res = p["res"]
+    dct_flops = sum(12 * r ** 4 * F for r in res) + 12 * 4 ** 4 * 2
+    dct_bytes = sum(6 * 8 * r ** 3 * F for r in res) + 6 * 8 * 4 ** 3 * 2
+    n_params = sum(r ** 3 * F for r in res) + 4 ** 3 * 2
+    return {
+        "decode": ("alu", fwd_row * rows, "FLOP"),
+        "mlp_bwd": ("alu", bwd_row * rows, "FLOP"),
+        "precond": ("alu", dct_flops, "FLOP", dct_bytes),
+        "adam": ("hbm", 28 * n_params, "B"),
+        "encode": ("hbm", N * (8 * L * F + 8 * 2) * 4 + N * 16 * 2, "B"),
+        "scatter": ("hbm", N * (8 * L * F + 8 * 2) * 4 * 2, "B"),
+    }
+
+
+# ----------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample(p, seq, frames=1, level=1):
+    """Time the FP64 oracle on a bounded sample of the workload and extrapolate
+    one full iteration: `frames` frames of the per-frame work (decode, Chamfer
+    by brute force, loss and reverse pass) and the preconditioner (CG) + Adam
+    on one grid level, scaled to all levels by node count x sqrt(1 + 12 lambda)
+    (CG iterations grow with the square root of the condition number)."""
+    import oracle as O
+    cfg = O.make_cfg(L=p["L"], res=p["res"], F=p["F"], H=p["H"], D=p["D"], slope=p["slope"])
+    sub = seq.offsets[:frames + 1]
+    prob = O.Problem(cfg, seq.x, seq.n, seq.faces, seq.points[:sub[-1]], sub, 0)
+    from paper_2602_22212_gb300 import inputs as I
+    rng = np.random.default_rng(0)
+    grid = rng.normal(scale=0.01, size=O.grid_len(cfg))
+    mlp = I.mlp_init(O.k_in(cfg), p["H"], p["D"], O.n_out(cfg), seed=0,
+                     zero_last=False).astype(np.float64)
+    t0 = time.perf_counter()
+    O.loss_full(prob, grid, mlp, 1, 10)
+    t_frames = time.perf_counter() - t0
+    r = p["res"][level]
+    lam = [0.4 * 1.5 ** l for l in range(p["L"])]
+    g = rng.normal(size=r ** 3 * p["F"])
+    t0 = time.perf_counter()
+    pc, _ = O.precondition(r, p["F"], lam[level], g)
+    O.adam(np.zeros_like(g), pc, np.zeros_like(g), np.zeros_like(g), 0.01, 1)
+    t_lvl = time.perf_counter() - t0
+    scale = sum((rr / r) ** 3 * np.sqrt((1 + 12 * lam[l]) / (1 + 12 * lam[level]))
+                for l, rr in enumerate(p["res"]))
+    t_iter = t_frames / frames * seq.T + t_lvl * scale
+    desc = (f"{frames} frame(s) of N={seq.N}, M={int(seq.offsets[1])} (decode, brute-force "
+            f"Chamfer, loss, reverse pass: {t_frames:.2f} s) + CG preconditioner and Adam on "
+            f"the {r}^3 x {p['F']} level ({t_lvl:.2f} s), extrapolated to T={seq.T} and all "
+            f"{p['L']} levels")
+    return seq.N * seq.T / t_iter, t_frames + t_lvl, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p, seq = workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(p, seq)
+    vals, secs = [], 0.0
+    desc = ""
+    for _ in range(args.steps):
+        v, s, desc = oracle_sample(p, seq)
+        vals.append(v)
+        secs += s
+    value = float(np.mean(vals))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(p, seq, "f64 CPU oracle", False),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def config_dict(p, seq, form, graph):
+    return {"workload": f"{p['gen']} N={seq.N} T={seq.T} M={int(seq.offsets[1])}/frame, "
+                        f"{p['L']}-level grid {p['res'][0]}->{p['res'][-1]} x F={p['F']}, "
+                        f"MLP {p['D']}x{p['H']}",
+            "form": form, "cuda_graph": bool(graph),
+            "l2": "working set (~3 GB of grid state per step) exceeds L2; no flush",
+            "N": seq.N, "T": seq.T, "M": int(seq.offsets[1]), "levels": p["res"], "F": p["F"],
+            "H": p["H"], "depth": p["D"]}
+
+
+# ----------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="npg", choices=["npg", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--graph", dest="graph", action="store_true", default=None)
+    ap.add_argument("--no-graph", dest="graph", action="store_false")
+    ap.add_argument("--workload", default="paper", choices=["paper", "tiny"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2602_22212_gb300 import build, npg
+    build.build()
+    graph = (args.precision == "bf16") if args.graph is None else args.graph
+
+    p, seq = workload(args.workload, seed=rank)
+    stream = torch.cuda.Stream()
+    from paper_2602_22212_gb300 import inputs as I
+    H, D = p["H"], p["D"]
+    K, Z, NO = 2 + p["F"] + 8, 2 + p["F"], 7
+    mlp = I.mlp_init(K, H, D, NO, seed=rank)
+    e_max = p["iters"]
+    cfg = make_cfg(npg, p, args.precision, graph, stream, e_max)
+    ctx = npg.Context(cfg, seq, mlp, device_inputs=True)
+    N, T, MT = seq.N, seq.T, int(seq.offsets[-1])
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        ctx.iteration()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = npg.npg_launch_count(ctx.h)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        npg.npg_iteration(ctx.h, None)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    launches = npg.npg_launch_count(ctx.h) - launches0
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N * T * args.steps / (ms * 1e-3)
+
+    # per-stage attribution: the same iteration, eager, with CUDA events per stage
+    sctx = ctx
+    if graph:
+        cfg2 = make_cfg(npg, p, args.precision, False, stream, e_max)
+        sctx = npg.Context(cfg2, seq, mlp, device_inputs=True)
+        for _ in range(args.warmup):
+            sctx.iteration()
+    npg.npg_timing(sctx.h, args.steps)
+    for _ in range(args.steps):
+        npg.npg_iteration(sctx.h, None)
+    stages = {}
+    for k, name in enumerate(npg.STAGES):
+        tot, n = npg.npg_timing_read(sctx.h, k)
+        stages[name] = tot / max(n, 1)
+    npg.npg_timing(sctx.h, 0)
+
+    # e2e: host buffers through the public API; each step uploads the step's
+    # point clouds from pinned memory and reads the loss back
+    e2e_steps = args.e2e_steps or max(3, args.steps // 2)
+    pts_pin = torch.from_numpy(np.ascontiguousarray(seq.points)).pin_memory()
+    off_pin = torch.from_numpy(np.ascontiguousarray(seq.offsets)).pin_memory()
+    loss_out = np.zeros(3)
+    npg.npg_set_points(ctx.h, pts_pin, off_pin)
+    npg.npg_iteration(ctx.h, loss_out)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        npg.npg_set_points(ctx.h, pts_pin, off_pin)
+        npg.npg_iteration(ctx.h, loss_out)
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = world * N * T * e2e_steps / t_e2e
+
+    peaks = load_peaks()
+    work = stage_work(p, N, T, MT, (H, D, K, Z, NO), None)
+    dom = max((s for s in stages if s in work), key=lambda s: stages[s])
+    kind, amount, u = work[dom][:3]
+    dur = stages[dom] * 1e-3
+    if kind == "hbm":
+        ach = amount / dur / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm"], "unit": "GB/s",
+                "frac": ach / peaks["hbm"], "traffic": None,
+                "peak_source": f"{peaks['src']} copy bandwidth"}
+    else:
+        ach = amount / dur / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP32_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                "frac": ach / FP32_TFLOPS_NOMINAL, "traffic": None,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+    roof["kernel"] = dom
+    roof["ms_per_launch"] = stages[dom]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, s, desc = oracle_sample(p, seq, frames=2)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        form = ("batched BF16 tensor-core MLP, graph-captured" if args.precision == "bf16"
+                else "plain FP32") + (" (CUDA graph)" if graph and args.precision != "bf16" else "")
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if args.precision == "bf16" else "f32",
+            "data": "synthetic (seeded capsule-figure sequence; no dataset)",
+            "config": config_dict(p, seq, form, graph),
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(seq.points.nbytes + seq.offsets.nbytes),
+                    "d2h_bytes_per_step": 24},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,284 @@
+/*
+ * npg.h - C ABI of libnpg.so, the GB300 (sm_103a) implementation of one
+ * Neu-PiG per-sequence optimisation iteration.
+ *
+ * One iteration (Sec. 3 of the paper) is
+ *   npg_forward   latent-grid lookup at every reference vertex by position and
+ *                 normal (Sec. 3.2, Eq. 1), Fourier time encoding (Sec. 3.3,
+ *                 Eq. 3), MLP decode of the input vector of Eq. 2 (Eq. 4),
+ *                 quaternion / exponential-map rotation and tanh translation
+ *                 (Sec. 3.4, Eq. 5-7) -> deformed vertices x-hat for all frames
+ *   npg_loss      bidirectional Chamfer nearest neighbours per frame, the
+ *                 confidence weights (Eq. 11-12), L_def (Eq. 10), L_iso (Eq. 13)
+ *                 and L (Eq. 8)
+ *   npg_backward  reverse-mode gradient of L w.r.t. the grids and the MLP
+ *   npg_step      Sobolev preconditioner (I + lambda_l L_l)^-2 on every grid
+ *                 level (Eq. 9), then Adam with per-level learning rates
+ *                 (Sec. 3.5, implementation details); e += 1
+ *
+ * Conventions shared by every call:
+ *   - every function returns NPG_OK (0) or a negative NPG_E* code and never
+ *     aborts; npg_last_error() gives a message. A sticky CUDA error makes the
+ *     context unusable (every later call returns NPG_ECUDA).
+ *   - inputs are copied at npg_create (the caller keeps ownership); outputs go
+ *     to caller buffers. "device" pointers are CUDA device (or managed)
+ *     addresses on the context's device; "host" pointers are ordinary memory.
+ *   - all device work is ordered on cfg.stream (a cudaStream_t; NULL = the
+ *     legacy default stream). Calls that return host data synchronize it.
+ *   - calls follow forward -> loss -> backward -> step; a call out of order
+ *     returns NPG_ESTATE and changes nothing. forward may be repeated at any
+ *     point (it restarts the sequence for the current parameters).
+ *   - coordinates are expected in [-1, 1]^3 (Sec. 3.4); grid queries outside
+ *     are clamped to the boundary.
+ */
+#ifndef NPG_H
+#define NPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define NPG_API __attribute__((visibility("default")))
+#else
+#define NPG_API
+#endif
+
+#define NPG_MAX_LEVELS 16
+
+/* status codes */
+#define NPG_OK 0
+#define NPG_EINVAL (-1)   /* bad argument, shape or configuration            */
+#define NPG_ENOMEM (-2)   /* device or host allocation failed                */
+#define NPG_ECUDA (-3)    /* CUDA runtime / launch error (may be sticky)     */
+#define NPG_ESTATE (-4)   /* call out of order                               */
+#define NPG_ETIMEOUT (-5) /* a bounded device wait gave up                   */
+#define NPG_ENOTIMPL (-6) /* configuration not supported by this build       */
+
+/* rotation parameterisation of the decoder output */
+#define NPG_ROT_QUAT 0   /* Eq. 5: q = (1 + o0, o1, o2, o3) / norm, d = o4..6 */
+#define NPG_ROT_EXPMAP 1 /* exponential map: omega = o0..2, d = o3..5        */
+
+/* arithmetic of the MLP decode and its backward pass */
+#define NPG_FP32 0     /* FP32 SIMT                                          */
+#define NPG_BF16_MLP 1 /* BF16 operands, FP32 accumulation on tcgen05 tensor cores */
+
+typedef struct npg_ctx npg_ctx; /* opaque; owns all device memory it allocates */
+
+/*
+ * Configuration (POD, copied at npg_create).
+ *   L, res[l]        position-grid levels and nodes per axis of level l
+ *                    (l = 0 coarsest; res >= 2). Nodes sit at -1 + 2k/(r-1).
+ *   F_p, F_n, res_n  features per position node (1..32), per normal node
+ *                    (1..8), nodes per axis of the normal grid (Sec. 3.2).
+ *   H, depth         hidden width and number of hidden layers (Sec. 3.3);
+ *                    NPG_FP32 supports H in {16, 32, 64}, NPG_BF16_MLP
+ *                    H in {64, 128}; depth 1..8.
+ *   leaky_slope      LeakyReLU negative slope (0 = ReLU).
+ *   rot_mode         NPG_ROT_QUAT or NPG_ROT_EXPMAP.
+ *   n_freq           Fourier frequencies M (Eq. 3; 1..8).
+ *   alpha            translation squashing factor (Eq. 6).
+ *   lr_mlp           Adam learning rate of the MLP.
+ *   lr_grid[l]       Adam learning rate of level l; lr_grid[L] = normal grid.
+ *   lambda[l]        Sobolev smoothing of level l; lambda[L] = normal grid.
+ *   adam_*           Adam beta1, beta2, epsilon.
+ *   w_iso            isometry weight (Eq. 8).
+ *   e_max            iteration count normalising the catch-up variable delta.
+ *   precision        NPG_FP32 or NPG_BF16_MLP.
+ *   nn_cells         bucket cells per axis of the Chamfer search grids; 0 =
+ *                    chosen from the point and vertex counts.
+ *   use_graph        npg_iteration replays one captured CUDA graph.
+ *   stream           cudaStream_t for all device work.
+ *   alloc/free/user  optional device allocator (e.g. PyTorch's caching
+ *                    allocator); NULL = cudaMalloc / cudaFree.
+ */
+typedef struct npg_config {
+  int L;
+  int res[NPG_MAX_LEVELS];
+  int F_p;
+  int F_n;
+  int res_n;
+  int H;
+  int depth;
+  float leaky_slope;
+  int rot_mode;
+  int n_freq;
+  float alpha;
+  float lr_mlp;
+  float lr_grid[NPG_MAX_LEVELS + 1];
+  float lambda[NPG_MAX_LEVELS + 1];
+  float adam_beta1;
+  float adam_beta2;
+  float adam_eps;
+  float w_iso;
+  int e_max;
+  int precision;
+  int nn_cells;
+  int use_graph;
+  void* stream;
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* alloc_user;
+} npg_config;
+
+/* Paper defaults (Sec. 3.2-3.5): resolutions r_l = round(r_min + (r_max -
+ * r_min)(l-1)/(L-1)), F_n = 2, res_n = 4, LeakyReLU 0.01, quaternions, M = 4,
+ * alpha = 0.1, lr_mlp = 1e-3, lr_l = 0.005 * 2.5^(l-1), lambda_l = 0.4 *
+ * 1.5^(l-1) (l = 1 coarsest; the normal grid takes the level-1 values), Adam
+ * (0.9, 0.999, 1e-8), w_iso = 100, e_max = 1000, FP32. */
+NPG_API int npg_config_default(npg_config* cfg, int L, int r_min, int r_max, int F_p, int H, int depth);
+
+/*
+ * Create a context for one sequence (Sec. 3, problem statement).
+ *   ref_xyz, ref_nrm  N x 3 FP32: keyframe reference vertices and unit normals.
+ *   faces             F_tri x 3 int32 triangles; the isometry edges are the
+ *                     unique undirected edges of these faces.
+ *   points            sum_t M_t x 3 FP32, the T clouds concatenated in frame order;
+ *   frame_offsets     T + 1 int64, frame t owns points [off[t], off[t+1]);
+ *                     every frame needs M_t >= 1.
+ *   t_key             keyframe index, 0-based.
+ *   mlp_init          flat FP32 MLP parameters (mlp_len floats): layer 0 W
+ *                     (H x K, row-major, K = F_n + F_p + 2 n_freq, input order
+ *                     (z_n, z_p, gamma)) then b (H); hidden layers W (H x H) + b;
+ *                     output W (O x H) + b, O = 7 (quaternion) or 6
+ *                     (exponential map). Zeroing the output layer gives the
+ *                     identity initialisation of Sec. 3.1.
+ *   inputs_on_device  0: every input pointer is host memory; 1: device memory.
+ * Grids and Adam moments start at zero, e = 0. On failure *out is NULL.
+ */
+NPG_API int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref_xyz, const float* ref_nrm,
+               int N, const int32_t* faces, int F_tri, const float* points,
+               const int64_t* frame_offsets, int T, int t_key, const float* mlp_init,
+               size_t mlp_len, int inputs_on_device);
+
+/* Deformed vertices for every frame. xhat_out: nullable device pointer to
+ * T x N x 3 FP32 (frame-major) that receives a copy. */
+NPG_API int npg_forward(npg_ctx* ctx, float* xhat_out);
+
+/* Chamfer nearest neighbours, cd_t, w_conf(t), L_def, L_iso and L for the last
+ * forward pass. loss_out (host, nullable): 3 doubles {L, L_def, L_iso};
+ * cd_out (host, nullable): T doubles. Non-null outputs synchronize the stream. */
+NPG_API int npg_loss(npg_ctx* ctx, double* loss_out, double* cd_out);
+
+/* Gradient of L w.r.t. every grid value and MLP parameter (stop-grad on
+ * w_conf and on the keyframe edge lengths, as Eq. 11-13 prescribe). */
+NPG_API int npg_backward(npg_ctx* ctx);
+
+/* Reverse pass from a given dL/dx-hat: back through Eq. 7-5, the MLP, the
+ * input vector (Eq. 2) and the grid lookups (Eq. 1) into the parameter
+ * gradients, as npg_backward does after forming dL/dx-hat from the loss.
+ * dxhat: nullable device pointer to T x N x 3 FP32 (frame-major); NULL reuses
+ * the dL/dx-hat of the last npg_backward. Needs a preceding npg_forward; the
+ * next call may be npg_step. Lets a caller differentiate its own loss of x-hat. */
+NPG_API int npg_backprop(npg_ctx* ctx, const float* dxhat);
+
+/* Eq. 9 preconditioner on every grid level, then Adam (step e + 1); e += 1. */
+NPG_API int npg_step(npg_ctx* ctx);
+
+/* forward + loss + backward + step. loss_out (host, nullable): 3 doubles
+ * {L, L_def, L_iso} of this iteration (synchronizes). With cfg.use_graph the
+ * four calls are captured once into a CUDA graph and replayed. */
+NPG_API int npg_iteration(npg_ctx* ctx, double* loss_out);
+
+/* Replace the point clouds (same T; per-frame counts may change, total at most
+ * the count given at create). on_device as for npg_create. Resets the call
+ * order to "before forward". */
+NPG_API int npg_set_points(npg_ctx* ctx, const float* points, const int64_t* frame_offsets, int on_device);
+
+/* Buffers readable with npg_get (and writable with npg_set where marked). Grid
+ * vectors use the flat layout: levels 0..L-1 then the normal grid; level l is
+ * res^3 x F with node (ix,iy,iz) at ((iz r + iy) r + ix) and features innermost. */
+#define NPG_BUF_GRID 0        /* FP32 grid values (settable)                 */
+#define NPG_BUF_MLP 1         /* FP32 MLP parameters (settable)              */
+#define NPG_BUF_GRID_GRAD 2   /* FP32 dL/dgrid of the last backward           */
+#define NPG_BUF_GRID_PC 3     /* FP32 preconditioned grid gradient of the last step */
+#define NPG_BUF_MLP_GRAD 4    /* FP32 dL/dmlp of the last backward            */
+#define NPG_BUF_XHAT 5        /* FP32 T x N x 3                              */
+#define NPG_BUF_NN_X 6        /* int32 T x N: nearest point (frame-local index) */
+#define NPG_BUF_NN_P 7        /* int32 sum M_t: nearest vertex of every point  */
+#define NPG_BUF_CD 8          /* FP64 T                                      */
+#define NPG_BUF_WCONF 9       /* FP64 T                                      */
+#define NPG_BUF_ADAM_M_GRID 10 /* FP32, grid layout (settable)               */
+#define NPG_BUF_ADAM_V_GRID 11 /* FP32, grid layout (settable)               */
+#define NPG_BUF_ADAM_M_MLP 12  /* FP32 (settable)                            */
+#define NPG_BUF_ADAM_V_MLP 13  /* FP32 (settable)                            */
+#define NPG_BUF_DIST_X 14     /* FP32 T x N squared NN distances             */
+#define NPG_BUF_DIST_P 15     /* FP32 sum M_t squared NN distances           */
+#define NPG_BUF_DXHAT 16      /* FP32 T x N x 3 dL/dx-hat of the last backward */
+
+/* Size in bytes of a buffer (0 for an unknown id). */
+NPG_API size_t npg_size(const npg_ctx* ctx, int which);
+/* Copy a buffer out (dst host or device per dst_on_device; bytes must equal
+ * npg_size). Synchronizes the stream. */
+NPG_API int npg_get(npg_ctx* ctx, int which, void* dst, size_t bytes, int dst_on_device);
+/* Overwrite a settable buffer (bytes must equal npg_size); resets the call order. */
+NPG_API int npg_set(npg_ctx* ctx, int which, const void* src, size_t bytes, int src_on_device);
+/* Iteration counter e (0-based index of the next iteration). */
+NPG_API int npg_get_epoch(const npg_ctx* ctx);
+NPG_API int npg_set_epoch(npg_ctx* ctx, int e);
+
+/* Checkpoint: grids, MLP, Adam moments and e as one host blob. With blob ==
+ * NULL, *bytes receives the size. npg_set_state restores it exactly. */
+NPG_API int npg_get_state(npg_ctx* ctx, void* blob, size_t* bytes);
+NPG_API int npg_set_state(npg_ctx* ctx, const void* blob, size_t bytes);
+
+/* Per-stage device timing (CUDA events on cfg.stream) of eager iterations.
+ * npg_timing(ctx, n) keeps event sets for the next n iterations (n = 0 turns
+ * timing off and frees them); npg_timing_read synchronizes and returns, for
+ * one stage, the summed milliseconds and the number of iterations measured
+ * since timing was enabled. Graph replays are not timed per stage. */
+#define NPG_STAGE_ENCODE 0   /* grid lookup, level mean, first layer, time modulation */
+#define NPG_STAGE_DECODE 1   /* MLP decode + rigid transform                        */
+#define NPG_STAGE_BUCKET 2   /* counting sort of x-hat into the search cells         */
+#define NPG_STAGE_NN_X 3     /* nearest point of every vertex                       */
+#define NPG_STAGE_NN_P 4     /* nearest vertex of every point                       */
+#define NPG_STAGE_LOSS 5     /* keyframe edge lengths, cd_t, w_conf, L              */
+#define NPG_STAGE_DXHAT 6    /* dL/dx-hat                                           */
+#define NPG_STAGE_MLP_BWD 7  /* MLP backward with forward recompute                 */
+#define NPG_STAGE_SCATTER 8  /* grid gradient                                       */
+#define NPG_STAGE_PRECOND 9  /* Sobolev preconditioner, all levels                  */
+#define NPG_STAGE_ADAM 10    /* Adam, all parameters                                */
+#define NPG_NUM_STAGES 11
+NPG_API int npg_timing(npg_ctx* ctx, int n_iters);
+NPG_API int npg_timing_read(npg_ctx* ctx, int stage, double* total_ms, int* n_iters);
+
+/* Number of kernels this context has launched (graph replays count every
+ * kernel node they contain). */
+NPG_API long long npg_launch_count(const npg_ctx* ctx);
+
+/* Release everything the context owns; NULL is allowed. */
+NPG_API int npg_destroy(npg_ctx* ctx);
+
+/* Message of the last failure on ctx (or of the calling thread when ctx is NULL). */
+NPG_API const char* npg_last_error(const npg_ctx* ctx);
+
+/*
+ * Standalone exact nearest neighbours (the Chamfer search of Sec. 3.5, one
+ * point set). For each of nq queries q[i] the index of the closest of the nc
+ * candidates c[j] in squared Euclidean distance, formed in FP32 as
+ * d = dx*dx; d = fma(dy,dy,d); d = fma(dz,dz,d); ties go to the lowest index.
+ * All pointers are device pointers: q (nq x 3 FP32), c (nc x 3 FP32), idx
+ * (nq int32), dist (nq FP32, nullable). cells = bucket cells per axis (0 =
+ * automatic). Allocates its bucket scratch with cudaMallocAsync on stream and
+ * frees it before returning. nq >= 0, nc >= 1.
+ */
+NPG_API int npg_nearest(const float* q, int nq, const float* c, int nc, int32_t* idx, float* dist,
+                int cells, void* stream);
+
+/*
+ * Standalone Sobolev preconditioner (Eq. 9) of one r^3 x F block:
+ * out = (I + lambda L)^-2 g per channel, L the 6-neighbour lattice Laplacian
+ * with natural (Neumann) boundary. g and out are device pointers (r^3 x F
+ * FP32, node-major, features innermost; they may alias). 2 <= r <= 512,
+ * 1 <= F <= 32. Allocates its transform scratch with cudaMallocAsync on
+ * stream and frees it before returning.
+ */
+NPG_API int npg_precondition(const float* g, float* out, int r, int F, float lambda, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NPG_H */

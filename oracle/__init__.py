@@ -90,9 +90,10 @@ def lib():
                 "or_edge_lengths": (None, [i, pd, i, l, pi32, pd]),
                 "or_iso": (d, [i, i, pd, l, pi32, pd]),
                 "or_loss_grad": (d, [cfg, i, pd, pd, i, pi64, pd, l, pi32, pd, pd, pd, pd, i,
-                                     pd, pd, pd, pd, pd, pi32, pi32]),
+                                     pd, pd, pd, pd, pd, pi32, pi32, pd]),
                 "or_loss_full": (d, [cfg, i, pd, pd, i, pi64, pd, l, pi32, i, d, d, pd, pd, i,
-                                     pd, pd, pd, pd, pd, pd, pi32, pi32]),
+                                     pd, pd, pd, pd, pd, pd, pi32, pi32, pd]),
+                "or_backprop": (None, [cfg, i, pd, pd, i, pd, pd, pd, pd, pd]),
                 "or_precondition": (i, [i, i, d, pd, pd, d, i]),
                 "or_adam": (None, [l, pd, pd, pd, pd, d, d, d, d, i]),
                 "or_iteration": (d, [cfg, i, pd, pd, i, pi64, pd, l, pi32, i, i, i, pd, pd, pd,
@@ -324,7 +325,7 @@ def loss_grad(prob: Problem, grid, mlp, w_fixed, lref, decide_f32=False, want_gr
     nulli = C.POINTER(C.c_int32)()
     L = lib().or_loss_grad(C.byref(c), N, px, pn, T, po, pp, prob.E, pe, pg, pm, pw, plr,
                            int(bool(decide_f32)), pgg if want_grad else null,
-                           pgm if want_grad else null, null, null, pparts, nulli, nulli)
+                           pgm if want_grad else null, null, null, pparts, nulli, nulli, null)
     return float(L), gg, gm, parts
 
 
@@ -348,14 +349,30 @@ def loss_full(prob: Problem, grid, mlp, e, e_max, decide_f32=False, want_grad=Tr
     parts, pparts = _out_d(2)
     nnx, pnnx = _out_i32(T * N)
     nnp, pnnp = _out_i32(MT)
+    gx, pgx = _out_d(T * N * 3)
     null = C.POINTER(C.c_double)()
     L = lib().or_loss_full(C.byref(c), N, px, pn, T, po, pp, prob.E, pe, prob.t_key, float(e),
                            float(e_max), pg, pm, int(bool(decide_f32)),
                            pgg if want_grad else null, pgm if want_grad else null, pxh, pcd,
-                           pw, pparts, pnnx, pnnp)
+                           pw, pparts, pnnx, pnnp, pgx if want_grad else null)
     return dict(loss=float(L), g_grid=gg, g_mlp=gm, xhat=xh.reshape(T, N, 3), cd=cd, w=w,
                 L_def=parts[0], L_iso=parts[1], nn_x=nnx[: T * N].reshape(T, N),
-                nn_p=nnp[:MT])
+                nn_p=nnp[:MT], g_xhat=gx.reshape(T, N, 3))
+
+
+def backprop(prob: Problem, grid, mlp, g_xhat):
+    """Parameter gradient of a given dL/dx-hat (T x N x 3): the reverse pass
+    through Eq. 7-5, Eq. 4, Eq. 2 and Eq. 1."""
+    c, N, T = prob.cfg, prob.N, prob.T
+    _, px = _d(prob.x)
+    _, pn = _d(prob.n)
+    g, pg = _d(grid)
+    m, pm = _d(mlp)
+    gx, pgx = _d(np.asarray(g_xhat).reshape(-1))
+    gg, pgg = _out_d(grid_len(c))
+    gm, pgm = _out_d(mlp_len(c))
+    lib().or_backprop(C.byref(c), N, px, pn, T, pg, pm, pgx, pgg, pgm)
+    return gg, gm
 
 
 def precondition(r, F, lam, g, tol=1e-13, max_iter=100000):

@@ -496,20 +496,106 @@ double or_iso(int T, int N, const double* xhat, long E, const int32_t* edges,
 
 /* ------------------------------ loss and hand-written reverse-mode gradient */
 
+/* Reverse pass from a given dL/dx-hat (T x N x 3): back through Eq. 7-5, the
+ * MLP (Eq. 4), the input vector (Eq. 2), the trilinear lookups and the level
+ * mean (Eq. 1). g_grid and g_mlp (nullable) are overwritten. */
+void or_backprop(const or_cfg* c, int N, const double* x, const double* n, int T,
+                 const double* grid, const double* mlp, const double* gx, double* g_grid,
+                 double* g_mlp) {
+  int F = c->F, Fn = c->Fn, Z = Fn + F, G2 = 2 * c->n_freq, K = or_k_in(c);
+  int H = c->H, D = c->D, O = or_n_out(c);
+  double* z = (double*)malloc(sizeof(double) * (size_t)N * Z);
+  double* gamma = (double*)malloc(sizeof(double) * (size_t)T * G2);
+  or_encode(c, N, x, n, grid, z);
+  or_time_embedding(c, T, gamma);
+  /* back through Eq. 7-5, the MLP (Eq. 4) and the input vector (Eq. 2) */
+  double* gm = (double*)calloc((size_t)or_mlp_len(c), sizeof(double));
+  double* gz = (double*)calloc((size_t)N * Z, sizeof(double));
+  double* y = (double*)malloc(sizeof(double) * K);
+  double* pre = (double*)malloc(sizeof(double) * H * D);
+  double* h = (double*)malloc(sizeof(double) * H * D);
+  double* dh = (double*)malloc(sizeof(double) * H);
+  double* dp = (double*)malloc(sizeof(double) * H);
+  double o[8], go[8];
+  for (int t = 0; t < T; ++t)
+    for (int i = 0; i < N; ++i) {
+      for (int k = 0; k < Z; ++k) y[k] = z[(long)i * Z + k];
+      for (int k = 0; k < G2; ++k) y[Z + k] = gamma[(long)t * G2 + k];
+      mlp_row(c, mlp, y, pre, h, o);
+      transform_row_backward(c, o, x + 3L * i, gx + ((long)t * N + i) * 3, go);
+      /* layer offsets in the flat parameter vector */
+      long offW0 = 0, offb0 = (long)H * K;
+      long offHid = offb0 + H; /* hidden layer k>=1 at offHid + (k-1)(H*H+H) */
+      long offWo = offHid + (long)(D - 1) * (H * H + H), offbo = offWo + (long)O * H;
+      /* output layer */
+      const double* hl = h + (long)(D - 1) * H;
+      for (int k = 0; k < H; ++k) dh[k] = 0.0;
+      for (int j = 0; j < O; ++j) {
+        gm[offbo + j] += go[j];
+        for (int k = 0; k < H; ++k) {
+          gm[offWo + (long)j * H + k] += go[j] * hl[k];
+          dh[k] += mlp[offWo + (long)j * H + k] * go[j];
+        }
+      }
+      /* hidden layers D-1 .. 1 */
+      for (int layer = D - 1; layer >= 1; --layer) {
+        long offW = offHid + (long)(layer - 1) * (H * H + H), offb = offW + (long)H * H;
+        const double* hin = h + (long)(layer - 1) * H;
+        for (int j = 0; j < H; ++j) dp[j] = dh[j] * dact(pre[(long)layer * H + j], c->slope);
+        for (int k = 0; k < H; ++k) dh[k] = 0.0;
+        for (int j = 0; j < H; ++j) {
+          gm[offb + j] += dp[j];
+          for (int k = 0; k < H; ++k) {
+            gm[offW + (long)j * H + k] += dp[j] * hin[k];
+            dh[k] += mlp[offW + (long)j * H + k] * dp[j];
+          }
+        }
+      }
+      /* first layer */
+      for (int j = 0; j < H; ++j) dp[j] = dh[j] * dact(pre[j], c->slope);
+      for (int j = 0; j < H; ++j) {
+        gm[offb0 + j] += dp[j];
+        for (int k = 0; k < K; ++k) gm[offW0 + (long)j * K + k] += dp[j] * y[k];
+        for (int k = 0; k < Z; ++k) gz[(long)i * Z + k] += mlp[offW0 + (long)j * K + k] * dp[j];
+      }
+    }
+  if (g_mlp) memcpy(g_mlp, gm, sizeof(double) * (size_t)or_mlp_len(c));
+
+  /* back through the trilinear lookups and the level mean (Eq. 1) */
+  if (g_grid) {
+    memset(g_grid, 0, sizeof(double) * (size_t)or_grid_len(c));
+    long idx[8];
+    double w[8];
+    for (int i = 0; i < N; ++i) {
+      const double* gzi = gz + (long)i * Z;
+      or_trilinear(c->rn, n + 3L * i, idx, w);
+      double* gn = g_grid + or_level_offset(c, c->L);
+      for (int k = 0; k < 8; ++k)
+        for (int f = 0; f < Fn; ++f) gn[idx[k] * Fn + f] += w[k] * gzi[f];
+      for (int l = 0; l < c->L; ++l) {
+        double* gl = g_grid + or_level_offset(c, l);
+        or_trilinear(c->res[l], x + 3L * i, idx, w);
+        for (int k = 0; k < 8; ++k)
+          for (int f = 0; f < F; ++f) gl[idx[k] * F + f] += w[k] * gzi[Fn + f] / (double)c->L;
+      }
+    }
+  }
+  free(gm); free(gz); free(y); free(pre); free(h); free(dh); free(dp); free(z); free(gamma);
+}
+
 /* L = L_def + w_iso L_iso (Eq. 8, 10, 13) with the stop-grad quantities held
  * fixed: w_fixed (T confidence weights) and lref (E keyframe edge lengths).
  * Writes dL/d grid and dL/d mlp when the pointers are non-null (they are
  * overwritten, not accumulated). parts (nullable) receives {L_def, L_iso}.
  * xhat_out (nullable, T x N x 3), cd_out (nullable, T). nn_x/nn_p (nullable)
- * receive the nearest-neighbour indices. */
+ * receive the nearest-neighbour indices; gx_out (nullable, T x N x 3) dL/dx-hat. */
 double or_loss_grad(const or_cfg* c, int N, const double* x, const double* n, int T,
                     const int64_t* off, const double* pts, long E, const int32_t* edges,
                     const double* grid, const double* mlp, const double* w_fixed,
                     const double* lref, int decide_f32, double* g_grid, double* g_mlp,
                     double* xhat_out, double* cd_out, double* parts, int32_t* nn_x_out,
-                    int32_t* nn_p_out) {
-  int F = c->F, Fn = c->Fn, Z = Fn + F, G2 = 2 * c->n_freq, K = or_k_in(c);
-  int H = c->H, D = c->D, O = or_n_out(c);
+                    int32_t* nn_p_out, double* gx_out) {
+  int Z = c->Fn + c->F, G2 = 2 * c->n_freq;
   long MT = off[T];
   double* z = (double*)malloc(sizeof(double) * (size_t)N * Z);
   double* gamma = (double*)malloc(sizeof(double) * (size_t)T * G2);
@@ -533,7 +619,7 @@ double or_loss_grad(const or_cfg* c, int N, const double* x, const double* n, in
   double Lval = Ldef + c->w_iso * Liso;
   if (parts) { parts[0] = Ldef; parts[1] = Liso; }
 
-  if (g_grid || g_mlp) {
+  if (g_grid || g_mlp || gx_out) {
     /* dL/dx-hat (T x N x 3) */
     double* gx = (double*)calloc((size_t)T * N * 3, sizeof(double));
     for (int t = 0; t < T; ++t) {
@@ -570,79 +656,9 @@ double or_loss_grad(const or_cfg* c, int N, const double* x, const double* n, in
       }
     }
 
-    /* back through Eq. 7-5, the MLP (Eq. 4) and the input vector (Eq. 2) */
-    double* gm = (double*)calloc((size_t)or_mlp_len(c), sizeof(double));
-    double* gz = (double*)calloc((size_t)N * Z, sizeof(double));
-    double* y = (double*)malloc(sizeof(double) * K);
-    double* pre = (double*)malloc(sizeof(double) * H * D);
-    double* h = (double*)malloc(sizeof(double) * H * D);
-    double* dh = (double*)malloc(sizeof(double) * H);
-    double* dp = (double*)malloc(sizeof(double) * H);
-    double o[8], go[8];
-    for (int t = 0; t < T; ++t)
-      for (int i = 0; i < N; ++i) {
-        for (int k = 0; k < Z; ++k) y[k] = z[(long)i * Z + k];
-        for (int k = 0; k < G2; ++k) y[Z + k] = gamma[(long)t * G2 + k];
-        mlp_row(c, mlp, y, pre, h, o);
-        transform_row_backward(c, o, x + 3L * i, gx + ((long)t * N + i) * 3, go);
-        /* layer offsets in the flat parameter vector */
-        long offW0 = 0, offb0 = (long)H * K;
-        long offHid = offb0 + H; /* hidden layer k>=1 at offHid + (k-1)(H*H+H) */
-        long offWo = offHid + (long)(D - 1) * (H * H + H), offbo = offWo + (long)O * H;
-        /* output layer */
-        const double* hl = h + (long)(D - 1) * H;
-        for (int k = 0; k < H; ++k) dh[k] = 0.0;
-        for (int j = 0; j < O; ++j) {
-          gm[offbo + j] += go[j];
-          for (int k = 0; k < H; ++k) {
-            gm[offWo + (long)j * H + k] += go[j] * hl[k];
-            dh[k] += mlp[offWo + (long)j * H + k] * go[j];
-          }
-        }
-        /* hidden layers D-1 .. 1 */
-        for (int layer = D - 1; layer >= 1; --layer) {
-          long offW = offHid + (long)(layer - 1) * (H * H + H), offb = offW + (long)H * H;
-          const double* hin = h + (long)(layer - 1) * H;
-          for (int j = 0; j < H; ++j) dp[j] = dh[j] * dact(pre[(long)layer * H + j], c->slope);
-          for (int k = 0; k < H; ++k) dh[k] = 0.0;
-          for (int j = 0; j < H; ++j) {
-            gm[offb + j] += dp[j];
-            for (int k = 0; k < H; ++k) {
-              gm[offW + (long)j * H + k] += dp[j] * hin[k];
-              dh[k] += mlp[offW + (long)j * H + k] * dp[j];
-            }
-          }
-        }
-        /* first layer */
-        for (int j = 0; j < H; ++j) dp[j] = dh[j] * dact(pre[j], c->slope);
-        for (int j = 0; j < H; ++j) {
-          gm[offb0 + j] += dp[j];
-          for (int k = 0; k < K; ++k) gm[offW0 + (long)j * K + k] += dp[j] * y[k];
-          for (int k = 0; k < Z; ++k) gz[(long)i * Z + k] += mlp[offW0 + (long)j * K + k] * dp[j];
-        }
-      }
-    if (g_mlp) memcpy(g_mlp, gm, sizeof(double) * (size_t)or_mlp_len(c));
-
-    /* back through the trilinear lookups and the level mean (Eq. 1) */
-    if (g_grid) {
-      memset(g_grid, 0, sizeof(double) * (size_t)or_grid_len(c));
-      long idx[8];
-      double w[8];
-      for (int i = 0; i < N; ++i) {
-        const double* gzi = gz + (long)i * Z;
-        or_trilinear(c->rn, n + 3L * i, idx, w);
-        double* gn = g_grid + or_level_offset(c, c->L);
-        for (int k = 0; k < 8; ++k)
-          for (int f = 0; f < Fn; ++f) gn[idx[k] * Fn + f] += w[k] * gzi[f];
-        for (int l = 0; l < c->L; ++l) {
-          double* gl = g_grid + or_level_offset(c, l);
-          or_trilinear(c->res[l], x + 3L * i, idx, w);
-          for (int k = 0; k < 8; ++k)
-            for (int f = 0; f < F; ++f) gl[idx[k] * F + f] += w[k] * gzi[Fn + f] / (double)c->L;
-        }
-      }
-    }
-    free(gx); free(gm); free(gz); free(y); free(pre); free(h); free(dh); free(dp);
+    or_backprop(c, N, x, n, T, grid, mlp, gx, g_grid, g_mlp);
+    if (gx_out) memcpy(gx_out, gx, sizeof(double) * (size_t)T * N * 3);
+    free(gx);
   }
 
   if (xhat_out) memcpy(xhat_out, xhat, sizeof(double) * (size_t)T * N * 3);
@@ -662,7 +678,7 @@ double or_loss_full(const or_cfg* c, int N, const double* x, const double* n, in
                     int t_key, double e, double e_max, const double* grid, const double* mlp,
                     int decide_f32, double* g_grid, double* g_mlp, double* xhat_out,
                     double* cd_out, double* w_out, double* parts, int32_t* nn_x_out,
-                    int32_t* nn_p_out) {
+                    int32_t* nn_p_out, double* gx_out) {
   int Z = c->Fn + c->F, G2 = 2 * c->n_freq;
   long MT = off[T];
   double* z = (double*)malloc(sizeof(double) * (size_t)N * Z);
@@ -682,7 +698,7 @@ double or_loss_full(const or_cfg* c, int N, const double* x, const double* n, in
   or_conf_weights(T, cd, t_key, e, e_max, w);
   or_edge_lengths(N, xhat, t_key, E, edges, lref);
   double L = or_loss_grad(c, N, x, n, T, off, pts, E, edges, grid, mlp, w, lref, decide_f32,
-                          g_grid, g_mlp, xhat_out, cd_out, parts, nn_x_out, nn_p_out);
+                          g_grid, g_mlp, xhat_out, cd_out, parts, nn_x_out, nn_p_out, gx_out);
   if (w_out) memcpy(w_out, w, sizeof(double) * T);
   free(z); free(gamma); free(xhat); free(nn_x); free(d_x); free(nn_p); free(d_p);
   free(cd); free(w); free(lref);
@@ -798,7 +814,7 @@ double or_iteration(const or_cfg* c, int N, const double* x, const double* n, in
   double* gp = (double*)malloc(sizeof(double) * GL);
   double* gm = (double*)malloc(sizeof(double) * ML);
   double L = or_loss_full(c, N, x, n, T, off, pts, E, edges, t_key, (double)e, (double)e_max,
-                          grid, mlp, decide_f32, gg, gm, NULL, cd_out, NULL, NULL, NULL, NULL);
+                          grid, mlp, decide_f32, gg, gm, NULL, cd_out, NULL, NULL, NULL, NULL, NULL);
   for (int l = 0; l <= c->L; ++l) {
     int r = l < c->L ? c->res[l] : c->rn;
     int F = l < c->L ? c->F : c->Fn;

@@ -1,0 +1,371 @@
+// Bidirectional Chamfer term (Sec. 3.5): per-frame uniform-grid bucketing
+// (counting sort), exact bucketed nearest-neighbour search in both directions,
+// the per-frame FP64 reductions of cd_t and L_iso, the confidence weights
+// (Eq. 11-12), the loss (Eq. 8, 10, 13), and dL/dx-hat.
+#include <float.h>
+
+#include "npg_device.cuh"
+#include "npg_internal.cuh"
+
+namespace npg {
+
+__device__ __forceinline__ int set_of(long long k, long long uniform, const long long* off,
+                                      int nsets) {
+  if (off == nullptr) return (int)(k / uniform);
+  int lo = 0, hi = nsets - 1;  // largest s with off[s] <= k
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= k) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ long long set_base(int s, long long uniform, const long long* off) {
+  return off == nullptr ? (long long)s * uniform : off[s];
+}
+
+__device__ __forceinline__ int cell_axis(float v, int G) {
+  int c = (int)floorf((v + 1.f) * (0.5f * (float)G));
+  return min(max(c, 0), G - 1);
+}
+
+// ----------------------------------------------------------------- bucketing
+
+__global__ void bucket_count_kernel(const float4* __restrict__ pts, const long long* off,
+                                    long long uniform, int nsets, long long total, int G,
+                                    int* __restrict__ counts, int* __restrict__ slot) {
+  const long long G3 = (long long)G * G * G;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int s = set_of(k, uniform, off, nsets);
+    const float4 p = pts[k];
+    const int cell = (cell_axis(p.z, G) * G + cell_axis(p.y, G)) * G + cell_axis(p.x, G);
+    slot[k] = atomicAdd(&counts[s * G3 + cell], 1);
+  }
+}
+
+// One block per set: exclusive scan of G^3 counts -> G^3 + 1 starts.
+__global__ void __launch_bounds__(1024) bucket_scan_kernel(const int* __restrict__ counts,
+                                                           int* __restrict__ starts, int G) {
+  const long long G3 = (long long)G * G * G;
+  const int* cnt = counts + blockIdx.x * G3;
+  int* st = starts + blockIdx.x * (G3 + 1);
+  const int nt = blockDim.x;
+  const long long chunk = (G3 + nt - 1) / nt;
+  const long long b = threadIdx.x * chunk, e = min(G3, b + chunk);
+  int local = 0;
+  for (long long k = b; k < e; ++k) local += cnt[k];
+  __shared__ int warp_sums[32];
+  // inclusive scan of "local" across the block
+  int v = local;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  if (lane == 31) warp_sums[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < (nt >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int n = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += n;
+    }
+    warp_sums[lane] = w;
+  }
+  __syncthreads();
+  int run = v - local + (wid > 0 ? warp_sums[wid - 1] : 0);
+  for (long long k = b; k < e; ++k) {
+    st[k] = run;
+    run += cnt[k];
+  }
+  if (threadIdx.x == nt - 1) st[G3] = run;
+}
+
+__global__ void bucket_scatter_kernel(const float4* __restrict__ pts, const long long* off,
+                                      long long uniform, int nsets, long long total, int G,
+                                      const int* __restrict__ starts, const int* __restrict__ slot,
+                                      float4* __restrict__ sorted) {
+  const long long G3 = (long long)G * G * G;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int s = set_of(k, uniform, off, nsets);
+    const long long base = set_base(s, uniform, off);
+    float4 p = pts[k];
+    const int cell = (cell_axis(p.z, G) * G + cell_axis(p.y, G)) * G + cell_axis(p.x, G);
+    const long long dst = base + starts[s * (G3 + 1) + cell] + slot[k];
+    p.w = __int_as_float((int)(k - base));
+    sorted[dst] = p;
+  }
+}
+
+static int grid_blocks(long long n, int per) {
+  long long b = (n + per - 1) / per;
+  if (b > 65535 * 16) b = 65535 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+cudaError_t bucket_build(const float4* pts, const long long* d_off, long long uniform_count,
+                         int nsets, long long total, int G, Buckets& b, cudaStream_t s) {
+  const long long G3 = (long long)G * G * G;
+  cudaError_t e = cudaMemsetAsync(b.counts, 0, sizeof(int) * G3 * nsets, s);
+  if (e != cudaSuccess) return e;
+  if (total > 0)
+    bucket_count_kernel<<<grid_blocks(total, 256), 256, 0, s>>>(pts, d_off, uniform_count, nsets,
+                                                                total, G, b.counts, b.slot);
+  bucket_scan_kernel<<<nsets, 1024, 0, s>>>(b.counts, b.cell_start, G);
+  if (total > 0)
+    bucket_scatter_kernel<<<grid_blocks(total, 256), 256, 0, s>>>(
+        pts, d_off, uniform_count, nsets, total, G, b.cell_start, b.slot, b.sorted);
+  return cudaGetLastError();
+}
+
+int auto_cells(long long points_per_set, int nsets) {
+  // surface data: about 2.8 G^2 occupied cells; aim at ~8 points per occupied
+  // cell, capped so that nsets * G^3 cell starts stay below 32M entries
+  double g = sqrt((double)points_per_set / 8.0);
+  int G = (int)(g + 0.5);
+  if (G < 1) G = 1;
+  if (G > 96) G = 96;
+  while (G > 1 && (double)G * G * G * nsets > 32.0e6) --G;
+  return G;
+}
+
+// ----------------------------------------------------------------- NN search
+// Exact nearest neighbour by growing Chebyshev rings of cells around the
+// query's cell; stops once the best squared distance is below the squared
+// distance to every unexplored cell (with a safety margin for FP32 rounding
+// of the cell assignment). Ties go to the lowest candidate index.
+__global__ void __launch_bounds__(128) nn_kernel(
+    const float4* __restrict__ qs, long long q_uniform, const long long* q_off, int nsets,
+    long long q_total, const float4* __restrict__ cs, const int* __restrict__ cstart, int G,
+    const long long* c_off, long long c_uniform, int* __restrict__ out_idx,
+    float* __restrict__ out_d) {
+  const long long G3 = (long long)G * G * G;
+  const float h = 2.f / (float)G;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < q_total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int s = set_of(k, q_uniform, q_off, nsets);
+    const float4 q = qs[k];
+    const int local = __float_as_int(q.w);
+    const long long cb = set_base(s, c_uniform, c_off);
+    const int* st = cstart + s * (G3 + 1);
+    const int cx = cell_axis(q.x, G), cy = cell_axis(q.y, G), cz = cell_axis(q.z, G);
+    float best = FLT_MAX;
+    int bi = 0x7fffffff;
+    for (int ring = 0; ring < G; ++ring) {
+      const int x0 = cx - ring, x1 = cx + ring, y0 = cy - ring, y1 = cy + ring;
+      const int z0 = cz - ring, z1 = cz + ring;
+      const int xa = max(x0, 0), xb = min(x1, G - 1);
+      for (int z = max(z0, 0); z <= min(z1, G - 1); ++z) {
+        for (int y = max(y0, 0); y <= min(y1, G - 1); ++y) {
+          const bool full = (z == z0 || z == z1 || y == y0 || y == y1);
+          const int row = (z * G + y) * G;
+          for (int part = 0; part < (full ? 1 : 2); ++part) {
+            int lo, hi;
+            if (full) {
+              lo = st[row + xa];
+              hi = st[row + xb + 1];
+            } else if (part == 0) {
+              if (x0 < 0) continue;
+              lo = st[row + x0];
+              hi = st[row + x0 + 1];
+            } else {
+              if (x1 > G - 1 || x1 == x0) continue;
+              lo = st[row + x1];
+              hi = st[row + x1 + 1];
+            }
+            for (int j = lo; j < hi; ++j) {
+              const float4 p = cs[cb + j];
+              const float d = sqdist(q.x, q.y, q.z, p.x, p.y, p.z);
+              const int id = __float_as_int(p.w);
+              if (d < best || (d == best && id < bi)) {
+                best = d;
+                bi = id;
+              }
+            }
+          }
+        }
+      }
+      // distance to the unexplored region
+      float lb = FLT_MAX;
+      if (x0 > 0) lb = fminf(lb, q.x - fmaf((float)x0, h, -1.f));
+      if (x1 < G - 1) lb = fminf(lb, fmaf((float)(x1 + 1), h, -1.f) - q.x);
+      if (y0 > 0) lb = fminf(lb, q.y - fmaf((float)y0, h, -1.f));
+      if (y1 < G - 1) lb = fminf(lb, fmaf((float)(y1 + 1), h, -1.f) - q.y);
+      if (z0 > 0) lb = fminf(lb, q.z - fmaf((float)z0, h, -1.f));
+      if (z1 < G - 1) lb = fminf(lb, fmaf((float)(z1 + 1), h, -1.f) - q.z);
+      if (lb == FLT_MAX) break;
+      lb -= 4e-6f;
+      if (lb > 0.f && best < lb * lb * (1.f - 1e-5f)) break;
+    }
+    const long long ob = set_base(s, q_uniform, q_off) + local;
+    out_idx[ob] = bi;
+    if (out_d) out_d[ob] = best;
+  }
+}
+
+cudaError_t launch_nn(const float4* queries_sorted, long long q_uniform, const long long* q_off,
+                      int nsets, long long q_total, const Buckets& cand,
+                      const long long* c_off, long long c_uniform, int* out_idx, float* out_d,
+                      cudaStream_t s) {
+  if (q_total == 0) return cudaSuccess;
+  nn_kernel<<<grid_blocks(q_total, 128), 128, 0, s>>>(queries_sorted, q_uniform, q_off, nsets,
+                                                      q_total, cand.sorted, cand.cell_start, cand.G,
+                                                      c_off, c_uniform, out_idx, out_d);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- loss
+// One block per frame, fixed reduction order (deterministic): FP64 sums of
+// the FP32 squared distances and of |len_e(t) - lref_e|.
+__device__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sh[w];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) loss_frame_kernel(
+    const float* __restrict__ d_x, const float* __restrict__ d_p, const long long* __restrict__ off,
+    const float4* __restrict__ xhat, const int2* __restrict__ edges, const float* __restrict__ lref,
+    int N, int E, double* __restrict__ cd, double* __restrict__ iso_t) {
+  __shared__ double sh[32];
+  const int t = blockIdx.x;
+  double sx = 0.0, sp = 0.0, si = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sx += (double)d_x[(long long)t * N + i];
+  const long long b = off[t], e = off[t + 1];
+  for (long long j = b + threadIdx.x; j < e; j += blockDim.x) sp += (double)d_p[j];
+  const float4* X = xhat + (long long)t * N;
+  for (int k = threadIdx.x; k < E; k += blockDim.x) {
+    const float len = edge_len(X[edges[k].x], X[edges[k].y]);
+    si += fabs((double)len - (double)lref[k]);
+  }
+  sx = block_sum(sx, sh);
+  sp = block_sum(sp, sh);
+  si = block_sum(si, sh);
+  if (threadIdx.x == 0) {
+    cd[t] = sx / (double)N + sp / (double)(e - b);
+    iso_t[t] = si;
+  }
+}
+
+// Eq. 11-12 (cumulative products outward from the keyframe), Eq. 10, 13, 8.
+__global__ void loss_final_kernel(const double* __restrict__ cd, const double* __restrict__ iso_t,
+                                  const int* __restrict__ epoch, int e_max, int T, int t_key,
+                                  int E, double w_iso, double* __restrict__ w,
+                                  double* __restrict__ loss) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double eb = e_max > 0 ? (double)(*epoch) / (double)e_max : 1.0;
+  eb = fmin(fmax(eb, 0.0), 1.0);
+  const double delta = 1.0 - sqrt(eb);
+  const double ck = cd[t_key];
+  w[t_key] = 1.0;
+  for (int t = t_key + 1; t < T; ++t) {
+    const double ex = cd[t] - ck;
+    w[t] = w[t - 1] * pow(1.0 / (1.0 + (ex > 0 ? ex : 0.0)), delta);
+  }
+  for (int t = t_key - 1; t >= 0; --t) {
+    const double ex = cd[t] - ck;
+    w[t] = w[t + 1] * pow(1.0 / (1.0 + (ex > 0 ? ex : 0.0)), delta);
+  }
+  double ld = 0.0, li = 0.0;
+  for (int t = 0; t < T; ++t) {
+    ld += w[t] * cd[t];
+    li += iso_t[t];
+  }
+  ld /= (double)T;
+  li = E > 0 ? li / ((double)T * (double)E) : 0.0;
+  loss[0] = ld + w_iso * li;
+  loss[1] = ld;
+  loss[2] = li;
+}
+
+cudaError_t launch_loss(npg_ctx* c) {
+  loss_frame_kernel<<<c->T, 256, 0, c->stream>>>(c->d_x, c->d_p, c->p_off, c->xhat, c->edges,
+                                                 c->lref, c->N, c->E, c->cd, c->iso_t);
+  loss_final_kernel<<<1, 32, 0, c->stream>>>(c->cd, c->iso_t, c->d_epoch, c->cfg.e_max,
+                                             c->T, c->t_key, c->E, (double)c->cfg.w_iso, c->wconf,
+                                             c->loss);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- dL/dx-hat
+
+// Vertex side of the Chamfer term plus the isometry term (vertex-centric over
+// the edge adjacency, no atomics); writes dxhat.
+__global__ void __launch_bounds__(256) dxhat_vertex_kernel(
+    const float4* __restrict__ xhat, const int* __restrict__ nn_x, const long long* __restrict__ off,
+    const float4* __restrict__ praw, const double* __restrict__ w, const int* __restrict__ adj_off,
+    const int* __restrict__ adj, const int* __restrict__ adj_edge, const float* __restrict__ lref,
+    int N, int T, int E, double w_iso, float4* __restrict__ dxhat) {
+  const long long total = (long long)N * T;
+  for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < total;
+       row += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(row / N), i = (int)(row - (long long)t * N);
+    const float4 x = xhat[row];
+    const float4 p = praw[off[t] + nn_x[row]];
+    const float cx = (float)(w[t] / (double)T * 2.0 / (double)N);
+    float gx = cx * (x.x - p.x), gy = cx * (x.y - p.y), gz = cx * (x.z - p.z);
+    if (E > 0) {
+      const float ci = (float)(w_iso / ((double)T * (double)E));
+      const float4* X = xhat + (long long)t * N;
+      for (int a = adj_off[i]; a < adj_off[i + 1]; ++a) {
+        const int j = adj[a];
+        const float4 xj = X[j];
+        const float len = i < j ? edge_len(x, xj) : edge_len(xj, x);
+        const float lr = lref[adj_edge[a]];
+        if (len > 0.f && len != lr) {
+          const float sc = (len > lr ? ci : -ci) / len;
+          gx = fmaf(sc, x.x - xj.x, gx);
+          gy = fmaf(sc, x.y - xj.y, gy);
+          gz = fmaf(sc, x.z - xj.z, gz);
+        }
+      }
+    }
+    dxhat[row] = make_float4(gx, gy, gz, 0.f);
+  }
+}
+
+// Point side of the Chamfer term: every point adds to its nearest vertex.
+__global__ void __launch_bounds__(256) dxhat_point_kernel(
+    const float4* __restrict__ praw, const long long* __restrict__ off, int T, long long MT,
+    const int* __restrict__ nn_p, const float4* __restrict__ xhat, const double* __restrict__ w,
+    int N, float4* __restrict__ dxhat) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < MT;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int t = set_of(k, 0, off, T);
+    const long long M = off[t + 1] - off[t];
+    const float cp = (float)(w[t] / (double)T * 2.0 / (double)M);
+    const int i = nn_p[k];
+    const float4 p = praw[k];
+    const long long row = (long long)t * N + i;
+    const float4 x = xhat[row];
+    float* g = reinterpret_cast<float*>(dxhat + row);
+    atomicAdd(g + 0, cp * (x.x - p.x));
+    atomicAdd(g + 1, cp * (x.y - p.y));
+    atomicAdd(g + 2, cp * (x.z - p.z));
+  }
+}
+
+cudaError_t launch_dxhat(npg_ctx* c) {
+  const float4* praw = c->praw;
+  const long long rows = (long long)c->N * c->T;
+  dxhat_vertex_kernel<<<grid_blocks(rows, 256), 256, 0, c->stream>>>(
+      c->xhat, c->nn_x, c->p_off, praw, c->wconf, c->adj_off,
+      c->adj, c->adj_edge, c->lref, c->N, c->T, c->E, (double)c->cfg.w_iso, c->dxhat);
+  dxhat_point_kernel<<<grid_blocks(c->MT, 256), 256, 0, c->stream>>>(
+      praw, c->p_off, c->T, c->MT, c->nn_p, c->xhat, c->wconf, c->N, c->dxhat);
+  return cudaGetLastError();
+}
+
+}  // namespace npg

@@ -1,0 +1,179 @@
+// Step kernels: the Sobolev preconditioner (I + lambda L)^-2 of Eq. 9 applied
+// exactly through the DCT-II eigenbasis of the Neumann lattice Laplacian, and
+// Adam with per-level learning rates (Sec. 3.5, implementation details).
+//
+// L = L_x (+) L_y (+) L_z on the r^3 node lattice; the 1-D Neumann path
+// Laplacian has eigenvectors C[k][n] = a_k cos(pi k (2n+1) / 2r) (orthonormal
+// DCT-II) and eigenvalues mu_k = 2 - 2 cos(pi k / r). Hence
+//   (I + lambda L)^-2 g = (C^T)^{x3} diag(1 / (1 + lambda (mu_kx + mu_ky + mu_kz))^2) C^{x3} g.
+// Each of the six separable passes is a GEMM that transforms the outermost
+// axis of a [r][r*r][F] array and writes it as the innermost spatial axis:
+// three passes return the axes to their original order.
+#include <math.h>
+
+#include "npg_device.cuh"
+#include "npg_internal.cuh"
+
+namespace npg {
+
+constexpr int PBM = 64, PBN = 64, PBK = 16;
+
+// out[p][k][c] = s(p,k) * sum_n Mx[k][n] in[n][p*F + c], p < r^2, c < F.
+template <bool SCALE>
+__global__ void __launch_bounds__(256) dct_pass_kernel(const float* __restrict__ in,
+                                                       float* __restrict__ out,
+                                                       const float* __restrict__ Mx, int r, int F,
+                                                       const float* __restrict__ mu, float lambda) {
+  __shared__ __align__(16) float Ms[PBK][PBM];
+  __shared__ __align__(16) float Is[PBK][PBN];
+  __shared__ float Os[PBN][PBM + 1];
+  const long long ncol = (long long)r * r * F;
+  const long long col0 = (long long)blockIdx.x * PBN;
+  const int k0 = blockIdx.y * PBM;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int n0 = 0; n0 < r; n0 += PBK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      // M tile: e -> (kk = e / 16, nn = e % 16)
+      const int kk = e >> 4, nn = e & 15;
+      const int k = k0 + kk, n = n0 + nn;
+      Ms[nn][kk] = (k < r && n < r) ? Mx[(long long)k * r + n] : 0.f;
+      // in tile: e -> (nn = e / 64, cc = e % 64)
+      const int nn2 = e >> 6, cc = e & 63;
+      const long long col = col0 + cc;
+      const int n2 = n0 + nn2;
+      Is[nn2][cc] = (n2 < r && col < ncol) ? in[(long long)n2 * ncol + col] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int nn = 0; nn < PBK; ++nn) {
+      const float4 m4 = *reinterpret_cast<const float4*>(&Ms[nn][ty * 4]);
+      const float4 i4 = *reinterpret_cast<const float4*>(&Is[nn][tx * 4]);
+      const float mv[4] = {m4.x, m4.y, m4.z, m4.w};
+      const float iv[4] = {i4.x, i4.y, i4.z, i4.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(mv[a], iv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) Os[tx * 4 + b][ty * 4 + a] = acc[a][b];
+  __syncthreads();
+  const long long rF = (long long)r * F;
+  if ((PBN % F) == 0) {
+    // tile = PBN/F whole p rows; each p row writes (k, c) contiguously
+    const long long p0 = col0 / F;
+    for (int e = tid; e < PBN * PBM; e += 256) {
+      const int c = e % F, kk = (e / F) % PBM, pl = e / (F * PBM);
+      const long long p = p0 + pl;
+      const int k = k0 + kk;
+      if (k >= r || p * F >= ncol) continue;
+      float v = Os[pl * F + c][kk];
+      if (SCALE) {
+        const float s = 1.f + lambda * (mu[p / r] + mu[p % r] + mu[k]);
+        v = v / (s * s);
+      }
+      out[p * rF + (long long)k * F + c] = v;
+    }
+  } else {
+    for (int e = tid; e < PBN * PBM; e += 256) {
+      const int cc = e / PBM, kk = e % PBM;
+      const long long col = col0 + cc;
+      const int k = k0 + kk;
+      if (k >= r || col >= ncol) continue;
+      const long long p = col / F;
+      const int c = (int)(col % F);
+      float v = Os[cc][kk];
+      if (SCALE) {
+        const float s = 1.f + lambda * (mu[p / r] + mu[p % r] + mu[k]);
+        v = v / (s * s);
+      }
+      out[p * rF + (long long)k * F + c] = v;
+    }
+  }
+}
+
+cudaError_t launch_precondition(const float* g, float* out, float* t0, float* t1, const float* C,
+                                const float* Ct, const float* mu, int r, int F, float lambda,
+                                cudaStream_t s) {
+  const long long ncol = (long long)r * r * F;
+  dim3 grid((unsigned)((ncol + PBN - 1) / PBN), (unsigned)((r + PBM - 1) / PBM));
+  dct_pass_kernel<false><<<grid, 256, 0, s>>>(g, t0, C, r, F, mu, lambda);
+  dct_pass_kernel<false><<<grid, 256, 0, s>>>(t0, t1, C, r, F, mu, lambda);
+  dct_pass_kernel<true><<<grid, 256, 0, s>>>(t1, t0, C, r, F, mu, lambda);
+  dct_pass_kernel<false><<<grid, 256, 0, s>>>(t0, t1, Ct, r, F, mu, lambda);
+  dct_pass_kernel<false><<<grid, 256, 0, s>>>(t1, t0, Ct, r, F, mu, lambda);
+  dct_pass_kernel<false><<<grid, 256, 0, s>>>(t0, out, Ct, r, F, mu, lambda);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- Adam
+// cc[0] = 1 - beta1^s, cc[1] = 1 - beta2^s for the step s = e + 1.
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v, long long n, float lr,
+                            float b1, float b2, float eps, const float* __restrict__ cc) {
+  const float c1 = cc[0], c2 = cc[1];
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const float gk = g[k];
+    const float mk = fmaf(b1, m[k], (1.f - b1) * gk);
+    const float vk = fmaf(b2, v[k], (1.f - b2) * gk * gk);
+    m[k] = mk;
+    v[k] = vk;
+    p[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+  }
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr,
+                        float b1, float b2, float eps, const float* cc, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  adam_kernel<<<(int)blocks, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, cc);
+  return cudaGetLastError();
+}
+
+// bias corrections for the step e + 1 (before Adam) and e += 1 (after)
+__global__ void step_prepare_kernel(const int* epoch, float b1, float b2, float* cc) {
+  const double s = (double)(*epoch) + 1.0;
+  cc[0] = (float)(1.0 - pow((double)b1, s));
+  cc[1] = (float)(1.0 - pow((double)b2, s));
+}
+
+__global__ void step_finish_kernel(int* epoch) { *epoch += 1; }
+
+cudaError_t launch_step_prepare(const int* epoch, float b1, float b2, float* cc, cudaStream_t s) {
+  step_prepare_kernel<<<1, 1, 0, s>>>(epoch, b1, b2, cc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_finish(int* epoch, cudaStream_t s) {
+  step_finish_kernel<<<1, 1, 0, s>>>(epoch);
+  return cudaGetLastError();
+}
+
+// DCT tables of one level: C (r x r), C^T (r x r), mu (r), computed in FP64.
+void dct_tables(int r, float* C, float* Ct, float* mu) {
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < r; ++k) {
+    const double a = k == 0 ? sqrt(1.0 / r) : sqrt(2.0 / r);
+    for (int n = 0; n < r; ++n) {
+      const double v = a * cos(pi * k * (2.0 * n + 1.0) / (2.0 * r));
+      C[(long long)k * r + n] = (float)v;
+      Ct[(long long)n * r + k] = (float)v;
+    }
+    mu[k] = (float)(2.0 - 2.0 * cos(pi * k / r));
+  }
+}
+
+}  // namespace npg

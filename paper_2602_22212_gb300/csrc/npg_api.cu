@@ -1,0 +1,990 @@
+// C ABI of libnpg.so (declared in include/npg.h): context lifetime, argument
+// validation, device buffers, and the order of kernel launches for one
+// Neu-PiG iteration (Sec. 3.2-3.5).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "npg_internal.cuh"
+
+using namespace npg;
+
+static thread_local std::string g_thread_err;
+
+static int set_err(npg_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  g_thread_err = buf;
+  return code;
+}
+
+static bool is_sticky(cudaError_t e) {
+  switch (e) {
+    case cudaErrorIllegalAddress:
+    case cudaErrorLaunchFailure:
+    case cudaErrorIllegalInstruction:
+    case cudaErrorMisalignedAddress:
+    case cudaErrorInvalidAddressSpace:
+    case cudaErrorInvalidPc:
+    case cudaErrorHardwareStackError:
+    case cudaErrorAssert:
+    case cudaErrorLaunchTimeout:
+    case cudaErrorECCUncorrectable:
+      return true;
+    default:
+      return false;
+  }
+}
+
+static int cuda_fail(npg_ctx* c, cudaError_t e, const char* what) {
+  if (c && is_sticky(e)) c->sticky = 1;
+  return set_err(c, e == cudaErrorMemoryAllocation ? NPG_ENOMEM : NPG_ECUDA, "%s: %s (%s)", what,
+                 cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(c, call)                                              \
+  do {                                                           \
+    cudaError_t _e = (call);                                     \
+    if (_e != cudaSuccess) return cuda_fail((c), _e, #call);     \
+  } while (0)
+
+// ----------------------------------------------------------------- memory
+
+static void* dev_alloc(npg_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (c->cfg.alloc) {
+    p = c->cfg.alloc(bytes, c->cfg.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p && c->n_allocs < 64) c->allocs[c->n_allocs++] = p;
+  return p;
+}
+
+static void dev_free_all(npg_ctx* c) {
+  for (int k = 0; k < c->n_allocs; ++k) {
+    if (c->cfg.free)
+      c->cfg.free(c->allocs[k], c->cfg.alloc_user);
+    else
+      cudaFree(c->allocs[k]);
+  }
+  c->n_allocs = 0;
+}
+
+template <class T>
+static bool alloc_n(npg_ctx* c, T*& p, long long n) {
+  p = static_cast<T*>(dev_alloc(c, sizeof(T) * (size_t)(n > 0 ? n : 1)));
+  return p != nullptr;
+}
+
+// ----------------------------------------------------------------- timing
+
+static void mark(npg_ctx* c, int k) {
+  if (!c->tev || c->capturing || c->t_cur < 0) return;
+  if (cudaEventRecord(c->tev[c->t_cur * (NPG_NUM_STAGES + 1) + k], c->stream) == cudaSuccess)
+    c->t_mask[c->t_cur] |= 1u << k;
+  else
+    cudaGetLastError();
+}
+
+static void begin_iteration_timing(npg_ctx* c) {
+  c->t_cur = (c->tev && !c->capturing && c->t_next < c->t_slots) ? c->t_next : -1;
+  if (c->t_cur >= 0) c->t_mask[c->t_cur] = 0;
+}
+
+static void end_iteration_timing(npg_ctx* c) {
+  if (c->t_cur >= 0) {
+    c->t_next++;
+    c->t_cur = -1;
+  }
+}
+
+static void free_timing(npg_ctx* c) {
+  if (c->tev) {
+    for (int k = 0; k < c->t_slots * (NPG_NUM_STAGES + 1); ++k) cudaEventDestroy(c->tev[k]);
+    delete[] c->tev;
+    delete[] c->t_mask;
+  }
+  c->tev = nullptr;
+  c->t_mask = nullptr;
+  c->t_slots = c->t_next = 0;
+  c->t_cur = -1;
+}
+
+// ----------------------------------------------------------------- config
+
+extern "C" int npg_config_default(npg_config* cfg, int L, int r_min, int r_max, int F_p, int H,
+                                  int depth) {
+  if (!cfg) return set_err(nullptr, NPG_EINVAL, "cfg is NULL");
+  if (L < 1 || L > NPG_MAX_LEVELS || r_min < 2 || r_max < r_min)
+    return set_err(nullptr, NPG_EINVAL, "bad level schedule L=%d r=%d..%d", L, r_min, r_max);
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->L = L;
+  for (int l = 0; l < L; ++l)
+    cfg->res[l] = L == 1 ? r_max
+                         : (int)lround(r_min + (double)(r_max - r_min) * l / (double)(L - 1));
+  cfg->F_p = F_p;
+  cfg->F_n = 2;
+  cfg->res_n = 4;
+  cfg->H = H;
+  cfg->depth = depth;
+  cfg->leaky_slope = 0.01f;
+  cfg->rot_mode = NPG_ROT_QUAT;
+  cfg->n_freq = 4;
+  cfg->alpha = 0.1f;
+  cfg->lr_mlp = 1e-3f;
+  for (int l = 0; l < L; ++l) {
+    cfg->lr_grid[l] = (float)(0.005 * pow(2.5, l));
+    cfg->lambda[l] = (float)(0.4 * pow(1.5, l));
+  }
+  cfg->lr_grid[L] = 0.005f;
+  cfg->lambda[L] = 0.4f;
+  cfg->adam_beta1 = 0.9f;
+  cfg->adam_beta2 = 0.999f;
+  cfg->adam_eps = 1e-8f;
+  cfg->w_iso = 100.f;
+  cfg->e_max = 1000;
+  cfg->precision = NPG_FP32;
+  return NPG_OK;
+}
+
+static int validate(const npg_config* c, char* why, size_t n) {
+  if (c->L < 1 || c->L > NPG_MAX_LEVELS) return snprintf(why, n, "L=%d out of 1..16", c->L), 0;
+  for (int l = 0; l < c->L; ++l)
+    if (c->res[l] < 2 || c->res[l] > 1024)
+      return snprintf(why, n, "res[%d]=%d out of 2..1024", l, c->res[l]), 0;
+  if (c->F_p < 1 || c->F_p > NPG_MAX_F) return snprintf(why, n, "F_p=%d out of 1..32", c->F_p), 0;
+  if (c->F_n < 1 || c->F_n > NPG_MAX_FN) return snprintf(why, n, "F_n=%d out of 1..8", c->F_n), 0;
+  if (c->res_n < 2 || c->res_n > 64) return snprintf(why, n, "res_n=%d out of 2..64", c->res_n), 0;
+  if (c->depth < 1 || c->depth > NPG_MAX_DEPTH)
+    return snprintf(why, n, "depth=%d out of 1..8", c->depth), 0;
+  if (c->n_freq < 1 || c->n_freq > NPG_MAX_FREQ)
+    return snprintf(why, n, "n_freq=%d out of 1..8", c->n_freq), 0;
+  if (c->rot_mode != NPG_ROT_QUAT && c->rot_mode != NPG_ROT_EXPMAP)
+    return snprintf(why, n, "rot_mode=%d", c->rot_mode), 0;
+  if (!(c->leaky_slope >= 0.f)) return snprintf(why, n, "leaky_slope must be >= 0"), 0;
+  for (int l = 0; l <= c->L; ++l)
+    if (!(c->lambda[l] >= 0.f) || !(c->lr_grid[l] >= 0.f))
+      return snprintf(why, n, "lambda/lr of level %d must be >= 0", l), 0;
+  if (c->e_max < 0) return snprintf(why, n, "e_max < 0"), 0;
+  if (c->nn_cells < 0 || c->nn_cells > 256) return snprintf(why, n, "nn_cells out of 0..256"), 0;
+  return 1;
+}
+
+// ----------------------------------------------------------------- create
+
+static int copy_in(npg_ctx* c, void* dst, const void* src, size_t bytes, int on_device) {
+  if (bytes == 0) return NPG_OK;
+  CK(c, cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice
+                                                   : cudaMemcpyHostToDevice, c->stream));
+  return NPG_OK;
+}
+
+static int fetch_host(npg_ctx* c, std::vector<char>& out, const void* src, size_t bytes,
+                      int on_device) {
+  out.resize(bytes);
+  if (bytes == 0) return NPG_OK;
+  if (on_device) {
+    CK(c, cudaMemcpyAsync(out.data(), src, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+  } else {
+    memcpy(out.data(), src, bytes);
+  }
+  return NPG_OK;
+}
+
+static int build_point_buckets(npg_ctx* c) {
+  CK(c, bucket_build(c->praw, c->p_off, 0, c->T, c->MT, c->pb.G, c->pb, c->stream));
+  return NPG_OK;
+}
+
+static int set_points_impl(npg_ctx* c, const float* points, const int64_t* off, int on_device) {
+  std::vector<char> hoff;
+  int rc = fetch_host(c, hoff, off, sizeof(int64_t) * (c->T + 1), on_device);
+  if (rc) return rc;
+  const int64_t* o = reinterpret_cast<const int64_t*>(hoff.data());
+  if (o[0] != 0) return set_err(c, NPG_EINVAL, "frame_offsets[0] must be 0");
+  for (int t = 0; t < c->T; ++t)
+    if (o[t + 1] - o[t] < 1)
+      return set_err(c, NPG_EINVAL, "frame %d has no points (every frame needs M_t >= 1)", t);
+  const long long MT = o[c->T];
+  if (c->MT_cap > 0 && MT > c->MT_cap)
+    return set_err(c, NPG_EINVAL, "%lld points exceed the %lld given at create", MT, c->MT_cap);
+  if (MT > 0x7fffffffLL) return set_err(c, NPG_EINVAL, "too many points");
+  for (int t = 0; t <= c->T; ++t) c->h_off[t] = o[t];
+  if (MT != c->MT && c->graph_exec) {  // the total is baked into the captured launches
+    cudaGraphExecDestroy(c->graph_exec);
+    cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+  }
+  c->MT = MT;
+  rc = copy_in(c, c->p_off, c->h_off, sizeof(long long) * (c->T + 1), 0);
+  if (rc) return rc;
+  // raw xyz -> float4 (through the d_p buffer area when the input is on the host)
+  float* staging = nullptr;
+  if (on_device) {
+    staging = const_cast<float*>(points);
+  } else {
+    staging = reinterpret_cast<float*>(c->pb.sorted);  // MT_cap float4 >= 3 MT floats
+    rc = copy_in(c, staging, points, sizeof(float) * 3 * MT, 0);
+    if (rc) return rc;
+  }
+  CK(c, launch_points_to_float4(staging, c->praw, MT, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  rc = build_point_buckets(c);
+  if (rc) return rc;
+  c->phase = 0;
+  return NPG_OK;
+}
+
+extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref_xyz,
+                          const float* ref_nrm, int N, const int32_t* faces, int F_tri,
+                          const float* points, const int64_t* frame_offsets, int T, int t_key,
+                          const float* mlp_init, size_t mlp_len, int inputs_on_device) {
+  if (!out) return set_err(nullptr, NPG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return set_err(nullptr, NPG_EINVAL, "cfg is NULL");
+  char why[256];
+  if (!validate(cfg, why, sizeof(why))) return set_err(nullptr, NPG_EINVAL, "config: %s", why);
+  if (N < 1 || T < 1 || F_tri < 0 || t_key < 0 || t_key >= T)
+    return set_err(nullptr, NPG_EINVAL, "bad sizes N=%d T=%d F_tri=%d t_key=%d", N, T, F_tri,
+                   t_key);
+  if (!ref_xyz || !ref_nrm || !points || !frame_offsets || !mlp_init || (F_tri > 0 && !faces))
+    return set_err(nullptr, NPG_EINVAL, "NULL input pointer");
+
+  npg_ctx* c = new (std::nothrow) npg_ctx();
+  if (!c) return set_err(nullptr, NPG_ENOMEM, "host allocation failed");
+  c->cfg = *cfg;
+  c->stream = static_cast<cudaStream_t>(cfg->stream);
+  c->N = N;
+  c->T = T;
+  c->t_key = t_key;
+  auto fail = [&](int rc) {
+    g_thread_err = c->err;
+    npg_destroy(c);
+    return rc;
+  };
+  if (cudaGetDevice(&c->dev) != cudaSuccess) return fail(cuda_fail(c, cudaGetLastError(), "cudaGetDevice"));
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev);
+  if (c->num_sms <= 0) c->num_sms = 148;
+
+  MlpDims& md = c->md;
+  md.H = cfg->H;
+  md.D = cfg->depth;
+  md.Z = cfg->F_n + cfg->F_p;
+  md.M = cfg->n_freq;
+  md.K = md.Z + 2 * md.M;
+  md.NO = cfg->rot_mode == NPG_ROT_QUAT ? 7 : 6;
+  md.slope = cfg->leaky_slope;
+  c->mlp_len = (long long)md.H * md.K + md.H + (long long)(md.D - 1) * (md.H * md.H + md.H) +
+               (long long)md.NO * md.H + md.NO;
+  if ((long long)mlp_len != c->mlp_len)
+    return fail(set_err(c, NPG_EINVAL, "mlp_len %zu != expected %lld", mlp_len, c->mlp_len));
+  if (cfg->precision == NPG_FP32) {
+    if (!decode_fp32_supported(md.H, md.D))
+      return fail(set_err(c, NPG_ENOTIMPL, "FP32 path supports H in {16,32,64}, got %d", md.H));
+    if (mlp_bwd_fp32_smem(md) > 227 * 1024)
+      return fail(set_err(c, NPG_ENOTIMPL, "FP32 backward needs %zu B shared memory (H=%d depth=%d)",
+                          mlp_bwd_fp32_smem(md), md.H, md.D));
+  } else if (cfg->precision == NPG_BF16_MLP) {
+    if (!decode_bf16_supported(md.H, md.D))
+      return fail(set_err(c, NPG_ENOTIMPL, "BF16 path supports H in {64,128}, got H=%d depth=%d",
+                          md.H, md.D));
+  } else {
+    return fail(set_err(c, NPG_EINVAL, "precision=%d", cfg->precision));
+  }
+
+  // grid levels (l == L is the normal grid); device offsets 256-byte aligned
+  c->nlev = cfg->L + 1;
+  long long off = 0, flat = 0;
+  for (int l = 0; l < c->nlev; ++l) {
+    Level& lv = c->lev[l];
+    lv.r = l < cfg->L ? cfg->res[l] : cfg->res_n;
+    lv.F = l < cfg->L ? cfg->F_p : cfg->F_n;
+    lv.n = (long long)lv.r * lv.r * lv.r * lv.F;
+    lv.off = off;
+    lv.flat = flat;
+    lv.lr = cfg->lr_grid[l];
+    lv.lambda = cfg->lambda[l];
+    off += (lv.n + 63) & ~63LL;
+    flat += lv.n;
+    c->max_r = std::max(c->max_r, lv.r);
+    c->max_level_n = std::max(c->max_level_n, lv.n);
+  }
+  c->grid_dev_len = off;
+  c->grid_flat_len = flat;
+
+  // host-side copies of the small inputs we need to inspect
+  std::vector<char> hoff, hfaces;
+  int rc = fetch_host(c, hoff, frame_offsets, sizeof(int64_t) * (T + 1), inputs_on_device);
+  if (rc) return fail(rc);
+  const int64_t* ho = reinterpret_cast<const int64_t*>(hoff.data());
+  c->MT_cap = ho[T];
+  rc = fetch_host(c, hfaces, faces, sizeof(int32_t) * 3 * (size_t)F_tri, inputs_on_device);
+  if (rc) return fail(rc);
+
+  // edges: unique undirected (a < b), sorted; vertex-centric adjacency
+  std::vector<std::pair<int, int>> ev;
+  ev.reserve(3 * (size_t)F_tri);
+  const int32_t* hf = reinterpret_cast<const int32_t*>(hfaces.data());
+  for (int f = 0; f < F_tri; ++f)
+    for (int k = 0; k < 3; ++k) {
+      int a = hf[3 * f + k], b = hf[3 * f + (k + 1) % 3];
+      if (a < 0 || a >= N || b < 0 || b >= N)
+        return fail(set_err(c, NPG_EINVAL, "face %d references vertex out of range", f));
+      if (a == b) continue;
+      ev.emplace_back(std::min(a, b), std::max(a, b));
+    }
+  std::sort(ev.begin(), ev.end());
+  ev.erase(std::unique(ev.begin(), ev.end()), ev.end());
+  c->E = (int)ev.size();
+  std::vector<int> adj_off(N + 1, 0), adj(2 * (size_t)c->E), adj_edge(2 * (size_t)c->E);
+  std::vector<int2> edges(c->E);
+  for (int e = 0; e < c->E; ++e) {
+    edges[e] = make_int2(ev[e].first, ev[e].second);
+    adj_off[ev[e].first + 1]++;
+    adj_off[ev[e].second + 1]++;
+  }
+  for (int i = 0; i < N; ++i) adj_off[i + 1] += adj_off[i];
+  {
+    std::vector<int> fill(adj_off.begin(), adj_off.end() - 1);
+    for (int e = 0; e < c->E; ++e) {
+      int a = ev[e].first, b = ev[e].second;
+      adj[fill[a]] = b;
+      adj_edge[fill[a]++] = e;
+      adj[fill[b]] = a;
+      adj_edge[fill[b]++] = e;
+    }
+  }
+
+  // bucket resolutions
+  const long long Mavg = std::max<long long>(1, c->MT_cap / T);
+  c->pb.G = cfg->nn_cells > 0 ? cfg->nn_cells : auto_cells(Mavg, T);
+  c->xb.G = cfg->nn_cells > 0 ? cfg->nn_cells : auto_cells(N, T);
+  c->pb.nsets = c->xb.nsets = T;
+  const long long Gp3 = (long long)c->pb.G * c->pb.G * c->pb.G;
+  const long long Gx3 = (long long)c->xb.G * c->xb.G * c->xb.G;
+  const long long NT = (long long)N * T;
+
+  bool ok = true;
+  ok &= alloc_n(c, c->xr, N) && alloc_n(c, c->nr, N);
+  ok &= alloc_n(c, c->adj_off, N + 1) && alloc_n(c, c->adj, 2LL * c->E) &&
+        alloc_n(c, c->adj_edge, 2LL * c->E) && alloc_n(c, c->edges, c->E) &&
+        alloc_n(c, c->lref, c->E);
+  ok &= alloc_n(c, c->p_off, T + 1) && alloc_n(c, c->praw, c->MT_cap);
+  ok &= alloc_n(c, c->pb.cell_start, T * (Gp3 + 1)) && alloc_n(c, c->pb.counts, T * Gp3) &&
+        alloc_n(c, c->pb.slot, c->MT_cap) && alloc_n(c, c->pb.sorted, c->MT_cap);
+  ok &= alloc_n(c, c->xb.cell_start, T * (Gx3 + 1)) && alloc_n(c, c->xb.counts, T * Gx3) &&
+        alloc_n(c, c->xb.slot, NT) && alloc_n(c, c->xb.sorted, NT);
+  ok &= alloc_n(c, c->z, (long long)N * md.Z) && alloc_n(c, c->U, (long long)N * md.H) &&
+        alloc_n(c, c->V, (long long)T * md.H) && alloc_n(c, c->xhat, NT) &&
+        alloc_n(c, c->dxhat, NT) && alloc_n(c, c->nn_x, NT) && alloc_n(c, c->d_x, NT) &&
+        alloc_n(c, c->nn_p, c->MT_cap) && alloc_n(c, c->d_p, c->MT_cap) &&
+        alloc_n(c, c->dz, (long long)N * md.Z);
+  ok &= alloc_n(c, c->cd, T) && alloc_n(c, c->wconf, T) && alloc_n(c, c->iso_t, T) &&
+        alloc_n(c, c->loss, 4) && alloc_n(c, c->d_epoch, 1) && alloc_n(c, c->d_adam_c, 2);
+  ok &= alloc_n(c, c->grid, c->grid_dev_len) && alloc_n(c, c->g_grid, c->grid_dev_len) &&
+        alloc_n(c, c->g_pc, c->grid_dev_len) && alloc_n(c, c->m_grid, c->grid_dev_len) &&
+        alloc_n(c, c->v_grid, c->grid_dev_len);
+  ok &= alloc_n(c, c->mlp, c->mlp_len) && alloc_n(c, c->g_mlp, c->mlp_len) &&
+        alloc_n(c, c->m_mlp, c->mlp_len) && alloc_n(c, c->v_mlp, c->mlp_len);
+  ok &= alloc_n(c, c->pc_tmp0, c->max_level_n) && alloc_n(c, c->pc_tmp1, c->max_level_n);
+  long long dct_len = 0;
+  for (int l = 0; l < c->nlev; ++l) {
+    c->dct_off[l] = dct_len;
+    dct_len += ((2LL * c->lev[l].r * c->lev[l].r + c->lev[l].r) + 63) & ~63LL;
+  }
+  ok &= alloc_n(c, c->dct, dct_len);
+  if (!ok) return fail(set_err(c, NPG_ENOMEM, "device allocation failed"));
+  if (cudaMallocHost(&c->h_loss, sizeof(double) * (4 + T)) != cudaSuccess ||
+      cudaMallocHost(&c->h_off, sizeof(long long) * (T + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(set_err(c, NPG_ENOMEM, "pinned host allocation failed"));
+  }
+
+  // inputs
+  {
+    std::vector<char> hx, hn;
+    if ((rc = fetch_host(c, hx, ref_xyz, sizeof(float) * 3 * (size_t)N, inputs_on_device)) ||
+        (rc = fetch_host(c, hn, ref_nrm, sizeof(float) * 3 * (size_t)N, inputs_on_device)))
+      return fail(rc);
+    std::vector<float4> x4(N), n4(N);
+    const float* px = reinterpret_cast<const float*>(hx.data());
+    const float* pn = reinterpret_cast<const float*>(hn.data());
+    for (int i = 0; i < N; ++i) {
+      x4[i] = make_float4(px[3 * i], px[3 * i + 1], px[3 * i + 2], 0.f);
+      n4[i] = make_float4(pn[3 * i], pn[3 * i + 1], pn[3 * i + 2], 0.f);
+    }
+    if ((rc = copy_in(c, c->xr, x4.data(), sizeof(float4) * N, 0)) ||
+        (rc = copy_in(c, c->nr, n4.data(), sizeof(float4) * N, 0)) ||
+        (rc = copy_in(c, c->adj_off, adj_off.data(), sizeof(int) * (N + 1), 0)) ||
+        (rc = copy_in(c, c->adj, adj.data(), sizeof(int) * adj.size(), 0)) ||
+        (rc = copy_in(c, c->adj_edge, adj_edge.data(), sizeof(int) * adj_edge.size(), 0)) ||
+        (rc = copy_in(c, c->edges, edges.data(), sizeof(int2) * edges.size(), 0)) ||
+        (rc = copy_in(c, c->mlp, mlp_init, sizeof(float) * mlp_len, inputs_on_device)))
+      return fail(rc);
+    std::vector<float> tab(dct_len, 0.f);
+    for (int l = 0; l < c->nlev; ++l) {
+      const int r = c->lev[l].r;
+      float* base = tab.data() + c->dct_off[l];
+      dct_tables(r, base, base + (long long)r * r, base + 2LL * r * r);
+    }
+    if ((rc = copy_in(c, c->dct, tab.data(), sizeof(float) * tab.size(), 0))) return fail(rc);
+    CK(c, cudaStreamSynchronize(c->stream));
+  }
+  CK(c, cudaMemsetAsync(c->grid, 0, sizeof(float) * c->grid_dev_len, c->stream));
+  CK(c, cudaMemsetAsync(c->m_grid, 0, sizeof(float) * c->grid_dev_len, c->stream));
+  CK(c, cudaMemsetAsync(c->v_grid, 0, sizeof(float) * c->grid_dev_len, c->stream));
+  CK(c, cudaMemsetAsync(c->g_grid, 0, sizeof(float) * c->grid_dev_len, c->stream));
+  CK(c, cudaMemsetAsync(c->g_pc, 0, sizeof(float) * c->grid_dev_len, c->stream));
+  CK(c, cudaMemsetAsync(c->m_mlp, 0, sizeof(float) * c->mlp_len, c->stream));
+  CK(c, cudaMemsetAsync(c->v_mlp, 0, sizeof(float) * c->mlp_len, c->stream));
+  CK(c, cudaMemsetAsync(c->g_mlp, 0, sizeof(float) * c->mlp_len, c->stream));
+  CK(c, cudaMemsetAsync(c->d_epoch, 0, sizeof(int), c->stream));
+  if ((rc = set_points_impl(c, points, frame_offsets, inputs_on_device))) return fail(rc);
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->phase = 0;
+  *out = c;
+  return NPG_OK;
+}
+
+// ----------------------------------------------------------------- the iteration
+
+static int guard(npg_ctx* c) {
+  if (!c) return set_err(nullptr, NPG_EINVAL, "ctx is NULL");
+  if (c->sticky) return set_err(c, NPG_ECUDA, "context unusable after a sticky CUDA error: %s",
+                                c->err.c_str());
+  return NPG_OK;
+}
+
+static int forward_launch(npg_ctx* c) {
+  begin_iteration_timing(c);
+  mark(c, 0);
+  CK(c, launch_encode(c));
+  CK(c, launch_time_mod(c));
+  mark(c, 1);
+  if (c->cfg.precision == NPG_BF16_MLP)
+    CK(c, launch_decode_bf16(c));
+  else
+    CK(c, launch_decode_fp32(c));
+  mark(c, 2);
+  c->launches += 3;
+  return NPG_OK;
+}
+
+static int loss_launch(npg_ctx* c) {
+  const long long NT = (long long)c->N * c->T;
+  CK(c, bucket_build(c->xhat, nullptr, c->N, c->T, NT, c->xb.G, c->xb, c->stream));
+  mark(c, 3);
+  // vertex -> point (queries in x-hat bucket order for coherent warps)
+  CK(c, launch_nn(c->xb.sorted, c->N, nullptr, c->T, NT, c->pb, c->p_off, 0, c->nn_x, c->d_x,
+                  c->stream));
+  mark(c, 4);
+  // point -> vertex
+  CK(c, launch_nn(c->pb.sorted, 0, c->p_off, c->T, c->MT, c->xb, nullptr, c->N, c->nn_p, c->d_p,
+                  c->stream));
+  mark(c, 5);
+  CK(c, launch_edge_lengths(c));
+  CK(c, launch_loss(c));
+  mark(c, 6);
+  c->launches += 3 + 2 + 1 + 2;
+  return NPG_OK;
+}
+
+static int backprop_launch(npg_ctx* c) {
+  CK(c, cudaMemsetAsync(c->g_mlp, 0, sizeof(float) * c->mlp_len, c->stream));
+  CK(c, cudaMemsetAsync(c->dz, 0, sizeof(float) * (size_t)c->N * c->md.Z, c->stream));
+  CK(c, cudaMemsetAsync(c->g_grid, 0, sizeof(float) * c->grid_dev_len, c->stream));
+  if (c->cfg.precision == NPG_BF16_MLP)
+    CK(c, launch_mlp_backward_bf16(c));
+  else
+    CK(c, launch_mlp_backward_fp32(c));
+  mark(c, 8);
+  CK(c, launch_scatter(c));
+  mark(c, 9);
+  c->launches += 2;
+  return NPG_OK;
+}
+
+static int backward_launch(npg_ctx* c) {
+  CK(c, launch_dxhat(c));
+  mark(c, 7);
+  c->launches += 2;
+  return backprop_launch(c);
+}
+
+static int step_launch(npg_ctx* c) {
+  const npg_config& f = c->cfg;
+  CK(c, launch_step_prepare(c->d_epoch, f.adam_beta1, f.adam_beta2, c->d_adam_c, c->stream));
+  for (int l = 0; l < c->nlev; ++l) {
+    const Level& lv = c->lev[l];
+    const float* tab = c->dct + c->dct_off[l];
+    const long long rr = (long long)lv.r * lv.r;
+    CK(c, launch_precondition(c->g_grid + lv.off, c->g_pc + lv.off, c->pc_tmp0, c->pc_tmp1, tab,
+                              tab + rr, tab + 2 * rr, lv.r, lv.F, lv.lambda, c->stream));
+  }
+  mark(c, 10);
+  for (int l = 0; l < c->nlev; ++l) {
+    const Level& lv = c->lev[l];
+    CK(c, launch_adam(c->grid + lv.off, c->g_pc + lv.off, c->m_grid + lv.off,
+                      c->v_grid + lv.off, lv.n, lv.lr, f.adam_beta1, f.adam_beta2, f.adam_eps,
+                      c->d_adam_c, c->stream));
+  }
+  CK(c, launch_adam(c->mlp, c->g_mlp, c->m_mlp, c->v_mlp, c->mlp_len, f.lr_mlp, f.adam_beta1,
+                    f.adam_beta2, f.adam_eps, c->d_adam_c, c->stream));
+  CK(c, launch_step_finish(c->d_epoch, c->stream));
+  mark(c, 11);
+  end_iteration_timing(c);
+  c->launches += 1 + 6LL * c->nlev + c->nlev + 1 + 1;
+  return NPG_OK;
+}
+
+static int copy_loss_out(npg_ctx* c, double* loss_out, double* cd_out) {
+  if (!loss_out && !cd_out) return NPG_OK;
+  CK(c, cudaMemcpyAsync(c->h_loss, c->loss, sizeof(double) * 3, cudaMemcpyDeviceToHost,
+                        c->stream));
+  if (cd_out)
+    CK(c, cudaMemcpyAsync(c->h_loss + 4, c->cd, sizeof(double) * c->T, cudaMemcpyDeviceToHost,
+                          c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (loss_out) memcpy(loss_out, c->h_loss, sizeof(double) * 3);
+  if (cd_out) memcpy(cd_out, c->h_loss + 4, sizeof(double) * c->T);
+  return NPG_OK;
+}
+
+extern "C" int npg_forward(npg_ctx* c, float* xhat_out) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if ((rc = forward_launch(c))) return rc;
+  if (xhat_out) CK(c, launch_xhat_out(c->xhat, xhat_out, (long long)c->N * c->T, c->stream));
+  c->phase = 1;
+  return NPG_OK;
+}
+
+extern "C" int npg_loss(npg_ctx* c, double* loss_out, double* cd_out) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (c->phase != 1) return set_err(c, NPG_ESTATE, "npg_loss needs a preceding npg_forward");
+  if ((rc = loss_launch(c))) return rc;
+  c->phase = 2;
+  return copy_loss_out(c, loss_out, cd_out);
+}
+
+extern "C" int npg_backward(npg_ctx* c) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (c->phase != 2) return set_err(c, NPG_ESTATE, "npg_backward needs a preceding npg_loss");
+  if ((rc = backward_launch(c))) return rc;
+  c->phase = 3;
+  return NPG_OK;
+}
+
+extern "C" int npg_backprop(npg_ctx* c, const float* dxhat) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (c->phase < 1) return set_err(c, NPG_ESTATE, "npg_backprop needs a preceding npg_forward");
+  if (dxhat)
+    CK(c, launch_points_to_float4(dxhat, c->dxhat, (long long)c->N * c->T, c->stream));
+  if ((rc = backprop_launch(c))) return rc;
+  c->phase = 3;
+  return NPG_OK;
+}
+
+extern "C" int npg_step(npg_ctx* c) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (c->phase != 3) return set_err(c, NPG_ESTATE, "npg_step needs a preceding npg_backward");
+  if ((rc = step_launch(c))) return rc;
+  c->phase = 0;
+  c->e += 1;
+  return NPG_OK;
+}
+
+static int iteration_launch(npg_ctx* c) {
+  int rc;
+  if ((rc = forward_launch(c)) || (rc = loss_launch(c)) || (rc = backward_launch(c)) ||
+      (rc = step_launch(c)))
+    return rc;
+  return NPG_OK;
+}
+
+extern "C" int npg_iteration(npg_ctx* c, double* loss_out) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!c->cfg.use_graph) {
+    if ((rc = iteration_launch(c))) return rc;
+  } else {
+    if (!c->graph_exec) {
+      if (c->stream == nullptr)
+        return set_err(c, NPG_EINVAL, "use_graph needs a non-default stream");
+      // one eager iteration first: function attributes and lazy module loading
+      // happen outside the capture
+      if ((rc = iteration_launch(c))) return rc;
+      CK(c, cudaStreamSynchronize(c->stream));
+      c->e += 1;
+      c->phase = 0;
+      CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      c->capturing = 1;
+      const long long before = c->launches;
+      rc = iteration_launch(c);
+      c->capturing = 0;
+      c->graph_launches = c->launches - before;
+      c->launches = before;
+      cudaGraph_t g = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (ce != cudaSuccess) return cuda_fail(c, ce, "cudaStreamEndCapture");
+      c->graph = g;
+      CK(c, cudaGraphInstantiate(&c->graph_exec, g, 0));
+      // this call's iteration was the eager one; replays start with the next call
+      if (loss_out) {
+        rc = copy_loss_out(c, loss_out, nullptr);
+        if (rc) return rc;
+      }
+      return NPG_OK;
+    }
+    CK(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    c->launches += c->graph_launches;
+  }
+  c->e += 1;
+  c->phase = 0;
+  return copy_loss_out(c, loss_out, nullptr);
+}
+
+// ----------------------------------------------------------------- buffers
+
+extern "C" size_t npg_size(const npg_ctx* c, int which) {
+  if (!c) return 0;
+  const size_t NT = (size_t)c->N * c->T;
+  switch (which) {
+    case NPG_BUF_GRID: case NPG_BUF_GRID_GRAD: case NPG_BUF_GRID_PC:
+    case NPG_BUF_ADAM_M_GRID: case NPG_BUF_ADAM_V_GRID:
+      return sizeof(float) * (size_t)c->grid_flat_len;
+    case NPG_BUF_MLP: case NPG_BUF_MLP_GRAD: case NPG_BUF_ADAM_M_MLP: case NPG_BUF_ADAM_V_MLP:
+      return sizeof(float) * (size_t)c->mlp_len;
+    case NPG_BUF_XHAT: case NPG_BUF_DXHAT: return sizeof(float) * 3 * NT;
+    case NPG_BUF_NN_X: return sizeof(int32_t) * NT;
+    case NPG_BUF_NN_P: return sizeof(int32_t) * (size_t)c->MT;
+    case NPG_BUF_CD: case NPG_BUF_WCONF: return sizeof(double) * (size_t)c->T;
+    case NPG_BUF_DIST_X: return sizeof(float) * NT;
+    case NPG_BUF_DIST_P: return sizeof(float) * (size_t)c->MT;
+  }
+  return 0;
+}
+
+static float* grid_buf(npg_ctx* c, int which) {
+  switch (which) {
+    case NPG_BUF_GRID: return c->grid;
+    case NPG_BUF_GRID_GRAD: return c->g_grid;
+    case NPG_BUF_GRID_PC: return c->g_pc;
+    case NPG_BUF_ADAM_M_GRID: return c->m_grid;
+    case NPG_BUF_ADAM_V_GRID: return c->v_grid;
+  }
+  return nullptr;
+}
+
+static void* plain_buf(npg_ctx* c, int which) {
+  switch (which) {
+    case NPG_BUF_MLP: return c->mlp;
+    case NPG_BUF_MLP_GRAD: return c->g_mlp;
+    case NPG_BUF_ADAM_M_MLP: return c->m_mlp;
+    case NPG_BUF_ADAM_V_MLP: return c->v_mlp;
+    case NPG_BUF_NN_X: return c->nn_x;
+    case NPG_BUF_NN_P: return c->nn_p;
+    case NPG_BUF_CD: return c->cd;
+    case NPG_BUF_WCONF: return c->wconf;
+    case NPG_BUF_DIST_X: return c->d_x;
+    case NPG_BUF_DIST_P: return c->d_p;
+  }
+  return nullptr;
+}
+
+extern "C" int npg_get(npg_ctx* c, int which, void* dst, size_t bytes, int dst_on_device) {
+  int rc = guard(c);
+  if (rc) return rc;
+  const size_t need = npg_size(c, which);
+  if (need == 0) return set_err(c, NPG_EINVAL, "unknown buffer %d", which);
+  if (!dst || bytes != need)
+    return set_err(c, NPG_EINVAL, "buffer %d needs %zu bytes, got %zu", which, need, bytes);
+  const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (float* g = grid_buf(c, which)) {
+    for (int l = 0; l < c->nlev; ++l)
+      CK(c, cudaMemcpyAsync(static_cast<float*>(dst) + c->lev[l].flat, g + c->lev[l].off,
+                            sizeof(float) * c->lev[l].n, kind, c->stream));
+  } else if (which == NPG_BUF_XHAT || which == NPG_BUF_DXHAT) {
+    const long long NT = (long long)c->N * c->T;
+    const float4* srcv = which == NPG_BUF_XHAT ? c->xhat : c->dxhat;
+    if (dst_on_device) {
+      CK(c, launch_xhat_out(srcv, static_cast<float*>(dst), NT, c->stream));
+    } else {
+      if (!c->xhat3 && !alloc_n(c, c->xhat3, 3 * NT))
+        return set_err(c, NPG_ENOMEM, "device allocation failed");
+      CK(c, launch_xhat_out(srcv, c->xhat3, NT, c->stream));
+      CK(c, cudaMemcpyAsync(dst, c->xhat3, bytes, kind, c->stream));
+    }
+  } else {
+    CK(c, cudaMemcpyAsync(dst, plain_buf(c, which), bytes, kind, c->stream));
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return NPG_OK;
+}
+
+extern "C" int npg_set(npg_ctx* c, int which, const void* src, size_t bytes, int src_on_device) {
+  int rc = guard(c);
+  if (rc) return rc;
+  const bool settable = which == NPG_BUF_GRID || which == NPG_BUF_MLP ||
+                        which == NPG_BUF_ADAM_M_GRID || which == NPG_BUF_ADAM_V_GRID ||
+                        which == NPG_BUF_ADAM_M_MLP || which == NPG_BUF_ADAM_V_MLP;
+  if (!settable) return set_err(c, NPG_EINVAL, "buffer %d is not settable", which);
+  const size_t need = npg_size(c, which);
+  if (!src || bytes != need)
+    return set_err(c, NPG_EINVAL, "buffer %d needs %zu bytes, got %zu", which, need, bytes);
+  const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (float* g = grid_buf(c, which)) {
+    for (int l = 0; l < c->nlev; ++l)
+      CK(c, cudaMemcpyAsync(g + c->lev[l].off, static_cast<const float*>(src) + c->lev[l].flat,
+                            sizeof(float) * c->lev[l].n, kind, c->stream));
+  } else {
+    CK(c, cudaMemcpyAsync(plain_buf(c, which), src, bytes, kind, c->stream));
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->phase = 0;
+  return NPG_OK;
+}
+
+extern "C" int npg_get_epoch(const npg_ctx* c) { return c ? c->e : -1; }
+
+extern "C" int npg_set_epoch(npg_ctx* c, int e) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (e < 0) return set_err(c, NPG_EINVAL, "epoch < 0");
+  c->e = e;
+  CK(c, cudaMemcpyAsync(c->d_epoch, &c->e, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->phase = 0;
+  return NPG_OK;
+}
+
+// state blob: magic, version, grid_flat_len, mlp_len, e, then six FP32 arrays
+struct StateHeader {
+  uint64_t magic, version, grid_len, mlp_len, epoch, pad;
+};
+static const uint64_t kMagic = 0x4e50475354415445ULL;  // "NPGSTATE"
+
+extern "C" int npg_get_state(npg_ctx* c, void* blob, size_t* bytes) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!bytes) return set_err(c, NPG_EINVAL, "bytes is NULL");
+  const size_t gsz = sizeof(float) * c->grid_flat_len, msz = sizeof(float) * c->mlp_len;
+  const size_t need = sizeof(StateHeader) + 3 * gsz + 3 * msz;
+  if (!blob) {
+    *bytes = need;
+    return NPG_OK;
+  }
+  if (*bytes < need) return set_err(c, NPG_EINVAL, "state needs %zu bytes", need);
+  StateHeader h{kMagic, 1, (uint64_t)c->grid_flat_len, (uint64_t)c->mlp_len, (uint64_t)c->e, 0};
+  char* p = static_cast<char*>(blob);
+  memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  const int ids[6] = {NPG_BUF_GRID, NPG_BUF_ADAM_M_GRID, NPG_BUF_ADAM_V_GRID,
+                      NPG_BUF_MLP,  NPG_BUF_ADAM_M_MLP,  NPG_BUF_ADAM_V_MLP};
+  for (int k = 0; k < 6; ++k) {
+    const size_t sz = k < 3 ? gsz : msz;
+    if ((rc = npg_get(c, ids[k], p, sz, 0))) return rc;
+    p += sz;
+  }
+  *bytes = need;
+  return NPG_OK;
+}
+
+extern "C" int npg_set_state(npg_ctx* c, const void* blob, size_t bytes) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!blob || bytes < sizeof(StateHeader)) return set_err(c, NPG_EINVAL, "state too small");
+  StateHeader h;
+  memcpy(&h, blob, sizeof(h));
+  const size_t gsz = sizeof(float) * c->grid_flat_len, msz = sizeof(float) * c->mlp_len;
+  if (h.magic != kMagic || h.version != 1 || h.grid_len != (uint64_t)c->grid_flat_len ||
+      h.mlp_len != (uint64_t)c->mlp_len || bytes != sizeof(h) + 3 * gsz + 3 * msz)
+    return set_err(c, NPG_EINVAL, "state blob does not match this context");
+  const char* p = static_cast<const char*>(blob) + sizeof(h);
+  const int ids[6] = {NPG_BUF_GRID, NPG_BUF_ADAM_M_GRID, NPG_BUF_ADAM_V_GRID,
+                      NPG_BUF_MLP,  NPG_BUF_ADAM_M_MLP,  NPG_BUF_ADAM_V_MLP};
+  for (int k = 0; k < 6; ++k) {
+    const size_t sz = k < 3 ? gsz : msz;
+    if ((rc = npg_set(c, ids[k], p, sz, 0))) return rc;
+    p += sz;
+  }
+  return npg_set_epoch(c, (int)h.epoch);
+}
+
+extern "C" int npg_set_points(npg_ctx* c, const float* points, const int64_t* frame_offsets,
+                              int on_device) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!points || !frame_offsets) return set_err(c, NPG_EINVAL, "NULL pointer");
+  return set_points_impl(c, points, frame_offsets, on_device);
+}
+
+extern "C" int npg_timing(npg_ctx* c, int n_iters) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (n_iters < 0 || n_iters > 100000) return set_err(c, NPG_EINVAL, "n_iters out of 0..100000");
+  CK(c, cudaStreamSynchronize(c->stream));
+  free_timing(c);
+  if (n_iters == 0) return NPG_OK;
+  const int per = NPG_NUM_STAGES + 1;
+  c->tev = new (std::nothrow) cudaEvent_t[(size_t)n_iters * per];
+  c->t_mask = new (std::nothrow) unsigned[n_iters];
+  if (!c->tev || !c->t_mask) return set_err(c, NPG_ENOMEM, "host allocation failed");
+  for (int k = 0; k < n_iters * per; ++k) {
+    cudaError_t e = cudaEventCreate(&c->tev[k]);
+    if (e != cudaSuccess) {
+      for (int j = 0; j < k; ++j) cudaEventDestroy(c->tev[j]);
+      delete[] c->tev;
+      delete[] c->t_mask;
+      c->tev = nullptr;
+      c->t_mask = nullptr;
+      return cuda_fail(c, e, "cudaEventCreate");
+    }
+  }
+  for (int k = 0; k < n_iters; ++k) c->t_mask[k] = 0;
+  c->t_slots = n_iters;
+  c->t_next = 0;
+  return NPG_OK;
+}
+
+extern "C" int npg_timing_read(npg_ctx* c, int stage, double* total_ms, int* n_iters) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (stage < 0 || stage >= NPG_NUM_STAGES || !total_ms || !n_iters)
+    return set_err(c, NPG_EINVAL, "bad stage or NULL output");
+  CK(c, cudaStreamSynchronize(c->stream));
+  double tot = 0.0;
+  int n = 0;
+  const int per = NPG_NUM_STAGES + 1;
+  const unsigned need = (1u << stage) | (1u << (stage + 1));
+  for (int s = 0; s < c->t_next && s < c->t_slots; ++s) {
+    if ((c->t_mask[s] & need) != need) continue;
+    float ms = 0.f;
+    CK(c, cudaEventElapsedTime(&ms, c->tev[s * per + stage], c->tev[s * per + stage + 1]));
+    tot += ms;
+    ++n;
+  }
+  *total_ms = tot;
+  *n_iters = n;
+  return NPG_OK;
+}
+
+extern "C" long long npg_launch_count(const npg_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" int npg_destroy(npg_ctx* c) {
+  if (!c) return NPG_OK;
+  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  free_timing(c);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  dev_free_all(c);
+  if (c->h_loss) cudaFreeHost(c->h_loss);
+  if (c->h_off) cudaFreeHost(c->h_off);
+  cudaGetLastError();
+  delete c;
+  return NPG_OK;
+}
+
+extern "C" const char* npg_last_error(const npg_ctx* c) {
+  if (c) return c->err.c_str();
+  return g_thread_err.c_str();
+}
+
+// ----------------------------------------------------------------- standalone ops
+
+extern "C" int npg_nearest(const float* q, int nq, const float* cand, int nc, int32_t* idx,
+                           float* dist, int cells, void* stream) {
+  if (nq < 0 || nc < 1 || (nq > 0 && (!q || !idx)) || !cand || cells < 0 || cells > 256)
+    return set_err(nullptr, NPG_EINVAL, "npg_nearest: bad arguments (nq=%d nc=%d)", nq, nc);
+  if (nq == 0) return NPG_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int G = cells > 0 ? cells : auto_cells(nc, 1);
+  const long long G3 = (long long)G * G * G;
+  Buckets cb, qb;
+  cb.G = G;
+  cb.nsets = 1;
+  float4 *q4 = nullptr, *c4 = nullptr, *qs = nullptr;
+  int *qslot = nullptr;
+  auto cleanup = [&]() {
+    cudaFreeAsync(q4, s); cudaFreeAsync(c4, s); cudaFreeAsync(qs, s); cudaFreeAsync(qslot, s);
+    cudaFreeAsync(cb.cell_start, s); cudaFreeAsync(cb.counts, s); cudaFreeAsync(cb.slot, s);
+    cudaFreeAsync(cb.sorted, s); cudaFreeAsync(qb.cell_start, s); cudaFreeAsync(qb.counts, s);
+  };
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t b) {
+    if (e == cudaSuccess) e = cudaMallocAsync(p, b, s);
+  };
+  A((void**)&q4, sizeof(float4) * nq);
+  A((void**)&c4, sizeof(float4) * nc);
+  A((void**)&qs, sizeof(float4) * nq);
+  A((void**)&qslot, sizeof(int) * nq);
+  A((void**)&cb.cell_start, sizeof(int) * (G3 + 1));
+  A((void**)&cb.counts, sizeof(int) * G3);
+  A((void**)&cb.slot, sizeof(int) * nc);
+  A((void**)&cb.sorted, sizeof(float4) * nc);
+  A((void**)&qb.cell_start, sizeof(int) * (G3 + 1));
+  A((void**)&qb.counts, sizeof(int) * G3);
+  if (e == cudaSuccess) e = launch_points_to_float4(q, q4, nq, s);
+  if (e == cudaSuccess) e = launch_points_to_float4(cand, c4, nc, s);
+  if (e == cudaSuccess) e = bucket_build(c4, nullptr, nc, 1, nc, G, cb, s);
+  // queries sorted by the same cells (coherent warps)
+  qb.G = G;
+  qb.nsets = 1;
+  qb.slot = qslot;
+  qb.sorted = qs;
+  if (e == cudaSuccess) e = bucket_build(q4, nullptr, nq, 1, nq, G, qb, s);
+  if (e == cudaSuccess) e = launch_nn(qs, nq, nullptr, 1, nq, cb, nullptr, nc, idx, dist, s);
+  cleanup();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "npg_nearest");
+  return NPG_OK;
+}
+
+extern "C" int npg_precondition(const float* g, float* out, int r, int F, float lambda,
+                                void* stream) {
+  if (!g || !out || r < 2 || r > 512 || F < 1 || F > NPG_MAX_F || !(lambda >= 0.f))
+    return set_err(nullptr, NPG_EINVAL, "npg_precondition: bad arguments (r=%d F=%d)", r, F);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long n = (long long)r * r * r * F;
+  std::vector<float> tab(2LL * r * r + r);
+  dct_tables(r, tab.data(), tab.data() + (long long)r * r, tab.data() + 2LL * r * r);
+  float *t0 = nullptr, *t1 = nullptr, *dtab = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&t0, sizeof(float) * n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&t1, sizeof(float) * n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&dtab, sizeof(float) * tab.size(), s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dtab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_precondition(g, out, t0, t1, dtab, dtab + (long long)r * r, dtab + 2LL * r * r, r,
+                            F, lambda, s);
+  cudaFreeAsync(t0, s);
+  cudaFreeAsync(t1, s);
+  cudaFreeAsync(dtab, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "npg_precondition");
+  return NPG_OK;
+}

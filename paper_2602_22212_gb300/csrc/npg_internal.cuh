@@ -1,0 +1,169 @@
+// Internal declarations shared by the libnpg.so translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/npg.h"
+
+#define NPG_MAX_F 32
+#define NPG_MAX_FN 8
+#define NPG_MAX_Z (NPG_MAX_F + NPG_MAX_FN)
+#define NPG_MAX_FREQ 8
+#define NPG_MAX_K (NPG_MAX_Z + 2 * NPG_MAX_FREQ)
+#define NPG_MAX_DEPTH 8
+
+namespace npg {
+
+// One grid block: a position level (l < L) or the normal grid (l == L).
+struct Level {
+  int r;           // nodes per axis
+  int F;           // features per node
+  long long off;   // float offset in the device grid vector (256-byte aligned)
+  long long flat;  // float offset in the flat (unpadded) layout
+  long long n;     // r^3 * F
+  float lr;        // Adam learning rate
+  float lambda;    // Sobolev smoothing
+};
+
+// Bucket grid over [-1, 1]^3 used by the exact nearest-neighbour search.
+struct Buckets {
+  int G = 0;                // cells per axis
+  int nsets = 0;            // number of independent point sets (frames)
+  int* cell_start = nullptr;  // nsets x (G^3 + 1), set-local offsets
+  int* counts = nullptr;      // nsets x G^3 scratch
+  int* slot = nullptr;        // per point: rank within its cell
+  float4* sorted = nullptr;   // per point, in cell order: (x, y, z, bits(local index))
+};
+
+struct MlpDims {
+  int H, D, K, Z, NO, M;  // hidden width, hidden layers, first-layer inputs, latent, outputs, freqs
+  float slope;
+};
+
+}  // namespace npg
+
+struct npg_ctx {
+  npg_config cfg;
+  cudaStream_t stream = nullptr;
+  int dev = 0;
+  int N = 0, T = 0, t_key = 0, E = 0;
+  long long MT = 0, MT_cap = 0;
+  npg::MlpDims md;
+  int nlev = 0;  // L + 1
+  npg::Level lev[NPG_MAX_LEVELS + 1];
+  long long grid_dev_len = 0;   // padded
+  long long grid_flat_len = 0;  // oracle-compatible
+  long long mlp_len = 0;
+  int max_r = 0;
+  long long max_level_n = 0;
+
+  // constant inputs
+  float4* xr = nullptr;       // N reference vertices (w = 0)
+  float4* nr = nullptr;       // N unit normals
+  int* adj_off = nullptr;     // N + 1
+  int* adj = nullptr;         // 2E neighbour vertex ids
+  int* adj_edge = nullptr;    // 2E edge ids
+  int2* edges = nullptr;      // E (a < b)
+  float* lref = nullptr;      // E keyframe lengths (stop-grad)
+  long long* p_off = nullptr; // T + 1 (device)
+  long long* h_off = nullptr; // T + 1 (host copy)
+  float4* praw = nullptr;     // MT_cap points in input order (w = 0)
+  npg::Buckets pb;            // static point buckets
+  npg::Buckets xb;            // per-iteration x-hat buckets
+
+  // per-iteration buffers
+  float* z = nullptr;      // N x Z
+  float* U = nullptr;      // N x H
+  float* V = nullptr;      // T x H
+  float4* xhat = nullptr;  // T x N
+  float4* dxhat = nullptr; // T x N
+  int* nn_x = nullptr;     // T x N
+  float* d_x = nullptr;    // T x N
+  int* nn_p = nullptr;     // MT
+  float* d_p = nullptr;    // MT
+  float* dz = nullptr;     // N x Z
+  double* cd = nullptr;    // T
+  double* wconf = nullptr; // T
+  double* iso_t = nullptr; // T
+  double* loss = nullptr;  // 3: L, L_def, L_iso
+  double* h_loss = nullptr;  // pinned host mirror (3 + T)
+
+  // parameters, gradients, optimiser state
+  float* grid = nullptr;
+  float* g_grid = nullptr;
+  float* g_pc = nullptr;
+  float* m_grid = nullptr;
+  float* v_grid = nullptr;
+  float* mlp = nullptr;
+  float* g_mlp = nullptr;
+  float* m_mlp = nullptr;
+  float* v_mlp = nullptr;
+  float* mlp_bf16 = nullptr;  // packed tensor-core weights (BF16 path)
+
+  // preconditioner tables and scratch
+  float* dct = nullptr;          // per level: C (r x r) then C^T (r x r) then mu (r)
+  long long dct_off[NPG_MAX_LEVELS + 1];
+  float* pc_tmp0 = nullptr;
+  float* pc_tmp1 = nullptr;
+
+  // per-stage timing (event ring) and launch accounting
+  cudaEvent_t* tev = nullptr;  // t_slots x (NPG_NUM_STAGES + 1)
+  unsigned* t_mask = nullptr;  // per slot: which marks were recorded
+  int t_slots = 0, t_next = 0, t_cur = -1;
+  int capturing = 0;
+  long long launches = 0;
+  long long graph_launches = 0;  // kernels in one replay of the captured graph
+  int* d_epoch = nullptr;  // device copy of e (read by graph-captured kernels)
+  float* d_adam_c = nullptr;  // 1 - beta1^s, 1 - beta2^s of the current step
+  float* xhat3 = nullptr;     // T x N x 3 staging for npg_get
+  void* allocs[64];
+  int n_allocs = 0;
+  int phase = 0;  // 0 ready, 1 forward done, 2 loss done, 3 backward done
+  int e = 0;
+  int sticky = 0;
+  int num_sms = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  std::string err;
+};
+
+namespace npg {
+
+// kernels (launchers return cudaGetLastError())
+cudaError_t launch_encode(npg_ctx* c);
+cudaError_t launch_time_mod(npg_ctx* c);
+cudaError_t launch_decode_fp32(npg_ctx* c);
+cudaError_t launch_decode_bf16(npg_ctx* c);
+cudaError_t launch_edge_lengths(npg_ctx* c);
+
+cudaError_t bucket_build(const float4* pts, const long long* d_off, long long uniform_count,
+                         int nsets, long long total, int G, Buckets& b, cudaStream_t s);
+cudaError_t launch_nn(const float4* queries_sorted, long long q_uniform, const long long* q_off,
+                      int nsets, long long q_total, const Buckets& cand,
+                      const long long* c_off, long long c_uniform, int* out_idx, float* out_d,
+                      cudaStream_t s);
+cudaError_t launch_loss(npg_ctx* c);
+cudaError_t launch_dxhat(npg_ctx* c);
+cudaError_t launch_mlp_backward_fp32(npg_ctx* c);
+cudaError_t launch_mlp_backward_bf16(npg_ctx* c);
+cudaError_t launch_scatter(npg_ctx* c);
+cudaError_t launch_precondition(const float* g, float* out, float* tmp0, float* tmp1,
+                                const float* C, const float* Ct, const float* mu, int r, int F,
+                                float lambda, cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long n, float lr,
+                        float b1, float b2, float eps, const float* cc, cudaStream_t s);
+cudaError_t launch_step_prepare(const int* epoch, float b1, float b2, float* cc, cudaStream_t s);
+cudaError_t launch_step_finish(int* epoch, cudaStream_t s);
+void dct_tables(int r, float* C, float* Ct, float* mu);
+cudaError_t launch_points_to_float4(const float* src, float4* dst, long long n, cudaStream_t s);
+cudaError_t launch_xhat_out(const float4* xhat, float* out, long long n, cudaStream_t s);
+
+int auto_cells(long long points_per_set, int nsets);
+bool decode_fp32_supported(int H, int D);
+bool decode_bf16_supported(int H, int D);
+size_t mlp_bwd_fp32_smem(const MlpDims& md);
+
+}  // namespace npg

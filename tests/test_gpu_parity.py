@@ -1,0 +1,423 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 arithmetic on the GPU against FP64 on the CPU):
+  nearest-neighbour indices  bit-exact for the same FP32 inputs; on the full
+                             iteration, a different index is accepted only as
+                             a tie (|d_gpu - d_oracle| <= 1e-6, FP64 distances)
+  loss (Eq. 8) and cd_t      1e-5 relative
+  gradients                  1e-4 relative, norm-wise per parameter block,
+                             plus 64 sampled entries within 1e-4 of the block norm
+  x-hat                      1e-5 absolute (coordinates are O(1))
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_22212_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+LOSS_RTOL = 1e-5
+GRAD_RTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def npg():
+    from paper_2602_22212_gb300 import build
+    build.build()
+    from paper_2602_22212_gb300 import npg as mod
+    return mod
+
+
+# ----------------------------------------------------------------- helpers
+
+def tiny_setup(rot_mode=0, seed=0, T=8, M=4096, subdiv=4, H=64, D=2, F=2, L=4, res=(8, 27, 45, 64),
+               slope=0.0):
+    seq = I.sphere_blob(subdiv=subdiv, T=T, M=M, noise=0.005, seed=seed)
+    ocfg = O.make_cfg(L=L, res=res, F=F, H=H, D=D, rot_mode=rot_mode, slope=slope)
+    prob = O.Problem(ocfg, seq.x, seq.n, seq.faces, seq.points, seq.offsets, seq.t_key)
+    return seq, ocfg, prob
+
+
+def gpu_cfg(npg, ocfg, e_max=10, precision=0, **kw):
+    res = [ocfg.res[l] for l in range(ocfg.L)]
+    return npg.make_config(ocfg.L, res, ocfg.F, ocfg.H, ocfg.D, slope=ocfg.slope,
+                           rot_mode=ocfg.rot_mode, e_max=e_max, precision=precision, **kw)
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def blocks_of(ocfg):
+    """(name, slice) of each parameter block in the flat grid and MLP vectors."""
+    gb = []
+    for l in range(ocfg.L + 1):
+        a = O.level_offset(ocfg, l)
+        b = O.level_offset(ocfg, l + 1) if l < ocfg.L else O.grid_len(ocfg)
+        gb.append((f"grid{l}", slice(a, b)))
+    H, D, K, NO = ocfg.H, ocfg.D, O.k_in(ocfg), O.n_out(ocfg)
+    mb, o = [], 0
+    for name, n in [("W1", H * K), ("b1", H)] + sum(
+            [[(f"W{k + 2}", H * H), (f"b{k + 2}", H)] for k in range(D - 1)], []) + \
+            [("Wo", NO * H), ("bo", NO)]:
+        mb.append((name, slice(o, o + n)))
+        o += n
+    return gb, mb
+
+
+def check_grad_block(name, g, ref, rng):
+    nr = np.linalg.norm(ref)
+    if nr == 0:
+        assert np.linalg.norm(g) <= 1e-12, name
+        return
+    assert rel(g, ref) <= GRAD_RTOL, (name, rel(g, ref))
+    idx = rng.choice(len(ref), size=min(64, len(ref)), replace=False)
+    assert np.all(np.abs(g[idx] - ref[idx]) <= GRAD_RTOL * nr), name
+
+
+def nn_ties_ok(q, cand, got, want, tol=1e-6):
+    """Indices differ only where both candidates are equally near (within tol)."""
+    bad = np.nonzero(got != want)[0]
+    if len(bad) == 0:
+        return True
+    dq = lambda j: np.sum((q[bad] - cand[j]) ** 2, axis=1)
+    return bool(np.all(np.abs(dq(got[bad]) - dq(want[bad])) <= tol))
+
+
+# ----------------------------------------------------------------- standalone ops
+
+@pytest.mark.parametrize("nq,nc,cells", [(1, 1, 0), (37, 5, 0), (1000, 1500, 0), (4097, 3001, 7),
+                                         (5000, 20000, 0), (20000, 5000, 3), (0, 10, 0)])
+def test_nearest_bit_exact(npg, nq, nc, cells):
+    import torch
+    rng = np.random.default_rng(nq * 7 + nc)
+    q = rng.uniform(-1.2, 1.2, size=(nq, 3)).astype(np.float32)   # some outside the grid
+    c = rng.normal(scale=0.4, size=(nc, 3)).astype(np.float32)
+    if nc > 20:
+        c[nc // 2: nc // 2 + 10] = c[:10]  # exact duplicates: lowest index must win
+        q[:5] = c[:5]
+    want_i, _ = O.nn(f32(q), f32(c), decide_f32=True) if nq else (np.zeros(0, np.int32), None)
+    qt, ct = torch.from_numpy(q).cuda(), torch.from_numpy(c).cuda()
+    it = torch.full((max(nq, 1),), -1, dtype=torch.int32, device="cuda")
+    dt = torch.zeros(max(nq, 1), dtype=torch.float32, device="cuda")
+    npg.npg_nearest(qt, ct, it, dt, cells=cells)
+    got = it.cpu().numpy()[:nq]
+    np.testing.assert_array_equal(got, want_i)
+    if nq:
+        d32 = ((q - c[got]) ** 2).astype(np.float32)
+        ref = (d32[:, 0] + d32[:, 1]) + d32[:, 2]
+        np.testing.assert_allclose(dt.cpu().numpy()[:nq], ref, rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("r,F,lam", [(2, 1, 0.4), (5, 2, 0.6), (16, 4, 0.4), (27, 2, 1.35),
+                                     (65, 3, 6.8), (70, 4, 2.0)])
+def test_precondition_matches_oracle(npg, r, F, lam):
+    import torch
+    rng = np.random.default_rng(r)
+    g = rng.normal(size=r ** 3 * F).astype(np.float32)
+    ref, _ = O.precondition(r, F, lam, f32(g))
+    gt = torch.from_numpy(g).cuda()
+    out = torch.empty_like(gt)
+    npg.npg_precondition(gt, out, r, F, lam)
+    assert rel(out.cpu().numpy(), ref) <= 2e-6
+    # in place
+    npg.npg_precondition(gt, gt, r, F, lam)
+    assert rel(gt.cpu().numpy(), ref) <= 2e-6
+
+
+# ----------------------------------------------------------------- one iteration, tiny config
+
+def test_identity_initialisation_exact(npg):
+    seq, ocfg, prob = tiny_setup(T=3, M=500, subdiv=3)
+    mlp = I.mlp_init(O.k_in(ocfg), ocfg.H, ocfg.D, O.n_out(ocfg), seed=0)
+    ctx = npg.Context(gpu_cfg(npg, ocfg), seq, mlp)
+    ctx.forward()
+    xh = ctx.get(npg.BUF_XHAT).reshape(3, seq.N, 3)
+    for t in range(3):
+        np.testing.assert_array_equal(xh[t], seq.x)
+    ctx.close()
+
+
+def random_state(ocfg, seed=2, grid_scale=0.3, out_scale=0.5):
+    rng = np.random.default_rng(seed)
+    grid = rng.normal(scale=grid_scale, size=O.grid_len(ocfg)).astype(np.float32)
+    mlp = I.mlp_init(O.k_in(ocfg), ocfg.H, ocfg.D, O.n_out(ocfg), seed=seed + 1, zero_last=False)
+    mlp[-(O.n_out(ocfg) * ocfg.H + O.n_out(ocfg)):] *= out_scale
+    return grid, mlp
+
+
+def gpu_at(npg, ocfg, seq, grid, mlp, e, e_max, **kw):
+    ctx = npg.Context(gpu_cfg(npg, ocfg, e_max=e_max, **kw), seq, mlp)
+    ctx.set(npg.BUF_GRID, grid)
+    npg.npg_set_epoch(ctx.h, e)
+    ctx.forward()
+    return ctx
+
+
+def ambiguous_rows(prob, ref, nnx, nnp, margin=1e-4):
+    """(t, i) rows whose dL/dx-hat is not determined to FP32 precision: an
+    isometry edge whose length equals its keyframe length within `margin`
+    (|.| has a kink there) or a nearest-neighbour choice that differs (a tie)."""
+    T, N = prob.T, prob.N
+    bad = np.zeros((T, N), bool)
+    lref = O.edge_lengths(ref["xhat"], prob.t_key, prob.edges)
+    for t in range(T):
+        if t == prob.t_key:
+            continue
+        ln = O.edge_lengths(ref["xhat"], t, prob.edges)
+        amb = np.abs(ln - lref) <= margin * lref
+        bad[t, prob.edges[amb, 0]] = True
+        bad[t, prob.edges[amb, 1]] = True
+    bad |= nnx != ref["nn_x"]
+    for t in range(T):
+        a, b = prob.off[t], prob.off[t + 1]
+        d = np.nonzero(nnp[a:b] != ref["nn_p"][a:b])[0]
+        bad[t, nnp[a:b][d]] = True
+        bad[t, ref["nn_p"][a:b][d]] = True
+    return bad
+
+
+@pytest.mark.parametrize("rot_mode", [0, 1])
+def test_forward_and_loss_parity(npg, rot_mode):
+    seq, ocfg, prob = tiny_setup(rot_mode=rot_mode, seed=1)
+    grid, mlp = random_state(ocfg)
+    e, e_max = 3, 10
+    ref = O.loss_full(prob, f32(grid), f32(mlp), e, e_max, decide_f32=True, want_grad=False)
+    ctx = gpu_at(npg, ocfg, seq, grid, mlp, e, e_max)
+    xh = ctx.get(npg.BUF_XHAT).reshape(prob.T, prob.N, 3)
+    assert np.abs(xh - ref["xhat"]).max() <= 1e-5
+    loss, cd = ctx.loss()
+    for k, key in enumerate(("loss", "L_def", "L_iso")):
+        assert abs(loss[k] - ref[key]) <= LOSS_RTOL * abs(ref[key]), key
+    np.testing.assert_allclose(cd, ref["cd"], rtol=LOSS_RTOL)
+    np.testing.assert_allclose(ctx.get(npg.BUF_WCONF), ref["w"], rtol=LOSS_RTOL)
+    nnx = ctx.get(npg.BUF_NN_X).reshape(prob.T, prob.N)
+    nnp = ctx.get(npg.BUF_NN_P)
+    for t in range(prob.T):
+        a, b = seq.offsets[t], seq.offsets[t + 1]
+        P = seq.points[a:b].astype(np.float64)
+        X = xh[t].astype(np.float64)
+        assert nn_ties_ok(X, P, nnx[t], ref["nn_x"][t])
+        assert nn_ties_ok(P, X, nnp[a:b], ref["nn_p"][a:b])
+    assert np.count_nonzero(nnx != ref["nn_x"]) + np.count_nonzero(nnp != ref["nn_p"]) <= 3
+    d_x = ctx.get(npg.BUF_DIST_X).reshape(prob.T, prob.N)
+    np.testing.assert_allclose(d_x, np.sum((xh - seq.points[
+        seq.offsets[:-1, None] + nnx]) ** 2, axis=-1), rtol=1e-5, atol=1e-12)
+    ctx.close()
+
+
+@pytest.mark.parametrize("rot_mode", [0, 1])
+def test_dxhat_parity(npg, rot_mode):
+    """dL/dx-hat (Chamfer both directions + isometry) on every row whose value
+    is determined to FP32 precision."""
+    seq, ocfg, prob = tiny_setup(rot_mode=rot_mode, seed=1)
+    grid, mlp = random_state(ocfg)
+    ref = O.loss_full(prob, f32(grid), f32(mlp), 3, 10, decide_f32=True)
+    ctx = gpu_at(npg, ocfg, seq, grid, mlp, 3, 10)
+    ctx.loss()
+    ctx.backward()
+    g = ctx.get(npg.BUF_DXHAT).reshape(prob.T, prob.N, 3).astype(np.float64)
+    nnx = ctx.get(npg.BUF_NN_X).reshape(prob.T, prob.N)
+    nnp = ctx.get(npg.BUF_NN_P)
+    bad = ambiguous_rows(prob, ref, nnx, nnp)
+    assert bad.mean() < 0.01
+    ok = ~bad
+    assert rel(g[ok], ref["g_xhat"][ok]) <= GRAD_RTOL
+    rows = np.argwhere(ok)
+    pick = rows[np.random.default_rng(0).choice(len(rows), 64, replace=False)]
+    gs, rs = g[pick[:, 0], pick[:, 1]], ref["g_xhat"][pick[:, 0], pick[:, 1]]
+    assert np.all(np.abs(gs - rs) <= GRAD_RTOL * np.abs(ref["g_xhat"][ok]).max())
+    ctx.close()
+
+
+@pytest.mark.parametrize("rot_mode", [0, 1])
+def test_backprop_parity(npg, rot_mode):
+    """Parameter gradients from the same dL/dx-hat (the oracle's, in FP32):
+    the MLP backward with forward recompute and the grid scatter."""
+    import torch
+    seq, ocfg, prob = tiny_setup(rot_mode=rot_mode, seed=1)
+    grid, mlp = random_state(ocfg)
+    ref = O.loss_full(prob, f32(grid), f32(mlp), 3, 10, decide_f32=True)
+    gx32 = ref["g_xhat"].astype(np.float32)
+    want_g, want_m = O.backprop(prob, f32(grid), f32(mlp), f32(gx32))
+    ctx = gpu_at(npg, ocfg, seq, grid, mlp, 3, 10)
+    npg.npg_backprop(ctx.h, torch.from_numpy(gx32.reshape(-1)).cuda())
+    gg = ctx.get(npg.BUF_GRID_GRAD).astype(np.float64)
+    gm = ctx.get(npg.BUF_MLP_GRAD).astype(np.float64)
+    rng = np.random.default_rng(7)
+    gb, mb = blocks_of(ocfg)
+    for name, sl in gb:
+        check_grad_block(name, gg[sl], want_g[sl], rng)
+    for name, sl in mb:
+        check_grad_block(name, gm[sl], want_m[sl], rng)
+    # step: preconditioner on every level, then Adam (well-determined entries)
+    ctx.step()
+    pc = ctx.get(npg.BUF_GRID_PC).astype(np.float64)
+    new_grid = ctx.get(npg.BUF_GRID).astype(np.float64)
+    new_mlp = ctx.get(npg.BUF_MLP).astype(np.float64)
+    for l, (name, sl) in enumerate(gb):
+        r = ocfg.res[l] if l < ocfg.L else ocfg.rn
+        F = ocfg.F if l < ocfg.L else ocfg.Fn
+        lam = 0.4 * 1.5 ** l if l < ocfg.L else 0.4
+        lr = 0.005 * 2.5 ** l if l < ocfg.L else 0.005
+        want, _ = O.precondition(r, F, lam, want_g[sl])
+        assert rel(pc[sl], want) <= GRAD_RTOL, (name, rel(pc[sl], want))
+        p_ref, _, _ = O.adam(f32(grid)[sl], want, np.zeros(len(want)), np.zeros(len(want)), lr, 4)
+        det = np.abs(want) > 1e-3 * np.abs(want).max()
+        assert np.all(np.abs(new_grid[sl][det] - p_ref[det]) <= 1e-3 * lr), name
+    p_ref, _, _ = O.adam(f32(mlp), want_m, np.zeros(len(mlp)), np.zeros(len(mlp)), 1e-3, 4)
+    det = np.abs(want_m) > 1e-3 * np.abs(want_m).max()
+    assert np.all(np.abs(new_mlp[det] - p_ref[det]) <= 1e-6)
+    assert npg.npg_get_epoch(ctx.h) == 4
+    ctx.close()
+
+
+@pytest.mark.parametrize("rot_mode", [0, 1])
+def test_gradient_parity_end_to_end_chamfer(npg, rot_mode):
+    """npg_backward's gradient of L_def alone (w_iso = 0, no |.| kink):
+    loss -> dL/dx-hat -> parameters through the full kernel chain."""
+    seq, ocfg, prob = tiny_setup(rot_mode=rot_mode, seed=1)
+    ocfg.w_iso = 0.0
+    grid, mlp = random_state(ocfg)
+    ref = O.loss_full(prob, f32(grid), f32(mlp), 3, 10, decide_f32=True)
+    ctx = gpu_at(npg, ocfg, seq, grid, mlp, 3, 10, w_iso=0.0)
+    loss, _ = ctx.loss()
+    assert abs(loss[0] - ref["loss"]) <= LOSS_RTOL * ref["loss"]
+    nnx = ctx.get(npg.BUF_NN_X).reshape(prob.T, prob.N)
+    nnp = ctx.get(npg.BUF_NN_P)
+    if np.any(nnx != ref["nn_x"]) or np.any(nnp != ref["nn_p"]):
+        pytest.skip("an FP32 nearest-neighbour tie resolved differently on these inputs")
+    ctx.backward()
+    gg = ctx.get(npg.BUF_GRID_GRAD).astype(np.float64)
+    gm = ctx.get(npg.BUF_MLP_GRAD).astype(np.float64)
+    rng = np.random.default_rng(8)
+    gb, mb = blocks_of(ocfg)
+    for name, sl in gb:
+        check_grad_block(name, gg[sl], ref["g_grid"][sl], rng)
+    for name, sl in mb:
+        check_grad_block(name, gm[sl], ref["g_mlp"][sl], rng)
+    ctx.close()
+
+
+def test_trajectory_states_parity(npg):
+    """Config of 2562 vertices, 8 frames, 4096 points, 4 levels 8..64, F=2,
+    MLP 2 x 64 ReLU: 10 oracle iterations from the identity initialisation;
+    every state along the way, loaded into the GPU context, gives the same loss."""
+    seq, ocfg, prob = tiny_setup()
+    mlp = I.mlp_init(O.k_in(ocfg), ocfg.H, ocfg.D, O.n_out(ocfg), seed=0)
+    iters = 10
+    st = O.State(prob, np.zeros(O.grid_len(ocfg)), f32(mlp))
+    lr = [0.005 * 2.5 ** l for l in range(ocfg.L)] + [0.005]
+    lam = [0.4 * 1.5 ** l for l in range(ocfg.L)] + [0.4]
+    ctx = npg.Context(gpu_cfg(npg, ocfg, e_max=iters), seq, mlp)
+    for k in range(iters):
+        g32, m32 = st.grid.astype(np.float32), st.mlp.astype(np.float32)
+        ctx.set(npg.BUF_GRID, g32)
+        ctx.set(npg.BUF_MLP, m32)
+        npg.npg_set_epoch(ctx.h, k)
+        want = O.loss_full(prob, f32(g32), f32(m32), k, iters, decide_f32=True,
+                           want_grad=False)["loss"]
+        ctx.forward()
+        loss, _ = ctx.loss()
+        assert abs(loss[0] - want) <= LOSS_RTOL * want, (k, loss[0], want)
+        O.iteration(prob, st, iters, lr, 1e-3, lam, decide_f32=True)
+    ctx.close()
+
+
+def test_free_running_trajectory(npg):
+    """10 GPU iterations from the identity initialisation stay with the
+    oracle's trajectory (Adam's sign-like first steps amplify FP32 rounding
+    of near-zero gradient entries, so the bound is loose) and lower the
+    Chamfer distance."""
+    seq, ocfg, prob = tiny_setup()
+    mlp = I.mlp_init(O.k_in(ocfg), ocfg.H, ocfg.D, O.n_out(ocfg), seed=0)
+    iters = 10
+    st = O.State(prob, np.zeros(O.grid_len(ocfg)), f32(mlp))
+    lr = [0.005 * 2.5 ** l for l in range(ocfg.L)] + [0.005]
+    lam = [0.4 * 1.5 ** l for l in range(ocfg.L)] + [0.4]
+    ctx = npg.Context(gpu_cfg(npg, ocfg, e_max=iters), seq, mlp)
+    cds = []
+    for k in range(iters):
+        r = O.iteration(prob, st, iters, lr, 1e-3, lam, decide_f32=True)
+        ctx.forward()
+        loss, cd = ctx.loss()
+        ctx.backward()
+        ctx.step()
+        cds.append(cd.mean())
+        assert abs(loss[0] - r["loss"]) <= 1e-2 * abs(r["loss"]), (k, loss[0], r["loss"])
+    assert cds[-1] < cds[0]
+    ctx.close()
+
+
+def test_call_order_and_state_roundtrip(npg):
+    seq, ocfg, prob = tiny_setup(T=4, M=800, subdiv=3)
+    mlp = I.mlp_init(O.k_in(ocfg), ocfg.H, ocfg.D, O.n_out(ocfg), seed=0)
+    ctx = npg.Context(gpu_cfg(npg, ocfg), seq, mlp)
+    with pytest.raises(npg.NpgError) as ei:
+        ctx.backward()
+    assert ei.value.code == npg.ESTATE
+    with pytest.raises(npg.NpgError):
+        ctx.step()
+    for _ in range(3):
+        ctx.iteration()
+    blob = npg.npg_get_state(ctx.h)
+    ctx.forward()
+    l1, _ = ctx.loss()
+    ctx.backward()
+    ctx.step()
+    ctx.iteration()
+    npg.npg_set_state(ctx.h, blob)
+    assert npg.npg_get_epoch(ctx.h) == 3
+    ctx.forward()
+    l2, _ = ctx.loss()
+    assert l1[0] == l2[0]  # forward and loss are deterministic
+    ctx.close()
+
+
+def test_graph_replay_matches_eager(npg):
+    import torch
+    seq, ocfg, prob = tiny_setup(T=4, M=800, subdiv=3)
+    mlp = I.mlp_init(O.k_in(ocfg), ocfg.H, ocfg.D, O.n_out(ocfg), seed=0)
+    s = torch.cuda.Stream()
+    eager = npg.Context(gpu_cfg(npg, ocfg), seq, mlp)
+    graph = npg.Context(gpu_cfg(npg, ocfg, use_graph=True, stream=s), seq, mlp)
+    for k in range(5):
+        a = eager.iteration()
+        b = graph.iteration()
+        # forward and loss are deterministic; the gradient's float atomics are
+        # not, and Adam's first steps amplify that, so later losses agree loosely
+        tol = 0.0 if k == 0 else 1e-2
+        assert abs(a[0] - b[0]) <= tol * abs(a[0]), (k, a, b)
+    assert npg.npg_get_epoch(graph.h) == 5
+    assert npg.npg_launch_count(graph.h) > 0
+    eager.close()
+    graph.close()
+
+
+def test_set_points_and_uneven_frames(npg):
+    seq = I.sphere_blob(subdiv=2, T=3, M=[300, 1, 777], seed=4)
+    ocfg = O.make_cfg(L=2, res=(5, 9), F=2, H=32, D=3, slope=0.01)
+    prob = O.Problem(ocfg, seq.x, seq.n, seq.faces, seq.points, seq.offsets, seq.t_key)
+    mlp = I.mlp_init(O.k_in(ocfg), 32, 3, 7, seed=1, zero_last=False)
+    rng = np.random.default_rng(5)
+    grid = rng.normal(scale=0.2, size=O.grid_len(ocfg)).astype(np.float32)
+    ref = O.loss_full(prob, f32(grid), f32(mlp), 0, 10, decide_f32=True)
+    ctx = npg.Context(gpu_cfg(npg, ocfg), seq, mlp)
+    ctx.set(npg.BUF_GRID, grid)
+    ctx.forward()
+    loss, cd = ctx.loss()
+    assert abs(loss[0] - ref["loss"]) <= LOSS_RTOL * ref["loss"]
+    # new clouds with other per-frame counts (total not larger)
+    seq2 = I.sphere_blob(subdiv=2, T=3, M=[500, 400, 100], seed=9)
+    prob2 = O.Problem(ocfg, seq.x, seq.n, seq.faces, seq2.points, seq2.offsets, seq.t_key)
+    npg.npg_set_points(ctx.h, seq2.points, seq2.offsets)
+    ref2 = O.loss_full(prob2, f32(grid), f32(mlp), 0, 10, decide_f32=True)
+    ctx.forward()
+    loss2, _ = ctx.loss()
+    assert abs(loss2[0] - ref2["loss"]) <= LOSS_RTOL * ref2["loss"]
+    ctx.close()
