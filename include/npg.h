@@ -278,6 +278,7 @@ NPG_API int npg_nearest(const float* q, int nq, const float* c, int nc, int32_t*
  */
 NPG_API int npg_precondition(const float* g, float* out, int r, int F, float lambda, void* stream);
 
+
 #ifdef __cplusplus
 }
 #endif

@@ -220,8 +220,10 @@ cudaError_t launch_nn(const float4* queries_sorted, long long q_uniform, const l
 }
 
 // ----------------------------------------------------------------- loss
-// One block per frame, fixed reduction order (deterministic): FP64 sums of
-// the FP32 squared distances and of |len_e(t) - lref_e|.
+// One block per frame, fixed reduction order (deterministic). The squared
+// distances are re-formed from the displacement, |(x_i - p_j) + delta_i|^2,
+// and the isometry terms from iso_diff, so both keep their relative precision
+// when the motion is small; sums in FP64.
 __device__ double block_sum(double v, double* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -235,20 +237,39 @@ __device__ double block_sum(double v, double* sh) {
   return r;
 }
 
+__device__ __forceinline__ float resid_sq(float4 x, float4 d, float4 p) {
+  const float rx = (x.x - p.x) + d.x, ry = (x.y - p.y) + d.y, rz = (x.z - p.z) + d.z;
+  return rx * rx + ry * ry + rz * rz;
+}
+
 __global__ void __launch_bounds__(256) loss_frame_kernel(
-    const float* __restrict__ d_x, const float* __restrict__ d_p, const long long* __restrict__ off,
-    const float4* __restrict__ xhat, const int2* __restrict__ edges, const float* __restrict__ lref,
-    int N, int E, double* __restrict__ cd, double* __restrict__ iso_t) {
+    const int* __restrict__ nn_x, const int* __restrict__ nn_p, const long long* __restrict__ off,
+    const float4* __restrict__ praw, const float4* __restrict__ xr,
+    const float4* __restrict__ disp, const int2* __restrict__ edges, int N, int E, int t_key,
+    double* __restrict__ cd, double* __restrict__ iso_t) {
   __shared__ double sh[32];
   const int t = blockIdx.x;
-  double sx = 0.0, sp = 0.0, si = 0.0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) sx += (double)d_x[(long long)t * N + i];
   const long long b = off[t], e = off[t + 1];
-  for (long long j = b + threadIdx.x; j < e; j += blockDim.x) sp += (double)d_p[j];
-  const float4* X = xhat + (long long)t * N;
-  for (int k = threadIdx.x; k < E; k += blockDim.x) {
-    const float len = edge_len(X[edges[k].x], X[edges[k].y]);
-    si += fabs((double)len - (double)lref[k]);
+  const float4* Dl = disp + (long long)t * N;
+  const float4* Dk = disp + (long long)t_key * N;
+  double sx = 0.0, sp = 0.0, si = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x)
+    sx += (double)resid_sq(xr[i], Dl[i], praw[b + nn_x[(long long)t * N + i]]);
+  for (long long j = b + threadIdx.x; j < e; j += blockDim.x) {
+    const int i = nn_p[j];
+    sp += (double)resid_sq(xr[i], Dl[i], praw[j]);
+  }
+  if (t != t_key) {
+    for (int k = threadIdx.x; k < E; k += blockDim.x) {
+      const int a0 = edges[k].x, b0 = edges[k].y;
+      const float4 xa = xr[a0], xb = xr[b0], da = Dl[a0], db = Dl[b0], ka = Dk[a0], kb = Dk[b0];
+      float3 et;
+      float lt;
+      const float df = iso_diff(make_float3(xa.x - xb.x, xa.y - xb.y, xa.z - xb.z),
+                                make_float3(da.x - db.x, da.y - db.y, da.z - db.z),
+                                make_float3(ka.x - kb.x, ka.y - kb.y, ka.z - kb.z), et, lt);
+      si += fabs((double)df);
+    }
   }
   sx = block_sum(sx, sh);
   sp = block_sum(sp, sh);
@@ -291,8 +312,9 @@ __global__ void loss_final_kernel(const double* __restrict__ cd, const double* _
 }
 
 cudaError_t launch_loss(npg_ctx* c) {
-  loss_frame_kernel<<<c->T, 256, 0, c->stream>>>(c->d_x, c->d_p, c->p_off, c->xhat, c->edges,
-                                                 c->lref, c->N, c->E, c->cd, c->iso_t);
+  loss_frame_kernel<<<c->T, 256, 0, c->stream>>>(c->nn_x, c->nn_p, c->p_off, c->praw, c->xr,
+                                                 c->disp, c->edges, c->N, c->E, c->t_key, c->cd,
+                                                 c->iso_t);
   loss_final_kernel<<<1, 32, 0, c->stream>>>(c->cd, c->iso_t, c->d_epoch, c->cfg.e_max,
                                              c->T, c->t_key, c->E, (double)c->cfg.w_iso, c->wconf,
                                              c->loss);
@@ -302,33 +324,44 @@ cudaError_t launch_loss(npg_ctx* c) {
 // ----------------------------------------------------------------- dL/dx-hat
 
 // Vertex side of the Chamfer term plus the isometry term (vertex-centric over
-// the edge adjacency, no atomics); writes dxhat.
+// the edge adjacency, no atomics); writes dxhat. The sign of |e_t| - |e_key|
+// is 0 at the keyframe (stop-grad reference, d|u|/du at 0 taken as 0).
 __global__ void __launch_bounds__(256) dxhat_vertex_kernel(
-    const float4* __restrict__ xhat, const int* __restrict__ nn_x, const long long* __restrict__ off,
-    const float4* __restrict__ praw, const double* __restrict__ w, const int* __restrict__ adj_off,
-    const int* __restrict__ adj, const int* __restrict__ adj_edge, const float* __restrict__ lref,
-    int N, int T, int E, double w_iso, float4* __restrict__ dxhat) {
+    const float4* __restrict__ xr, const float4* __restrict__ disp, const int* __restrict__ nn_x,
+    const long long* __restrict__ off, const float4* __restrict__ praw,
+    const double* __restrict__ w, const int* __restrict__ adj_off, const int* __restrict__ adj,
+    int N, int T, int E, int t_key, double w_iso, float4* __restrict__ dxhat) {
   const long long total = (long long)N * T;
   for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < total;
        row += (long long)gridDim.x * blockDim.x) {
     const int t = (int)(row / N), i = (int)(row - (long long)t * N);
-    const float4 x = xhat[row];
+    const float4 xi = xr[i], di = disp[row];
     const float4 p = praw[off[t] + nn_x[row]];
     const float cx = (float)(w[t] / (double)T * 2.0 / (double)N);
-    float gx = cx * (x.x - p.x), gy = cx * (x.y - p.y), gz = cx * (x.z - p.z);
-    if (E > 0) {
+    float gx = cx * ((xi.x - p.x) + di.x), gy = cx * ((xi.y - p.y) + di.y),
+          gz = cx * ((xi.z - p.z) + di.z);
+    if (E > 0 && t != t_key) {
       const float ci = (float)(w_iso / ((double)T * (double)E));
-      const float4* X = xhat + (long long)t * N;
+      const float4* Dl = disp + (long long)t * N;
+      const float4* Dk = disp + (long long)t_key * N;
+      const float4 ki = Dk[i];
       for (int a = adj_off[i]; a < adj_off[i + 1]; ++a) {
         const int j = adj[a];
-        const float4 xj = X[j];
-        const float len = i < j ? edge_len(x, xj) : edge_len(xj, x);
-        const float lr = lref[adj_edge[a]];
-        if (len > 0.f && len != lr) {
-          const float sc = (len > lr ? ci : -ci) / len;
-          gx = fmaf(sc, x.x - xj.x, gx);
-          gy = fmaf(sc, x.y - xj.y, gy);
-          gz = fmaf(sc, x.z - xj.z, gz);
+        const float4 xj = xr[j], dj = Dl[j], kj = Dk[j];
+        // orient as (lower id) - (higher id), the orientation of the edge list
+        const float sg = i < j ? 1.f : -1.f;
+        float3 et;
+        float lt;
+        const float df = iso_diff(
+            make_float3(sg * (xi.x - xj.x), sg * (xi.y - xj.y), sg * (xi.z - xj.z)),
+            make_float3(sg * (di.x - dj.x), sg * (di.y - dj.y), sg * (di.z - dj.z)),
+            make_float3(sg * (ki.x - kj.x), sg * (ki.y - kj.y), sg * (ki.z - kj.z)), et, lt);
+        if (lt > 0.f && df != 0.f) {
+          // d|e_t|/dx_i = sg * e_t / |e_t|
+          const float sc = (df > 0.f ? ci : -ci) * sg / lt;
+          gx = fmaf(sc, et.x, gx);
+          gy = fmaf(sc, et.y, gy);
+          gz = fmaf(sc, et.z, gz);
         }
       }
     }
@@ -339,8 +372,8 @@ __global__ void __launch_bounds__(256) dxhat_vertex_kernel(
 // Point side of the Chamfer term: every point adds to its nearest vertex.
 __global__ void __launch_bounds__(256) dxhat_point_kernel(
     const float4* __restrict__ praw, const long long* __restrict__ off, int T, long long MT,
-    const int* __restrict__ nn_p, const float4* __restrict__ xhat, const double* __restrict__ w,
-    int N, float4* __restrict__ dxhat) {
+    const int* __restrict__ nn_p, const float4* __restrict__ xr, const float4* __restrict__ disp,
+    const double* __restrict__ w, int N, float4* __restrict__ dxhat) {
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < MT;
        k += (long long)gridDim.x * blockDim.x) {
     const int t = set_of(k, 0, off, T);
@@ -349,22 +382,21 @@ __global__ void __launch_bounds__(256) dxhat_point_kernel(
     const int i = nn_p[k];
     const float4 p = praw[k];
     const long long row = (long long)t * N + i;
-    const float4 x = xhat[row];
+    const float4 x = xr[i], d = disp[row];
     float* g = reinterpret_cast<float*>(dxhat + row);
-    atomicAdd(g + 0, cp * (x.x - p.x));
-    atomicAdd(g + 1, cp * (x.y - p.y));
-    atomicAdd(g + 2, cp * (x.z - p.z));
+    atomicAdd(g + 0, cp * ((x.x - p.x) + d.x));
+    atomicAdd(g + 1, cp * ((x.y - p.y) + d.y));
+    atomicAdd(g + 2, cp * ((x.z - p.z) + d.z));
   }
 }
 
 cudaError_t launch_dxhat(npg_ctx* c) {
-  const float4* praw = c->praw;
   const long long rows = (long long)c->N * c->T;
   dxhat_vertex_kernel<<<grid_blocks(rows, 256), 256, 0, c->stream>>>(
-      c->xhat, c->nn_x, c->p_off, praw, c->wconf, c->adj_off,
-      c->adj, c->adj_edge, c->lref, c->N, c->T, c->E, (double)c->cfg.w_iso, c->dxhat);
+      c->xr, c->disp, c->nn_x, c->p_off, c->praw, c->wconf, c->adj_off, c->adj, c->N, c->T,
+      c->E, c->t_key, (double)c->cfg.w_iso, c->dxhat);
   dxhat_point_kernel<<<grid_blocks(c->MT, 256), 256, 0, c->stream>>>(
-      praw, c->p_off, c->T, c->MT, c->nn_p, c->xhat, c->wconf, c->N, c->dxhat);
+      c->praw, c->p_off, c->T, c->MT, c->nn_p, c->xr, c->disp, c->wconf, c->N, c->dxhat);
   return cudaGetLastError();
 }
 

@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(128) decode_fp32_kernel(const float* __restric
                                                           const float* __restrict__ U,
                                                           const float* __restrict__ V,
                                                           const float4* __restrict__ xr,
-                                                          float4* __restrict__ xhat, int N, int T,
+                                                          float4* __restrict__ xhat,
+                                                          float4* __restrict__ disp, int N, int T,
                                                           int K, int D, int NO, float slope,
                                                           float alpha) {
   extern __shared__ float4 smem4[];
@@ -215,7 +216,10 @@ __global__ void __launch_bounds__(128) decode_fp32_kernel(const float* __restric
         o[j] = 0.f;
       }
     }
-    xhat[row] = transform<ROT>(o, alpha, xr[i]);
+    float4 xh, dl;
+    transform<ROT>(o, alpha, xr[i], xh, dl);
+    xhat[row] = xh;
+    disp[row] = dl;
   }
 }
 
@@ -234,7 +238,7 @@ static cudaError_t decode_fp32_h(npg_ctx* c) {
   long long blocks = (rows + 127) / 128;
   const long long cap = (long long)c->num_sms * 8;
   if (blocks > cap) blocks = cap;
-  k<<<(int)blocks, 128, smem, c->stream>>>(c->mlp, c->U, c->V, c->xr, c->xhat, c->N, c->T,
+  k<<<(int)blocks, 128, smem, c->stream>>>(c->mlp, c->U, c->V, c->xr, c->xhat, c->disp, c->N, c->T,
                                            c->md.K, D, NO, c->md.slope, c->cfg.alpha);
   return cudaGetLastError();
 }
@@ -249,20 +253,6 @@ cudaError_t launch_decode_fp32(npg_ctx* c) {
 }
 
 // ----------------------------------------------------------------- helpers
-
-// Keyframe edge lengths (stop-grad reference of Eq. 13).
-__global__ void edge_lengths_kernel(const float4* __restrict__ xhat_key, const int2* __restrict__ e,
-                                    float* __restrict__ len, int E) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < E) len[k] = edge_len(xhat_key[e[k].x], xhat_key[e[k].y]);
-}
-
-cudaError_t launch_edge_lengths(npg_ctx* c) {
-  if (c->E == 0) return cudaSuccess;
-  edge_lengths_kernel<<<(c->E + 255) / 256, 256, 0, c->stream>>>(
-      c->xhat + (long long)c->t_key * c->N, c->edges, c->lref, c->E);
-  return cudaGetLastError();
-}
 
 __global__ void points_to_float4_kernel(const float* __restrict__ s, float4* __restrict__ d,
                                         long long n) {

