@@ -278,6 +278,29 @@ NPG_API int npg_nearest(const float* q, int nq, const float* c, int nc, int32_t*
  */
 NPG_API int npg_precondition(const float* g, float* out, int r, int F, float lambda, void* stream);
 
+/*
+ * Allocation-free variant of npg_precondition (the paper has no counterpart:
+ * this is a deployment convenience). Some callers cannot allocate device
+ * memory where they need the preconditioner: a process whose GPU memory is
+ * already owned by another allocator (a framework's caching pool that has
+ * reserved the device), a loop with a fixed memory budget, or code that must
+ * not risk the implicit device synchronisation of cudaMalloc / cudaFree. This
+ * entry point takes the same arguments and gives the same result as
+ * npg_precondition, but allocates and frees nothing: its scratch is one
+ * file-scope device array of about 10.5 MB that every GPU which loads
+ * libnpg.so holds until the process exits.
+ *   - Limit: r <= 512 and r^3 * F <= 1,048,576 (e.g. r = 64 with F = 4);
+ *     larger blocks return NPG_EINVAL (use npg_precondition).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - The work is queued on stream and not waited for.
+ *   - Every call shares the one array. Calls whose work overlaps on the GPU
+ *     (different streams or host threads without ordering) race and corrupt
+ *     each other's results: order them, e.g. on one stream.
+ */
+NPG_API int npg_precondition_static(const float* g, float* out, int r, int F, float lambda,
+                                    void* stream);
 
 #ifdef __cplusplus
 }

@@ -28,6 +28,16 @@ static int set_err(npg_ctx* c, int code, const char* fmt, ...) {
   return code;
 }
 
+int npg::set_error_message(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_thread_err = buf;
+  return code;
+}
+
 static bool is_sticky(cudaError_t e) {
   switch (e) {
     case cudaErrorIllegalAddress:

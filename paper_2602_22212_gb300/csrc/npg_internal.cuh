@@ -161,6 +161,8 @@ cudaError_t launch_points_to_float4(const float* src, float4* dst, long long n, 
 cudaError_t launch_xhat_out(const float4* xhat, float* out, long long n, cudaStream_t s);
 
 int auto_cells(long long points_per_set, int nsets);
+// records a message for npg_last_error(NULL) and returns code
+int set_error_message(int code, const char* fmt, ...);
 bool decode_fp32_supported(int H, int D);
 bool decode_bf16_supported(int H, int D);
 size_t mlp_bwd_fp32_smem(const MlpDims& md);

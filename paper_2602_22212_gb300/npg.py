@@ -94,6 +94,7 @@ _SIG = {
     "npg_last_error": (C.c_char_p, [_vp]),
     "npg_nearest": (_i, [_vp, _i, _vp, _i, _vp, _vp, _i, _vp]),
     "npg_precondition": (_i, [_vp, _vp, _i, _i, C.c_float, _vp]),
+    "npg_precondition_static": (_i, [_vp, _vp, _i, _i, C.c_float, _vp]),
     "npg_timing": (_i, [_vp, _i]),
     "npg_timing_read": (_i, [_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "npg_launch_count": (C.c_longlong, [_vp]),
@@ -271,6 +272,12 @@ def npg_nearest(q, cand, idx, dist=None, cells=0, stream=None):
 def npg_precondition(g, out, r, F, lam, stream=None):
     _check(_lib.npg_precondition(_ptr(g), _ptr(out), int(r), int(F), float(lam),
                                  _stream_handle(stream)))
+
+
+def npg_precondition_static(g, out, r, F, lam, stream=None):
+    """Allocation-free npg_precondition (fixed-size scratch; see include/npg.h)."""
+    _check(_lib.npg_precondition_static(_ptr(g), _ptr(out), int(r), int(F), float(lam),
+                                        _stream_handle(stream)))
 
 
 # ----------------------------------------------------------------- convenience
