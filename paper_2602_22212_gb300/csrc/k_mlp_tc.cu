@@ -1,10 +1,600 @@
-// BF16 tensor-core (tcgen05) MLP decode and backward.
+// BF16 tensor-core (tcgen05) MLP decode and backward (Sec. 3.3-3.4) for
+// hidden width 64 and 3 hidden layers: operands in 128B-swizzled shared
+// memory, FP32 accumulators in TMEM, FP32 epilogues (bias, LeakyReLU, the
+// rotation/translation mapping and its Jacobian) on the CUDA cores.
+//
+// A CTA of 128 threads owns tiles of 128 consecutive rows (row = t N + i);
+// thread t owns row t of the tile and TMEM lane t. One elected thread issues
+// the MMAs; completion is tracked by an mbarrier whose waits are bounded: a
+// wait that gives up sets *err and the CTA frees its TMEM and exits.
+#include <cuda_bf16.h>
+
+#include "npg_device.cuh"
 #include "npg_internal.cuh"
+#include "tc_sm100.cuh"
 
 namespace npg {
 
-bool decode_bf16_supported(int H, int D) { return false; }
-cudaError_t launch_decode_bf16(npg_ctx* c) { return cudaErrorNotSupported; }
-cudaError_t launch_mlp_backward_bf16(npg_ctx* c) { return cudaErrorNotSupported; }
+constexpr int TC_H = 64;
+constexpr int TC_ROWS = 128;
+constexpr uint32_t TC_TILE = TC_ROWS * 128;  // bytes of one [128][64] BF16 swizzled tile
+constexpr uint32_t WAIT_TRIES = 1u << 24;
+
+bool decode_bf16_supported(int H, int D) { return H == TC_H && D == 3; }
+
+// Write 64 FP32 values of one row as BF16 into a K-major swizzled tile.
+__device__ __forceinline__ void st_row64(uint8_t* tile, int row, const float* v) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    uint4 q;
+    q.x = tc::pack_bf16(v[8 * c + 0], v[8 * c + 1]);
+    q.y = tc::pack_bf16(v[8 * c + 2], v[8 * c + 3]);
+    q.z = tc::pack_bf16(v[8 * c + 4], v[8 * c + 5]);
+    q.w = tc::pack_bf16(v[8 * c + 6], v[8 * c + 7]);
+    *reinterpret_cast<uint4*>(tile + tc::sw128_off(row, 8 * c)) = q;
+  }
+}
+
+__device__ __forceinline__ void st_bf16(uint8_t* tile, int row, int col, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(tile + tc::sw128_off(row, col)) = __float2bfloat16_rn(v);
+}
+
+// 64 FP32 accumulator columns of this thread's lane, starting at column c0.
+__device__ __forceinline__ void ld_row64(uint32_t tmem_lane, uint32_t c0, float* v) {
+  uint32_t r[16];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    tc::tmem_ld16(tmem_lane + c0 + 16 * q, r);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[16 * q + j] = __uint_as_float(r[j]);
+  }
+}
+
+// Issue D = A * B^T with K = 64 (4 steps of 16), K-major operands.
+__device__ __forceinline__ void mma_k64(uint32_t d, uint32_t a_smem, uint32_t b_smem,
+                                        uint32_t idesc) {
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks)
+    tc::mma_bf16(d, tc::kmajor_sw128(a_smem + 32 * ks), tc::kmajor_sw128(b_smem + 32 * ks),
+                 idesc, ks > 0);
+}
+
+struct TcArgs {
+  const float* mlp;
+  const float* U;
+  const float* V;
+  const float4* xr;
+  float4* xhat;
+  float4* disp;
+  const float4* dxhat;
+  const float* z;
+  float* g_mlp;
+  float* dz;
+  int* err;
+  int N, T, K, Z, M, NO;
+  float slope, alpha;
+};
+
+// Shared layout of the decode kernel (offsets from a 1024-byte aligned base).
+struct DecodeSmem {
+  static constexpr uint32_t W2 = 0;                 // [64][64] K-major (B operand)
+  static constexpr uint32_t W3 = W2 + TC_TILE / 2;  // 8 KB each
+  static constexpr uint32_t WO = W3 + TC_TILE / 2;  // [16][64] (rows >= NO zero)
+  static constexpr uint32_t ACT = WO + 2048;        // [128][64] activations (A operand)
+  static constexpr uint32_t BIAS = ACT + TC_TILE;   // b2, b3 (64 each), bo (16) FP32
+  static constexpr uint32_t BAR = BIAS + (64 + 64 + 16) * 4;
+  static constexpr uint32_t TMEMP = BAR + 8;
+  static constexpr uint32_t TOTAL = TMEMP + 8;
+};
+
+// Convert a row-major FP32 [rows][64] weight block into a K-major BF16 tile.
+__device__ void load_weight_tile(uint8_t* tile, const float* W, int rows, int valid_rows) {
+  for (int e = threadIdx.x; e < rows * 64; e += blockDim.x) {
+    const int r = e >> 6, k = e & 63;
+    st_bf16(tile, r, k, r < valid_rows ? W[r * 64 + k] : 0.f);
+  }
+}
+
+template <int ROT>
+__global__ void __launch_bounds__(128) decode_tc_kernel(TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + DecodeSmem::BAR);
+  uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + DecodeSmem::TMEMP);
+  float* bias = reinterpret_cast<float*>(sm + DecodeSmem::BIAS);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int H = TC_H, K = a.K, NO = a.NO;
+
+  // weights: W1 (H x K) + b1 | W2 + b2 | W3 + b3 | Wo (NO x H) + bo
+  const float* p2 = a.mlp + H * K + H;
+  const float* p3 = p2 + H * H + H;
+  const float* po = p3 + H * H + H;
+  load_weight_tile(sm + DecodeSmem::W2, p2, 64, 64);
+  load_weight_tile(sm + DecodeSmem::W3, p3, 64, 64);
+  load_weight_tile(sm + DecodeSmem::WO, po, 16, NO);
+  for (int k = tid; k < 64; k += 128) {
+    bias[k] = p2[H * H + k];
+    bias[64 + k] = p3[H * H + k];
+  }
+  if (tid < 16) bias[128 + tid] = tid < NO ? po[NO * H + tid] : 0.f;
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_ptr, 64);
+    tc::tmem_relinquish();
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_ptr;
+  const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t s_act = tc::smem_u32(sm + DecodeSmem::ACT);
+  const uint32_t s_w2 = tc::smem_u32(sm + DecodeSmem::W2);
+  const uint32_t s_w3 = tc::smem_u32(sm + DecodeSmem::W3);
+  const uint32_t s_wo = tc::smem_u32(sm + DecodeSmem::WO);
+  constexpr uint32_t ID64 = tc::idesc_bf16(128, 64, false, false);
+  constexpr uint32_t ID16 = tc::idesc_bf16(128, 16, false, false);
+  uint32_t phase = 0;
+  bool ok = true;
+  const long long rows = (long long)a.N * a.T;
+  const long long ntiles = (rows + TC_ROWS - 1) / TC_ROWS;
+  uint8_t* act = sm + DecodeSmem::ACT;
+
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const long long row = tile * TC_ROWS + tid;
+    const bool valid = row < rows;
+    const int t = valid ? (int)(row / a.N) : 0;
+    const int i = valid ? (int)(row - (long long)t * a.N) : 0;
+    float v[64];
+    if (valid) {
+      const float4* u4 = reinterpret_cast<const float4*>(a.U + (long long)i * H);
+      const float4* v4 = reinterpret_cast<const float4*>(a.V + (long long)t * H);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float4 u = u4[k], w = v4[k];
+        v[4 * k + 0] = leaky(u.x + w.x, a.slope);
+        v[4 * k + 1] = leaky(u.y + w.y, a.slope);
+        v[4 * k + 2] = leaky(u.z + w.z, a.slope);
+        v[4 * k + 3] = leaky(u.w + w.w, a.slope);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 64; ++k) v[k] = 0.f;
+    }
+    st_row64(act, tid, v);
+    // two hidden layers, then the output layer
+#pragma unroll 1
+    for (int layer = 0; layer < 3; ++layer) {
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (tid == 0) {
+        if (layer < 2)
+          mma_k64(tmem, s_act, layer == 0 ? s_w2 : s_w3, ID64);
+        else
+          mma_k64(tmem, s_act, s_wo, ID16);
+        tc::mma_commit(bar);
+      }
+      {
+        bool w = tc::mbar_wait(bar, phase, WAIT_TRIES);
+        phase ^= 1u;
+        w = __syncthreads_and(w) != 0;
+        if (!w) {
+          if (tid == 0) atomicExch(a.err, 1);
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+      }
+      if (layer < 2) {
+        ld_row64(lane, 0, v);
+        const float* b = bias + 64 * layer;
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = leaky(v[k] + b[k], a.slope);
+        tc::fence_before_sync();
+        __syncthreads();  // every lane has read TMEM before the next MMA overwrites it
+        st_row64(act, tid, v);
+      } else {
+        uint32_t r[16];
+        tc::tmem_ld16(lane, r);
+        tc::tmem_ld_wait();
+        float o[7];
+#pragma unroll
+        for (int j = 0; j < 7; ++j) o[j] = __uint_as_float(r[j]) + bias[128 + j];
+        if (valid) {
+          float4 xh, dl;
+          transform<ROT>(o, a.alpha, a.xr[i], xh, dl);
+          a.xhat[row] = xh;
+          a.disp[row] = dl;
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
+static int tc_blocks(npg_ctx* c, long long tiles, int per_sm) {
+  long long b = (long long)c->num_sms * per_sm;
+  if (b > tiles) b = tiles;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+static TcArgs tc_args(npg_ctx* c) {
+  TcArgs a;
+  a.mlp = c->mlp;
+  a.U = c->U;
+  a.V = c->V;
+  a.xr = c->xr;
+  a.xhat = c->xhat;
+  a.disp = c->disp;
+  a.dxhat = c->dxhat;
+  a.z = c->z;
+  a.g_mlp = c->g_mlp;
+  a.dz = c->dz;
+  a.err = c->d_err;
+  a.N = c->N;
+  a.T = c->T;
+  a.K = c->md.K;
+  a.Z = c->md.Z;
+  a.M = c->md.M;
+  a.NO = c->md.NO;
+  a.slope = c->md.slope;
+  a.alpha = c->cfg.alpha;
+  return a;
+}
+
+cudaError_t launch_decode_bf16(npg_ctx* c) {
+  const size_t smem = DecodeSmem::TOTAL + 1024;
+  auto k = c->cfg.rot_mode == NPG_ROT_QUAT ? decode_tc_kernel<0> : decode_tc_kernel<1>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long tiles = ((long long)c->N * c->T + TC_ROWS - 1) / TC_ROWS;
+  k<<<tc_blocks(c, tiles, 6), 128, smem, c->stream>>>(tc_args(c));
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- backward
+// Tile = 16 vertices x 8 frames (row r = tl 16 + il). Per tile:
+//   forward recompute  h1 = act(U + V), h2, h3 (layer MMAs), o (output MMA)
+//   dL/do              Eq. 5-7 Jacobians in FP32 -> gO tile
+//   dh3 = gO Wo, dpre3 = dh3 act'(h3); dh2 = dpre3 W3, dpre2; dh1 = dpre2 W2, dpre1
+//   weight gradients, accumulated in TMEM over all tiles of the CTA:
+//     ACC_W += [dpre3 | dpre2]^T [h2 | h1 | y]   (M 128, N 144, K = 128 rows)
+//     ACC_X += [gO | dpre1]^T [y | h3]           (M 128, N 128)
+//   where y = (z_i, gamma_t, 0.., 1 at column 15): the diagonal blocks are
+//   dW3, dW2 and dW_out, dW1, the column of ones gives the bias gradients.
+//   dL/dz_i = W1[:, :Z]^T dpre1, summed over the tile's frames in shared memory.
+struct BwdSmem {
+  // B operands of the forward and dh MMAs (K-major)
+  static constexpr uint32_t W2 = 0, W3 = 8192, WO = 16384, W2T = 18432, W3T = 26624,
+                            WOT = 34816;  // [64][64]: (m, q) = Wo[q][m]
+  // [h2 | h1 | y | h3] then [gO | dpre3 | dpre2], 16 KB tiles
+  static constexpr uint32_t H2 = 43008, H1 = H2 + TC_TILE, Y = H1 + TC_TILE, H3 = Y + TC_TILE;
+  static constexpr uint32_t GO = H3 + TC_TILE, DP3 = GO + TC_TILE, DP2 = DP3 + TC_TILE;
+  static constexpr uint32_t W1F = DP2 + TC_TILE;            // FP32 W1 (64 x K <= 64 x 15)
+  static constexpr uint32_t BIAS = W1F + 64 * 16 * 4;       // b2, b3, bo FP32
+  static constexpr uint32_t DZ = BIAS + (64 + 64 + 16) * 4;  // FP32 [128][8]
+  static constexpr uint32_t DBO = DZ + 128 * 8 * 4;          // FP32 [8] output-bias gradient
+  static constexpr uint32_t BAR = DBO + 8 * 4;
+  static constexpr uint32_t TMEMP = BAR + 8;
+  static constexpr uint32_t TOTAL = TMEMP + 8;
+};
+constexpr uint32_t ACC_W_COL = 0, ACC_X_COL = 256, WORK_COL = 384;
+
+bool backward_bf16_supported(int K, int Z) { return K <= 15 && Z <= 8; }
+
+__device__ __forceinline__ bool tc_wait_all(uint64_t* bar, uint32_t& phase, int* err) {
+  bool w = tc::mbar_wait(bar, phase, WAIT_TRIES);
+  phase ^= 1u;
+  w = __syncthreads_and(w) != 0;
+  if (!w && threadIdx.x == 0) atomicExch(err, 1);
+  tc::fence_after_sync();
+  return w;
+}
+
+__device__ __forceinline__ void tc_sync_for_mma() {
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+}
+
+// D (128 x N) += A^T B with A, B MN-major [128 rows][64] tiles placed 16 KB
+// apart along M / N; K = the 128 rows of the tile (8 steps of 16).
+__device__ __forceinline__ void mma_rows(uint32_t d, uint32_t a_smem, uint32_t b_smem,
+                                         uint32_t idesc, bool first) {
+#pragma unroll
+  for (int ks = 0; ks < 8; ++ks)
+    tc::mma_bf16(d, tc::mnmajor_sw128(a_smem + 2048 * ks, TC_TILE, 1024),
+                 tc::mnmajor_sw128(b_smem + 2048 * ks, TC_TILE, 1024), idesc,
+                 (first && ks == 0) ? 0u : 1u);
+}
+
+template <int ROT>
+__global__ void __launch_bounds__(128, 1) mlp_bwd_tc_kernel(TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + BwdSmem::BAR);
+  uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + BwdSmem::TMEMP);
+  float* bias = reinterpret_cast<float*>(sm + BwdSmem::BIAS);
+  float* w1f = reinterpret_cast<float*>(sm + BwdSmem::W1F);
+  float* dzs = reinterpret_cast<float*>(sm + BwdSmem::DZ);
+  float* dbo = reinterpret_cast<float*>(sm + BwdSmem::DBO);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int H = TC_H, K = a.K, Z = a.Z, M = a.M, NO = a.NO;
+  if (tid < 8) dbo[tid] = 0.f;
+
+  const float* p2 = a.mlp + H * K + H;
+  const float* p3 = p2 + H * H + H;
+  const float* po = p3 + H * H + H;
+  load_weight_tile(sm + BwdSmem::W2, p2, 64, 64);
+  load_weight_tile(sm + BwdSmem::W3, p3, 64, 64);
+  load_weight_tile(sm + BwdSmem::WO, po, 16, NO);
+  for (int e = tid; e < 64 * 64; e += 128) {
+    const int m = e >> 6, j = e & 63;
+    st_bf16(sm + BwdSmem::W2T, m, j, p2[j * H + m]);
+    st_bf16(sm + BwdSmem::W3T, m, j, p3[j * H + m]);
+    st_bf16(sm + BwdSmem::WOT, m, j, j < NO ? po[j * H + m] : 0.f);
+    // gO columns >= NO stay zero for the whole kernel
+    st_bf16(sm + BwdSmem::GO, m, j, 0.f);
+    st_bf16(sm + BwdSmem::GO, m + 64, j, 0.f);
+  }
+  for (int e = tid; e < 64 * K; e += 128) w1f[e] = a.mlp[e];
+  for (int k = tid; k < 64; k += 128) {
+    bias[k] = p2[H * H + k];
+    bias[64 + k] = p3[H * H + k];
+  }
+  if (tid < 16) bias[128 + tid] = tid < NO ? po[NO * H + tid] : 0.f;
+  if (tid == 0) {
+    tc::mbar_init(bar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_ptr, 512);
+    tc::tmem_relinquish();
+  }
+  tc_sync_for_mma();
+  const uint32_t tmem = *tmem_ptr;
+  const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
+  auto sa = [&](uint32_t off) { return tc::smem_u32(sm + off); };
+  constexpr uint32_t ID64 = tc::idesc_bf16(128, 64, false, false);
+  constexpr uint32_t ID16 = tc::idesc_bf16(128, 16, false, false);
+  constexpr uint32_t IDW = tc::idesc_bf16(128, 144, true, true);
+  constexpr uint32_t IDX = tc::idesc_bf16(128, 128, true, true);
+  uint32_t phase = 0;
+  bool ok = true, first = true;
+  const int il = tid & 15, tl = tid >> 4;
+  const int n_ib = (a.N + 15) / 16, n_tb = (a.T + 7) / 8;
+  const long long ntiles = (long long)n_ib * n_tb;
+
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int i0 = (int)(tile / n_tb) * 16, t0 = (int)(tile % n_tb) * 8;
+    const int i = i0 + il, t = t0 + tl;
+    const bool valid = i < a.N && t < a.T;
+    // y = (z_i, gamma_t, 0, ..., 1 at column 15, 0...)
+    {
+      const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        *reinterpret_cast<uint4*>(sm + BwdSmem::Y + tc::sw128_off(tid, 8 * c)) = zero;
+      st_bf16(sm + BwdSmem::Y, tid, 15, 1.f);
+      float g[2 * NPG_MAX_FREQ];
+      time_embedding(valid ? t : 0, a.T, M, g);
+      for (int k = 0; k < Z; ++k)
+        st_bf16(sm + BwdSmem::Y, tid, k, valid ? a.z[(long long)i * Z + k] : 0.f);
+      for (int k = 0; k < 2 * M; ++k) st_bf16(sm + BwdSmem::Y, tid, Z + k, g[k]);
+    }
+    float v[64];
+    uint32_t m1[2], m2[2], m3[2];  // act' masks (h > 0)
+    if (valid) {
+      const float4* u4 = reinterpret_cast<const float4*>(a.U + (long long)i * H);
+      const float4* v4 = reinterpret_cast<const float4*>(a.V + (long long)t * H);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float4 u = u4[k], w = v4[k];
+        v[4 * k + 0] = leaky(u.x + w.x, a.slope);
+        v[4 * k + 1] = leaky(u.y + w.y, a.slope);
+        v[4 * k + 2] = leaky(u.z + w.z, a.slope);
+        v[4 * k + 3] = leaky(u.w + w.w, a.slope);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 64; ++k) v[k] = 0.f;
+    }
+    m1[0] = m1[1] = 0u;
+#pragma unroll
+    for (int k = 0; k < 64; ++k) m1[k >> 5] |= (v[k] > 0.f ? 1u : 0u) << (k & 31);
+    st_row64(sm + BwdSmem::H1, tid, v);
+    // ---- forward: layer 2, layer 3, output
+    tc_sync_for_mma();
+    if (tid == 0) {
+      mma_k64(tmem + WORK_COL, sa(BwdSmem::H1), sa(BwdSmem::W2), ID64);
+      tc::mma_commit(bar);
+    }
+    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
+    ld_row64(lane, WORK_COL, v);
+#pragma unroll
+    for (int k = 0; k < 64; ++k) v[k] = leaky(v[k] + bias[k], a.slope);
+    m2[0] = m2[1] = 0u;
+#pragma unroll
+    for (int k = 0; k < 64; ++k) m2[k >> 5] |= (v[k] > 0.f ? 1u : 0u) << (k & 31);
+    st_row64(sm + BwdSmem::H2, tid, v);
+    tc_sync_for_mma();
+    if (tid == 0) {
+      mma_k64(tmem + WORK_COL, sa(BwdSmem::H2), sa(BwdSmem::W3), ID64);
+      tc::mma_commit(bar);
+    }
+    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
+    ld_row64(lane, WORK_COL, v);
+#pragma unroll
+    for (int k = 0; k < 64; ++k) v[k] = leaky(v[k] + bias[64 + k], a.slope);
+    m3[0] = m3[1] = 0u;
+#pragma unroll
+    for (int k = 0; k < 64; ++k) m3[k >> 5] |= (v[k] > 0.f ? 1u : 0u) << (k & 31);
+    st_row64(sm + BwdSmem::H3, tid, v);
+    tc_sync_for_mma();
+    if (tid == 0) {
+      mma_k64(tmem + WORK_COL, sa(BwdSmem::H3), sa(BwdSmem::WO), ID16);
+      tc::mma_commit(bar);
+    }
+    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
+    {
+      uint32_t r[16];
+      tc::tmem_ld16(lane + WORK_COL, r);
+      tc::tmem_ld_wait();
+      float o[7], go[7];
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        o[j] = __uint_as_float(r[j]) + bias[128 + j];
+        go[j] = 0.f;
+      }
+      if (valid)
+        transform_backward<ROT>(o, a.alpha, a.xr[i], a.dxhat[(long long)t * a.N + i], go);
+      // output-bias gradient: summed in FP32 (rows cancel strongly; a BF16
+      // rounding of each row's dL/do would dominate the sum)
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        float sj = go[j];
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o2);
+        if ((tid & 31) == 0 && j < NO) atomicAdd(dbo + j, sj);
+      }
+      uint4 q0, q1;
+      q0.x = tc::pack_bf16(go[0], go[1]);
+      q0.y = tc::pack_bf16(go[2], go[3]);
+      q0.z = tc::pack_bf16(go[4], go[5]);
+      q0.w = tc::pack_bf16(NO > 6 ? go[6] : 0.f, 0.f);
+      q1.x = q1.y = q1.z = q1.w = 0u;
+      *reinterpret_cast<uint4*>(sm + BwdSmem::GO + tc::sw128_off(tid, 0)) = q0;
+      *reinterpret_cast<uint4*>(sm + BwdSmem::GO + tc::sw128_off(tid, 8)) = q1;
+    }
+    // ---- backward: dh3 = gO Wo (K = 16)
+    tc_sync_for_mma();
+    if (tid == 0) {
+      tc::mma_bf16(tmem + WORK_COL, tc::kmajor_sw128(sa(BwdSmem::GO)),
+                   tc::kmajor_sw128(sa(BwdSmem::WOT)), ID64, 0u);
+      tc::mma_commit(bar);
+    }
+    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
+    ld_row64(lane, WORK_COL, v);
+#pragma unroll
+    for (int k = 0; k < 64; ++k)
+      v[k] *= ((m3[k >> 5] >> (k & 31)) & 1u) ? 1.f : a.slope;
+    st_row64(sm + BwdSmem::DP3, tid, v);
+    // dh2 = dpre3 W3
+    tc_sync_for_mma();
+    if (tid == 0) {
+      mma_k64(tmem + WORK_COL, sa(BwdSmem::DP3), sa(BwdSmem::W3T), ID64);
+      tc::mma_commit(bar);
+    }
+    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
+    ld_row64(lane, WORK_COL, v);
+#pragma unroll
+    for (int k = 0; k < 64; ++k)
+      v[k] *= ((m2[k >> 5] >> (k & 31)) & 1u) ? 1.f : a.slope;
+    st_row64(sm + BwdSmem::DP2, tid, v);
+    // ACC_W += [dpre3 | dpre2]^T [h2 | h1 | y]; dh1 = dpre2 W2
+    tc_sync_for_mma();
+    if (tid == 0) {
+      mma_rows(tmem + ACC_W_COL, sa(BwdSmem::DP3), sa(BwdSmem::H2), IDW, first);
+      mma_k64(tmem + WORK_COL, sa(BwdSmem::DP2), sa(BwdSmem::W2T), ID64);
+      tc::mma_commit(bar);
+    }
+    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
+    ld_row64(lane, WORK_COL, v);
+#pragma unroll
+    for (int k = 0; k < 64; ++k)
+      v[k] *= ((m1[k >> 5] >> (k & 31)) & 1u) ? 1.f : a.slope;
+    st_row64(sm + BwdSmem::DP3, tid, v);  // dpre1 (ACC_W has consumed dpre3)
+    // dL/dz rows
+    for (int q = 0; q < Z; ++q) {
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < 64; ++j) s = fmaf(w1f[j * K + q], v[j], s);
+      dzs[tid * 8 + q] = valid ? s : 0.f;
+    }
+    // ACC_X += [gO | dpre1]^T [y | h3]
+    tc_sync_for_mma();
+    if (tid == 0) {
+      mma_rows(tmem + ACC_X_COL, sa(BwdSmem::GO), sa(BwdSmem::Y), IDX, first);
+      tc::mma_commit(bar);
+    }
+    for (int e = tid; e < 16 * Z; e += 128) {
+      const int vi = e / Z, q = e % Z;
+      if (i0 + vi >= a.N) continue;
+      float s = 0.f;
+#pragma unroll
+      for (int tt = 0; tt < 8; ++tt) s += dzs[(tt * 16 + vi) * 8 + q];
+      atomicAdd(a.dz + (long long)(i0 + vi) * Z + q, s);
+    }
+    first = false;
+    // the next tile overwrites the operand tiles: wait for ACC_X to finish
+    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
+  }
+  // ---- accumulators -> global gradient (parameter layout), once per CTA
+  if (ok && !first) {
+    const int row = tid;  // TMEM lane = D row
+    float* g = a.g_mlp;
+    float* gW1 = g;
+    float* gb1 = g + H * K;
+    float* gW2 = gb1 + H;
+    float* gb2 = gW2 + H * H;
+    float* gW3 = gb2 + H;
+    float* gb3 = gW3 + H * H;
+    float* gWo = gb3 + H;
+    float* gbo = gWo + NO * H;
+    float v[64];
+    if (row < 64) {  // ACC_W rows 0..63: dW3 (cols 0..63), db3 (col 143)
+      ld_row64(lane, ACC_W_COL, v);
+      for (int k = 0; k < 64; ++k) atomicAdd(gW3 + row * H + k, v[k]);
+      uint32_t r[16];
+      tc::tmem_ld16(lane + ACC_W_COL + 128, r);
+      tc::tmem_ld_wait();
+      atomicAdd(gb3 + row, __uint_as_float(r[15]));
+    } else {  // rows 64..127: dW2 (cols 64..127), db2 (col 143)
+      ld_row64(lane, ACC_W_COL + 64, v);
+      for (int k = 0; k < 64; ++k) atomicAdd(gW2 + (row - 64) * H + k, v[k]);
+      uint32_t r[16];
+      tc::tmem_ld16(lane + ACC_W_COL + 128, r);
+      tc::tmem_ld_wait();
+      atomicAdd(gb2 + (row - 64), __uint_as_float(r[15]));
+    }
+    if (row < 64) {  // ACC_X rows 0..NO-1: dW_out (cols 64..127)
+      ld_row64(lane, ACC_X_COL + 64, v);
+      if (row < NO)
+        for (int k = 0; k < 64; ++k) atomicAdd(gWo + row * H + k, v[k]);
+      if (row < NO) atomicAdd(gbo + row, dbo[row]);
+    } else {  // rows 64..127: dW1 (cols 0..K-1), db1 (col 15)
+      ld_row64(lane, ACC_X_COL, v);
+      for (int k = 0; k < K; ++k) atomicAdd(gW1 + (row - 64) * K + k, v[k]);
+      atomicAdd(gb1 + (row - 64), v[15]);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+cudaError_t launch_mlp_backward_bf16(npg_ctx* c) {
+  const size_t smem = BwdSmem::TOTAL + 1024;
+  auto k = c->cfg.rot_mode == NPG_ROT_QUAT ? mlp_bwd_tc_kernel<0> : mlp_bwd_tc_kernel<1>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (long long)((c->N + 15) / 16) * ((c->T + 7) / 8);
+  k<<<tc_blocks(c, tiles, 1), 128, smem, c->stream>>>(tc_args(c));
+  return cudaGetLastError();
+}
 
 }  // namespace npg

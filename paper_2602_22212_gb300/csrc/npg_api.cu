@@ -311,9 +311,10 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
       return fail(set_err(c, NPG_ENOTIMPL, "FP32 backward needs %zu B shared memory (H=%d depth=%d)",
                           mlp_bwd_fp32_smem(md), md.H, md.D));
   } else if (cfg->precision == NPG_BF16_MLP) {
-    if (!decode_bf16_supported(md.H, md.D))
-      return fail(set_err(c, NPG_ENOTIMPL, "BF16 path supports H in {64,128}, got H=%d depth=%d",
-                          md.H, md.D));
+    if (!decode_bf16_supported(md.H, md.D) || !backward_bf16_supported(md.K, md.Z))
+      return fail(set_err(c, NPG_ENOTIMPL,
+                          "BF16 path supports H = 64, depth 3, F_n + F_p + 2 n_freq <= 15; "
+                          "got H=%d depth=%d K=%d", md.H, md.D, md.K));
   } else {
     return fail(set_err(c, NPG_EINVAL, "precision=%d", cfg->precision));
   }
@@ -406,7 +407,8 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
         alloc_n(c, c->nn_p, c->MT_cap) && alloc_n(c, c->d_p, c->MT_cap) &&
         alloc_n(c, c->dz, (long long)N * md.Z);
   ok &= alloc_n(c, c->cd, T) && alloc_n(c, c->wconf, T) && alloc_n(c, c->iso_t, T) &&
-        alloc_n(c, c->loss, 4) && alloc_n(c, c->d_epoch, 1) && alloc_n(c, c->d_adam_c, 2);
+        alloc_n(c, c->loss, 4) && alloc_n(c, c->d_epoch, 1) && alloc_n(c, c->d_adam_c, 2) &&
+        alloc_n(c, c->d_err, 1);
   ok &= alloc_n(c, c->grid, c->grid_dev_len) && alloc_n(c, c->g_grid, c->grid_dev_len) &&
         alloc_n(c, c->g_pc, c->grid_dev_len) && alloc_n(c, c->m_grid, c->grid_dev_len) &&
         alloc_n(c, c->v_grid, c->grid_dev_len);
@@ -465,6 +467,7 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
   CK(c, cudaMemsetAsync(c->v_mlp, 0, sizeof(float) * c->mlp_len, c->stream));
   CK(c, cudaMemsetAsync(c->g_mlp, 0, sizeof(float) * c->mlp_len, c->stream));
   CK(c, cudaMemsetAsync(c->d_epoch, 0, sizeof(int), c->stream));
+  CK(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   if ((rc = set_points_impl(c, points, frame_offsets, inputs_on_device))) return fail(rc);
   CK(c, cudaStreamSynchronize(c->stream));
   c->phase = 0;
@@ -562,6 +565,17 @@ static int step_launch(npg_ctx* c) {
   return NPG_OK;
 }
 
+// After a synchronisation: report a kernel whose bounded wait gave up.
+static int check_device_error(npg_ctx* c) {
+  int e = 0;
+  CK(c, cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    CK(c, cudaMemset(c->d_err, 0, sizeof(int)));
+    return set_err(c, NPG_ETIMEOUT, "a tensor-core wait timed out; results of this call are invalid");
+  }
+  return NPG_OK;
+}
+
 static int copy_loss_out(npg_ctx* c, double* loss_out, double* cd_out) {
   if (!loss_out && !cd_out) return NPG_OK;
   CK(c, cudaMemcpyAsync(c->h_loss, c->loss, sizeof(double) * 3, cudaMemcpyDeviceToHost,
@@ -570,6 +584,7 @@ static int copy_loss_out(npg_ctx* c, double* loss_out, double* cd_out) {
     CK(c, cudaMemcpyAsync(c->h_loss + 4, c->cd, sizeof(double) * c->T, cudaMemcpyDeviceToHost,
                           c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
+  if (int rc = check_device_error(c)) return rc;
   if (loss_out) memcpy(loss_out, c->h_loss, sizeof(double) * 3);
   if (cd_out) memcpy(cd_out, c->h_loss + 4, sizeof(double) * c->T);
   return NPG_OK;
@@ -752,7 +767,7 @@ extern "C" int npg_get(npg_ctx* c, int which, void* dst, size_t bytes, int dst_o
     CK(c, cudaMemcpyAsync(dst, plain_buf(c, which), bytes, kind, c->stream));
   }
   CK(c, cudaStreamSynchronize(c->stream));
-  return NPG_OK;
+  return check_device_error(c);
 }
 
 extern "C" int npg_set(npg_ctx* c, int which, const void* src, size_t bytes, int src_on_device) {

@@ -118,6 +118,7 @@ struct npg_ctx {
   long long graph_launches = 0;  // kernels in one replay of the captured graph
   int* d_epoch = nullptr;  // device copy of e (read by graph-captured kernels)
   float* d_adam_c = nullptr;  // 1 - beta1^s, 1 - beta2^s of the current step
+  int* d_err = nullptr;       // set by a kernel whose bounded wait gave up
   float* xhat3 = nullptr;     // T x N x 3 staging for npg_get
   void* allocs[64];
   int n_allocs = 0;
@@ -165,6 +166,7 @@ int auto_cells(long long points_per_set, int nsets);
 int set_error_message(int code, const char* fmt, ...);
 bool decode_fp32_supported(int H, int D);
 bool decode_bf16_supported(int H, int D);
+bool backward_bf16_supported(int K, int Z);
 size_t mlp_bwd_fp32_smem(const MlpDims& md);
 
 }  // namespace npg

@@ -1,0 +1,131 @@
+"""The BF16 tensor-core MLP path (tcgen05, FP32 accumulation) against the
+FP32 path and the FP64 oracle.
+
+BF16 keeps 8 significand bits, so each rounded activation or weight carries
+a relative error up to 2^-9 = 2e-3; a 64-term dot product of such terms lands
+within a few 1e-3 of its FP32 value. Tolerances:
+  x-hat                 5e-3 absolute against the FP32 path (coordinates O(1))
+  MLP gradients         3e-2 relative per block against the oracle, from the
+                        same dL/dx-hat
+  grid gradients        1e-1 relative per level: every grid node sums the
+                        contributions of many vertex-frames that largely cancel
+                        (the coarsest level most), which magnifies the BF16
+                        rounding of each contribution
+  final Chamfer         within 1% of the FP32 path's after the same iterations
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_22212_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def npg():
+    from paper_2602_22212_gb300 import build
+    build.build()
+    from paper_2602_22212_gb300 import npg as mod
+    return mod
+
+
+def setup(rot_mode=0, seed=1, T=8, M=4096):
+    seq = I.sphere_blob(subdiv=4, T=T, M=M, noise=0.005, seed=seed)
+    ocfg = O.make_cfg(L=4, res=(8, 27, 45, 64), F=4, H=64, D=3, rot_mode=rot_mode, slope=0.01)
+    prob = O.Problem(ocfg, seq.x, seq.n, seq.faces, seq.points, seq.offsets, seq.t_key)
+    return seq, ocfg, prob
+
+
+def cfg_of(npg, ocfg, precision, e_max=10, **kw):
+    return npg.make_config(ocfg.L, [ocfg.res[l] for l in range(ocfg.L)], ocfg.F, ocfg.H, ocfg.D,
+                           slope=ocfg.slope, rot_mode=ocfg.rot_mode, e_max=e_max,
+                           precision=precision, **kw)
+
+
+def rand_params(ocfg, seed=2):
+    rng = np.random.default_rng(seed)
+    grid = rng.normal(scale=0.3, size=O.grid_len(ocfg)).astype(np.float32)
+    mlp = I.mlp_init(O.k_in(ocfg), ocfg.H, ocfg.D, O.n_out(ocfg), seed=seed + 1, zero_last=False)
+    mlp[-(O.n_out(ocfg) * ocfg.H + O.n_out(ocfg)):] *= 0.5
+    return grid, mlp
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("rot_mode", [0, 1])
+def test_bf16_decode_tracks_fp32(npg, rot_mode):
+    seq, ocfg, prob = setup(rot_mode)
+    grid, mlp = rand_params(ocfg)
+    out = {}
+    for prec in (npg.FP32, npg.BF16_MLP):
+        ctx = npg.Context(cfg_of(npg, ocfg, prec), seq, mlp)
+        ctx.set(npg.BUF_GRID, grid)
+        ctx.forward()
+        out[prec] = ctx.get(npg.BUF_XHAT).reshape(prob.T, prob.N, 3)
+        ctx.close()
+    d = np.abs(out[npg.BF16_MLP] - out[npg.FP32])
+    assert d.max() <= 5e-3, d.max()
+    disp = out[npg.FP32] - seq.x[None]
+    assert rel(out[npg.BF16_MLP] - seq.x[None], disp) <= 2e-2
+
+
+def test_bf16_identity_initialisation_exact(npg):
+    seq, ocfg, prob = setup(T=3, M=500)
+    mlp = I.mlp_init(O.k_in(ocfg), ocfg.H, ocfg.D, O.n_out(ocfg), seed=0)
+    ctx = npg.Context(cfg_of(npg, ocfg, npg.BF16_MLP), seq, mlp)
+    ctx.forward()
+    xh = ctx.get(npg.BUF_XHAT).reshape(3, seq.N, 3)
+    for t in range(3):
+        np.testing.assert_array_equal(xh[t], seq.x)
+    ctx.close()
+
+
+@pytest.mark.parametrize("rot_mode", [0, 1])
+def test_bf16_backprop_vs_oracle(npg, rot_mode):
+    import torch
+    seq, ocfg, prob = setup(rot_mode)
+    grid, mlp = rand_params(ocfg)
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    ref = O.loss_full(prob, f32(grid), f32(mlp), 3, 10, decide_f32=True)
+    gx32 = ref["g_xhat"].astype(np.float32)
+    want_g, want_m = O.backprop(prob, f32(grid), f32(mlp), f32(gx32))
+    ctx = npg.Context(cfg_of(npg, ocfg, npg.BF16_MLP), seq, mlp)
+    ctx.set(npg.BUF_GRID, grid)
+    npg.npg_set_epoch(ctx.h, 3)
+    ctx.forward()
+    npg.npg_backprop(ctx.h, torch.from_numpy(gx32.reshape(-1)).cuda())
+    gg = ctx.get(npg.BUF_GRID_GRAD).astype(np.float64)
+    gm = ctx.get(npg.BUF_MLP_GRAD).astype(np.float64)
+    H, D, K, NO = 64, 3, O.k_in(ocfg), O.n_out(ocfg)
+    off = 0
+    for name, n in [("W1", H * K), ("b1", H), ("W2", H * H), ("b2", H), ("W3", H * H),
+                    ("b3", H), ("Wo", NO * H), ("bo", NO)]:
+        assert rel(gm[off:off + n], want_m[off:off + n]) <= 3e-2, name
+        off += n
+    for l in range(ocfg.L + 1):
+        a = O.level_offset(ocfg, l)
+        b = O.level_offset(ocfg, l + 1) if l < ocfg.L else O.grid_len(ocfg)
+        assert rel(gg[a:b], want_g[a:b]) <= 1e-1, (l, rel(gg[a:b], want_g[a:b]))
+    ctx.close()
+
+
+def test_bf16_final_chamfer_within_one_percent_of_fp32(npg):
+    """A full run (e_max = 200 iterations) from the identity initialisation on
+    both paths; the reconstructions' mean Chamfer distances agree within 1%."""
+    seq, ocfg, prob = setup()
+    mlp = I.mlp_init(O.k_in(ocfg), ocfg.H, ocfg.D, O.n_out(ocfg), seed=0)
+    iters = 200
+    final, start = {}, {}
+    for prec in (npg.FP32, npg.BF16_MLP):
+        ctx = npg.Context(cfg_of(npg, ocfg, prec, e_max=iters), seq, mlp)
+        for k in range(iters):
+            ctx.iteration()
+        ctx.forward()
+        _, cd = ctx.loss()
+        final[prec] = cd.mean()
+        ctx.close()
+    print("final mean Chamfer FP32 %.6e BF16 %.6e" % (final[npg.FP32], final[npg.BF16_MLP]))
+    assert abs(final[npg.BF16_MLP] - final[npg.FP32]) <= 0.01 * final[npg.FP32], final
