@@ -62,6 +62,10 @@ extern "C" {
 #define NPG_ROT_QUAT 0   /* Eq. 5: q = (1 + o0, o1, o2, o3) / norm, d = o4..6 */
 #define NPG_ROT_EXPMAP 1 /* exponential map: omega = o0..2, d = o3..5        */
 
+/* arithmetic of the preconditioner's DCT passes */
+#define NPG_PRECOND_FP32 0
+#define NPG_PRECOND_TC 1
+
 /* arithmetic of the MLP decode and its backward pass */
 #define NPG_FP32 0     /* FP32 SIMT                                          */
 #define NPG_BF16_MLP 1 /* BF16 operands, FP32 accumulation on tcgen05 tensor cores */
@@ -90,6 +94,10 @@ typedef struct npg_ctx npg_ctx; /* opaque; owns all device memory it allocates *
  *   precision        NPG_FP32 or NPG_BF16_MLP.
  *   nn_cells         bucket cells per axis of the Chamfer search grids; 0 =
  *                    chosen from the point and vertex counts.
+ *   precond_mode     NPG_PRECOND_FP32: the DCT passes of the preconditioner on
+ *                    the CUDA cores in FP32; NPG_PRECOND_TC: on tcgen05 tensor
+ *                    cores in split BF16 (hi + lo, three products, FP32
+ *                    accumulation; ~1e-5 relative) for levels with r >= 24.
  *   use_graph        npg_iteration replays one captured CUDA graph.
  *   stream           cudaStream_t for all device work.
  *   alloc/free/user  optional device allocator (e.g. PyTorch's caching
@@ -117,6 +125,7 @@ typedef struct npg_config {
   int e_max;
   int precision;
   int nn_cells;
+  int precond_mode;
   int use_graph;
   void* stream;
   void* (*alloc)(size_t bytes, void* user);
@@ -277,6 +286,13 @@ NPG_API int npg_nearest(const float* q, int nq, const float* c, int nc, int32_t*
  * stream and frees it before returning.
  */
 NPG_API int npg_precondition(const float* g, float* out, int r, int F, float lambda, void* stream);
+
+/* npg_precondition with the DCT passes on the tensor cores (split BF16, FP32
+ * accumulation, ~1e-5 relative error): same arguments, layout and errors;
+ * 2 <= r <= 256. Allocates its scratch and tables with cudaMallocAsync on
+ * stream and frees them before returning. */
+NPG_API int npg_precondition_tc(const float* g, float* out, int r, int F, float lambda,
+                                void* stream);
 
 /*
  * Allocation-free variant of npg_precondition (the paper has no counterpart:

@@ -191,6 +191,11 @@ static int validate(const npg_config* c, char* why, size_t n) {
       return snprintf(why, n, "lambda/lr of level %d must be >= 0", l), 0;
   if (c->e_max < 0) return snprintf(why, n, "e_max < 0"), 0;
   if (c->nn_cells < 0 || c->nn_cells > 256) return snprintf(why, n, "nn_cells out of 0..256"), 0;
+  if (c->precond_mode != NPG_PRECOND_FP32 && c->precond_mode != NPG_PRECOND_TC)
+    return snprintf(why, n, "precond_mode=%d", c->precond_mode), 0;
+  if (c->precond_mode == NPG_PRECOND_TC)
+    for (int l = 0; l < c->L; ++l)
+      if (c->res[l] > 256) return snprintf(why, n, "tensor-core preconditioner needs res <= 256"), 0;
   return 1;
 }
 
@@ -421,6 +426,14 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
     dct_len += ((2LL * c->lev[l].r * c->lev[l].r + c->lev[l].r) + 63) & ~63LL;
   }
   ok &= alloc_n(c, c->dct, dct_len);
+  long long tc_len = 0;
+  if (cfg->precond_mode == NPG_PRECOND_TC)
+    for (int l = 0; l < c->nlev; ++l)
+      for (int m = 0; m < 2; ++m) {
+        c->dct_tc_off[l][m] = tc_len;
+        tc_len += ((long long)dct_tc_table_elems(c->lev[l].r) + 127) & ~127LL;
+      }
+  if (tc_len > 0) ok &= alloc_n(c, c->dct_tc, tc_len);
   if (!ok) return fail(set_err(c, NPG_ENOMEM, "device allocation failed"));
   if (cudaMallocHost(&c->h_loss, sizeof(double) * (4 + T)) != cudaSuccess ||
       cudaMallocHost(&c->h_off, sizeof(long long) * (T + 1)) != cudaSuccess) {
@@ -456,6 +469,18 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
       dct_tables(r, base, base + (long long)r * r, base + 2LL * r * r);
     }
     if ((rc = copy_in(c, c->dct, tab.data(), sizeof(float) * tab.size(), 0))) return fail(rc);
+    if (tc_len > 0) {
+      std::vector<uint16_t> tt((size_t)tc_len, 0);
+      for (int l = 0; l < c->nlev; ++l) {
+        const int r = c->lev[l].r;
+        const float* base = tab.data() + c->dct_off[l];
+        dct_tc_tables(r, base, tt.data() + c->dct_tc_off[l][0]);
+        dct_tc_tables(r, base + (long long)r * r, tt.data() + c->dct_tc_off[l][1]);
+      }
+      CK(c, cudaMemcpyAsync(c->dct_tc, tt.data(), sizeof(uint16_t) * tt.size(),
+                            cudaMemcpyHostToDevice, c->stream));
+      CK(c, cudaStreamSynchronize(c->stream));
+    }
     CK(c, cudaStreamSynchronize(c->stream));
   }
   CK(c, cudaMemsetAsync(c->grid, 0, sizeof(float) * c->grid_dev_len, c->stream));
@@ -546,8 +571,14 @@ static int step_launch(npg_ctx* c) {
     const Level& lv = c->lev[l];
     const float* tab = c->dct + c->dct_off[l];
     const long long rr = (long long)lv.r * lv.r;
-    CK(c, launch_precondition(c->g_grid + lv.off, c->g_pc + lv.off, c->pc_tmp0, c->pc_tmp1, tab,
-                              tab + rr, tab + 2 * rr, lv.r, lv.F, lv.lambda, c->stream));
+    if (c->cfg.precond_mode == NPG_PRECOND_TC && lv.r >= PRECOND_TC_MIN_R)
+      CK(c, launch_precondition_tc(c->g_grid + lv.off, c->g_pc + lv.off, c->pc_tmp0, c->pc_tmp1,
+                                   c->dct_tc + c->dct_tc_off[l][0],
+                                   c->dct_tc + c->dct_tc_off[l][1], tab + 2 * rr, lv.r, lv.F,
+                                   lv.lambda, c->d_err, c->stream));
+    else
+      CK(c, launch_precondition(c->g_grid + lv.off, c->g_pc + lv.off, c->pc_tmp0, c->pc_tmp1,
+                                tab, tab + rr, tab + 2 * rr, lv.r, lv.F, lv.lambda, c->stream));
   }
   mark(c, 10);
   for (int l = 0; l < c->nlev; ++l) {
@@ -985,6 +1016,46 @@ extern "C" int npg_nearest(const float* q, int nq, const float* cand, int nc, in
   cleanup();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "npg_nearest");
+  return NPG_OK;
+}
+
+extern "C" int npg_precondition_tc(const float* g, float* out, int r, int F, float lambda,
+                                   void* stream) {
+  if (!g || !out || r < 2 || r > 256 || F < 1 || F > NPG_MAX_F || !(lambda >= 0.f))
+    return set_err(nullptr, NPG_EINVAL, "npg_precondition_tc: bad arguments (r=%d F=%d)", r, F);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long n = (long long)r * r * r * F;
+  std::vector<float> tab(2LL * r * r + r);
+  dct_tables(r, tab.data(), tab.data() + (long long)r * r, tab.data() + 2LL * r * r);
+  const size_t te = dct_tc_table_elems(r);
+  std::vector<uint16_t> tt(2 * te);
+  dct_tc_tables(r, tab.data(), tt.data());
+  dct_tc_tables(r, tab.data() + (long long)r * r, tt.data() + te);
+  float *t0 = nullptr, *t1 = nullptr, *dmu = nullptr;
+  uint16_t* dtt = nullptr;
+  int* derr = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&t0, sizeof(float) * n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&t1, sizeof(float) * n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&dmu, sizeof(float) * r, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&dtt, sizeof(uint16_t) * tt.size(), s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&derr, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dmu, tab.data() + 2LL * r * r, sizeof(float) * r, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dtt, tt.data(), sizeof(uint16_t) * tt.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_precondition_tc(g, out, t0, t1, dtt, dtt + te, dmu, r, F, lambda, derr, s);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(t0, s);
+  cudaFreeAsync(t1, s);
+  cudaFreeAsync(dmu, s);
+  cudaFreeAsync(dtt, s);
+  cudaFreeAsync(derr, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "npg_precondition_tc");
+  if (herr) return set_err(nullptr, NPG_ETIMEOUT, "npg_precondition_tc: a tensor-core wait timed out");
   return NPG_OK;
 }
 

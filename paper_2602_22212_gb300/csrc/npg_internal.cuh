@@ -106,6 +106,8 @@ struct npg_ctx {
   // preconditioner tables and scratch
   float* dct = nullptr;          // per level: C (r x r) then C^T (r x r) then mu (r)
   long long dct_off[NPG_MAX_LEVELS + 1];
+  uint16_t* dct_tc = nullptr;     // split BF16 tables per level: C then C^T (hi, lo each)
+  long long dct_tc_off[NPG_MAX_LEVELS + 1][2];
   float* pc_tmp0 = nullptr;
   float* pc_tmp1 = nullptr;
 
@@ -158,6 +160,12 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, long long 
 cudaError_t launch_step_prepare(const int* epoch, float b1, float b2, float* cc, cudaStream_t s);
 cudaError_t launch_step_finish(int* epoch, cudaStream_t s);
 void dct_tables(int r, float* C, float* Ct, float* mu);
+size_t dct_tc_table_elems(int r);
+void dct_tc_tables(int r, const float* Mx, uint16_t* dst);
+cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float* t1,
+                                   const uint16_t* tabC, const uint16_t* tabCt, const float* mu,
+                                   int r, int F, float lambda, int* err, cudaStream_t s);
+constexpr int PRECOND_TC_MIN_R = 24;
 cudaError_t launch_points_to_float4(const float* src, float4* dst, long long n, cudaStream_t s);
 cudaError_t launch_xhat_out(const float4* xhat, float* out, long long n, cudaStream_t s);
 

@@ -27,6 +27,7 @@ MAX_LEVELS = 16
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
 ROT_QUAT, ROT_EXPMAP = 0, 1
 FP32, BF16_MLP = 0, 1
+PRECOND_FP32, PRECOND_TC = 0, 1
 (BUF_GRID, BUF_MLP, BUF_GRID_GRAD, BUF_GRID_PC, BUF_MLP_GRAD, BUF_XHAT, BUF_NN_X, BUF_NN_P,
  BUF_CD, BUF_WCONF, BUF_ADAM_M_GRID, BUF_ADAM_V_GRID, BUF_ADAM_M_MLP, BUF_ADAM_V_MLP,
  BUF_DIST_X, BUF_DIST_P, BUF_DXHAT) = range(17)
@@ -62,6 +63,7 @@ class npg_config(C.Structure):
         ("e_max", C.c_int),
         ("precision", C.c_int),
         ("nn_cells", C.c_int),
+        ("precond_mode", C.c_int),
         ("use_graph", C.c_int),
         ("stream", C.c_void_p),
         ("alloc", ALLOC_FN),
@@ -95,6 +97,7 @@ _SIG = {
     "npg_nearest": (_i, [_vp, _i, _vp, _i, _vp, _vp, _i, _vp]),
     "npg_precondition": (_i, [_vp, _vp, _i, _i, C.c_float, _vp]),
     "npg_precondition_static": (_i, [_vp, _vp, _i, _i, C.c_float, _vp]),
+    "npg_precondition_tc": (_i, [_vp, _vp, _i, _i, C.c_float, _vp]),
     "npg_timing": (_i, [_vp, _i]),
     "npg_timing_read": (_i, [_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "npg_launch_count": (C.c_longlong, [_vp]),
@@ -274,6 +277,12 @@ def npg_precondition(g, out, r, F, lam, stream=None):
                                  _stream_handle(stream)))
 
 
+def npg_precondition_tc(g, out, r, F, lam, stream=None):
+    """npg_precondition with the DCT passes on the tensor cores (split BF16)."""
+    _check(_lib.npg_precondition_tc(_ptr(g), _ptr(out), int(r), int(F), float(lam),
+                                    _stream_handle(stream)))
+
+
 def npg_precondition_static(g, out, r, F, lam, stream=None):
     """Allocation-free npg_precondition (fixed-size scratch; see include/npg.h)."""
     _check(_lib.npg_precondition_static(_ptr(g), _ptr(out), int(r), int(F), float(lam),
@@ -284,7 +293,8 @@ def npg_precondition_static(g, out, r, F, lam, stream=None):
 
 def make_config(L, res, F_p, H, depth, *, F_n=2, res_n=4, slope=0.01, rot_mode=ROT_QUAT,
                 precision=FP32, e_max=1000, w_iso=100.0, lr_mlp=1e-3, lr_grid=None,
-                lam=None, n_freq=4, alpha=0.1, nn_cells=0, use_graph=False, stream=None):
+                lam=None, n_freq=4, alpha=0.1, nn_cells=0, use_graph=False, stream=None,
+                precond_mode=PRECOND_FP32):
     """npg_config with the paper's defaults (Sec. 3.2-3.5) and explicit resolutions."""
     cfg = npg_config_default(L, 2, 2, F_p, H, depth)
     for k, r in enumerate(res):
@@ -295,6 +305,7 @@ def make_config(L, res, F_p, H, depth, *, F_n=2, res_n=4, slope=0.01, rot_mode=R
         float(lr_mlp)
     cfg.n_freq, cfg.alpha, cfg.nn_cells, cfg.use_graph = int(n_freq), float(alpha), int(
         nn_cells), int(bool(use_graph))
+    cfg.precond_mode = int(precond_mode)
     if lr_grid is not None:
         for k, v in enumerate(lr_grid):
             cfg.lr_grid[k] = float(v)

@@ -112,15 +112,22 @@ def test_bf16_backprop_vs_oracle(npg, rot_mode):
     ctx.close()
 
 
-def test_bf16_final_chamfer_within_one_percent_of_fp32(npg):
-    """A full run (e_max = 200 iterations) from the identity initialisation on
-    both paths; the reconstructions' mean Chamfer distances agree within 1%."""
-    seq, ocfg, prob = setup()
+@pytest.mark.parametrize("precond", [0, 1])
+def test_bf16_final_chamfer_within_one_percent_of_fp32(npg, precond):
+    """A full 250-iteration run (the paper's short schedule) from the identity
+    initialisation on the articulated figure, FP32 against BF16 (with the FP32
+    or the tensor-core preconditioner): the reconstructions' mean Chamfer
+    distances agree within 1%. The isometry weight is 1: on this synthetic
+    data w_iso = 100 makes the isometry term dominate L_def and the paper's
+    per-level learning rates diverge."""
+    seq = I.figure(subdiv=4, T=8, M=4096, noise_rel=0.003, seed=1)
+    ocfg = O.make_cfg(L=4, res=(8, 27, 45, 64), F=4, H=64, D=3, slope=0.01, w_iso=1.0)
     mlp = I.mlp_init(O.k_in(ocfg), ocfg.H, ocfg.D, O.n_out(ocfg), seed=0)
-    iters = 200
-    final, start = {}, {}
+    iters = 250
+    final = {}
     for prec in (npg.FP32, npg.BF16_MLP):
-        ctx = npg.Context(cfg_of(npg, ocfg, prec, e_max=iters), seq, mlp)
+        ctx = npg.Context(cfg_of(npg, ocfg, prec, e_max=iters, w_iso=1.0,
+                                 precond_mode=precond if prec == npg.BF16_MLP else 0), seq, mlp)
         for k in range(iters):
             ctx.iteration()
         ctx.forward()

@@ -130,6 +130,45 @@ def test_precondition_matches_oracle(npg, r, F, lam):
     assert rel(gt.cpu().numpy(), ref) <= 2e-6
 
 
+@pytest.mark.parametrize("r,F,lam", [(24, 1, 0.4), (27, 2, 1.35), (50, 4, 0.6), (64, 3, 6.8),
+                                     (85, 4, 0.9)])
+def test_precondition_tc_matches_oracle(npg, r, F, lam):
+    """Tensor-core DCT passes (split BF16, FP32 accumulation): ~1e-5 relative."""
+    import torch
+    rng = np.random.default_rng(r + F)
+    g = rng.normal(size=r ** 3 * F).astype(np.float32)
+    ref, _ = O.precondition(r, F, lam, f32(g), tol=1e-12)
+    gt = torch.from_numpy(g).cuda()
+    out = torch.empty_like(gt)
+    npg.npg_precondition_tc(gt, out, r, F, lam)
+    assert rel(out.cpu().numpy(), ref) <= 5e-5
+
+
+@pytest.mark.parametrize("r,F,k", [(256, 4, (3, 0, 7)), (222, 2, (1, 100, 0)), (153, 1, (152, 5, 9)),
+                                   (130, 4, (0, 0, 0))])
+def test_precondition_tc_eigenvectors(npg, r, F, k):
+    """At full level size: a product of DCT-II basis vectors is an eigenvector
+    of (I + lambda L)^-2 with eigenvalue 1 / (1 + lambda sum_a (2 - 2 cos(pi k_a / r)))^2
+    (the Neumann path Laplacian's spectrum), so the output is the input scaled.
+    Rounding enters at the input's scale and is not attenuated with a
+    high-frequency mode, so the error is measured relative to the input."""
+    import torch
+    lam = 6.8
+    n = np.arange(r)
+    basis = [np.cos(np.pi * ka * (2 * n + 1) / (2 * r)) for ka in k]
+    g = np.einsum("z,y,x->zyx", basis[2], basis[1], basis[0])  # node (x, y, z) at [z][y][x]
+    gf = np.repeat(g.reshape(-1, 1), F, axis=1) * (1.0 + np.arange(F))
+    mu = sum(2 - 2 * np.cos(np.pi * ka / r) for ka in k)
+    want = gf / (1 + lam * mu) ** 2
+    gt = torch.from_numpy(gf.astype(np.float32).ravel()).cuda()
+    out = torch.empty_like(gt)
+    gn = np.linalg.norm(gf)
+    npg.npg_precondition_tc(gt, out, r, F, lam)
+    assert np.linalg.norm(out.cpu().numpy() - want.ravel()) <= 2e-5 * gn
+    npg.npg_precondition(gt, out, r, F, lam)
+    assert np.linalg.norm(out.cpu().numpy() - want.ravel()) <= 1e-6 * gn
+
+
 # ----------------------------------------------------------------- one iteration, tiny config
 
 def test_identity_initialisation_exact(npg):
@@ -235,8 +274,8 @@ def test_dxhat_parity(npg, rot_mode):
     ctx.close()
 
 
-@pytest.mark.parametrize("rot_mode", [0, 1])
-def test_backprop_parity(npg, rot_mode):
+@pytest.mark.parametrize("rot_mode,precond", [(0, 0), (1, 0), (0, 1)])
+def test_backprop_parity(npg, rot_mode, precond):
     """Parameter gradients from the same dL/dx-hat (the oracle's, in FP32):
     the MLP backward with forward recompute and the grid scatter."""
     import torch
@@ -245,7 +284,7 @@ def test_backprop_parity(npg, rot_mode):
     ref = O.loss_full(prob, f32(grid), f32(mlp), 3, 10, decide_f32=True)
     gx32 = ref["g_xhat"].astype(np.float32)
     want_g, want_m = O.backprop(prob, f32(grid), f32(mlp), f32(gx32))
-    ctx = gpu_at(npg, ocfg, seq, grid, mlp, 3, 10)
+    ctx = gpu_at(npg, ocfg, seq, grid, mlp, 3, 10, precond_mode=precond)
     npg.npg_backprop(ctx.h, torch.from_numpy(gx32.reshape(-1)).cuda())
     gg = ctx.get(npg.BUF_GRID_GRAD).astype(np.float64)
     gm = ctx.get(npg.BUF_MLP_GRAD).astype(np.float64)
