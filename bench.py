@@ -135,6 +135,8 @@ def stage_work(p, N, T, MT, mlp_dims, precond="fp32", precision="fp32"):
     n_params = sum(r ** 3 * F for r in res) + 4 ** 3 * 2
     mlp_kind = "tensor" if precision == "bf16" else "alu"
     return {
+        "nn_x": ("alu", None, "FLOP"),
+        "nn_p": ("alu", None, "FLOP"),
         "decode": (mlp_kind, fwd_row * rows, "FLOP"),
         "mlp_bwd": (mlp_kind, bwd_row * rows, "FLOP"),
         "precond": ("hbm", dct_bytes, "B") if precond == "tc" else ("alu", dct_flops, "FLOP"),
@@ -228,7 +230,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--graph", dest="graph", action="store_true", default=None)
     ap.add_argument("--no-graph", dest="graph", action="store_false")
-    ap.add_argument("--workload", default="paper", choices=["paper", "tiny"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "tiny", "profile"])
     ap.add_argument("--precond", default=None, choices=["fp32", "tc"],
                     help="preconditioner DCT arithmetic (default: tc with bf16, fp32 with fp32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -302,9 +304,14 @@ def main():
     for _ in range(args.steps):
         npg.npg_iteration(sctx.h, None)
     stages = {}
+    n_timed = 1
     for k, name in enumerate(npg.STAGES):
         tot, n = npg.npg_timing_read(sctx.h, k)
         stages[name] = tot / max(n, 1)
+        n_timed = max(n_timed, n)
+    cx, rx, cp, rp = npg.npg_search_stats(sctx.h)
+    search = {"cand_per_query_x": cx / n_timed / (N * T), "rows_per_query_x": rx / n_timed / (N * T),
+              "cand_per_query_p": cp / n_timed / MT, "rows_per_query_p": rp / n_timed / MT}
     npg.npg_timing(sctx.h, 0)
 
     # e2e: host buffers through the public API; each step uploads the step's
@@ -330,6 +337,9 @@ def main():
 
     peaks = load_peaks()
     work = stage_work(p, N, T, MT, (H, D, K, Z, NO), precond, args.precision)
+    # search work: 8 FLOP per candidate pair (3 sub, 1 mul, 2 fma, compare)
+    work["nn_x"] = ("alu", 8 * search["cand_per_query_x"] * N * T, "FLOP")
+    work["nn_p"] = ("alu", 8 * search["cand_per_query_p"] * MT, "FLOP")
     dom = max((s for s in stages if s in work), key=lambda s: stages[s])
     kind, amount, u = work[dom][:3]
     dur = stages[dom] * 1e-3
@@ -373,6 +383,7 @@ def main():
             "gpu_launches": int(launches),
             "roofline": roof,
             "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+            "search": {k: round(v, 2) for k, v in search.items()},
             "cpu_baseline": cpu,
             "clocks": clocks,
         }

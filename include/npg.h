@@ -254,6 +254,11 @@ NPG_API int npg_set_state(npg_ctx* ctx, const void* blob, size_t bytes);
 NPG_API int npg_timing(npg_ctx* ctx, int n_iters);
 NPG_API int npg_timing_read(npg_ctx* ctx, int stage, double* total_ms, int* n_iters);
 
+/* Work counters of the nearest-neighbour search, summed over the iterations
+ * timed since the last npg_timing call: out4 = {candidate pairs evaluated and
+ * cell rows visited, vertex -> point; the same, point -> vertex}. */
+NPG_API int npg_search_stats(npg_ctx* ctx, long long* out4);
+
 /* Number of kernels this context has launched (graph replays count every
  * kernel node they contain). */
 NPG_API long long npg_launch_count(const npg_ctx* ctx);

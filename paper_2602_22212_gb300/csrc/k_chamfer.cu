@@ -136,86 +136,211 @@ int auto_cells(long long points_per_set, int nsets) {
 
 // ----------------------------------------------------------------- NN search
 // Exact nearest neighbour by growing Chebyshev rings of cells around the
-// query's cell; stops once the best squared distance is below the squared
-// distance to every unexplored cell (with a safety margin for FP32 rounding
-// of the cell assignment). Ties go to the lowest candidate index.
-__global__ void __launch_bounds__(128) nn_kernel(
-    const float4* __restrict__ qs, long long q_uniform, const long long* q_off, int nsets,
-    long long q_total, const float4* __restrict__ cs, const int* __restrict__ cstart, int G,
-    const long long* c_off, long long c_uniform, int* __restrict__ out_idx,
-    float* __restrict__ out_d) {
+// query's cell; a search stops once its best squared distance is below the
+// squared distance to every unexplored cell (with a safety margin for FP32
+// rounding of the cell assignment). Ties go to the lowest candidate index.
+//
+// Two passes balance the work: pass 1 (one thread per query, queries in cell
+// order) searches rings 0..NN_NEAR_RINGS and finishes most queries; a query
+// that is still open is appended to a queue with its best so far. Pass 2
+// (one warp per queued query, lanes splitting each ring's cell rows) finishes
+// the far queries, whose rings hold many (mostly empty) cells.
+constexpr int NN_NEAR_RINGS = 1;
+
+struct NnGeom {
+  const float4* qs;
+  long long q_uniform;
+  const long long* q_off;
+  int nsets;
+  long long q_total;
+  const float4* cs;
+  const int* cstart;
+  int G;
+  const long long* c_off;
+  long long c_uniform;
+  int* out_idx;
+  float* out_d;
+  unsigned long long* stats;
+  int* qcount;  // [0] pushed, [1] popped
+  int4* qitems;
+};
+
+__device__ __forceinline__ void scan_range(const float4* __restrict__ cs, long long cb, int lo,
+                                           int hi, float4 q, float& best, int& bi) {
+  for (int j = lo; j < hi; ++j) {
+    const float4 p = cs[cb + j];
+    const float d = sqdist(q.x, q.y, q.z, p.x, p.y, p.z);
+    const int id = __float_as_int(p.w);
+    if (d < best || (d == best && id < bi)) {
+      best = d;
+      bi = id;
+    }
+  }
+}
+
+// Scan the cells of row (z, y) that belong to the shell of ring `ring`.
+__device__ __forceinline__ void scan_row(const NnGeom& g, const int* st, long long cb, int z,
+                                         int y, int cx, int cy, int cz, int ring, float4 q,
+                                         float& best, int& bi, unsigned long long& nc) {
+  const int G = g.G;
+  const int x0 = cx - ring, x1 = cx + ring;
+  const bool full = (z == cz - ring || z == cz + ring || y == cy - ring || y == cy + ring);
+  const int row = (z * G + y) * G;
+  if (full) {
+    const int lo = st[row + max(x0, 0)], hi = st[row + min(x1, G - 1) + 1];
+    nc += (unsigned long long)(hi - lo);
+    scan_range(g.cs, cb, lo, hi, q, best, bi);
+  } else {
+    if (x0 >= 0) {
+      const int lo = st[row + x0], hi = st[row + x0 + 1];
+      nc += (unsigned long long)(hi - lo);
+      scan_range(g.cs, cb, lo, hi, q, best, bi);
+    }
+    if (x1 <= G - 1 && x1 != x0) {
+      const int lo = st[row + x1], hi = st[row + x1 + 1];
+      nc += (unsigned long long)(hi - lo);
+      scan_range(g.cs, cb, lo, hi, q, best, bi);
+    }
+  }
+}
+
+// Squared lower bound on the distance to any cell outside rings 0..ring
+// (FLT_MAX when the rings cover the whole grid).
+__device__ __forceinline__ float ring_bound(float4 q, int cx, int cy, int cz, int ring, int G,
+                                            float h) {
+  const int x0 = cx - ring, x1 = cx + ring, y0 = cy - ring, y1 = cy + ring;
+  const int z0 = cz - ring, z1 = cz + ring;
+  float lb = FLT_MAX;
+  if (x0 > 0) lb = fminf(lb, q.x - fmaf((float)x0, h, -1.f));
+  if (x1 < G - 1) lb = fminf(lb, fmaf((float)(x1 + 1), h, -1.f) - q.x);
+  if (y0 > 0) lb = fminf(lb, q.y - fmaf((float)y0, h, -1.f));
+  if (y1 < G - 1) lb = fminf(lb, fmaf((float)(y1 + 1), h, -1.f) - q.y);
+  if (z0 > 0) lb = fminf(lb, q.z - fmaf((float)z0, h, -1.f));
+  if (z1 < G - 1) lb = fminf(lb, fmaf((float)(z1 + 1), h, -1.f) - q.z);
+  return lb;
+}
+
+// true when no unexplored cell can hold a point closer than best
+__device__ __forceinline__ bool ring_done(float lb, float best) {
+  if (lb == FLT_MAX) return true;
+  lb -= 4e-6f;
+  return lb > 0.f && best < lb * lb * (1.f - 1e-5f);
+}
+
+__device__ __forceinline__ void warp_stats(unsigned long long* stats, unsigned long long nc,
+                                           unsigned long long nr) {
+  if (!stats) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nc += __shfl_xor_sync(0xffffffffu, nc, o);
+    nr += __shfl_xor_sync(0xffffffffu, nr, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(stats, nc);
+    atomicAdd(stats + 1, nr);
+  }
+}
+
+__global__ void __launch_bounds__(128) nn_near_kernel(NnGeom g) {
+  const int G = g.G;
   const long long G3 = (long long)G * G * G;
   const float h = 2.f / (float)G;
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < q_total;
+  unsigned long long n_cand = 0, n_rows = 0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < g.q_total;
        k += (long long)gridDim.x * blockDim.x) {
-    const int s = set_of(k, q_uniform, q_off, nsets);
-    const float4 q = qs[k];
-    const int local = __float_as_int(q.w);
-    const long long cb = set_base(s, c_uniform, c_off);
-    const int* st = cstart + s * (G3 + 1);
+    const int s = set_of(k, g.q_uniform, g.q_off, g.nsets);
+    const float4 q = g.qs[k];
+    const long long cb = set_base(s, g.c_uniform, g.c_off);
+    const int* st = g.cstart + s * (G3 + 1);
     const int cx = cell_axis(q.x, G), cy = cell_axis(q.y, G), cz = cell_axis(q.z, G);
     float best = FLT_MAX;
     int bi = 0x7fffffff;
-    for (int ring = 0; ring < G; ++ring) {
-      const int x0 = cx - ring, x1 = cx + ring, y0 = cy - ring, y1 = cy + ring;
-      const int z0 = cz - ring, z1 = cz + ring;
-      const int xa = max(x0, 0), xb = min(x1, G - 1);
-      for (int z = max(z0, 0); z <= min(z1, G - 1); ++z) {
-        for (int y = max(y0, 0); y <= min(y1, G - 1); ++y) {
-          const bool full = (z == z0 || z == z1 || y == y0 || y == y1);
-          const int row = (z * G + y) * G;
-          for (int part = 0; part < (full ? 1 : 2); ++part) {
-            int lo, hi;
-            if (full) {
-              lo = st[row + xa];
-              hi = st[row + xb + 1];
-            } else if (part == 0) {
-              if (x0 < 0) continue;
-              lo = st[row + x0];
-              hi = st[row + x0 + 1];
-            } else {
-              if (x1 > G - 1 || x1 == x0) continue;
-              lo = st[row + x1];
-              hi = st[row + x1 + 1];
-            }
-            for (int j = lo; j < hi; ++j) {
-              const float4 p = cs[cb + j];
-              const float d = sqdist(q.x, q.y, q.z, p.x, p.y, p.z);
-              const int id = __float_as_int(p.w);
-              if (d < best || (d == best && id < bi)) {
-                best = d;
-                bi = id;
-              }
-            }
-          }
+    bool done = false;
+    for (int ring = 0; ring <= NN_NEAR_RINGS && ring < G; ++ring) {
+      for (int z = max(cz - ring, 0); z <= min(cz + ring, G - 1); ++z)
+        for (int y = max(cy - ring, 0); y <= min(cy + ring, G - 1); ++y) {
+          ++n_rows;
+          scan_row(g, st, cb, z, y, cx, cy, cz, ring, q, best, bi, n_cand);
+        }
+      if (ring_done(ring_bound(q, cx, cy, cz, ring, G, h), best)) {
+        done = true;
+        break;
+      }
+    }
+    if (done) {
+      const long long ob = set_base(s, g.q_uniform, g.q_off) + __float_as_int(q.w);
+      g.out_idx[ob] = bi;
+      if (g.out_d) g.out_d[ob] = best;
+    } else {
+      const int pos = atomicAdd(g.qcount, 1);
+      g.qitems[pos] = make_int4((int)k, __float_as_int(best), bi, 0);
+    }
+  }
+  warp_stats(g.stats, n_cand, n_rows);
+}
+
+__global__ void __launch_bounds__(128) nn_far_kernel(NnGeom g) {
+  const int G = g.G;
+  const long long G3 = (long long)G * G * G;
+  const float h = 2.f / (float)G;
+  const int lane = threadIdx.x & 31;
+  const int nq = *g.qcount;
+  unsigned long long n_cand = 0, n_rows = 0;
+  while (true) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(g.qcount + 1, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= nq) break;
+    const int4 it = g.qitems[item];
+    const long long k = it.x;
+    const int s = set_of(k, g.q_uniform, g.q_off, g.nsets);
+    const float4 q = g.qs[k];
+    const long long cb = set_base(s, g.c_uniform, g.c_off);
+    const int* st = g.cstart + s * (G3 + 1);
+    const int cx = cell_axis(q.x, G), cy = cell_axis(q.y, G), cz = cell_axis(q.z, G);
+    float best = __int_as_float(it.y);
+    int bi = it.z;
+    for (int ring = NN_NEAR_RINGS + 1; ring < G; ++ring) {
+      const int za = max(cz - ring, 0), zb = min(cz + ring, G - 1);
+      const int ya = max(cy - ring, 0), yb = min(cy + ring, G - 1);
+      const int ny = yb - ya + 1, nrows = (zb - za + 1) * ny;
+      for (int p = lane; p < nrows; p += 32) {
+        const int z = za + p / ny, y = ya + p % ny;
+        ++n_rows;
+        scan_row(g, st, cb, z, y, cx, cy, cz, ring, q, best, bi, n_cand);
+      }
+      // warp minimum of (best, index)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob < best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
         }
       }
-      // distance to the unexplored region
-      float lb = FLT_MAX;
-      if (x0 > 0) lb = fminf(lb, q.x - fmaf((float)x0, h, -1.f));
-      if (x1 < G - 1) lb = fminf(lb, fmaf((float)(x1 + 1), h, -1.f) - q.x);
-      if (y0 > 0) lb = fminf(lb, q.y - fmaf((float)y0, h, -1.f));
-      if (y1 < G - 1) lb = fminf(lb, fmaf((float)(y1 + 1), h, -1.f) - q.y);
-      if (z0 > 0) lb = fminf(lb, q.z - fmaf((float)z0, h, -1.f));
-      if (z1 < G - 1) lb = fminf(lb, fmaf((float)(z1 + 1), h, -1.f) - q.z);
-      if (lb == FLT_MAX) break;
-      lb -= 4e-6f;
-      if (lb > 0.f && best < lb * lb * (1.f - 1e-5f)) break;
+      if (ring_done(ring_bound(q, cx, cy, cz, ring, G, h), best)) break;
     }
-    const long long ob = set_base(s, q_uniform, q_off) + local;
-    out_idx[ob] = bi;
-    if (out_d) out_d[ob] = best;
+    if (lane == 0) {
+      const long long ob = set_base(s, g.q_uniform, g.q_off) + __float_as_int(q.w);
+      g.out_idx[ob] = bi;
+      if (g.out_d) g.out_d[ob] = best;
+    }
   }
+  warp_stats(g.stats, n_cand, n_rows);
 }
 
 cudaError_t launch_nn(const float4* queries_sorted, long long q_uniform, const long long* q_off,
                       int nsets, long long q_total, const Buckets& cand,
                       const long long* c_off, long long c_uniform, int* out_idx, float* out_d,
-                      cudaStream_t s) {
+                      NnQueue queue, cudaStream_t s, unsigned long long* stats) {
   if (q_total == 0) return cudaSuccess;
-  nn_kernel<<<grid_blocks(q_total, 128), 128, 0, s>>>(queries_sorted, q_uniform, q_off, nsets,
-                                                      q_total, cand.sorted, cand.cell_start, cand.G,
-                                                      c_off, c_uniform, out_idx, out_d);
+  NnGeom g{queries_sorted, q_uniform, q_off, nsets, q_total, cand.sorted, cand.cell_start,
+           cand.G, c_off, c_uniform, out_idx, out_d, stats, queue.counters, queue.items};
+  cudaError_t e = cudaMemsetAsync(queue.counters, 0, 2 * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  nn_near_kernel<<<grid_blocks(q_total, 128), 128, 0, s>>>(g);
+  nn_far_kernel<<<queue.far_blocks, 128, 0, s>>>(g);
   return cudaGetLastError();
 }
 
@@ -242,25 +367,31 @@ __device__ __forceinline__ float resid_sq(float4 x, float4 d, float4 p) {
   return rx * rx + ry * ry + rz * rz;
 }
 
+// Grid (T, LOSS_SPLIT): block (t, b) sums a strided share of frame t; the
+// partial sums are combined in a fixed order by loss_final_kernel.
+constexpr int LOSS_SPLIT = 8;
+
 __global__ void __launch_bounds__(256) loss_frame_kernel(
     const int* __restrict__ nn_x, const int* __restrict__ nn_p, const long long* __restrict__ off,
     const float4* __restrict__ praw, const float4* __restrict__ xr,
     const float4* __restrict__ disp, const int2* __restrict__ edges, int N, int E, int t_key,
-    double* __restrict__ cd, double* __restrict__ iso_t) {
+    double* __restrict__ part) {
   __shared__ double sh[32];
   const int t = blockIdx.x;
+  const int stride = blockDim.x * LOSS_SPLIT;
+  const int first = blockIdx.y * blockDim.x + threadIdx.x;
   const long long b = off[t], e = off[t + 1];
   const float4* Dl = disp + (long long)t * N;
   const float4* Dk = disp + (long long)t_key * N;
   double sx = 0.0, sp = 0.0, si = 0.0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x)
+  for (int i = first; i < N; i += stride)
     sx += (double)resid_sq(xr[i], Dl[i], praw[b + nn_x[(long long)t * N + i]]);
-  for (long long j = b + threadIdx.x; j < e; j += blockDim.x) {
+  for (long long j = b + first; j < e; j += stride) {
     const int i = nn_p[j];
     sp += (double)resid_sq(xr[i], Dl[i], praw[j]);
   }
   if (t != t_key) {
-    for (int k = threadIdx.x; k < E; k += blockDim.x) {
+    for (int k = first; k < E; k += stride) {
       const int a0 = edges[k].x, b0 = edges[k].y;
       const float4 xa = xr[a0], xb = xr[b0], da = Dl[a0], db = Dl[b0], ka = Dk[a0], kb = Dk[b0];
       float3 et;
@@ -275,9 +406,27 @@ __global__ void __launch_bounds__(256) loss_frame_kernel(
   sp = block_sum(sp, sh);
   si = block_sum(si, sh);
   if (threadIdx.x == 0) {
-    cd[t] = sx / (double)N + sp / (double)(e - b);
-    iso_t[t] = si;
+    double* o = part + ((long long)t * LOSS_SPLIT + blockIdx.y) * 3;
+    o[0] = sx;
+    o[1] = sp;
+    o[2] = si;
   }
+}
+
+__global__ void loss_combine_kernel(const double* __restrict__ part,
+                                    const long long* __restrict__ off, int N, int T,
+                                    double* __restrict__ cd, double* __restrict__ iso_t) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  double sx = 0.0, sp = 0.0, si = 0.0;
+  for (int b = 0; b < LOSS_SPLIT; ++b) {
+    const double* o = part + ((long long)t * LOSS_SPLIT + b) * 3;
+    sx += o[0];
+    sp += o[1];
+    si += o[2];
+  }
+  cd[t] = sx / (double)N + sp / (double)(off[t + 1] - off[t]);
+  iso_t[t] = si;
 }
 
 // Eq. 11-12 (cumulative products outward from the keyframe), Eq. 10, 13, 8.
@@ -312,9 +461,11 @@ __global__ void loss_final_kernel(const double* __restrict__ cd, const double* _
 }
 
 cudaError_t launch_loss(npg_ctx* c) {
-  loss_frame_kernel<<<c->T, 256, 0, c->stream>>>(c->nn_x, c->nn_p, c->p_off, c->praw, c->xr,
-                                                 c->disp, c->edges, c->N, c->E, c->t_key, c->cd,
-                                                 c->iso_t);
+  loss_frame_kernel<<<dim3(c->T, LOSS_SPLIT), 256, 0, c->stream>>>(
+      c->nn_x, c->nn_p, c->p_off, c->praw, c->xr, c->disp, c->edges, c->N, c->E, c->t_key,
+      c->loss_part);
+  loss_combine_kernel<<<(c->T + 127) / 128, 128, 0, c->stream>>>(c->loss_part, c->p_off, c->N,
+                                                                 c->T, c->cd, c->iso_t);
   loss_final_kernel<<<1, 32, 0, c->stream>>>(c->cd, c->iso_t, c->d_epoch, c->cfg.e_max,
                                              c->T, c->t_key, c->E, (double)c->cfg.w_iso, c->wconf,
                                              c->loss);

@@ -412,8 +412,11 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
         alloc_n(c, c->nn_p, c->MT_cap) && alloc_n(c, c->d_p, c->MT_cap) &&
         alloc_n(c, c->dz, (long long)N * md.Z);
   ok &= alloc_n(c, c->cd, T) && alloc_n(c, c->wconf, T) && alloc_n(c, c->iso_t, T) &&
+        alloc_n(c, c->loss_part, (long long)T * 8 * 3) &&
         alloc_n(c, c->loss, 4) && alloc_n(c, c->d_epoch, 1) && alloc_n(c, c->d_adam_c, 2) &&
-        alloc_n(c, c->d_err, 1);
+        alloc_n(c, c->d_err, 1) && alloc_n(c, c->d_nnstats, 4) &&
+        alloc_n(c, c->nnq.counters, 4) && alloc_n(c, c->nnq.items, std::max(NT, c->MT_cap));
+  c->nnq.far_blocks = c->num_sms * 16;
   ok &= alloc_n(c, c->grid, c->grid_dev_len) && alloc_n(c, c->g_grid, c->grid_dev_len) &&
         alloc_n(c, c->g_pc, c->grid_dev_len) && alloc_n(c, c->m_grid, c->grid_dev_len) &&
         alloc_n(c, c->v_grid, c->grid_dev_len);
@@ -493,6 +496,7 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
   CK(c, cudaMemsetAsync(c->g_mlp, 0, sizeof(float) * c->mlp_len, c->stream));
   CK(c, cudaMemsetAsync(c->d_epoch, 0, sizeof(int), c->stream));
   CK(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  CK(c, cudaMemsetAsync(c->d_nnstats, 0, sizeof(unsigned long long) * 4, c->stream));
   if ((rc = set_points_impl(c, points, frame_offsets, inputs_on_device))) return fail(rc);
   CK(c, cudaStreamSynchronize(c->stream));
   c->phase = 0;
@@ -529,16 +533,17 @@ static int loss_launch(npg_ctx* c) {
   CK(c, bucket_build(c->xhat, nullptr, c->N, c->T, NT, c->xb.G, c->xb, c->stream));
   mark(c, 3);
   // vertex -> point (queries in x-hat bucket order for coherent warps)
+  const bool count = c->tev && !c->capturing && c->t_cur >= 0;
   CK(c, launch_nn(c->xb.sorted, c->N, nullptr, c->T, NT, c->pb, c->p_off, 0, c->nn_x, c->d_x,
-                  c->stream));
+                  c->nnq, c->stream, count ? c->d_nnstats : nullptr));
   mark(c, 4);
   // point -> vertex
   CK(c, launch_nn(c->pb.sorted, 0, c->p_off, c->T, c->MT, c->xb, nullptr, c->N, c->nn_p, c->d_p,
-                  c->stream));
+                  c->nnq, c->stream, count ? c->d_nnstats + 2 : nullptr));
   mark(c, 5);
   CK(c, launch_loss(c));
   mark(c, 6);
-  c->launches += 3 + 2 + 2;
+  c->launches += 3 + 4 + 3;
   return NPG_OK;
 }
 
@@ -923,6 +928,18 @@ extern "C" int npg_timing(npg_ctx* c, int n_iters) {
   for (int k = 0; k < n_iters; ++k) c->t_mask[k] = 0;
   c->t_slots = n_iters;
   c->t_next = 0;
+  CK(c, cudaMemsetAsync(c->d_nnstats, 0, sizeof(unsigned long long) * 4, c->stream));
+  return NPG_OK;
+}
+
+extern "C" int npg_search_stats(npg_ctx* c, long long* out4) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!out4) return set_err(c, NPG_EINVAL, "out4 is NULL");
+  unsigned long long h[4];
+  CK(c, cudaMemcpyAsync(h, c->d_nnstats, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 4; ++k) out4[k] = (long long)h[k];
   return NPG_OK;
 }
 
@@ -984,8 +1001,11 @@ extern "C" int npg_nearest(const float* q, int nq, const float* cand, int nc, in
   cb.nsets = 1;
   float4 *q4 = nullptr, *c4 = nullptr, *qs = nullptr;
   int *qslot = nullptr;
+  NnQueue queue;
+  queue.far_blocks = 152 * 16;
   auto cleanup = [&]() {
     cudaFreeAsync(q4, s); cudaFreeAsync(c4, s); cudaFreeAsync(qs, s); cudaFreeAsync(qslot, s);
+    cudaFreeAsync(queue.counters, s); cudaFreeAsync(queue.items, s);
     cudaFreeAsync(cb.cell_start, s); cudaFreeAsync(cb.counts, s); cudaFreeAsync(cb.slot, s);
     cudaFreeAsync(cb.sorted, s); cudaFreeAsync(qb.cell_start, s); cudaFreeAsync(qb.counts, s);
   };
@@ -1003,6 +1023,8 @@ extern "C" int npg_nearest(const float* q, int nq, const float* cand, int nc, in
   A((void**)&cb.sorted, sizeof(float4) * nc);
   A((void**)&qb.cell_start, sizeof(int) * (G3 + 1));
   A((void**)&qb.counts, sizeof(int) * G3);
+  A((void**)&queue.counters, sizeof(int) * 2);
+  A((void**)&queue.items, sizeof(int4) * nq);
   if (e == cudaSuccess) e = launch_points_to_float4(q, q4, nq, s);
   if (e == cudaSuccess) e = launch_points_to_float4(cand, c4, nc, s);
   if (e == cudaSuccess) e = bucket_build(c4, nullptr, nc, 1, nc, G, cb, s);
@@ -1012,7 +1034,7 @@ extern "C" int npg_nearest(const float* q, int nq, const float* cand, int nc, in
   qb.slot = qslot;
   qb.sorted = qs;
   if (e == cudaSuccess) e = bucket_build(q4, nullptr, nq, 1, nq, G, qb, s);
-  if (e == cudaSuccess) e = launch_nn(qs, nq, nullptr, 1, nq, cb, nullptr, nc, idx, dist, s);
+  if (e == cudaSuccess) e = launch_nn(qs, nq, nullptr, 1, nq, cb, nullptr, nc, idx, dist, queue, s);
   cleanup();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "npg_nearest");

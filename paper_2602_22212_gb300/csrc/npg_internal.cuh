@@ -38,6 +38,13 @@ struct Buckets {
   float4* sorted = nullptr;   // per point, in cell order: (x, y, z, bits(local index))
 };
 
+// Work queue of the far-query pass of the nearest-neighbour search.
+struct NnQueue {
+  int* counters = nullptr;  // 2 ints: pushed, popped
+  int4* items = nullptr;    // capacity >= number of queries
+  int far_blocks = 1;
+};
+
 struct MlpDims {
   int H, D, K, Z, NO, M;  // hidden width, hidden layers, first-layer inputs, latent, outputs, freqs
   float slope;
@@ -88,6 +95,7 @@ struct npg_ctx {
   double* cd = nullptr;    // T
   double* wconf = nullptr; // T
   double* iso_t = nullptr; // T
+  double* loss_part = nullptr;  // T x 8 x 3 partial sums
   double* loss = nullptr;  // 3: L, L_def, L_iso
   double* h_loss = nullptr;  // pinned host mirror (3 + T)
 
@@ -117,6 +125,8 @@ struct npg_ctx {
   int t_slots = 0, t_next = 0, t_cur = -1;
   int capturing = 0;
   long long launches = 0;
+  unsigned long long* d_nnstats = nullptr;  // per direction: candidates, cell rows (timing mode)
+  npg::NnQueue nnq;
   long long graph_launches = 0;  // kernels in one replay of the captured graph
   int* d_epoch = nullptr;  // device copy of e (read by graph-captured kernels)
   float* d_adam_c = nullptr;  // 1 - beta1^s, 1 - beta2^s of the current step
@@ -146,7 +156,7 @@ cudaError_t bucket_build(const float4* pts, const long long* d_off, long long un
 cudaError_t launch_nn(const float4* queries_sorted, long long q_uniform, const long long* q_off,
                       int nsets, long long q_total, const Buckets& cand,
                       const long long* c_off, long long c_uniform, int* out_idx, float* out_d,
-                      cudaStream_t s);
+                      NnQueue queue, cudaStream_t s, unsigned long long* stats = nullptr);
 cudaError_t launch_loss(npg_ctx* c);
 cudaError_t launch_dxhat(npg_ctx* c);
 cudaError_t launch_mlp_backward_fp32(npg_ctx* c);

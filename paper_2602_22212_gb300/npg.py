@@ -101,6 +101,7 @@ _SIG = {
     "npg_timing": (_i, [_vp, _i]),
     "npg_timing_read": (_i, [_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "npg_launch_count": (C.c_longlong, [_vp]),
+    "npg_search_stats": (_i, [_vp, C.POINTER(C.c_longlong)]),
 }
 for _name, (_res, _args) in _SIG.items():
     _f = getattr(_lib, _name)
@@ -251,6 +252,13 @@ def npg_timing_read(ctx, stage):
     ms, n = C.c_double(0), C.c_int(0)
     _check(_lib.npg_timing_read(ctx, int(stage), C.byref(ms), C.byref(n)), ctx)
     return ms.value, n.value
+
+
+def npg_search_stats(ctx):
+    """(candidates, rows) vertex->point, (candidates, rows) point->vertex."""
+    a = (C.c_longlong * 4)()
+    _check(_lib.npg_search_stats(ctx, a), ctx)
+    return tuple(int(x) for x in a)
 
 
 def npg_launch_count(ctx) -> int:
