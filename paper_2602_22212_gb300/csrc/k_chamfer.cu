@@ -178,30 +178,58 @@ __device__ __forceinline__ void scan_range(const float4* __restrict__ cs, long l
   }
 }
 
-// Scan the cells of row (z, y) that belong to the shell of ring `ring`.
-__device__ __forceinline__ void scan_row(const NnGeom& g, const int* st, long long cb, int z,
+// Distance from coordinate v to the extent of cell c along one axis, less a
+// slack for FP32 rounding of the cell assignment; the boundary cells extend
+// to infinity (they hold the clamped points).
+__device__ __forceinline__ float axis_gap(float v, int c, int G, float h) {
+  const float lo = c == 0 ? -FLT_MAX : fmaf((float)c, h, -1.f);
+  const float hi = c == G - 1 ? FLT_MAX : fmaf((float)(c + 1), h, -1.f);
+  const float gap = v < lo ? lo - v : (v > hi ? v - hi : 0.f);
+  return fmaxf(gap - 4e-6f, 0.f);
+}
+
+// Scan the cells of row (z, y) that belong to the shell of ring `ring` and
+// can still hold a point at squared distance <= best: a row whose (y, z)
+// extent is farther than best is skipped, and only the x cells within reach
+// of the best-ball are read (with a relative margin, so ties are kept).
+// Returns whether the row's cell starts were read.
+__device__ __forceinline__ bool scan_row(const NnGeom& g, const int* st, long long cb, int z,
                                          int y, int cx, int cy, int cz, int ring, float4 q,
-                                         float& best, int& bi, unsigned long long& nc) {
+                                         float h, float& best, int& bi,
+                                         unsigned long long& nc) {
   const int G = g.G;
+  const float gz = axis_gap(q.z, z, G, h), gy = axis_gap(q.y, y, G, h);
+  const float base = gz * gz + gy * gy;
+  const float reach = best * (1.f + 2e-5f);
+  if (base > reach) return false;
+  const float rx = fminf(sqrtf(reach - base) + 4e-6f, 8.f);
+  const int xlo = cell_axis(q.x - rx, G), xhi = cell_axis(q.x + rx, G);
   const int x0 = cx - ring, x1 = cx + ring;
   const bool full = (z == cz - ring || z == cz + ring || y == cy - ring || y == cy + ring);
   const int row = (z * G + y) * G;
   if (full) {
-    const int lo = st[row + max(x0, 0)], hi = st[row + min(x1, G - 1) + 1];
+    const int a = max(max(x0, 0), xlo), b = min(min(x1, G - 1), xhi);
+    if (a > b) return false;
+    const int lo = st[row + a], hi = st[row + b + 1];
     nc += (unsigned long long)(hi - lo);
     scan_range(g.cs, cb, lo, hi, q, best, bi);
   } else {
-    if (x0 >= 0) {
+    bool any = false;
+    if (x0 >= 0 && x0 >= xlo && x0 <= xhi) {
       const int lo = st[row + x0], hi = st[row + x0 + 1];
       nc += (unsigned long long)(hi - lo);
       scan_range(g.cs, cb, lo, hi, q, best, bi);
+      any = true;
     }
-    if (x1 <= G - 1 && x1 != x0) {
+    if (x1 <= G - 1 && x1 != x0 && x1 >= xlo && x1 <= xhi) {
       const int lo = st[row + x1], hi = st[row + x1 + 1];
       nc += (unsigned long long)(hi - lo);
       scan_range(g.cs, cb, lo, hi, q, best, bi);
+      any = true;
     }
+    if (!any) return false;
   }
+  return true;
 }
 
 // Squared lower bound on the distance to any cell outside rings 0..ring
@@ -258,10 +286,8 @@ __global__ void __launch_bounds__(128) nn_near_kernel(NnGeom g) {
     bool done = false;
     for (int ring = 0; ring <= NN_NEAR_RINGS && ring < G; ++ring) {
       for (int z = max(cz - ring, 0); z <= min(cz + ring, G - 1); ++z)
-        for (int y = max(cy - ring, 0); y <= min(cy + ring, G - 1); ++y) {
-          ++n_rows;
-          scan_row(g, st, cb, z, y, cx, cy, cz, ring, q, best, bi, n_cand);
-        }
+        for (int y = max(cy - ring, 0); y <= min(cy + ring, G - 1); ++y)
+          n_rows += scan_row(g, st, cb, z, y, cx, cy, cz, ring, q, h, best, bi, n_cand) ? 1 : 0;
       if (ring_done(ring_bound(q, cx, cy, cz, ring, G, h), best)) {
         done = true;
         break;
@@ -306,8 +332,7 @@ __global__ void __launch_bounds__(128) nn_far_kernel(NnGeom g) {
       const int ny = yb - ya + 1, nrows = (zb - za + 1) * ny;
       for (int p = lane; p < nrows; p += 32) {
         const int z = za + p / ny, y = ya + p % ny;
-        ++n_rows;
-        scan_row(g, st, cb, z, y, cx, cy, cz, ring, q, best, bi, n_cand);
+        n_rows += scan_row(g, st, cb, z, y, cx, cy, cz, ring, q, h, best, bi, n_cand) ? 1 : 0;
       }
       // warp minimum of (best, index)
 #pragma unroll
