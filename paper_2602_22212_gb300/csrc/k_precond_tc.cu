@@ -9,12 +9,14 @@
 // (the dropped lo.lo term is below 2^-16 relative), accumulated in FP32 in
 // TMEM: about 1e-5 relative per pass.
 //
-// CTA = 128 threads, tile = all r output rows (one or two 128-row MMA
-// blocks) x 128 columns; K (the transformed axis n) streamed in chunks of 64.
-// Each chunk: the tables' hi/lo rows are copied into K-major swizzled tiles,
-// the input columns are loaded, split and written as MN-major tiles, then one
-// thread issues 12 MMAs per 128-row block. The epilogue stores the rotated
-// layout with coalesced float4 writes (F = 4) or scalar writes.
+// Persistent, warp-specialised CTA of 288 threads, one per SM, looping over
+// column tiles of 128: the tile covers all r output rows (one or two 128-row
+// MMA blocks); K (the transformed axis n) is streamed in chunks of 64 through
+// a two-stage shared-memory ring. Per chunk, a bulk copy brings the tables'
+// pre-swizzled hi/lo rows, the producer warps load, split and store the input
+// columns as MN-major tiles, and one thread issues 12 MMAs per 128-row block
+// into one of two TMEM accumulators while the epilogue warps drain the other
+// with coalesced rotated stores (float4 for F = 4).
 #include <cuda_bf16.h>
 
 #include "npg_internal.cuh"
@@ -23,18 +25,20 @@
 namespace npg {
 
 namespace {
-constexpr uint32_t TILE_A = 128 * 128;  // [128][64] BF16
+constexpr uint32_t TILE_A = 128 * 128;  // [128][64] BF16, 128B-swizzled
 constexpr uint32_t ATOM_B = 64 * 128;   // MN-major atom: 64 K-rows x 64 columns BF16
-constexpr uint32_t WAIT = 1u << 24;
+constexpr uint32_t WAIT = 1u << 22;
+constexpr int PRODUCERS = 128, EPILOGUE = 128, THREADS = PRODUCERS + EPILOGUE + 32;
 
+// Per stage: A chunk [hi m0, hi m1, lo m0, lo m1] (a straight copy of the
+// pre-swizzled table chunk), B chunk [hi (2 atoms), lo (2 atoms)].
 struct PcSmem {
-  // A: [hi m0, hi m1, lo m0, lo m1], B: [hi (2 atoms), lo (2 atoms)]
-  static constexpr uint32_t A = 0;
-  static constexpr uint32_t B = 4 * TILE_A;
-  static constexpr uint32_t MU = B + 4 * ATOM_B;
+  static constexpr uint32_t STAGE = 4 * TILE_A + 4 * ATOM_B;  // 96 KB
+  static constexpr uint32_t MU = 2 * STAGE;
+  // full[2], empty[2], acc_full[2], acc_empty[2], fin
   static constexpr uint32_t BAR = MU + 1024 * 4;
-  static constexpr uint32_t TMEMP = BAR + 8;
-  static constexpr uint32_t TOTAL = TMEMP + 8;
+  static constexpr uint32_t FLAGS = BAR + 9 * 8;
+  static constexpr uint32_t TOTAL = FLAGS + 16;
 };
 
 __device__ __forceinline__ uint32_t mn_off(uint32_t m, uint32_t k) {
@@ -56,163 +60,239 @@ __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
   hi = make_uint4(h[0], h[1], h[2], h[3]);
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
+
+// Bounded wait shared by every role; gives up (and flags the CTA) once any
+// thread of the CTA has timed out.
+__device__ __forceinline__ bool pc_wait(uint64_t* bar, uint32_t phase, volatile int* abort,
+                                        int* err) {
+  for (uint32_t k = 0; k < WAIT; ++k) {
+    if (tc::mbar_try_wait(bar, phase)) return true;
+    if ((k & 1023u) == 1023u && *abort) return false;
+  }
+  *abort = 1;
+  atomicExch(err, 1);
+  return false;
+}
 }  // namespace
 
-// tabs: hi then lo, each [rm][rk] BF16 row-major (rm = nM * 128, rk = K chunks * 64),
-// zero-padded.
+// One pass, persistent and warp-specialised: warps 0-3 produce (bulk copy of
+// the table chunk, load + split of the input chunk) into a two-stage ring,
+// warp 8 issues the MMAs into one of two TMEM accumulators, warps 4-7 drain
+// the other accumulator to global memory. CTAs loop over column tiles of 128.
+// tabs: pre-swizzled chunks [kc][hi m0, hi m1, lo m0, lo m1] of 16 KB each.
 template <bool SCALE>
-__global__ void __launch_bounds__(128) dct_pass_tc_kernel(const float* __restrict__ in,
-                                                          float* __restrict__ out,
-                                                          const __nv_bfloat16* __restrict__ tabs,
-                                                          const float* __restrict__ mu, int r,
-                                                          int F, float lambda, int* err) {
+__global__ void __launch_bounds__(THREADS, 1) dct_pass_tc_kernel(
+    const float* __restrict__ in, float* __restrict__ out, const uint8_t* __restrict__ tabs,
+    const float* __restrict__ mu, int r, int F, float lambda, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + PcSmem::BAR);
-  uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + PcSmem::TMEMP);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + PcSmem::BAR);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + 2;
+  uint64_t* acc_full = bars + 4;
+  uint64_t* acc_empty = bars + 6;
+  uint64_t* fin = bars + 8;
+  volatile int* abort = reinterpret_cast<volatile int*>(sm + PcSmem::FLAGS);
+  uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + PcSmem::FLAGS + 4);
   float* smu = reinterpret_cast<float*>(sm + PcSmem::MU);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nM = (r + 127) >> 7, nK = (r + 63) >> 6;
-  const int rm = nM * 128, rk = nK * 64;
+  const uint32_t a_bytes = (uint32_t)nM * 2u * TILE_A;
+  const uint32_t acc_cols = (uint32_t)nM * 128u;
+  const uint32_t tm_cols = nM == 2 ? 512u : 256u;
   const long long ncol = (long long)r * r * F;
-  const long long col0 = (long long)blockIdx.x * 128;
-  for (int k = tid; k < r; k += 128) smu[k] = mu[k];
+  const long long ntiles = (ncol + 127) / 128;
+  for (int k = tid; k < r; k += THREADS) smu[k] = mu[k];
   if (tid == 0) {
-    tc::mbar_init(bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(full + b, PRODUCERS + 1);
+      tc::mbar_init(empty + b, 1);
+      tc::mbar_init(acc_full + b, 1);
+      tc::mbar_init(acc_empty + b, EPILOGUE);
+    }
+    tc::mbar_init(fin, 1);
+    *abort = 0;
     tc::fence_mbar_init();
   }
-  if (warp == 0) {
-    tc::tmem_alloc(tmem_ptr, 256);
+  if (warp == 8) {
+    tc::tmem_alloc(tmem_ptr, tm_cols);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_ptr;
-  const uint32_t sA = tc::smem_u32(sm + PcSmem::A), sB = tc::smem_u32(sm + PcSmem::B);
-  constexpr uint32_t IDESC = tc::idesc_bf16(128, 128, false, true);
-  const bool vec = (ncol & 3) == 0;
-  uint32_t phase = 0;
-  bool ok = true;
 
-  for (int kc = 0; kc < nK && ok; ++kc) {
-    // A: table rows [mt 128, +128) x columns [kc 64, +64), hi and lo
-    const __nv_bfloat16* th = tabs;
-    const __nv_bfloat16* tl = tabs + (long long)rm * rk;
-    for (int e = tid; e < nM * 128 * 8; e += 128) {
-      const int row = e >> 3, c = e & 7;  // row < nM * 128, 16-byte chunk c
-      const long long g = (long long)row * rk + kc * 64 + c * 8;
-      const uint4 vh = *reinterpret_cast<const uint4*>(th + g);
-      const uint4 vl = *reinterpret_cast<const uint4*>(tl + g);
-      const int mt = row >> 7, rr = row & 127;
-      *reinterpret_cast<uint4*>(sm + PcSmem::A + mt * TILE_A + tc::sw128_off(rr, c * 8)) = vh;
-      *reinterpret_cast<uint4*>(sm + PcSmem::A + (2 + mt) * TILE_A + tc::sw128_off(rr, c * 8)) =
-          vl;
-    }
-    // B: input rows n in [kc 64, +64) x columns [col0, col0 + 128), split hi / lo
-    for (int e = tid; e < 64 * 16; e += 128) {
-      const int kk = e >> 4, g8 = e & 15;  // K-row, group of 8 columns
-      const int n = kc * 64 + kk;
-      const long long c0 = col0 + g8 * 8;
-      float x[8];
-      if (n < r && vec && c0 + 8 <= ncol) {
-        const float4* p = reinterpret_cast<const float4*>(in + (long long)n * ncol + c0);
-        const float4 a = p[0], b = p[1];
-        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
-      } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          x[j] = (n < r && c0 + j < ncol) ? in[(long long)n * ncol + c0 + j] : 0.f;
-      }
-      uint4 hi, lo;
-      split8(x, hi, lo);
-      const uint32_t o = mn_off((uint32_t)(g8 * 8), (uint32_t)kk);
-      *reinterpret_cast<uint4*>(sm + PcSmem::B + o) = hi;
-      *reinterpret_cast<uint4*>(sm + PcSmem::B + 2 * ATOM_B + o) = lo;
-    }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (tid == 0) {
-      for (int mt = 0; mt < nM; ++mt) {
-        const uint32_t d = tmem + mt * 128;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint64_t ah = tc::kmajor_sw128(sA + mt * TILE_A + 32 * ks);
-          const uint64_t al = tc::kmajor_sw128(sA + (2 + mt) * TILE_A + 32 * ks);
-          const uint64_t bh = tc::mnmajor_sw128(sB + 2048 * ks, ATOM_B, 1024);
-          const uint64_t bl = tc::mnmajor_sw128(sB + 2 * ATOM_B + 2048 * ks, ATOM_B, 1024);
-          tc::mma_bf16(d, ah, bh, IDESC, (kc > 0 || ks > 0) ? 1u : 0u);
-          tc::mma_bf16(d, ah, bl, IDESC, 1u);
-          tc::mma_bf16(d, al, bh, IDESC, 1u);
+  if (warp < 4) {
+    // ------------------------------------------------------------ producers
+    // Thread 0 arrives with the table copy's transaction count when it issues
+    // it; every producer arrives once its share of the input chunk is stored.
+    uint32_t u = 0, last_copy = 0;
+    bool copied = false;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const long long col0 = tile * 128;
+      for (int kc = 0; kc < nK; ++kc, ++u) {
+        const uint32_t s = u & 1u, ph = (u >> 1) & 1u;
+        if (!pc_wait(empty + s, ph ^ 1u, abort, err)) goto producers_done;
+        uint8_t* st = sm + s * PcSmem::STAGE;
+        if (tid == 0) {
+          tc::mbar_arrive_expect_tx(full + s, a_bytes);
+          tc::bulk_g2s(st, tabs + (size_t)kc * a_bytes, a_bytes, full + s);
+          last_copy = u;
+          copied = true;
         }
+        uint8_t* sb = st + 4 * TILE_A;
+        // 64 K-rows x 16 groups of 8 columns; all loads issued before any store.
+        constexpr int PER = 64 * 16 / PRODUCERS;
+        float x[PER][8];
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+          const int e = tid + i * PRODUCERS;
+          const int n = kc * 64 + (e >> 4);
+          const long long c0 = col0 + (e & 15) * 8;
+          if (n < r && (ncol & 3) == 0 && c0 + 8 <= ncol) {
+            const float4* p = reinterpret_cast<const float4*>(in + (long long)n * ncol + c0);
+            const float4 a = __ldcs(p), b = __ldcs(p + 1);
+            x[i][0] = a.x; x[i][1] = a.y; x[i][2] = a.z; x[i][3] = a.w;
+            x[i][4] = b.x; x[i][5] = b.y; x[i][6] = b.z; x[i][7] = b.w;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              x[i][j] = (n < r && c0 + j < ncol) ? in[(long long)n * ncol + c0 + j] : 0.f;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+          const int e = tid + i * PRODUCERS;
+          uint4 hi, lo;
+          split8(x[i], hi, lo);
+          const uint32_t o = mn_off((uint32_t)((e & 15) * 8), (uint32_t)(e >> 4));
+          *reinterpret_cast<uint4*>(sb + o) = hi;
+          *reinterpret_cast<uint4*>(sb + 2 * ATOM_B + o) = lo;
+        }
+        tc::fence_async_smem();
+        tc::mbar_arrive(full + s);
       }
-      tc::mma_commit(bar);
     }
-    bool w = tc::mbar_wait(bar, phase, WAIT);
-    phase ^= 1u;
-    w = __syncthreads_and(w) != 0;
-    if (!w) {
-      ok = false;
-      if (tid == 0) atomicExch(err, 1);
+  producers_done:
+    // Do not leave with a table copy in flight (bounded).
+    if (tid == 0 && copied) tc::mbar_wait(full + (last_copy & 1u), (last_copy >> 1) & 1u, WAIT);
+  } else if (warp == 8) {
+    // ------------------------------------------------------------ MMA issuer
+    // The whole warp follows the barriers; lane 0 issues.
+    const bool leader = (tid & 31) == 0;
+    constexpr uint32_t IDESC = tc::idesc_bf16(128, 128, false, true);
+    uint32_t u = 0, lt = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+      const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
+      if (!pc_wait(acc_empty + acc, aph ^ 1u, abort, err)) break;
+      tc::fence_after_sync();
+      const uint32_t d0 = tmem + acc * acc_cols;
+      bool ok = true;
+      for (int kc = 0; kc < nK; ++kc, ++u) {
+        const uint32_t s = u & 1u, ph = (u >> 1) & 1u;
+        if (!pc_wait(full + s, ph, abort, err)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        if (leader) {
+          const uint32_t sA = tc::smem_u32(sm + s * PcSmem::STAGE);
+          const uint32_t sB = sA + 4 * TILE_A;
+          for (int mt = 0; mt < nM; ++mt) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint64_t ah = tc::kmajor_sw128(sA + mt * TILE_A + 32 * ks);
+              const uint64_t al = tc::kmajor_sw128(sA + (nM + mt) * TILE_A + 32 * ks);
+              const uint64_t bh = tc::mnmajor_sw128(sB + 2048 * ks, ATOM_B, 1024);
+              const uint64_t bl = tc::mnmajor_sw128(sB + 2 * ATOM_B + 2048 * ks, ATOM_B, 1024);
+              const uint32_t d = d0 + mt * 128;
+              tc::mma_bf16(d, ah, bh, IDESC, (kc > 0 || ks > 0) ? 1u : 0u);
+              tc::mma_bf16(d, ah, bl, IDESC, 1u);
+              tc::mma_bf16(d, al, bh, IDESC, 1u);
+            }
+          }
+          tc::mma_commit(empty + s);
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (leader) tc::mma_commit(acc_full + acc);
+      __syncwarp();
     }
-    tc::fence_after_sync();
-  }
-  if (ok) {
+    __syncwarp();
+    // Do not free TMEM with MMAs in flight (bounded).
+    if (leader) tc::mma_commit(fin);
+    __syncwarp();
+    tc::mbar_wait(fin, 0, WAIT);
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int et = tid - PRODUCERS;  // 0..127 = TMEM lane
+    const uint32_t qlane = (uint32_t)((warp & 3) * 32) << 16;
     const long long rF = (long long)r * F;
-    for (int mt = 0; mt < nM; ++mt) {
-      const int k = mt * 128 + tid;  // output row of this lane
-      const uint32_t lane = tmem + mt * 128 + ((uint32_t)(warp * 32) << 16);
-      for (int cg = 0; cg < 128; cg += 16) {
-        uint32_t v[16];
-        tc::tmem_ld16(lane + cg, v);
-        tc::tmem_ld_wait();
-        if (k >= r) continue;
-        if (F == 4) {
+    uint32_t lt = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+      const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
+      if (!pc_wait(acc_full + acc, aph, abort, err)) break;
+      tc::fence_after_sync();
+      const long long col0 = tile * 128;
+      for (int mt = 0; mt < nM; ++mt) {
+        const int k = mt * 128 + et;
+        const uint32_t lane = tmem + acc * acc_cols + mt * 128 + qlane;
+        for (int cg = 0; cg < 128; cg += 16) {
+          uint32_t v[16];
+          tc::tmem_ld16(lane + cg, v);
+          tc::tmem_ld_wait();
+          if (k >= r) continue;
+          if (F == 4) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const long long col = col0 + cg + 4 * q;
-            if (col >= ncol) break;
-            const long long p = col >> 2;
-            float s = 1.f;
-            if (SCALE) {
-              const float d = 1.f + lambda * (smu[p / r] + smu[p % r] + smu[k]);
-              s = 1.f / (d * d);
+            for (int q = 0; q < 4; ++q) {
+              const long long col = col0 + cg + 4 * q;
+              if (col >= ncol) break;
+              const long long p = col >> 2;
+              float sc = 1.f;
+              if (SCALE) {
+                const float dd = 1.f + lambda * (smu[p / r] + smu[p % r] + smu[k]);
+                sc = 1.f / (dd * dd);
+              }
+              __stcs(reinterpret_cast<float4*>(out + p * rF + (long long)k * 4),
+                     make_float4(__uint_as_float(v[4 * q]) * sc, __uint_as_float(v[4 * q + 1]) * sc,
+                                 __uint_as_float(v[4 * q + 2]) * sc,
+                                 __uint_as_float(v[4 * q + 3]) * sc));
             }
-            float4 o4 = make_float4(__uint_as_float(v[4 * q]) * s, __uint_as_float(v[4 * q + 1]) * s,
-                                    __uint_as_float(v[4 * q + 2]) * s,
-                                    __uint_as_float(v[4 * q + 3]) * s);
-            *reinterpret_cast<float4*>(out + p * rF + (long long)k * 4) = o4;
-          }
-        } else {
+          } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const long long col = col0 + cg + j;
-            if (col >= ncol) break;
-            const long long p = col / F;
-            const int c = (int)(col - p * F);
-            float s = 1.f;
-            if (SCALE) {
-              const float d = 1.f + lambda * (smu[p / r] + smu[p % r] + smu[k]);
-              s = 1.f / (d * d);
+            for (int j = 0; j < 16; ++j) {
+              const long long col = col0 + cg + j;
+              if (col >= ncol) break;
+              const long long p = col / F;
+              const int c = (int)(col - p * F);
+              float sc = 1.f;
+              if (SCALE) {
+                const float dd = 1.f + lambda * (smu[p / r] + smu[p % r] + smu[k]);
+                sc = 1.f / (dd * dd);
+              }
+              out[p * rF + (long long)k * F + c] = __uint_as_float(v[j]) * sc;
             }
-            out[p * rF + (long long)k * F + c] = __uint_as_float(v[j]) * s;
           }
         }
       }
+      tc::fence_before_sync();
+      tc::mbar_arrive(acc_empty + acc);
     }
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+  if (warp == 8) {
+    __syncwarp();
+    tc::tmem_dealloc(tmem, tm_cols);
+  }
 }
 
 size_t dct_tc_table_elems(int r) {
   const int nM = (r + 127) / 128, nK = (r + 63) / 64;
-  return (size_t)2 * (nM * 128) * (nK * 64);  // hi and lo
+  return (size_t)nK * nM * 2 * (TILE_A / 2);  // BF16 elements
 }
 
 static uint16_t bf16_bits_rne(float f) {
@@ -231,20 +311,29 @@ static float bf16_to_float(uint16_t b) {
   return f;
 }
 
-// Split BF16 tables of an FP32 r x r matrix (row-major) into the padded
-// layout the kernel reads: hi block then lo block.
+// Split BF16 hi / lo tables of an FP32 r x r matrix (row-major), stored as the
+// shared-memory image the kernel copies per K chunk: for chunk kc, the blocks
+// [hi m0, hi m1, lo m0, lo m1], each [128 rows][64 columns] 128B-swizzled.
 void dct_tc_tables(int r, const float* Mx, uint16_t* dst) {
   const int nM = (r + 127) / 128, nK = (r + 63) / 64;
-  const int rm = nM * 128, rk = nK * 64;
-  uint16_t* hi = dst;
-  uint16_t* lo = dst + (size_t)rm * rk;
-  for (int i = 0; i < rm; ++i)
-    for (int j = 0; j < rk; ++j) {
-      const float v = (i < r && j < r) ? Mx[(size_t)i * r + j] : 0.f;
-      const uint16_t h = bf16_bits_rne(v);
-      hi[(size_t)i * rk + j] = h;
-      lo[(size_t)i * rk + j] = bf16_bits_rne(v - bf16_to_float(h));
-    }
+  uint8_t* base = reinterpret_cast<uint8_t*>(dst);
+  memset(base, 0, dct_tc_table_elems(r) * 2);
+  for (int kc = 0; kc < nK; ++kc)
+    for (int part = 0; part < 2; ++part)
+      for (int mt = 0; mt < nM; ++mt) {
+        uint8_t* blk = base + ((size_t)kc * nM * 2 + part * nM + mt) * TILE_A;
+        for (int rr = 0; rr < 128; ++rr)
+          for (int k = 0; k < 64; ++k) {
+            const int i = mt * 128 + rr, j = kc * 64 + k;
+            const float v = (i < r && j < r) ? Mx[(size_t)i * r + j] : 0.f;
+            const uint16_t h = bf16_bits_rne(v);
+            const uint16_t b = part == 0 ? h : bf16_bits_rne(v - bf16_to_float(h));
+            const uint32_t off = (uint32_t)(rr >> 3) * 1024u + (uint32_t)(rr & 7) * 128u +
+                                 ((((uint32_t)(k >> 3)) ^ (uint32_t)(rr & 7)) << 4) +
+                                 (uint32_t)(k & 7) * 2u;
+            memcpy(blk + off, &b, 2);
+          }
+      }
 }
 
 cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float* t1,
@@ -252,6 +341,9 @@ cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float*
                                    int r, int F, float lambda, int* err, cudaStream_t s) {
   const size_t smem = PcSmem::TOTAL + 1024;
   static bool attr = false;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(dct_pass_tc_kernel<false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -262,15 +354,16 @@ cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float*
     attr = true;
   }
   const long long ncol = (long long)r * r * F;
-  const unsigned grid = (unsigned)((ncol + 127) / 128);
-  const __nv_bfloat16* C = reinterpret_cast<const __nv_bfloat16*>(tabC);
-  const __nv_bfloat16* Ct = reinterpret_cast<const __nv_bfloat16*>(tabCt);
-  dct_pass_tc_kernel<false><<<grid, 128, smem, s>>>(g, t0, C, mu, r, F, lambda, err);
-  dct_pass_tc_kernel<false><<<grid, 128, smem, s>>>(t0, t1, C, mu, r, F, lambda, err);
-  dct_pass_tc_kernel<true><<<grid, 128, smem, s>>>(t1, t0, C, mu, r, F, lambda, err);
-  dct_pass_tc_kernel<false><<<grid, 128, smem, s>>>(t0, t1, Ct, mu, r, F, lambda, err);
-  dct_pass_tc_kernel<false><<<grid, 128, smem, s>>>(t1, t0, Ct, mu, r, F, lambda, err);
-  dct_pass_tc_kernel<false><<<grid, 128, smem, s>>>(t0, out, Ct, mu, r, F, lambda, err);
+  const long long tiles = (ncol + 127) / 128;
+  const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
+  const uint8_t* C = reinterpret_cast<const uint8_t*>(tabC);
+  const uint8_t* Ct = reinterpret_cast<const uint8_t*>(tabCt);
+  dct_pass_tc_kernel<false><<<grid, THREADS, smem, s>>>(g, t0, C, mu, r, F, lambda, err);
+  dct_pass_tc_kernel<false><<<grid, THREADS, smem, s>>>(t0, t1, C, mu, r, F, lambda, err);
+  dct_pass_tc_kernel<true><<<grid, THREADS, smem, s>>>(t1, t0, C, mu, r, F, lambda, err);
+  dct_pass_tc_kernel<false><<<grid, THREADS, smem, s>>>(t0, t1, Ct, mu, r, F, lambda, err);
+  dct_pass_tc_kernel<false><<<grid, THREADS, smem, s>>>(t1, t0, Ct, mu, r, F, lambda, err);
+  dct_pass_tc_kernel<false><<<grid, THREADS, smem, s>>>(t0, out, Ct, mu, r, F, lambda, err);
   return cudaGetLastError();
 }
 
