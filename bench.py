@@ -209,6 +209,39 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_micro(args):
+    """Standalone preconditioner call (six DCT passes) on one r^3 x 4 grid
+    level: the small case for kernel profiles. Each call also builds its
+    tables on the host, allocates scratch and synchronises, so ms_per_call is
+    an upper bound on the kernels' time; the in-step stage timing of the
+    benchmark proper is the kernel figure."""
+    import torch
+    from paper_2602_22212_gb300 import build, npg
+    build.build()
+    r, F = args.micro_res, 4
+    stream = torch.cuda.Stream()
+    g = torch.randn(r ** 3 * F, device="cuda")
+    out = torch.empty_like(g)
+    fn = npg.npg_precondition_tc if args.micro == "precond_tc" else npg.npg_precondition
+    lam = 0.4 * 1.5 ** 7
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            fn(g, out, r, F, lam, stream=stream)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fn(g, out, r, F, lam, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    nbytes = 6 * 8 * r ** 3 * F
+    peaks = load_peaks()
+    print(json.dumps({"micro": args.micro, "r": r, "F": F, "ms_per_call": ms,
+                      "algorithmic_bytes": nbytes, "gbs_lower_bound": nbytes / ms / 1e6,
+                      "hbm_peak_gbs": peaks["hbm"], "peak_source": peaks["src"]}))
+
+
 def config_dict(p, seq, form, graph):
     return {"workload": f"{p['gen']} N={seq.N} T={seq.T} M={int(seq.offsets[1])}/frame, "
                         f"{p['L']}-level grid {p['res'][0]}->{p['res'][-1]} x F={p['F']}, "
@@ -235,10 +268,15 @@ def main():
                     help="preconditioner DCT arithmetic (default: tc with bf16, fp32 with fp32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--micro", default=None, choices=["precond_tc", "precond_fp32"],
+                    help="time one kernel family alone on a standalone grid instead of the step")
+    ap.add_argument("--micro-res", type=int, default=256)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.micro:
+        return run_micro(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -272,6 +310,10 @@ def main():
     for _ in range(args.warmup):
         ctx.iteration()
     torch.cuda.synchronize()
+    # the optimisation state the timed region starts from; the stage
+    # attribution and the end-to-end run restart from it, so that all three
+    # see the same nearest-neighbour workload
+    state0 = npg.npg_get_state(ctx.h)
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = npg.npg_launch_count(ctx.h)
@@ -295,6 +337,7 @@ def main():
 
     # per-stage attribution: the same iteration, eager, with CUDA events per stage
     sctx = ctx
+    npg.npg_set_state(ctx.h, state0)
     if graph:
         cfg2 = make_cfg(npg, p, args.precision, False, stream, e_max, precond)
         sctx = npg.Context(cfg2, seq, mlp, device_inputs=True)
@@ -320,6 +363,7 @@ def main():
     pts_pin = torch.from_numpy(np.ascontiguousarray(seq.points)).pin_memory()
     off_pin = torch.from_numpy(np.ascontiguousarray(seq.offsets)).pin_memory()
     loss_out = np.zeros(3)
+    npg.npg_set_state(ctx.h, state0)
     npg.npg_set_points(ctx.h, pts_pin, off_pin)
     npg.npg_iteration(ctx.h, loss_out)
     torch.cuda.synchronize()

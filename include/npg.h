@@ -199,15 +199,20 @@ NPG_API int npg_set_points(npg_ctx* ctx, const float* points, const int64_t* fra
 
 /* Buffers readable with npg_get (and writable with npg_set where marked). Grid
  * vectors use the flat layout: levels 0..L-1 then the normal grid; level l is
- * res^3 x F with node (ix,iy,iz) at ((iz r + iy) r + ix) and features innermost. */
+ * res^3 x F with node (ix,iy,iz) at ((iz r + iy) r + ix) and features innermost.
+ * The nearest-neighbour buffers also seed the next search: each search starts
+ * from the index already stored for its query (the previous result, -1 after
+ * create) and only visits the cells within that candidate's distance. Any
+ * value may be written; an index outside the candidate set means no seed. The
+ * search result is the exact nearest neighbour whatever the seeds. */
 #define NPG_BUF_GRID 0        /* FP32 grid values (settable)                 */
 #define NPG_BUF_MLP 1         /* FP32 MLP parameters (settable)              */
 #define NPG_BUF_GRID_GRAD 2   /* FP32 dL/dgrid of the last backward           */
 #define NPG_BUF_GRID_PC 3     /* FP32 preconditioned grid gradient of the last step */
 #define NPG_BUF_MLP_GRAD 4    /* FP32 dL/dmlp of the last backward            */
 #define NPG_BUF_XHAT 5        /* FP32 T x N x 3                              */
-#define NPG_BUF_NN_X 6        /* int32 T x N: nearest point (frame-local index) */
-#define NPG_BUF_NN_P 7        /* int32 sum M_t: nearest vertex of every point  */
+#define NPG_BUF_NN_X 6        /* int32 T x N: nearest point (frame-local index) (settable) */
+#define NPG_BUF_NN_P 7        /* int32 sum M_t: nearest vertex of every point (settable) */
 #define NPG_BUF_CD 8          /* FP64 T                                      */
 #define NPG_BUF_WCONF 9       /* FP64 T                                      */
 #define NPG_BUF_ADAM_M_GRID 10 /* FP32, grid layout (settable)               */

@@ -111,6 +111,7 @@ static int grid_blocks(long long n, int per) {
 cudaError_t bucket_build(const float4* pts, const long long* d_off, long long uniform_count,
                          int nsets, long long total, int G, Buckets& b, cudaStream_t s) {
   const long long G3 = (long long)G * G * G;
+  b.src = pts;
   cudaError_t e = cudaMemsetAsync(b.counts, 0, sizeof(int) * G3 * nsets, s);
   if (e != cudaSuccess) return e;
   if (total > 0)
@@ -145,7 +146,16 @@ int auto_cells(long long points_per_set, int nsets) {
 // that is still open is appended to a queue with its best so far. Pass 2
 // (one warp per queued query, lanes splitting each ring's cell rows) finishes
 // the far queries, whose rings hold many (mostly empty) cells.
+//
+// Seeded search: when a starting candidate is known (the previous result of
+// an optimisation loop; any index in range will do), its distance bounds the
+// ball that can hold the nearest neighbour. The ball is then covered directly,
+// one row segment per (z, y) cell row within reach, instead of ring by ring:
+// every cell row costs two loads of cell starts, however many cells its
+// segment spans. The result is the same exact nearest neighbour; the seed only
+// changes how much of the grid is visited.
 constexpr int NN_NEAR_RINGS = 1;
+constexpr int NN_NEAR_BALL_ROWS = 25;  // ball scans up to this many cell rows stay in pass 1
 
 struct NnGeom {
   const float4* qs;
@@ -163,6 +173,8 @@ struct NnGeom {
   unsigned long long* stats;
   int* qcount;  // [0] pushed, [1] popped
   int4* qitems;
+  const float4* csrc;  // candidates in their own order (seed lookups)
+  bool seeded;         // out_idx holds a starting candidate per query (or an invalid index)
 };
 
 __device__ __forceinline__ void scan_range(const float4* __restrict__ cs, long long cb, int lo,
@@ -232,6 +244,49 @@ __device__ __forceinline__ bool scan_row(const NnGeom& g, const int* st, long lo
   return true;
 }
 
+// Scan the part of cell row (z, y) that can hold a point at squared distance
+// <= best (with the same margins as scan_row): one contiguous range of the
+// cell-sorted candidates. Returns whether the row's cell starts were read.
+__device__ __forceinline__ bool ball_row(const NnGeom& g, const int* st, long long cb, int z,
+                                         int y, float4 q, float h, float& best, int& bi,
+                                         unsigned long long& nc) {
+  const int G = g.G;
+  const float gz = axis_gap(q.z, z, G, h), gy = axis_gap(q.y, y, G, h);
+  const float base = gz * gz + gy * gy;
+  const float reach = best * (1.f + 2e-5f);
+  if (base > reach) return false;
+  const float rx = fminf(sqrtf(reach - base) + 4e-6f, 8.f);
+  const int xlo = cell_axis(q.x - rx, G), xhi = cell_axis(q.x + rx, G);
+  const int row = (z * G + y) * G;
+  const int lo = st[row + xlo], hi = st[row + xhi + 1];
+  nc += (unsigned long long)(hi - lo);
+  scan_range(g.cs, cb, lo, hi, q, best, bi);
+  return true;
+}
+
+// Cell range [a, b] along one axis that a ball of squared radius best
+// (with margins) around v can reach.
+__device__ __forceinline__ void ball_axis(float v, float best, int G, int& a, int& b) {
+  const float R = fminf(sqrtf(best * (1.f + 2e-5f)) + 8e-6f, 8.f);
+  a = cell_axis(v - R, G);
+  b = cell_axis(v + R, G);
+}
+
+// The seed of query `ob`: its candidate and squared distance, if in range.
+__device__ __forceinline__ void seed_start(const NnGeom& g, long long ob, long long cb,
+                                           long long ccount, float4 q, float& best, int& bi) {
+  if (!g.seeded) return;
+  const int sd = g.out_idx[ob];
+  if (sd < 0 || sd >= ccount) return;
+  const float4 p = g.csrc[cb + sd];
+  best = sqdist(q.x, q.y, q.z, p.x, p.y, p.z);
+  bi = sd;
+}
+
+__device__ __forceinline__ long long set_count(int s, long long uniform, const long long* off) {
+  return off == nullptr ? uniform : off[s + 1] - off[s];
+}
+
 // Squared lower bound on the distance to any cell outside rings 0..ring
 // (FLT_MAX when the rings cover the whole grid).
 __device__ __forceinline__ float ring_bound(float4 q, int cx, int cy, int cz, int ring, int G,
@@ -281,20 +336,33 @@ __global__ void __launch_bounds__(128) nn_near_kernel(NnGeom g) {
     const long long cb = set_base(s, g.c_uniform, g.c_off);
     const int* st = g.cstart + s * (G3 + 1);
     const int cx = cell_axis(q.x, G), cy = cell_axis(q.y, G), cz = cell_axis(q.z, G);
+    const long long ob = set_base(s, g.q_uniform, g.q_off) + __float_as_int(q.w);
     float best = FLT_MAX;
     int bi = 0x7fffffff;
     bool done = false;
-    for (int ring = 0; ring <= NN_NEAR_RINGS && ring < G; ++ring) {
-      for (int z = max(cz - ring, 0); z <= min(cz + ring, G - 1); ++z)
-        for (int y = max(cy - ring, 0); y <= min(cy + ring, G - 1); ++y)
-          n_rows += scan_row(g, st, cb, z, y, cx, cy, cz, ring, q, h, best, bi, n_cand) ? 1 : 0;
-      if (ring_done(ring_bound(q, cx, cy, cz, ring, G, h), best)) {
+    seed_start(g, ob, cb, set_count(s, g.c_uniform, g.c_off), q, best, bi);
+    if (best < FLT_MAX) {
+      int za, zb, ya, yb;
+      ball_axis(q.z, best, G, za, zb);
+      ball_axis(q.y, best, G, ya, yb);
+      if ((zb - za + 1) * (yb - ya + 1) <= NN_NEAR_BALL_ROWS) {
+        for (int z = za; z <= zb; ++z)
+          for (int y = ya; y <= yb; ++y)
+            n_rows += ball_row(g, st, cb, z, y, q, h, best, bi, n_cand) ? 1 : 0;
         done = true;
-        break;
+      }
+    } else {
+      for (int ring = 0; ring <= NN_NEAR_RINGS && ring < G; ++ring) {
+        for (int z = max(cz - ring, 0); z <= min(cz + ring, G - 1); ++z)
+          for (int y = max(cy - ring, 0); y <= min(cy + ring, G - 1); ++y)
+            n_rows += scan_row(g, st, cb, z, y, cx, cy, cz, ring, q, h, best, bi, n_cand) ? 1 : 0;
+        if (ring_done(ring_bound(q, cx, cy, cz, ring, G, h), best)) {
+          done = true;
+          break;
+        }
       }
     }
     if (done) {
-      const long long ob = set_base(s, g.q_uniform, g.q_off) + __float_as_int(q.w);
       g.out_idx[ob] = bi;
       if (g.out_d) g.out_d[ob] = best;
     } else {
@@ -303,6 +371,40 @@ __global__ void __launch_bounds__(128) nn_near_kernel(NnGeom g) {
     }
   }
   warp_stats(g.stats, n_cand, n_rows);
+}
+
+// warp minimum of (best, index), lowest index on ties
+__device__ __forceinline__ void warp_min(float& best, int& bi) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob < best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+}
+
+// Rings NN_NEAR_RINGS + 1 .. for a query with no candidate yet, lanes
+// splitting each ring's cell rows, until no unexplored cell can be closer.
+__device__ __forceinline__ void ring_search_far(const NnGeom& g, const int* st, long long cb,
+                                                float4 q, int cx, int cy, int cz, float h,
+                                                int lane, float& best, int& bi,
+                                                unsigned long long& n_cand,
+                                                unsigned long long& n_rows) {
+  const int G = g.G;
+  for (int ring = NN_NEAR_RINGS + 1; ring < G; ++ring) {
+    const int za = max(cz - ring, 0), zb = min(cz + ring, G - 1);
+    const int ya = max(cy - ring, 0), yb = min(cy + ring, G - 1);
+    const int ny = yb - ya + 1, nrows = (zb - za + 1) * ny;
+    for (int p = lane; p < nrows; p += 32) {
+      const int z = za + p / ny, y = ya + p % ny;
+      n_rows += scan_row(g, st, cb, z, y, cx, cy, cz, ring, q, h, best, bi, n_cand) ? 1 : 0;
+    }
+    warp_min(best, bi);
+    if (ring_done(ring_bound(q, cx, cy, cz, ring, G, h), best)) break;
+  }
 }
 
 __global__ void __launch_bounds__(128) nn_far_kernel(NnGeom g) {
@@ -326,25 +428,21 @@ __global__ void __launch_bounds__(128) nn_far_kernel(NnGeom g) {
     const int cx = cell_axis(q.x, G), cy = cell_axis(q.y, G), cz = cell_axis(q.z, G);
     float best = __int_as_float(it.y);
     int bi = it.z;
-    for (int ring = NN_NEAR_RINGS + 1; ring < G; ++ring) {
-      const int za = max(cz - ring, 0), zb = min(cz + ring, G - 1);
-      const int ya = max(cy - ring, 0), yb = min(cy + ring, G - 1);
+    if (best < FLT_MAX) {
+      // a candidate is known: cover its ball, lanes splitting the cell rows;
+      // the warp's best is shared after every 32 rows
+      int za, zb, ya, yb;
+      ball_axis(q.z, best, G, za, zb);
+      ball_axis(q.y, best, G, ya, yb);
       const int ny = yb - ya + 1, nrows = (zb - za + 1) * ny;
-      for (int p = lane; p < nrows; p += 32) {
-        const int z = za + p / ny, y = ya + p % ny;
-        n_rows += scan_row(g, st, cb, z, y, cx, cy, cz, ring, q, h, best, bi, n_cand) ? 1 : 0;
+      for (int p0 = 0; p0 < nrows; p0 += 32) {
+        const int p = p0 + lane;
+        if (p < nrows)
+          n_rows += ball_row(g, st, cb, za + p / ny, ya + p % ny, q, h, best, bi, n_cand) ? 1 : 0;
+        warp_min(best, bi);
       }
-      // warp minimum of (best, index)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob < best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
-        }
-      }
-      if (ring_done(ring_bound(q, cx, cy, cz, ring, G, h), best)) break;
+    } else {
+      ring_search_far(g, st, cb, q, cx, cy, cz, h, lane, best, bi, n_cand, n_rows);
     }
     if (lane == 0) {
       const long long ob = set_base(s, g.q_uniform, g.q_off) + __float_as_int(q.w);
@@ -358,10 +456,12 @@ __global__ void __launch_bounds__(128) nn_far_kernel(NnGeom g) {
 cudaError_t launch_nn(const float4* queries_sorted, long long q_uniform, const long long* q_off,
                       int nsets, long long q_total, const Buckets& cand,
                       const long long* c_off, long long c_uniform, int* out_idx, float* out_d,
-                      NnQueue queue, cudaStream_t s, unsigned long long* stats) {
+                      NnQueue queue, cudaStream_t s, unsigned long long* stats,
+                      bool seeded) {
   if (q_total == 0) return cudaSuccess;
   NnGeom g{queries_sorted, q_uniform, q_off, nsets, q_total, cand.sorted, cand.cell_start,
-           cand.G, c_off, c_uniform, out_idx, out_d, stats, queue.counters, queue.items};
+           cand.G, c_off, c_uniform, out_idx, out_d, stats, queue.counters, queue.items,
+           cand.src, seeded && cand.src != nullptr};
   cudaError_t e = cudaMemsetAsync(queue.counters, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   nn_near_kernel<<<grid_blocks(q_total, 128), 128, 0, s>>>(g);

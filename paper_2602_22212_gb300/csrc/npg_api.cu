@@ -497,6 +497,9 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
   CK(c, cudaMemsetAsync(c->d_epoch, 0, sizeof(int), c->stream));
   CK(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   CK(c, cudaMemsetAsync(c->d_nnstats, 0, sizeof(unsigned long long) * 4, c->stream));
+  // no nearest-neighbour seeds before the first search
+  CK(c, cudaMemsetAsync(c->nn_x, 0xff, sizeof(int) * NT, c->stream));
+  CK(c, cudaMemsetAsync(c->nn_p, 0xff, sizeof(int) * c->MT_cap, c->stream));
   if ((rc = set_points_impl(c, points, frame_offsets, inputs_on_device))) return fail(rc);
   CK(c, cudaStreamSynchronize(c->stream));
   c->phase = 0;
@@ -535,11 +538,11 @@ static int loss_launch(npg_ctx* c) {
   // vertex -> point (queries in x-hat bucket order for coherent warps)
   const bool count = c->tev && !c->capturing && c->t_cur >= 0;
   CK(c, launch_nn(c->xb.sorted, c->N, nullptr, c->T, NT, c->pb, c->p_off, 0, c->nn_x, c->d_x,
-                  c->nnq, c->stream, count ? c->d_nnstats : nullptr));
+                  c->nnq, c->stream, count ? c->d_nnstats : nullptr, true));
   mark(c, 4);
   // point -> vertex
   CK(c, launch_nn(c->pb.sorted, 0, c->p_off, c->T, c->MT, c->xb, nullptr, c->N, c->nn_p, c->d_p,
-                  c->nnq, c->stream, count ? c->d_nnstats + 2 : nullptr));
+                  c->nnq, c->stream, count ? c->d_nnstats + 2 : nullptr, true));
   mark(c, 5);
   CK(c, launch_loss(c));
   mark(c, 6);
@@ -811,7 +814,8 @@ extern "C" int npg_set(npg_ctx* c, int which, const void* src, size_t bytes, int
   if (rc) return rc;
   const bool settable = which == NPG_BUF_GRID || which == NPG_BUF_MLP ||
                         which == NPG_BUF_ADAM_M_GRID || which == NPG_BUF_ADAM_V_GRID ||
-                        which == NPG_BUF_ADAM_M_MLP || which == NPG_BUF_ADAM_V_MLP;
+                        which == NPG_BUF_ADAM_M_MLP || which == NPG_BUF_ADAM_V_MLP ||
+                        which == NPG_BUF_NN_X || which == NPG_BUF_NN_P;
   if (!settable) return set_err(c, NPG_EINVAL, "buffer %d is not settable", which);
   const size_t need = npg_size(c, which);
   if (!src || bytes != need)

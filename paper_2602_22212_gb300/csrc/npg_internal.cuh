@@ -36,6 +36,7 @@ struct Buckets {
   int* counts = nullptr;      // nsets x G^3 scratch
   int* slot = nullptr;        // per point: rank within its cell
   float4* sorted = nullptr;   // per point, in cell order: (x, y, z, bits(local index))
+  const float4* src = nullptr;  // the points in their own order (set by bucket_build)
 };
 
 // Work queue of the far-query pass of the nearest-neighbour search.
@@ -156,7 +157,8 @@ cudaError_t bucket_build(const float4* pts, const long long* d_off, long long un
 cudaError_t launch_nn(const float4* queries_sorted, long long q_uniform, const long long* q_off,
                       int nsets, long long q_total, const Buckets& cand,
                       const long long* c_off, long long c_uniform, int* out_idx, float* out_d,
-                      NnQueue queue, cudaStream_t s, unsigned long long* stats = nullptr);
+                      NnQueue queue, cudaStream_t s, unsigned long long* stats = nullptr,
+                      bool seeded = false);
 cudaError_t launch_loss(npg_ctx* c);
 cudaError_t launch_dxhat(npg_ctx* c);
 cudaError_t launch_mlp_backward_fp32(npg_ctx* c);

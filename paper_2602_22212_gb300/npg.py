@@ -371,7 +371,8 @@ class Context:
         return npg_get(self.h, which, out)
 
     def set(self, which, arr):
-        npg_set(self.h, which, np.ascontiguousarray(arr, dtype=np.float32))
+        dt = _BUF_DTYPE.get(which, np.float32)
+        npg_set(self.h, which, np.ascontiguousarray(arr, dtype=dt))
 
     def forward(self):
         npg_forward(self.h)

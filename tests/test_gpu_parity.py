@@ -250,6 +250,41 @@ def test_forward_and_loss_parity(npg, rot_mode):
     ctx.close()
 
 
+def assert_nn_exact(npg, ctx, seq):
+    """Both searches against brute force on the GPU's own x-hat (identical
+    FP32 inputs): bit-exact indices, lowest index on ties."""
+    T, N = len(seq.offsets) - 1, seq.x.shape[0]
+    xh = ctx.get(npg.BUF_XHAT).reshape(T, N, 3).astype(np.float64)
+    nnx, _, nnp, _, _ = O.chamfer(xh, seq.offsets, f32(seq.points), decide_f32=True)
+    np.testing.assert_array_equal(ctx.get(npg.BUF_NN_X).reshape(T, N), nnx)
+    np.testing.assert_array_equal(ctx.get(npg.BUF_NN_P), nnp)
+
+
+def test_seeded_search_bit_exact(npg):
+    """The search result does not depend on its seeds: none (first search),
+    arbitrary indices (in range, negative, past the end), and the previous
+    result of another state, near and far from the clouds."""
+    seq, ocfg, prob = tiny_setup(seed=3)
+    grid, mlp = random_state(ocfg)
+    T, N, MT = prob.T, prob.N, int(seq.offsets[-1])
+    ctx = gpu_at(npg, ocfg, seq, grid, mlp, 3, 10)
+    ctx.loss()
+    assert_nn_exact(npg, ctx, seq)
+    rng = np.random.default_rng(11)
+    M = int(seq.offsets[1])
+    ctx.set(npg.BUF_NN_X, rng.integers(-5, M + 50, size=T * N))
+    ctx.set(npg.BUF_NN_P, rng.integers(-5, N + 50, size=MT))
+    ctx.forward()
+    ctx.loss()
+    assert_nn_exact(npg, ctx, seq)
+    for scale in (0.05, 1.0):   # seeds of a nearby state, then of a distant one
+        ctx.set(npg.BUF_GRID, grid + rng.normal(scale=scale, size=grid.shape).astype(np.float32))
+        ctx.forward()
+        ctx.loss()
+        assert_nn_exact(npg, ctx, seq)
+    ctx.close()
+
+
 @pytest.mark.parametrize("rot_mode", [0, 1])
 def test_dxhat_parity(npg, rot_mode):
     """dL/dx-hat (Chamfer both directions + isometry) on every row whose value
