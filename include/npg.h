@@ -222,6 +222,9 @@ NPG_API int npg_set_points(npg_ctx* ctx, const float* points, const int64_t* fra
 #define NPG_BUF_DIST_X 14     /* FP32 T x N squared NN distances             */
 #define NPG_BUF_DIST_P 15     /* FP32 sum M_t squared NN distances           */
 #define NPG_BUF_DXHAT 16      /* FP32 T x N x 3 dL/dx-hat of the last backward */
+#define NPG_BUF_DISP 17       /* FP32 T x N x 3 displacement x-hat - x of the last forward,
+                                 formed directly as (R - I) x + d-hat (keeps its relative
+                                 precision when the motion is small) */
 
 /* Size in bytes of a buffer (0 for an unknown id). */
 NPG_API size_t npg_size(const npg_ctx* ctx, int which);

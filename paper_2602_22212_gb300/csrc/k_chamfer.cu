@@ -44,44 +44,78 @@ __global__ void bucket_count_kernel(const float4* __restrict__ pts, const long l
   }
 }
 
-// One block per set: exclusive scan of G^3 counts -> G^3 + 1 starts.
-__global__ void __launch_bounds__(1024) bucket_scan_kernel(const int* __restrict__ counts,
-                                                           int* __restrict__ starts, int G) {
+// One block per set: exclusive scan of G^3 counts -> G^3 + 1 starts, in
+// tiles of SCAN_TILE counts. A tile is loaded with coalesced thread-strided
+// reads (the next tile's loads are issued before the current tile is
+// scanned), transposed through padded shared memory so that each thread owns
+// SCAN_PER consecutive counts, scanned, and stored back coalesced.
+constexpr int SCAN_THREADS = 1024, SCAN_PER = 8, SCAN_TILE = SCAN_THREADS * SCAN_PER;
+
+__device__ __forceinline__ int scan_pad(int i) { return i + (i >> 5); }
+
+__global__ void __launch_bounds__(SCAN_THREADS) bucket_scan_kernel(const int* __restrict__ counts,
+                                                                    int* __restrict__ starts,
+                                                                    int G) {
+  __shared__ int tile[SCAN_TILE + SCAN_TILE / 32];
+  __shared__ int warp_sums[32];
   const long long G3 = (long long)G * G * G;
   const int* cnt = counts + blockIdx.x * G3;
   int* st = starts + blockIdx.x * (G3 + 1);
-  const int nt = blockDim.x;
-  const long long chunk = (G3 + nt - 1) / nt;
-  const long long b = threadIdx.x * chunk, e = min(G3, b + chunk);
-  int local = 0;
-  for (long long k = b; k < e; ++k) local += cnt[k];
-  __shared__ int warp_sums[32];
-  // inclusive scan of "local" across the block
-  int v = local;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  int next[SCAN_PER];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int n = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += n;
+  for (int j = 0; j < SCAN_PER; ++j) {
+    const long long k = (long long)j * SCAN_THREADS + tid;
+    next[j] = k < G3 ? __ldcs(cnt + k) : 0;
   }
-  if (lane == 31) warp_sums[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    int w = lane < (nt >> 5) ? warp_sums[lane] : 0;
+  int carry = 0;
+  for (long long base = 0; base < G3; base += SCAN_TILE) {
+#pragma unroll
+    for (int j = 0; j < SCAN_PER; ++j) tile[scan_pad(j * SCAN_THREADS + tid)] = next[j];
+    const long long nb = base + SCAN_TILE;
+#pragma unroll
+    for (int j = 0; j < SCAN_PER; ++j) {
+      const long long k = nb + (long long)j * SCAN_THREADS + tid;
+      next[j] = k < G3 ? __ldcs(cnt + k) : 0;
+    }
+    __syncthreads();
+    int v[SCAN_PER], local = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_PER; ++j) {
+      v[j] = local;
+      local += tile[scan_pad(tid * SCAN_PER + j)];
+    }
+    int inc = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int n = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += n;
+      const int n = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += n;
     }
-    warp_sums[lane] = w;
+    if (lane == 31) warp_sums[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      int w = warp_sums[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += n;
+      }
+      warp_sums[lane] = w;
+    }
+    __syncthreads();
+    const int before = carry + (inc - local) + (wid > 0 ? warp_sums[wid - 1] : 0);
+#pragma unroll
+    for (int j = 0; j < SCAN_PER; ++j) tile[scan_pad(tid * SCAN_PER + j)] = before + v[j];
+    carry += warp_sums[31];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < SCAN_PER; ++j) {
+      const long long k = base + (long long)j * SCAN_THREADS + tid;
+      if (k < G3) st[k] = tile[scan_pad(j * SCAN_THREADS + tid)];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  int run = v - local + (wid > 0 ? warp_sums[wid - 1] : 0);
-  for (long long k = b; k < e; ++k) {
-    st[k] = run;
-    run += cnt[k];
-  }
-  if (threadIdx.x == nt - 1) st[G3] = run;
+  if (tid == 0) st[G3] = carry;
 }
 
 __global__ void bucket_scatter_kernel(const float4* __restrict__ pts, const long long* off,
@@ -117,7 +151,7 @@ cudaError_t bucket_build(const float4* pts, const long long* d_off, long long un
   if (total > 0)
     bucket_count_kernel<<<grid_blocks(total, 256), 256, 0, s>>>(pts, d_off, uniform_count, nsets,
                                                                 total, G, b.counts, b.slot);
-  bucket_scan_kernel<<<nsets, 1024, 0, s>>>(b.counts, b.cell_start, G);
+  bucket_scan_kernel<<<nsets, SCAN_THREADS, 0, s>>>(b.counts, b.cell_start, G);
   if (total > 0)
     bucket_scatter_kernel<<<grid_blocks(total, 256), 256, 0, s>>>(
         pts, d_off, uniform_count, nsets, total, G, b.cell_start, b.slot, b.sorted);
@@ -555,34 +589,42 @@ __global__ void loss_combine_kernel(const double* __restrict__ part,
 }
 
 // Eq. 11-12 (cumulative products outward from the keyframe), Eq. 10, 13, 8.
-__global__ void loss_final_kernel(const double* __restrict__ cd, const double* __restrict__ iso_t,
-                                  const int* __restrict__ epoch, int e_max, int T, int t_key,
-                                  int E, double w_iso, double* __restrict__ w,
-                                  double* __restrict__ loss) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// The per-frame factors (one FP64 power each) are computed in parallel; one
+// thread then forms the products outward from the keyframe; the sums use the
+// block's fixed-order reduction.
+__global__ void __launch_bounds__(256) loss_final_kernel(
+    const double* __restrict__ cd, const double* __restrict__ iso_t, const int* __restrict__ epoch,
+    int e_max, int T, int t_key, int E, double w_iso, double* __restrict__ w,
+    double* __restrict__ loss) {
+  __shared__ double sh[32];
   double eb = e_max > 0 ? (double)(*epoch) / (double)e_max : 1.0;
   eb = fmin(fmax(eb, 0.0), 1.0);
   const double delta = 1.0 - sqrt(eb);
   const double ck = cd[t_key];
-  w[t_key] = 1.0;
-  for (int t = t_key + 1; t < T; ++t) {
+  for (int t = threadIdx.x; t < T; t += blockDim.x) {
     const double ex = cd[t] - ck;
-    w[t] = w[t - 1] * pow(1.0 / (1.0 + (ex > 0 ? ex : 0.0)), delta);
+    w[t] = t == t_key ? 1.0 : pow(1.0 / (1.0 + (ex > 0 ? ex : 0.0)), delta);
   }
-  for (int t = t_key - 1; t >= 0; --t) {
-    const double ex = cd[t] - ck;
-    w[t] = w[t + 1] * pow(1.0 / (1.0 + (ex > 0 ? ex : 0.0)), delta);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int t = t_key + 1; t < T; ++t) w[t] *= w[t - 1];
+    for (int t = t_key - 1; t >= 0; --t) w[t] *= w[t + 1];
   }
+  __syncthreads();
   double ld = 0.0, li = 0.0;
-  for (int t = 0; t < T; ++t) {
+  for (int t = threadIdx.x; t < T; t += blockDim.x) {
     ld += w[t] * cd[t];
     li += iso_t[t];
   }
-  ld /= (double)T;
-  li = E > 0 ? li / ((double)T * (double)E) : 0.0;
-  loss[0] = ld + w_iso * li;
-  loss[1] = ld;
-  loss[2] = li;
+  ld = block_sum(ld, sh);
+  li = block_sum(li, sh);
+  if (threadIdx.x == 0) {
+    ld /= (double)T;
+    li = E > 0 ? li / ((double)T * (double)E) : 0.0;
+    loss[0] = ld + w_iso * li;
+    loss[1] = ld;
+    loss[2] = li;
+  }
 }
 
 cudaError_t launch_loss(npg_ctx* c) {
@@ -591,7 +633,7 @@ cudaError_t launch_loss(npg_ctx* c) {
       c->loss_part);
   loss_combine_kernel<<<(c->T + 127) / 128, 128, 0, c->stream>>>(c->loss_part, c->p_off, c->N,
                                                                  c->T, c->cd, c->iso_t);
-  loss_final_kernel<<<1, 32, 0, c->stream>>>(c->cd, c->iso_t, c->d_epoch, c->cfg.e_max,
+  loss_final_kernel<<<1, 256, 0, c->stream>>>(c->cd, c->iso_t, c->d_epoch, c->cfg.e_max,
                                              c->T, c->t_key, c->E, (double)c->cfg.w_iso, c->wconf,
                                              c->loss);
   return cudaGetLastError();

@@ -742,7 +742,7 @@ extern "C" size_t npg_size(const npg_ctx* c, int which) {
       return sizeof(float) * (size_t)c->grid_flat_len;
     case NPG_BUF_MLP: case NPG_BUF_MLP_GRAD: case NPG_BUF_ADAM_M_MLP: case NPG_BUF_ADAM_V_MLP:
       return sizeof(float) * (size_t)c->mlp_len;
-    case NPG_BUF_XHAT: case NPG_BUF_DXHAT: return sizeof(float) * 3 * NT;
+    case NPG_BUF_XHAT: case NPG_BUF_DXHAT: case NPG_BUF_DISP: return sizeof(float) * 3 * NT;
     case NPG_BUF_NN_X: return sizeof(int32_t) * NT;
     case NPG_BUF_NN_P: return sizeof(int32_t) * (size_t)c->MT;
     case NPG_BUF_CD: case NPG_BUF_WCONF: return sizeof(double) * (size_t)c->T;
@@ -791,9 +791,10 @@ extern "C" int npg_get(npg_ctx* c, int which, void* dst, size_t bytes, int dst_o
     for (int l = 0; l < c->nlev; ++l)
       CK(c, cudaMemcpyAsync(static_cast<float*>(dst) + c->lev[l].flat, g + c->lev[l].off,
                             sizeof(float) * c->lev[l].n, kind, c->stream));
-  } else if (which == NPG_BUF_XHAT || which == NPG_BUF_DXHAT) {
+  } else if (which == NPG_BUF_XHAT || which == NPG_BUF_DXHAT || which == NPG_BUF_DISP) {
     const long long NT = (long long)c->N * c->T;
-    const float4* srcv = which == NPG_BUF_XHAT ? c->xhat : c->dxhat;
+    const float4* srcv =
+        which == NPG_BUF_XHAT ? c->xhat : (which == NPG_BUF_DXHAT ? c->dxhat : c->disp);
     if (dst_on_device) {
       CK(c, launch_xhat_out(srcv, static_cast<float*>(dst), NT, c->stream));
     } else {

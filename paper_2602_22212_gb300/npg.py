@@ -30,7 +30,7 @@ FP32, BF16_MLP = 0, 1
 PRECOND_FP32, PRECOND_TC = 0, 1
 (BUF_GRID, BUF_MLP, BUF_GRID_GRAD, BUF_GRID_PC, BUF_MLP_GRAD, BUF_XHAT, BUF_NN_X, BUF_NN_P,
  BUF_CD, BUF_WCONF, BUF_ADAM_M_GRID, BUF_ADAM_V_GRID, BUF_ADAM_M_MLP, BUF_ADAM_V_MLP,
- BUF_DIST_X, BUF_DIST_P, BUF_DXHAT) = range(17)
+ BUF_DIST_X, BUF_DIST_P, BUF_DXHAT, BUF_DISP) = range(18)
 
 _BUF_DTYPE = {BUF_NN_X: np.int32, BUF_NN_P: np.int32, BUF_CD: np.float64, BUF_WCONF: np.float64}
 

@@ -1,0 +1,321 @@
+"""Parity at the benchmark's full size, in the launch configurations bench.py
+times: the capsule figure with N = 40962 vertices, T = 100 frames of
+M = 20000 points, an 8-level grid 16 -> 256 with F = 4 and a 3 x 64 MLP, run
+(a) plain FP32, eager, FP32 preconditioner, and (b) BF16 tensor-core MLP with
+the tensor-core preconditioner, replaying its CUDA graph.
+
+The oracle cannot run a whole iteration at this size, so each test compares
+what it can compute one by one, or a property that holds at any size:
+  decode        sampled vertices over all frames, against the oracle's decode
+  search        sampled queries of both directions, against brute force on the
+                GPU's own x-hat: bit-exact
+  loss          cd_t, L_def, L_iso recomputed in FP64 from the GPU's x-hat and
+                nearest-neighbour indices (all rows)
+  dL/dx-hat     sampled rows, from the same indices and the Sec. 3.5 formulas
+  reverse pass  a dL/dx-hat that is nonzero on sampled vertices only, through
+                the full-size kernels, against the oracle's reverse pass on
+                those vertices
+  precondition  every level, against an FP64 DCT-II solve (scipy.fft)
+  Adam          sampled parameters, from the GPU's own preconditioned gradient
+The first iteration (eager in both forms) fills the Adam moments; the grid
+and MLP are then set to a random state with large motion, and the checked
+iteration is the second (a graph replay in form b).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_22212_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def npg():
+    from paper_2602_22212_gb300 import build
+    build.build()
+    from paper_2602_22212_gb300 import npg as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def workload():
+    p = I.preset("paper")
+    seq = I.make_sequence(p, seed=0)
+    ocfg = O.make_cfg(L=p["L"], res=p["res"], F=p["F"], H=p["H"], D=p["D"], slope=p["slope"])
+    return p, seq, ocfg
+
+
+class Run:
+    pass
+
+
+def run_form(npg, workload, form):
+    import torch
+    p, seq, ocfg = workload
+    bf16 = form == "bf16"
+    stream = torch.cuda.Stream()
+    mlp = I.mlp_init(O.k_in(ocfg), p["H"], p["D"], O.n_out(ocfg), seed=0)
+    cfg = npg.make_config(p["L"], p["res"], p["F"], p["H"], p["D"], slope=p["slope"],
+                          precision=npg.BF16_MLP if bf16 else npg.FP32, e_max=p["iters"],
+                          use_graph=bf16, stream=stream,
+                          precond_mode=npg.PRECOND_TC if bf16 else npg.PRECOND_FP32)
+    ctx = npg.Context(cfg, seq, mlp, device_inputs=True)
+    ctx.iteration()
+    # a state with large, non-rigid motion (the first iteration from the
+    # identity moves the vertices by ~1e-3 only), Adam moments kept
+    rng = np.random.default_rng(7)
+    ctx.set(npg.BUF_GRID, rng.normal(scale=0.3, size=O.grid_len(ocfg)).astype(np.float32))
+    m = I.mlp_init(O.k_in(ocfg), p["H"], p["D"], O.n_out(ocfg), seed=8, zero_last=False)
+    m[-(O.n_out(ocfg) * p["H"] + O.n_out(ocfg)):] *= 0.5
+    ctx.set(npg.BUF_MLP, m)
+    r = Run()
+    r.cfg, r.ctx, r.form = cfg, ctx, form
+    r.e = npg.npg_get_epoch(ctx.h)
+    r.grid0 = ctx.get(npg.BUF_GRID)
+    r.mlp0 = ctx.get(npg.BUF_MLP)
+    r.m0 = ctx.get(npg.BUF_ADAM_M_GRID)
+    r.v0 = ctx.get(npg.BUF_ADAM_V_GRID)
+    r.mm0 = ctx.get(npg.BUF_ADAM_M_MLP)
+    r.mv0 = ctx.get(npg.BUF_ADAM_V_MLP)
+    r.loss = np.asarray(ctx.iteration())
+    T, N = seq.T, seq.N
+    r.xhat = ctx.get(npg.BUF_XHAT).reshape(T, N, 3)
+    r.disp = ctx.get(npg.BUF_DISP).reshape(T, N, 3)
+    r.nnx = ctx.get(npg.BUF_NN_X).reshape(T, N)
+    r.nnp = ctx.get(npg.BUF_NN_P)
+    r.cd = ctx.get(npg.BUF_CD)
+    r.w = ctx.get(npg.BUF_WCONF)
+    r.dxhat = ctx.get(npg.BUF_DXHAT).reshape(T, N, 3)
+    r.g = ctx.get(npg.BUF_GRID_GRAD)
+    r.gpc = ctx.get(npg.BUF_GRID_PC)
+    r.gm = ctx.get(npg.BUF_MLP_GRAD)
+    r.grid1 = ctx.get(npg.BUF_GRID)
+    r.mlp1 = ctx.get(npg.BUF_MLP)
+    r.m1 = ctx.get(npg.BUF_ADAM_M_GRID)
+    r.v1 = ctx.get(npg.BUF_ADAM_V_GRID)
+    r.mm1 = ctx.get(npg.BUF_ADAM_M_MLP)
+    r.mv1 = ctx.get(npg.BUF_ADAM_V_MLP)
+    return r
+
+
+@pytest.fixture(scope="module", params=["fp32", "bf16"])
+def run(request, npg, workload):
+    r = run_form(npg, workload, request.param)
+    yield r
+    r.ctx.close()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_decode_sampled_vertices(run, workload):
+    p, seq, ocfg = workload
+    rng = np.random.default_rng(1)
+    S = rng.choice(seq.N, size=48, replace=False)
+    x = seq.x[S].astype(np.float64)
+    z = O.encode(ocfg, x, seq.n[S].astype(np.float64), run.grid0.astype(np.float64))
+    gam = O.time_embedding(ocfg, seq.T)
+    want = O.decode(ocfg, x, z, gam, run.mlp0.astype(np.float64))
+    got = run.xhat[:, S]
+    tol = 5e-3 if run.form == "bf16" else 1e-5
+    assert np.abs(got - want).max() <= tol, np.abs(got - want).max()
+
+
+def test_search_sampled_queries_bit_exact(run, workload):
+    p, seq, ocfg = workload
+    rng = np.random.default_rng(2)
+    pts = seq.points.astype(np.float64)
+    for t in rng.choice(seq.T, size=6, replace=False):
+        a, b = int(seq.offsets[t]), int(seq.offsets[t + 1])
+        P = pts[a:b]
+        X = run.xhat[t].astype(np.float64)
+        qi = rng.choice(seq.N, size=200, replace=False)
+        want_x, _ = O.nn(X[qi], P, decide_f32=True)
+        np.testing.assert_array_equal(run.nnx[t, qi], want_x)
+        qj = rng.choice(b - a, size=200, replace=False)
+        want_p, _ = O.nn(P[qj], X, decide_f32=True)
+        np.testing.assert_array_equal(run.nnp[a + qj], want_p)
+
+
+def loss_terms(run, seq):
+    """cd_t, edge lengths, L_def, L_iso in FP64 from the GPU's x-hat and indices."""
+    T, N = seq.T, seq.N
+    xh = run.xhat.astype(np.float64)
+    pts = seq.points.astype(np.float64)
+    off = seq.offsets
+    cd = np.zeros(T)
+    for t in range(T):
+        P = pts[off[t]:off[t + 1]]
+        dx = np.sum((xh[t] - P[run.nnx[t]]) ** 2, axis=1)
+        dp = np.sum((P - xh[t][run.nnp[off[t]:off[t + 1]]]) ** 2, axis=1)
+        cd[t] = dx.mean() + dp.mean()
+    # edge vectors from the reference and the displacement: (x_a - x_b) +
+    # (delta_a - delta_b) keeps the length differences' relative precision
+    # when the motion is small (from the rounded x-hat they would drown in
+    # its rounding error)
+    e = O.edges(seq.faces)
+    x = seq.x.astype(np.float64)
+    de = x[e[:, 0]] - x[e[:, 1]]
+    dl = run.disp.astype(np.float64)
+    ek = de + dl[seq.t_key][e[:, 0]] - dl[seq.t_key][e[:, 1]]
+    lk = np.linalg.norm(ek, axis=1)
+    iso = 0.0
+    for t in range(T):
+        if t == seq.t_key:
+            continue
+        et = de + dl[t][e[:, 0]] - dl[t][e[:, 1]]
+        lt = np.linalg.norm(et, axis=1)
+        # |l_t - l_k| = |(e_t - e_k) . (e_t + e_k)| / (l_t + l_k), exact in FP64
+        iso += np.abs(np.sum((et - ek) * (et + ek), axis=1) / (lt + lk)).sum()
+    return cd, e, lk, iso / (T * len(e))
+
+
+def test_loss_from_gpu_indices(run, workload):
+    p, seq, ocfg = workload
+    cd, e, lk, l_iso = loss_terms(run, seq)
+    np.testing.assert_allclose(run.cd, cd, rtol=1e-5)
+    w = O.conf_weights(cd, seq.t_key, run.e, p["iters"])
+    np.testing.assert_allclose(run.w, w, rtol=1e-5)
+    l_def = np.mean(w * cd)
+    assert abs(run.loss[1] - l_def) <= 1e-5 * l_def
+    assert abs(run.loss[2] - l_iso) <= 1e-5 * l_iso
+    assert abs(run.loss[0] - (run.loss[1] + 100.0 * run.loss[2])) <= 1e-12 * run.loss[0]
+
+
+def test_dxhat_sampled_rows(run, workload):
+    p, seq, ocfg = workload
+    T, N = seq.T, seq.N
+    rng = np.random.default_rng(3)
+    xh = run.xhat.astype(np.float64)
+    pts = seq.points.astype(np.float64)
+    off = seq.offsets
+    e = O.edges(seq.faces)
+    E = len(e)
+    adj = [[] for _ in range(N)]
+    for k, (a, b) in enumerate(e):
+        adj[a].append((b, k))
+        adj[b].append((a, k))
+    x = seq.x.astype(np.float64)
+    de = x[e[:, 0]] - x[e[:, 1]]
+    dl = run.disp.astype(np.float64)
+    ek = de + dl[seq.t_key][e[:, 0]] - dl[seq.t_key][e[:, 1]]
+    lk = np.linalg.norm(ek, axis=1)
+    checked = 0
+    for t in rng.choice(T, size=5, replace=False):
+        P = pts[off[t]:off[t + 1]]
+        M = len(P)
+        nnp = run.nnp[off[t]:off[t + 1]]
+        et = de + dl[t][e[:, 0]] - dl[t][e[:, 1]]
+        lt = np.linalg.norm(et, axis=1)
+        dlen = np.sum((et - ek) * (et + ek), axis=1) / (lt + lk)  # l_t - l_k
+        for i in rng.choice(N, size=40, replace=False):
+            # residuals (x_i - p) + delta_i and edge vectors as above: the
+            # isometry terms (~1e-5 each) can cancel to a row of ~1e-7
+            g = 2.0 * run.w[t] / (T * N) * ((x[i] - P[run.nnx[t, i]]) + dl[t, i])
+            js = np.nonzero(nnp == i)[0]
+            if len(js):
+                g += 2.0 * run.w[t] / (T * M) * np.sum((x[i] - P[js]) + dl[t, i], axis=0)
+            kink = False
+            if t != seq.t_key:
+                for j, k in adj[i]:
+                    d = dlen[k]
+                    if abs(d) <= 2e-5 * lk[k]:
+                        kink = True
+                    vec = et[k] if e[k, 0] == i else -et[k]   # x-hat_i - x-hat_j
+                    g += 100.0 / (T * E) * np.sign(d) * vec / lt[k]
+            if kink:
+                continue
+            got = run.dxhat[t, i].astype(np.float64)
+            assert np.linalg.norm(got - g) <= 1e-4 * np.linalg.norm(g) + 1e-12, (t, i, got, g)
+            checked += 1
+    assert checked >= 150
+
+
+def test_reverse_pass_of_sampled_vertices(run, npg, workload):
+    """npg_backprop on the full-size context with dL/dx-hat nonzero on 32
+    vertices (all frames) only, against the oracle's reverse pass on those 32
+    vertices (at the updated parameters)."""
+    import torch
+    p, seq, ocfg = workload
+    T, N = seq.T, seq.N
+    rng = np.random.default_rng(4)
+    S = np.sort(rng.choice(N, size=32, replace=False))
+    gs = rng.normal(scale=1e-3, size=(T, len(S), 3)).astype(np.float32)
+    gx = np.zeros((T, N, 3), np.float32)
+    gx[:, S] = gs
+    run.ctx.forward()
+    npg.npg_backprop(run.ctx.h, torch.from_numpy(gx.reshape(-1)).cuda())
+    gg = run.ctx.get(npg.BUF_GRID_GRAD).astype(np.float64)
+    gm = run.ctx.get(npg.BUF_MLP_GRAD).astype(np.float64)
+    sub = O.Problem(ocfg, seq.x[S], seq.n[S], np.zeros((0, 3), np.int32),
+                    np.zeros((1, 3)), np.array([0] + [1] * T), seq.t_key)
+    want_g, want_m = O.backprop(sub, run.grid1.astype(np.float64), run.mlp1.astype(np.float64),
+                                gs.astype(np.float64))
+    tol_m, tol_g = (3e-2, 1e-1) if run.form == "bf16" else (1e-4, 1e-4)
+    assert rel(gm, want_m) <= tol_m, rel(gm, want_m)
+    for l in range(ocfg.L + 1):
+        a = O.level_offset(ocfg, l)
+        b = O.level_offset(ocfg, l + 1) if l < ocfg.L else O.grid_len(ocfg)
+        assert rel(gg[a:b], want_g[a:b]) <= tol_g, (l, rel(gg[a:b], want_g[a:b]))
+
+
+def dct_solve(g, r, F, lam):
+    """(I + lam L)^-2 g for the Neumann lattice Laplacian of an r^3 grid, by the
+    orthonormal DCT-II that diagonalises it (FP64)."""
+    from scipy import fft
+    a = g.reshape(r, r, r, F).astype(np.float64)
+    mu = 2.0 - 2.0 * np.cos(np.pi * np.arange(r) / r)
+    s = 1.0 / (1.0 + lam * (mu[:, None, None] + mu[None, :, None] + mu[None, None, :])) ** 2
+    c = fft.dctn(a, type=2, axes=(0, 1, 2), norm="ortho", workers=-1)
+    c *= s[..., None]
+    return fft.idctn(c, type=2, axes=(0, 1, 2), norm="ortho", workers=-1).reshape(-1)
+
+
+def test_preconditioner_every_level(run, workload):
+    p, seq, ocfg = workload
+    tol = 1e-4 if run.form == "bf16" else 1e-5
+    for l in range(ocfg.L + 1):
+        a = O.level_offset(ocfg, l)
+        b = O.level_offset(ocfg, l + 1) if l < ocfg.L else O.grid_len(ocfg)
+        r = p["res"][l] if l < ocfg.L else 4
+        F = p["F"] if l < ocfg.L else 2
+        want = dct_solve(run.g[a:b], r, F, float(run.cfg.lambda_[l]))
+        assert rel(run.gpc[a:b], want) <= tol, (l, r, rel(run.gpc[a:b], want))
+
+
+def adam_ref(p0, g, m0, v0, lr, step, b1=0.9, b2=0.999, eps=1e-8):
+    """Adam in FP64 with the FP32 hyper-parameters the library holds (1 - 0.999
+    differs from 1 - float32(0.999) by 1.3e-5 relative)."""
+    b1, b2, eps = (float(np.float32(v)) for v in (b1, b2, eps))
+    p0, g, m0, v0 = (np.asarray(a, np.float64) for a in (p0, g, m0, v0))
+    m = b1 * m0 + (1 - b1) * g
+    v = b2 * v0 + (1 - b2) * g * g
+    c1, c2 = 1 - b1 ** step, 1 - b2 ** step
+    return p0 - lr * (m / c1) / (np.sqrt(v / c2) + eps), m, v
+
+
+def test_adam_sampled_parameters(run, workload):
+    p, seq, ocfg = workload
+    rng = np.random.default_rng(5)
+    step = run.e + 1
+    for l in range(ocfg.L + 1):
+        a = O.level_offset(ocfg, l)
+        b = O.level_offset(ocfg, l + 1) if l < ocfg.L else O.grid_len(ocfg)
+        k = a + rng.choice(b - a, size=min(4096, b - a), replace=False)
+        lr = float(np.float32(run.cfg.lr_grid[l]))
+        pw, mw, vw = adam_ref(run.grid0[k], run.gpc[k], run.m0[k], run.v0[k], lr, step)
+        np.testing.assert_allclose(run.m1[k], mw, rtol=1e-5, atol=1e-30)
+        np.testing.assert_allclose(run.v1[k], vw, rtol=1e-5, atol=1e-30)
+        check_update(run.grid0[k], run.grid1[k], pw)
+    pw, mw, vw = adam_ref(run.mlp0, run.gm, run.mm0, run.mv0, 1e-3, step)
+    np.testing.assert_allclose(run.mm1, mw, rtol=1e-5, atol=1e-30)
+    check_update(run.mlp0, run.mlp1, pw)
+
+
+def check_update(p0, p1, want):
+    """p1 = want up to 1e-4 of the update plus the FP32 rounding of p1."""
+    err = np.abs(p1.astype(np.float64) - want)
+    bound = 1e-4 * np.abs(want - p0) + 2.0 * np.spacing(np.abs(p1).astype(np.float32))
+    assert np.all(err <= bound), (err.max(), np.argmax(err - bound))
