@@ -257,7 +257,7 @@ def config_dict(p, seq, form, graph):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="npg", choices=["npg", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
