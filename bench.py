@@ -64,6 +64,7 @@ def make_cfg(npg, p, precision, graph, stream, e_max, precond):
     return npg.make_config(p["L"], p["res"], p["F"], p["H"], p["D"], slope=p["slope"],
                            precision=npg.BF16_MLP if precision == "bf16" else npg.FP32,
                            e_max=e_max, use_graph=graph, stream=stream,
+                           w_iso=p.get("w_iso", 100.0),
                            precond_mode=npg.PRECOND_TC if precond == "tc" else npg.PRECOND_FP32)
 
 
@@ -155,7 +156,8 @@ def oracle_sample(p, seq, frames=1, level=1):
     on one grid level, scaled to all levels by node count x sqrt(1 + 12 lambda)
     (CG iterations grow with the square root of the condition number)."""
     import oracle as O
-    cfg = O.make_cfg(L=p["L"], res=p["res"], F=p["F"], H=p["H"], D=p["D"], slope=p["slope"])
+    cfg = O.make_cfg(L=p["L"], res=p["res"], F=p["F"], H=p["H"], D=p["D"], slope=p["slope"],
+                     w_iso=p.get("w_iso", 100.0))
     sub = seq.offsets[:frames + 1]
     prob = O.Problem(cfg, seq.x, seq.n, seq.faces, seq.points[:sub[-1]], sub, 0)
     from paper_2602_22212_gb300 import inputs as I
@@ -249,7 +251,7 @@ def config_dict(p, seq, form, graph):
             "form": form, "cuda_graph": bool(graph),
             "l2": "working set (~3 GB of grid state per step) exceeds L2; no flush",
             "N": seq.N, "T": seq.T, "M": int(seq.offsets[1]), "levels": p["res"], "F": p["F"],
-            "H": p["H"], "depth": p["D"]}
+            "H": p["H"], "depth": p["D"], "w_iso": p.get("w_iso", 100.0)}
 
 
 # ----------------------------------------------------------------- main

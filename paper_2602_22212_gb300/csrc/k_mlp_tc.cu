@@ -274,7 +274,24 @@ cudaError_t launch_decode_bf16(npg_ctx* c) {
 //     ACC_X += [gO | dpre1]^T [y | h3]           (M 128, N 128)
 //   where y = (z_i, gamma_t, 0.., 1 at column 15): the diagonal blocks are
 //   dW3, dW2 and dW_out, dW1, the column of ones gives the bias gradients.
-//   dL/dz_i = W1[:, :Z]^T dpre1, summed over the tile's frames in shared memory.
+//   dL/dz_i = W1[:, :Z]^T dpre1 in FP32, summed over the tile's frames.
+//
+// A CTA of 512 threads (16 warps) owns one tile at a time: warp w serves TMEM
+// lanes 32 (w % 4) .. + 31 (its tile rows) and the 16-column quarter
+// c = w / 4 of every 64-wide activation, so each thread converts, masks and
+// stores 16 values per layer. Per-row scalar work is spread over the
+// quarters: c = 0 forms dL/do, c = 1 writes the y row. The next tile's inputs
+// (U, V, z, x, dL/dx-hat rows) are copied into a second shared staging
+// buffer with cp.async while the current tile computes, and its h1 is written
+// while the last weight-gradient MMA of the current tile runs.
+struct BwdStage {  // inputs of one tile, FP32
+  static constexpr uint32_t U = 0;            // [16 vertices][64]
+  static constexpr uint32_t V = 4096;         // [8 frames][64]
+  static constexpr uint32_t X = 6144;         // [16] float4 x_i
+  static constexpr uint32_t G = 6400;         // [8][16] float4 dL/dx-hat
+  static constexpr uint32_t Z = 8448;         // [16][Z] z_i (Z <= 8)
+  static constexpr uint32_t BYTES = 9216;
+};
 struct BwdSmem {
   // B operands of the forward and dh MMAs (K-major)
   static constexpr uint32_t W2 = 0, W3 = 8192, WO = 16384, W2T = 18432, W3T = 26624,
@@ -282,32 +299,59 @@ struct BwdSmem {
   // [h2 | h1 | y | h3] then [gO | dpre3 | dpre2], 16 KB tiles
   static constexpr uint32_t H2 = 43008, H1 = H2 + TC_TILE, Y = H1 + TC_TILE, H3 = Y + TC_TILE;
   static constexpr uint32_t GO = H3 + TC_TILE, DP3 = GO + TC_TILE, DP2 = DP3 + TC_TILE;
-  static constexpr uint32_t W1F = DP2 + TC_TILE;            // FP32 W1 (64 x K <= 64 x 15)
-  static constexpr uint32_t BIAS = W1F + 64 * 16 * 4;       // b2, b3, bo FP32
-  static constexpr uint32_t DZ = BIAS + (64 + 64 + 16) * 4;  // FP32 [128][8]
-  static constexpr uint32_t DBO = DZ + 128 * 8 * 4;          // FP32 [8] output-bias gradient
-  static constexpr uint32_t BAR = DBO + 8 * 4;
-  static constexpr uint32_t TMEMP = BAR + 8;
+  static constexpr uint32_t W1F = DP2 + TC_TILE;                // FP32 W1 (64 x K <= 64 x 15)
+  static constexpr uint32_t BIAS = W1F + 64 * 16 * 4;           // b2, b3, bo FP32
+  static constexpr uint32_t DZP = BIAS + (64 + 64 + 16) * 4;    // FP32 [128 rows][4][8]
+  static constexpr uint32_t STG = DZP + 128 * 4 * 8 * 4;        // 2 x BwdStage
+  static constexpr uint32_t DBO = STG + 2 * BwdStage::BYTES;    // FP32 [8] output-bias gradient
+  static constexpr uint32_t BAR = DBO + 8 * 4;  // MMA completion, final drain
+  static constexpr uint32_t TMEMP = BAR + 16;
   static constexpr uint32_t TOTAL = TMEMP + 8;
 };
 constexpr uint32_t ACC_W_COL = 0, ACC_X_COL = 256, WORK_COL = 384;
+constexpr int BWD_THREADS = 512;
 
 bool backward_bf16_supported(int K, int Z) { return K <= 15 && Z <= 8; }
 
-__device__ __forceinline__ bool tc_wait_all(uint64_t* bar, uint32_t& phase, int* err) {
-  bool w = tc::mbar_wait(bar, phase, WAIT_TRIES);
+// Every thread polls the barrier; the outcome is folded into the next
+// CTA-wide barrier (tc_sync_ok), so a wait that gives up ends the kernel
+// uniformly without an extra barrier per wait.
+__device__ __forceinline__ void tc_wait(uint64_t* bar, uint32_t& phase, bool& ok) {
+  ok = ok && tc::mbar_wait(bar, phase, WAIT_TRIES);
   phase ^= 1u;
-  w = __syncthreads_and(w) != 0;
-  if (!w && threadIdx.x == 0) atomicExch(err, 1);
   tc::fence_after_sync();
-  return w;
 }
 
-__device__ __forceinline__ void tc_sync_for_mma() {
+// Shared-memory writes -> async proxy, TMEM reads complete, then a CTA
+// barrier that also agrees on `ok`.
+__device__ __forceinline__ bool tc_sync_ok(bool ok, int* err) {
   tc::fence_async_smem();
   tc::fence_before_sync();
-  __syncthreads();
+  ok = __syncthreads_and(ok) != 0;
   tc::fence_after_sync();
+  if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+  return ok;
+}
+
+// 16 FP32 values as BF16 into columns [c0, c0 + 16) of a row of a K-major tile.
+__device__ __forceinline__ void st_row16(uint8_t* tile, int row, int c0, const float* v) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint4 q;
+    q.x = tc::pack_bf16(v[8 * h + 0], v[8 * h + 1]);
+    q.y = tc::pack_bf16(v[8 * h + 2], v[8 * h + 3]);
+    q.z = tc::pack_bf16(v[8 * h + 4], v[8 * h + 5]);
+    q.w = tc::pack_bf16(v[8 * h + 6], v[8 * h + 7]);
+    *reinterpret_cast<uint4*>(tile + tc::sw128_off(row, c0 + 8 * h)) = q;
+  }
+}
+
+__device__ __forceinline__ void ld_col16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  tc::tmem_ld16(taddr, r);
+  tc::tmem_ld_wait();
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // D (128 x N) += A^T B with A, B MN-major [128 rows][64] tiles placed 16 KB
@@ -321,17 +365,75 @@ __device__ __forceinline__ void mma_rows(uint32_t d, uint32_t a_smem, uint32_t b
                  (first && ks == 0) ? 0u : 1u);
 }
 
+// 16-byte global -> shared copy; src_bytes < 16 zero-fills the rest (0: no read).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Issue the copies of one tile's inputs into a staging buffer (one commit group).
+__device__ void bwd_stage(const TcArgs& a, long long tile, int n_tb, uint8_t* stg) {
+  const int i0 = (int)(tile / n_tb) * 16, t0 = (int)(tile % n_tb) * 8;
+  const uint32_t zbytes = 16u * (uint32_t)a.Z * 4u;
+  const long long zend = (long long)a.N * a.Z * 4;  // bytes of the whole z array
+  for (int e = threadIdx.x; e < 256 + 128 + 16 + 128 + 32; e += BWD_THREADS) {
+    const void* src = a.U;
+    uint8_t* dst;
+    uint32_t n = 16u;
+    if (e < 256) {
+      const int v = e >> 4, ch = e & 15, i = i0 + v;
+      dst = stg + BwdStage::U + v * 256 + ch * 16;
+      if (i < a.N) src = a.U + (long long)i * TC_H + ch * 4; else n = 0u;
+    } else if (e < 384) {
+      const int f = (e - 256) >> 4, ch = (e - 256) & 15, t = t0 + f;
+      dst = stg + BwdStage::V + f * 256 + ch * 16;
+      if (t < a.T) src = a.V + (long long)t * TC_H + ch * 4; else n = 0u;
+    } else if (e < 400) {
+      const int v = e - 384, i = i0 + v;
+      dst = stg + BwdStage::X + v * 16;
+      if (i < a.N) src = a.xr + i; else n = 0u;
+    } else if (e < 528) {
+      const int f = (e - 400) >> 4, v = (e - 400) & 15, i = i0 + v, t = t0 + f;
+      dst = stg + BwdStage::G + (f * 16 + v) * 16;
+      if (i < a.N && t < a.T) src = a.dxhat + (long long)t * a.N + i; else n = 0u;
+    } else {
+      const uint32_t off = (uint32_t)(e - 528) * 16u;
+      if (off >= zbytes) continue;
+      dst = stg + BwdStage::Z + off;
+      const long long g = (long long)i0 * a.Z * 4 + off;  // byte offset in z
+      const long long left = zend - g;
+      if (left > 0) {
+        src = reinterpret_cast<const uint8_t*>(a.z) + g;
+        n = left < 16 ? (uint32_t)left : 16u;
+      } else {
+        n = 0u;
+      }
+    }
+    cp_async16(dst, src, n);
+  }
+  cp_async_commit();
+}
+
 template <int ROT>
-__global__ void __launch_bounds__(128, 1) mlp_bwd_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + BwdSmem::BAR);
   uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + BwdSmem::TMEMP);
   float* bias = reinterpret_cast<float*>(sm + BwdSmem::BIAS);
   float* w1f = reinterpret_cast<float*>(sm + BwdSmem::W1F);
-  float* dzs = reinterpret_cast<float*>(sm + BwdSmem::DZ);
+  float* dzp = reinterpret_cast<float*>(sm + BwdSmem::DZP);
   float* dbo = reinterpret_cast<float*>(sm + BwdSmem::DBO);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q4 = warp & 3, c = warp >> 2;  // lane quarter, column quarter
+  const int row = 32 * q4 + lane, il = row & 15, tl = row >> 4;
   const int H = TC_H, K = a.K, Z = a.Z, M = a.M, NO = a.NO;
   if (tid < 8) dbo[tid] = 0.f;
 
@@ -341,126 +443,160 @@ __global__ void __launch_bounds__(128, 1) mlp_bwd_tc_kernel(TcArgs a) {
   load_weight_tile(sm + BwdSmem::W2, p2, 64, 64);
   load_weight_tile(sm + BwdSmem::W3, p3, 64, 64);
   load_weight_tile(sm + BwdSmem::WO, po, 16, NO);
-  for (int e = tid; e < 64 * 64; e += 128) {
+  for (int e = tid; e < 64 * 64; e += BWD_THREADS) {
     const int m = e >> 6, j = e & 63;
     st_bf16(sm + BwdSmem::W2T, m, j, p2[j * H + m]);
     st_bf16(sm + BwdSmem::W3T, m, j, p3[j * H + m]);
     st_bf16(sm + BwdSmem::WOT, m, j, j < NO ? po[j * H + m] : 0.f);
-    // gO columns >= NO stay zero for the whole kernel
-    st_bf16(sm + BwdSmem::GO, m, j, 0.f);
-    st_bf16(sm + BwdSmem::GO, m + 64, j, 0.f);
   }
-  for (int e = tid; e < 64 * K; e += 128) w1f[e] = a.mlp[e];
-  for (int k = tid; k < 64; k += 128) {
+  {  // gO and y start zero; their columns >= 16 stay zero, y column 15 stays 1
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < 2 * TC_TILE / 16; e += BWD_THREADS) {
+      const uint32_t off = (uint32_t)(e % (TC_TILE / 16)) * 16u;
+      *reinterpret_cast<uint4*>(sm + (e < TC_TILE / 16 ? BwdSmem::GO : BwdSmem::Y) + off) = zero;
+    }
+  }
+  for (int e = tid; e < 64 * K; e += BWD_THREADS) w1f[e] = a.mlp[e];
+  for (int k = tid; k < 64; k += BWD_THREADS) {
     bias[k] = p2[H * H + k];
     bias[64 + k] = p3[H * H + k];
   }
   if (tid < 16) bias[128 + tid] = tid < NO ? po[NO * H + tid] : 0.f;
   if (tid == 0) {
     tc::mbar_init(bar, 1);
+    tc::mbar_init(bar + 1, 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) {
     tc::tmem_alloc(tmem_ptr, 512);
     tc::tmem_relinquish();
   }
-  tc_sync_for_mma();
+  const int n_ib = (a.N + 15) / 16, n_tb = (a.T + 7) / 8;
+  const long long ntiles = (long long)n_ib * n_tb;
+  long long tile = blockIdx.x;
+  if (tile < ntiles) bwd_stage(a, tile, n_tb, sm + BwdSmem::STG);
+  cp_async_wait_all();
+  __syncthreads();  // zeroed y before its column 15 is set
+  if (c == 1) st_bf16(sm + BwdSmem::Y, row, 15, 1.f);
+  bool ok = tc_sync_ok(true, a.err);
   const uint32_t tmem = *tmem_ptr;
-  const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t lane_addr = tmem + ((uint32_t)(q4 * 32) << 16);
   auto sa = [&](uint32_t off) { return tc::smem_u32(sm + off); };
   constexpr uint32_t ID64 = tc::idesc_bf16(128, 64, false, false);
   constexpr uint32_t ID16 = tc::idesc_bf16(128, 16, false, false);
   constexpr uint32_t IDW = tc::idesc_bf16(128, 144, true, true);
   constexpr uint32_t IDX = tc::idesc_bf16(128, 128, true, true);
   uint32_t phase = 0;
-  bool ok = true, first = true;
-  const int il = tid & 15, tl = tid >> 4;
-  const int n_ib = (a.N + 15) / 16, n_tb = (a.T + 7) / 8;
-  const long long ntiles = (long long)n_ib * n_tb;
+  bool first = true;
+  const float* b2 = bias + 16 * c;
+  const float* b3 = bias + 64 + 16 * c;
 
-  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const int i0 = (int)(tile / n_tb) * 16, t0 = (int)(tile % n_tb) * 8;
-    const int i = i0 + il, t = t0 + tl;
-    const bool valid = i < a.N && t < a.T;
-    // y = (z_i, gamma_t, 0, ..., 1 at column 15, 0...)
-    {
-      const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+  // h1 of the tile staged in `stg`: act' mask and the H1 store
+  auto put_h1 = [&](const uint8_t* stg, bool valid) {
+    const float4* u4 = reinterpret_cast<const float4*>(stg + BwdStage::U + il * 256 + 64 * c);
+    const float4* v4 = reinterpret_cast<const float4*>(stg + BwdStage::V + tl * 256 + 64 * c);
+    float v[16];
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
-        *reinterpret_cast<uint4*>(sm + BwdSmem::Y + tc::sw128_off(tid, 8 * c)) = zero;
-      st_bf16(sm + BwdSmem::Y, tid, 15, 1.f);
-      float g[2 * NPG_MAX_FREQ];
-      time_embedding(valid ? t : 0, a.T, M, g);
-      for (int k = 0; k < Z; ++k)
-        st_bf16(sm + BwdSmem::Y, tid, k, valid ? a.z[(long long)i * Z + k] : 0.f);
-      for (int k = 0; k < 2 * M; ++k) st_bf16(sm + BwdSmem::Y, tid, Z + k, g[k]);
+    for (int k = 0; k < 4; ++k) {
+      const float4 u = u4[k], w = v4[k];
+      v[4 * k + 0] = valid ? leaky(u.x + w.x, a.slope) : 0.f;
+      v[4 * k + 1] = valid ? leaky(u.y + w.y, a.slope) : 0.f;
+      v[4 * k + 2] = valid ? leaky(u.z + w.z, a.slope) : 0.f;
+      v[4 * k + 3] = valid ? leaky(u.w + w.w, a.slope) : 0.f;
     }
-    float v[64];
-    uint32_t m1[2], m2[2], m3[2];  // act' masks (h > 0)
-    if (valid) {
-      const float4* u4 = reinterpret_cast<const float4*>(a.U + (long long)i * H);
-      const float4* v4 = reinterpret_cast<const float4*>(a.V + (long long)t * H);
+    uint32_t m = 0u;
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const float4 u = u4[k], w = v4[k];
-        v[4 * k + 0] = leaky(u.x + w.x, a.slope);
-        v[4 * k + 1] = leaky(u.y + w.y, a.slope);
-        v[4 * k + 2] = leaky(u.z + w.z, a.slope);
-        v[4 * k + 3] = leaky(u.w + w.w, a.slope);
+    for (int k = 0; k < 16; ++k) m |= (v[k] > 0.f ? 1u : 0u) << k;
+    st_row16(sm + BwdSmem::H1, row, 16 * c, v);
+    return m;
+  };
+  auto tile_valid = [&](long long tl_) {
+    const int i = (int)(tl_ / n_tb) * 16 + il, t = (int)(tl_ % n_tb) * 8 + tl;
+    return i < a.N && t < a.T;
+  };
+
+  uint32_t m1 = 0u;
+  int buf = 0;
+  if (tile < ntiles) m1 = put_h1(sm + BwdSmem::STG, tile_valid(tile));
+  // `ok` leaves the loop only through tc_sync_ok, so every thread breaks at
+  // the same barrier
+  for (; tile < ntiles; tile += gridDim.x) {
+    const long long next = tile + gridDim.x;
+    uint8_t* stg = sm + BwdSmem::STG + buf * BwdStage::BYTES;
+    const int t = (int)(tile % n_tb) * 8 + tl;
+    const bool valid = tile_valid(tile);
+    // the next tile's inputs copy while this tile computes
+    if (next < ntiles) bwd_stage(a, next, n_tb, sm + BwdSmem::STG + (buf ^ 1) * BwdStage::BYTES);
+    // y row (quarter 1): z_i, gamma_t in columns 0..Z+2M-1
+    if (c == 1) {
+      const float* zs = reinterpret_cast<const float*>(stg + BwdStage::Z) + il * Z;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < Z) st_bf16(sm + BwdSmem::Y, row, k, valid ? zs[k] : 0.f);
+      const float tt = a.T > 1 ? (float)(valid ? t : 0) / (float)(a.T - 1) : 0.f;
+      for (int j = 0; j < M; ++j) {
+        float sn, cs;
+        sincospif(ldexpf(tt, j), &sn, &cs);
+        st_bf16(sm + BwdSmem::Y, row, Z + 2 * j, sn);
+        st_bf16(sm + BwdSmem::Y, row, Z + 2 * j + 1, cs);
       }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 64; ++k) v[k] = 0.f;
     }
-    m1[0] = m1[1] = 0u;
-#pragma unroll
-    for (int k = 0; k < 64; ++k) m1[k >> 5] |= (v[k] > 0.f ? 1u : 0u) << (k & 31);
-    st_row64(sm + BwdSmem::H1, tid, v);
-    // ---- forward: layer 2, layer 3, output
-    tc_sync_for_mma();
+    // ---- forward: layer 2
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
       mma_k64(tmem + WORK_COL, sa(BwdSmem::H1), sa(BwdSmem::W2), ID64);
       tc::mma_commit(bar);
     }
-    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
-    ld_row64(lane, WORK_COL, v);
+    tc_wait(bar, phase, ok);
+    uint32_t m2 = 0u, m3 = 0u;
+    {
+      float v[16];
+      ld_col16(lane_addr + WORK_COL + 16 * c, v);
 #pragma unroll
-    for (int k = 0; k < 64; ++k) v[k] = leaky(v[k] + bias[k], a.slope);
-    m2[0] = m2[1] = 0u;
-#pragma unroll
-    for (int k = 0; k < 64; ++k) m2[k >> 5] |= (v[k] > 0.f ? 1u : 0u) << (k & 31);
-    st_row64(sm + BwdSmem::H2, tid, v);
-    tc_sync_for_mma();
+      for (int k = 0; k < 16; ++k) {
+        v[k] = leaky(v[k] + b2[k], a.slope);
+        m2 |= (v[k] > 0.f ? 1u : 0u) << k;
+      }
+      st_row16(sm + BwdSmem::H2, row, 16 * c, v);
+    }
+    // ---- layer 3
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
       mma_k64(tmem + WORK_COL, sa(BwdSmem::H2), sa(BwdSmem::W3), ID64);
       tc::mma_commit(bar);
     }
-    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
-    ld_row64(lane, WORK_COL, v);
+    tc_wait(bar, phase, ok);
+    {
+      float v[16];
+      ld_col16(lane_addr + WORK_COL + 16 * c, v);
 #pragma unroll
-    for (int k = 0; k < 64; ++k) v[k] = leaky(v[k] + bias[64 + k], a.slope);
-    m3[0] = m3[1] = 0u;
-#pragma unroll
-    for (int k = 0; k < 64; ++k) m3[k >> 5] |= (v[k] > 0.f ? 1u : 0u) << (k & 31);
-    st_row64(sm + BwdSmem::H3, tid, v);
-    tc_sync_for_mma();
+      for (int k = 0; k < 16; ++k) {
+        v[k] = leaky(v[k] + b3[k], a.slope);
+        m3 |= (v[k] > 0.f ? 1u : 0u) << k;
+      }
+      st_row16(sm + BwdSmem::H3, row, 16 * c, v);
+    }
+    // ---- output layer, then dL/do (quarter 0)
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
       mma_k64(tmem + WORK_COL, sa(BwdSmem::H3), sa(BwdSmem::WO), ID16);
       tc::mma_commit(bar);
     }
-    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
-    {
-      uint32_t r[16];
-      tc::tmem_ld16(lane + WORK_COL, r);
-      tc::tmem_ld_wait();
+    tc_wait(bar, phase, ok);
+    if (c == 0) {
+      float r[16];
+      ld_col16(lane_addr + WORK_COL, r);
       float o[7], go[7];
 #pragma unroll
       for (int j = 0; j < 7; ++j) {
-        o[j] = __uint_as_float(r[j]) + bias[128 + j];
+        o[j] = r[j] + bias[128 + j];
         go[j] = 0.f;
       }
-      if (valid)
-        transform_backward<ROT>(o, a.alpha, a.xr[i], a.dxhat[(long long)t * a.N + i], go);
+      if (valid) {
+        const float4 x = reinterpret_cast<const float4*>(stg + BwdStage::X)[il];
+        const float4 g = reinterpret_cast<const float4*>(stg + BwdStage::G)[tl * 16 + il];
+        transform_backward<ROT>(o, a.alpha, x, g, go);
+      }
       // output-bias gradient: summed in FP32 (rows cancel strongly; a BF16
       // rounding of each row's dL/do would dominate the sum)
 #pragma unroll
@@ -468,83 +604,99 @@ __global__ void __launch_bounds__(128, 1) mlp_bwd_tc_kernel(TcArgs a) {
         float sj = go[j];
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o2);
-        if ((tid & 31) == 0 && j < NO) atomicAdd(dbo + j, sj);
+        if (lane == 0 && j < NO) atomicAdd(dbo + j, sj);
       }
-      uint4 q0, q1;
+      uint4 q0;
       q0.x = tc::pack_bf16(go[0], go[1]);
       q0.y = tc::pack_bf16(go[2], go[3]);
       q0.z = tc::pack_bf16(go[4], go[5]);
       q0.w = tc::pack_bf16(NO > 6 ? go[6] : 0.f, 0.f);
-      q1.x = q1.y = q1.z = q1.w = 0u;
-      *reinterpret_cast<uint4*>(sm + BwdSmem::GO + tc::sw128_off(tid, 0)) = q0;
-      *reinterpret_cast<uint4*>(sm + BwdSmem::GO + tc::sw128_off(tid, 8)) = q1;
+      *reinterpret_cast<uint4*>(sm + BwdSmem::GO + tc::sw128_off(row, 0)) = q0;
     }
     // ---- backward: dh3 = gO Wo (K = 16)
-    tc_sync_for_mma();
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
       tc::mma_bf16(tmem + WORK_COL, tc::kmajor_sw128(sa(BwdSmem::GO)),
                    tc::kmajor_sw128(sa(BwdSmem::WOT)), ID64, 0u);
       tc::mma_commit(bar);
     }
-    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
-    ld_row64(lane, WORK_COL, v);
+    tc_wait(bar, phase, ok);
+    {
+      float v[16];
+      ld_col16(lane_addr + WORK_COL + 16 * c, v);
 #pragma unroll
-    for (int k = 0; k < 64; ++k)
-      v[k] *= ((m3[k >> 5] >> (k & 31)) & 1u) ? 1.f : a.slope;
-    st_row64(sm + BwdSmem::DP3, tid, v);
-    // dh2 = dpre3 W3
-    tc_sync_for_mma();
+      for (int k = 0; k < 16; ++k) v[k] *= ((m3 >> k) & 1u) ? 1.f : a.slope;
+      st_row16(sm + BwdSmem::DP3, row, 16 * c, v);
+    }
+    // ---- dh2 = dpre3 W3
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
       mma_k64(tmem + WORK_COL, sa(BwdSmem::DP3), sa(BwdSmem::W3T), ID64);
       tc::mma_commit(bar);
     }
-    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
-    ld_row64(lane, WORK_COL, v);
+    tc_wait(bar, phase, ok);
+    {
+      float v[16];
+      ld_col16(lane_addr + WORK_COL + 16 * c, v);
 #pragma unroll
-    for (int k = 0; k < 64; ++k)
-      v[k] *= ((m2[k >> 5] >> (k & 31)) & 1u) ? 1.f : a.slope;
-    st_row64(sm + BwdSmem::DP2, tid, v);
-    // ACC_W += [dpre3 | dpre2]^T [h2 | h1 | y]; dh1 = dpre2 W2
-    tc_sync_for_mma();
+      for (int k = 0; k < 16; ++k) v[k] *= ((m2 >> k) & 1u) ? 1.f : a.slope;
+      st_row16(sm + BwdSmem::DP2, row, 16 * c, v);
+    }
+    // ---- ACC_W += [dpre3 | dpre2]^T [h2 | h1 | y]; dh1 = dpre2 W2
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
       mma_rows(tmem + ACC_W_COL, sa(BwdSmem::DP3), sa(BwdSmem::H2), IDW, first);
       mma_k64(tmem + WORK_COL, sa(BwdSmem::DP2), sa(BwdSmem::W2T), ID64);
       tc::mma_commit(bar);
     }
-    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
-    ld_row64(lane, WORK_COL, v);
+    tc_wait(bar, phase, ok);
+    {
+      float v[16];
+      ld_col16(lane_addr + WORK_COL + 16 * c, v);
 #pragma unroll
-    for (int k = 0; k < 64; ++k)
-      v[k] *= ((m1[k >> 5] >> (k & 31)) & 1u) ? 1.f : a.slope;
-    st_row64(sm + BwdSmem::DP3, tid, v);  // dpre1 (ACC_W has consumed dpre3)
-    // dL/dz rows
-    for (int q = 0; q < Z; ++q) {
-      float s = 0.f;
+      for (int k = 0; k < 16; ++k) v[k] *= ((m1 >> k) & 1u) ? 1.f : a.slope;
+      st_row16(sm + BwdSmem::DP3, row, 16 * c, v);  // dpre1 (ACC_W has consumed dpre3)
+      // dL/dz partial over this quarter's 16 hidden units, FP32
+      float* dz_row = dzp + (row * 4 + c) * 8;
+      for (int qz = 0; qz < Z; ++qz) {
+        float s = 0.f;
 #pragma unroll
-      for (int j = 0; j < 64; ++j) s = fmaf(w1f[j * K + q], v[j], s);
-      dzs[tid * 8 + q] = valid ? s : 0.f;
+        for (int j = 0; j < 16; ++j) s = fmaf(w1f[(16 * c + j) * K + qz], v[j], s);
+        dz_row[qz] = valid ? s : 0.f;
+      }
     }
-    // ACC_X += [gO | dpre1]^T [y | h3]
-    tc_sync_for_mma();
+    // the next tile's staged inputs must have landed before the barrier
+    cp_async_wait_all();
+    // ---- ACC_X += [gO | dpre1]^T [y | h3]
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
       mma_rows(tmem + ACC_X_COL, sa(BwdSmem::GO), sa(BwdSmem::Y), IDX, first);
       tc::mma_commit(bar);
     }
-    for (int e = tid; e < 16 * Z; e += 128) {
-      const int vi = e / Z, q = e % Z;
-      if (i0 + vi >= a.N) continue;
-      float s = 0.f;
-#pragma unroll
-      for (int tt = 0; tt < 8; ++tt) s += dzs[(tt * 16 + vi) * 8 + q];
-      atomicAdd(a.dz + (long long)(i0 + vi) * Z + q, s);
-    }
     first = false;
-    // the next tile overwrites the operand tiles: wait for ACC_X to finish
-    if (!(ok = tc_wait_all(bar, phase, a.err))) break;
+    // dL/dz of the tile's 16 vertices: sum over its 8 frames and 4 quarters
+    {
+      const int i0 = (int)(tile / n_tb) * 16;
+      for (int e = tid; e < 16 * Z; e += BWD_THREADS) {
+        const int vi = e / Z, qz = e % Z;
+        if (i0 + vi >= a.N) continue;
+        float s = 0.f;
+#pragma unroll
+        for (int tt = 0; tt < 8; ++tt)
+#pragma unroll
+          for (int cq = 0; cq < 4; ++cq) s += dzp[((tt * 16 + vi) * 4 + cq) * 8 + qz];
+        atomicAdd(a.dz + (long long)(i0 + vi) * Z + qz, s);
+      }
+    }
+    // the next tile's h1 goes to H1, which ACC_X does not read
+    buf ^= 1;
+    if (next < ntiles) m1 = put_h1(sm + BwdSmem::STG + buf * BwdStage::BYTES, tile_valid(next));
+    // ACC_X reads y, h3, gO and dpre1: wait before the next tile writes them
+    tc_wait(bar, phase, ok);
   }
   // ---- accumulators -> global gradient (parameter layout), once per CTA
+  ok = tc_sync_ok(ok, a.err);
   if (ok && !first) {
-    const int row = tid;  // TMEM lane = D row
     float* g = a.g_mlp;
     float* gW1 = g;
     float* gb1 = g + H * K;
@@ -554,32 +706,38 @@ __global__ void __launch_bounds__(128, 1) mlp_bwd_tc_kernel(TcArgs a) {
     float* gb3 = gW3 + H * H;
     float* gWo = gb3 + H;
     float* gbo = gWo + NO * H;
-    float v[64];
-    if (row < 64) {  // ACC_W rows 0..63: dW3 (cols 0..63), db3 (col 143)
-      ld_row64(lane, ACC_W_COL, v);
-      for (int k = 0; k < 64; ++k) atomicAdd(gW3 + row * H + k, v[k]);
-      uint32_t r[16];
-      tc::tmem_ld16(lane + ACC_W_COL + 128, r);
-      tc::tmem_ld_wait();
-      atomicAdd(gb3 + row, __uint_as_float(r[15]));
-    } else {  // rows 64..127: dW2 (cols 64..127), db2 (col 143)
-      ld_row64(lane, ACC_W_COL + 64, v);
-      for (int k = 0; k < 64; ++k) atomicAdd(gW2 + (row - 64) * H + k, v[k]);
-      uint32_t r[16];
-      tc::tmem_ld16(lane + ACC_W_COL + 128, r);
-      tc::tmem_ld_wait();
-      atomicAdd(gb2 + (row - 64), __uint_as_float(r[15]));
+    float v[16];
+    // ACC_W rows 0..63: dW3 (cols 0..63), db3 (col 143); rows 64..127: dW2
+    // (cols 64..127), db2 (col 143)
+    const int wr = row < 64 ? row : row - 64;
+    ld_col16(lane_addr + ACC_W_COL + (row < 64 ? 0 : 64) + 16 * c, v);
+    float* gW = row < 64 ? gW3 : gW2;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) atomicAdd(gW + wr * H + 16 * c + k, v[k]);
+    if (c == 0) {
+      ld_col16(lane_addr + ACC_W_COL + 128, v);
+      atomicAdd((row < 64 ? gb3 : gb2) + wr, v[15]);
     }
-    if (row < 64) {  // ACC_X rows 0..NO-1: dW_out (cols 64..127)
-      ld_row64(lane, ACC_X_COL + 64, v);
-      if (row < NO)
-        for (int k = 0; k < 64; ++k) atomicAdd(gWo + row * H + k, v[k]);
-      if (row < NO) atomicAdd(gbo + row, dbo[row]);
-    } else {  // rows 64..127: dW1 (cols 0..K-1), db1 (col 15)
-      ld_row64(lane, ACC_X_COL, v);
+    // ACC_X rows 0..NO-1: dW_out (cols 64..127); rows 64..127: dW1 (cols
+    // 0..K-1), db1 (col 15)
+    if (q4 < 2) {  // rows 0..63
+      ld_col16(lane_addr + ACC_X_COL + 64 + 16 * c, v);
+      if (row < NO) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) atomicAdd(gWo + row * H + 16 * c + k, v[k]);
+        if (c == 0) atomicAdd(gbo + row, dbo[row]);
+      }
+    } else if (c == 0) {
+      ld_col16(lane_addr + ACC_X_COL, v);
       for (int k = 0; k < K; ++k) atomicAdd(gW1 + (row - 64) * K + k, v[k]);
       atomicAdd(gb1 + (row - 64), v[15]);
     }
+  }
+  // drain (bounded): no copy or MMA of this CTA may be in flight when it exits
+  cp_async_wait_all();
+  if (tid == 0) {
+    tc::mma_commit(bar + 1);
+    tc::mbar_wait(bar + 1, 0, WAIT_TRIES);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -593,7 +751,7 @@ cudaError_t launch_mlp_backward_bf16(npg_ctx* c) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long tiles = (long long)((c->N + 15) / 16) * ((c->T + 7) / 8);
-  k<<<tc_blocks(c, tiles, 1), 128, smem, c->stream>>>(tc_args(c));
+  k<<<tc_blocks(c, tiles, 1), BWD_THREADS, smem, c->stream>>>(tc_args(c));
   return cudaGetLastError();
 }
 

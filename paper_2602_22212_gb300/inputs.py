@@ -316,10 +316,12 @@ def preset(name):
                     res=linear_resolutions(4, 8, 64), F=2, H=64, D=2, slope=0.0, iters=10)
     if name == "paper":     # 40962 vertices, 100 frames, 20000 points per frame
         return dict(gen="figure", subdiv=6, T=100, M=20000, noise_rel=0.003, L=8,
-                    res=linear_resolutions(8, 16, 256), F=4, H=64, D=3, slope=0.01, iters=500)
+                    res=linear_resolutions(8, 16, 256), F=4, H=64, D=3, slope=0.01, iters=500,
+                    w_iso=1.0)
     if name == "profile":   # 10242 vertices, 10 frames, 20000 points: search kernels at moderate size
         return dict(gen="figure", subdiv=5, T=10, M=20000, noise_rel=0.003, L=4,
-                    res=linear_resolutions(4, 16, 64), F=4, H=64, D=3, slope=0.01, iters=500)
+                    res=linear_resolutions(4, 16, 64), F=4, H=64, D=3, slope=0.01, iters=500,
+                    w_iso=1.0)
     raise KeyError(name)
 
 
