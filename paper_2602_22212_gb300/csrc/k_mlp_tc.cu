@@ -301,7 +301,7 @@ struct BwdSmem {
   static constexpr uint32_t GO = H3 + TC_TILE, DP3 = GO + TC_TILE, DP2 = DP3 + TC_TILE;
   static constexpr uint32_t W1F = DP2 + TC_TILE;                // FP32 W1 (64 x K <= 64 x 15)
   static constexpr uint32_t BIAS = W1F + 64 * 16 * 4;           // b2, b3, bo FP32
-  static constexpr uint32_t DZP = BIAS + (64 + 64 + 16) * 4;    // FP32 [128 rows][4][8]
+  static constexpr uint32_t DZP = BIAS + (64 + 64 + 16) * 4;    // FP32 [4][8][128 rows]
   static constexpr uint32_t STG = DZP + 128 * 4 * 8 * 4;        // 2 x BwdStage
   static constexpr uint32_t DBO = STG + 2 * BwdStage::BYTES;    // FP32 [8] output-bias gradient
   static constexpr uint32_t BAR = DBO + 8 * 4;  // MMA completion, final drain
@@ -657,12 +657,11 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
       for (int k = 0; k < 16; ++k) v[k] *= ((m1 >> k) & 1u) ? 1.f : a.slope;
       st_row16(sm + BwdSmem::DP3, row, 16 * c, v);  // dpre1 (ACC_W has consumed dpre3)
       // dL/dz partial over this quarter's 16 hidden units, FP32
-      float* dz_row = dzp + (row * 4 + c) * 8;
       for (int qz = 0; qz < Z; ++qz) {
         float s = 0.f;
 #pragma unroll
         for (int j = 0; j < 16; ++j) s = fmaf(w1f[(16 * c + j) * K + qz], v[j], s);
-        dz_row[qz] = valid ? s : 0.f;
+        dzp[(c * 8 + qz) * 128 + row] = valid ? s : 0.f;
       }
     }
     // the next tile's staged inputs must have landed before the barrier
@@ -678,13 +677,13 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
     {
       const int i0 = (int)(tile / n_tb) * 16;
       for (int e = tid; e < 16 * Z; e += BWD_THREADS) {
-        const int vi = e / Z, qz = e % Z;
+        const int vi = e & 15, qz = e >> 4;
         if (i0 + vi >= a.N) continue;
         float s = 0.f;
 #pragma unroll
         for (int tt = 0; tt < 8; ++tt)
 #pragma unroll
-          for (int cq = 0; cq < 4; ++cq) s += dzp[((tt * 16 + vi) * 4 + cq) * 8 + qz];
+          for (int cq = 0; cq < 4; ++cq) s += dzp[(cq * 8 + qz) * 128 + tt * 16 + vi];
         atomicAdd(a.dz + (long long)(i0 + vi) * Z + qz, s);
       }
     }
