@@ -244,6 +244,81 @@ def run_micro(args):
                       "hbm_peak_gbs": peaks["hbm"], "peak_source": peaks["src"]}))
 
 
+def run_batch(args):
+    """Uneven sequences (sizes from inputs.batch_specs: N 5k-50k, T 50-500, M
+    5k-30k, sphere blobs and capsule figures) optimised as one batch: every
+    iteration of all of them is one CUDA-graph launch with a branch per
+    sequence. value = total vertex-frames / batched iteration time; the same
+    contexts run one after the other (each its own graph, synchronised in
+    between) for `one_by_one`. Sequences are generated in worker processes
+    (spawned before any CUDA use); generation is outside the timed region."""
+    from concurrent.futures import ProcessPoolExecutor
+    import multiprocessing as mp
+    from paper_2602_22212_gb300 import inputs as I
+    specs = I.batch_specs(args.batch, seed=0)
+    with ProcessPoolExecutor(max_workers=min(len(specs), os.cpu_count() or 1),
+                             mp_context=mp.get_context("spawn")) as ex:
+        seqs = list(ex.map(I.make_batch_sequence, specs))
+    import torch
+    from paper_2602_22212_gb300 import build, npg
+    build.build()
+    p = dict(L=8, res=I.linear_resolutions(8, 16, 256), F=4, H=64, D=3, slope=0.01, w_iso=1.0)
+    K, NO = 2 + p["F"] + 8, 7
+    ctxs, streams = [], []
+    for k, seq in enumerate(seqs):
+        st = torch.cuda.Stream()
+        cfg = make_cfg(npg, p, "bf16", True, st, 200, "tc")
+        ctxs.append(npg.Context(cfg, seq, I.mlp_init(K, p["H"], p["D"], NO, seed=k),
+                                device_inputs=True))
+        streams.append(st)
+    main = torch.cuda.Stream()
+    batch = npg.npg_batch_create([c.h for c in ctxs], main)
+    vf = sum(s.N * s.T for s in seqs)
+    for _ in range(args.warmup):
+        npg.npg_batch_iteration(batch)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    l0 = sum(npg.npg_launch_count(c.h) for c in ctxs)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(main)
+    for _ in range(args.steps):
+        npg.npg_batch_iteration(batch)
+    ev1.record(main)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clocks = sampler.stop()
+    launches = sum(npg.npg_launch_count(c.h) for c in ctxs) - l0
+    # one by one: each sequence's own graph, the next one after it finishes
+    for c in ctxs:
+        npg.npg_iteration(c.h)  # eager + capture of the per-sequence graph
+    torch.cuda.synchronize()
+    steps1 = max(1, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(steps1):
+        for c in ctxs:
+            npg.npg_iteration(c.h)
+            torch.cuda.synchronize()
+    ms1 = (time.perf_counter() - t0) / steps1 * 1e3
+    npg.npg_batch_destroy(batch)
+    sizes = [dict(gen=s["gen"], N=q.N, T=q.T, M=s["M"]) for s, q in zip(specs, seqs)]
+    print(json.dumps({
+        "metric": f"batched uneven sequences: total vertex-frames/s ({len(seqs)} sequences)",
+        "value": vf / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded sphere blobs and "
+        "capsule figures of uneven sizes; no dataset)",
+        "config": {"workload": f"{len(seqs)} uneven sequences, {vf} vertex-frames per "
+                               "iteration, 8-level grid 16->256 x F=4, MLP 3x64, w_iso=1",
+                   "form": "one CUDA graph per batch iteration, a branch per sequence",
+                   "sequences": sizes},
+        "one_by_one": {"value": vf / (ms1 * 1e-3), "unit": UNIT, "ms_per_step": ms1,
+                       "timing": "host clock, each sequence's graph synchronised"},
+        "gpu_launches": int(launches), "clocks": clocks}))
+    for c in ctxs:
+        c.close()
+
+
 def config_dict(p, seq, form, graph):
     return {"workload": f"{p['gen']} N={seq.N} T={seq.T} M={int(seq.offsets[1])}/frame, "
                         f"{p['L']}-level grid {p['res'][0]}->{p['res'][-1]} x F={p['F']}, "
@@ -270,6 +345,9 @@ def main():
                     help="preconditioner DCT arithmetic (default: tc with bf16, fp32 with fp32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="time that many uneven sequences as one batch (npg_batch_*) against "
+                         "running them one by one, instead of the single-sequence step")
     ap.add_argument("--micro", default=None, choices=["precond_tc", "precond_fp32"],
                     help="time one kernel family alone on a standalone grid instead of the step")
     ap.add_argument("--micro-res", type=int, default=256)
@@ -279,6 +357,8 @@ def main():
         return run_reference(args)
     if args.micro:
         return run_micro(args)
+    if args.batch:
+        return run_batch(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))

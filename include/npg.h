@@ -192,6 +192,27 @@ NPG_API int npg_step(npg_ctx* ctx);
  * four calls are captured once into a CUDA graph and replayed. */
 NPG_API int npg_iteration(npg_ctx* ctx, double* loss_out);
 
+/*
+ * Batch of independent sequences (many sequences of uneven vertex, frame and
+ * point counts optimised together). The caller creates one context per
+ * sequence with npg_create, each with its own non-default stream, distinct
+ * from the others and from `stream`; the batch does not own them (destroy the
+ * batch first). npg_batch_iteration runs one iteration (forward, loss,
+ * backward, step) of every sequence: the first call runs them eagerly and
+ * captures the next iteration of all of them into one CUDA graph, in which
+ * every sequence is a branch forked from and joined back to `stream`, so
+ * small sequences share the GPU; later calls replay it. Each context's
+ * stream is ordered after the batch iteration (the contexts stay usable with
+ * the single-sequence calls, which reset nothing in the batch). loss_out
+ * (host, nullable): S x 3 doubles {L, L_def, L_iso} per sequence of this
+ * iteration (synchronizes). A context may belong to one batch at a time.
+ */
+typedef struct npg_batch npg_batch;
+NPG_API int npg_batch_create(npg_batch** out, int S, npg_ctx* const* ctxs, void* stream);
+NPG_API int npg_batch_iteration(npg_batch* batch, double* loss_out);
+/* NULL is allowed. Leaves the contexts alive. */
+NPG_API int npg_batch_destroy(npg_batch* batch);
+
 /* Replace the point clouds (same T; per-frame counts may change, total at most
  * the count given at create). on_device as for npg_create. Resets the call
  * order to "before forward". */

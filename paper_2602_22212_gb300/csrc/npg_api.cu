@@ -972,6 +972,147 @@ extern "C" int npg_timing_read(npg_ctx* c, int stage, double* total_ms, int* n_i
 
 extern "C" long long npg_launch_count(const npg_ctx* c) { return c ? c->launches : 0; }
 
+// ----------------------------------------------------------------- batch
+struct npg_batch {
+  std::vector<npg_ctx*> ctx;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<long long> graph_launches;
+};
+
+extern "C" int npg_batch_destroy(npg_batch* b) {
+  if (!b) return NPG_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete b;
+  return NPG_OK;
+}
+
+extern "C" int npg_batch_create(npg_batch** out, int S, npg_ctx* const* ctxs, void* stream) {
+  if (!out) return set_err(nullptr, NPG_EINVAL, "npg_batch_create: out is NULL");
+  *out = nullptr;
+  if (S < 1 || !ctxs || !stream)
+    return set_err(nullptr, NPG_EINVAL, "npg_batch_create: S=%d, ctxs and stream non-NULL", S);
+  cudaStream_t bs = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < S; ++i) {
+    npg_ctx* c = ctxs[i];
+    if (!c) return set_err(nullptr, NPG_EINVAL, "npg_batch_create: context %d is NULL", i);
+    if (int rc = guard(c)) return rc;
+    if (!c->stream || c->stream == bs)
+      return set_err(nullptr, NPG_EINVAL,
+                     "npg_batch_create: context %d needs its own non-default stream", i);
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c || ctxs[j]->stream == c->stream)
+        return set_err(nullptr, NPG_EINVAL,
+                       "npg_batch_create: contexts %d and %d share a stream", j, i);
+  }
+  npg_batch* b = new npg_batch;
+  b->ctx.assign(ctxs, ctxs + S);
+  b->stream = bs;
+  b->join.assign(S, nullptr);
+  b->graph_launches.assign(S, 0);
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  for (int i = 0; i < S && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    npg_batch_destroy(b);
+    return cuda_fail(nullptr, e, "npg_batch_create: cudaEventCreate");
+  }
+  *out = b;
+  return NPG_OK;
+}
+
+// The batch stream waits for every context's stream (prior single-sequence work).
+static cudaError_t batch_after_contexts(npg_batch* b) {
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    cudaError_t e = cudaEventRecord(b->join[i], b->ctx[i]->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Every context's stream waits for the batch stream (later single-sequence work).
+static cudaError_t contexts_after_batch(npg_batch* b) {
+  cudaError_t e = cudaEventRecord(b->done, b->stream);
+  for (size_t i = 0; i < b->ctx.size() && e == cudaSuccess; ++i)
+    e = cudaStreamWaitEvent(b->ctx[i]->stream, b->done, 0);
+  return e;
+}
+
+static int batch_loss_out(npg_batch* b, double* loss_out) {
+  if (!loss_out) return NPG_OK;
+  for (size_t i = 0; i < b->ctx.size(); ++i)
+    if (int rc = copy_loss_out(b->ctx[i], loss_out + 3 * i, nullptr)) return rc;
+  return NPG_OK;
+}
+
+extern "C" int npg_batch_iteration(npg_batch* b, double* loss_out) {
+  if (!b) return set_err(nullptr, NPG_EINVAL, "batch is NULL");
+  for (npg_ctx* c : b->ctx)
+    if (int rc = guard(c)) return rc;
+  const int S = (int)b->ctx.size();
+  if (!b->exec) {
+    // one eager iteration of every sequence, each on its own stream (function
+    // attributes and lazy module loading happen outside the capture)
+    for (npg_ctx* c : b->ctx) {
+      if (int rc = iteration_launch(c)) return rc;
+      c->e += 1;
+      c->phase = 0;
+    }
+    for (npg_ctx* c : b->ctx) CK(c, cudaStreamSynchronize(c->stream));
+    // capture: the batch stream forks to every context's stream and joins them
+    CK(nullptr, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = NPG_OK;
+    cudaError_t ce = cudaEventRecord(b->fork, b->stream);
+    for (int i = 0; i < S && ce == cudaSuccess && rc == NPG_OK; ++i) {
+      npg_ctx* c = b->ctx[i];
+      ce = cudaStreamWaitEvent(c->stream, b->fork, 0);
+      if (ce != cudaSuccess) break;
+      c->capturing = 1;
+      const long long before = c->launches;
+      rc = iteration_launch(c);
+      c->capturing = 0;
+      b->graph_launches[i] = c->launches - before;
+      c->launches = before;
+      if (rc) break;
+      ce = cudaEventRecord(b->join[i], c->stream);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+    if (rc || ce != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (rc) return rc;
+      return cuda_fail(nullptr, ce != cudaSuccess ? ce : ee, "npg_batch_iteration: capture");
+    }
+    b->graph = g;
+    CK(nullptr, cudaGraphInstantiate(&b->exec, g, 0));
+    // this call's iteration was the eager one; replays start with the next call
+    return batch_loss_out(b, loss_out);
+  }
+  CK(nullptr, batch_after_contexts(b));
+  CK(nullptr, cudaGraphLaunch(b->exec, b->stream));
+  CK(nullptr, contexts_after_batch(b));
+  for (int i = 0; i < S; ++i) {
+    npg_ctx* c = b->ctx[i];
+    c->e += 1;
+    c->phase = 0;
+    c->launches += b->graph_launches[i];
+  }
+  return batch_loss_out(b, loss_out);
+}
+
 extern "C" int npg_destroy(npg_ctx* c) {
   if (!c) return NPG_OK;
   if (c->stream || true) cudaStreamSynchronize(c->stream);

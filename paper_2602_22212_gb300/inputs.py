@@ -66,6 +66,27 @@ def icosphere(subdiv: int):
     return v, f.astype(np.int32)
 
 
+def fibonacci_sphere(n: int):
+    """n points on the unit sphere along the golden-angle spiral, triangulated
+    by their convex hull (outward-oriented faces): a sphere mesh of any size."""
+    from scipy.spatial import ConvexHull
+    k = np.arange(n, dtype=np.float64) + 0.5
+    z = 1.0 - 2.0 * k / n
+    r = np.sqrt(np.maximum(1.0 - z * z, 0.0))
+    phi = np.pi * (3.0 - 5.0 ** 0.5) * k
+    v = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+    f = ConvexHull(v).simplices.astype(np.int64)
+    nrm = np.cross(v[f[:, 1]] - v[f[:, 0]], v[f[:, 2]] - v[f[:, 0]])
+    flip = np.einsum("ij,ij->i", nrm, v[f[:, 0]]) < 0
+    f[flip] = f[flip][:, [0, 2, 1]]
+    return v, f.astype(np.int32)
+
+
+def sphere_mesh(subdiv=4, n_vertices=None):
+    """Icosphere of the given subdivision, or a Fibonacci sphere of n_vertices."""
+    return icosphere(subdiv) if n_vertices is None else fibonacci_sphere(int(n_vertices))
+
+
 def vertex_normals(v, f):
     """Area-weighted vertex normals (unit length)."""
     n = np.cross(v[f[:, 1]] - v[f[:, 0]], v[f[:, 2]] - v[f[:, 0]])
@@ -143,13 +164,13 @@ def _finish(frames, f, t_key, M, noise_rel, noise_abs, rng):
                     points=pts, offsets=off, t_key=int(t_key), gt_frames=frames)
 
 
-def sphere_blob(subdiv=4, T=8, M=4096, noise=0.005, seed=0, t_key=None):
+def sphere_blob(subdiv=4, T=8, M=4096, noise=0.005, seed=0, t_key=None, n_vertices=None):
     """Icosphere under three localized smooth rotations (centre c_k on the
     sphere, radius r_k ~ U(0.3, 0.8), random axis, angle 0.5 sin(2 pi t~ + phi_k)
     falling off as exp(-|x - c_k|^2 / r_k^2)) and a radial bulge of amplitude
     0.1; noise is an absolute standard deviation."""
     rng = np.random.default_rng(seed)
-    v0, f = icosphere(subdiv)
+    v0, f = sphere_mesh(subdiv, n_vertices)
     cs = _unit(rng, 3)
     rs = rng.uniform(0.3, 0.8, size=3)
     axes = _unit(rng, 3)
@@ -204,10 +225,10 @@ def _figure_sdf(p, limbs, k=0.08):
     return d
 
 
-def figure_mesh(subdiv=6):
-    """Icosphere radially projected onto the capsule figure's zero level set."""
+def figure_mesh(subdiv=6, n_vertices=None):
+    """Sphere mesh radially projected onto the capsule figure's zero level set."""
     limbs = _limb_defs()
-    u, f = icosphere(subdiv)
+    u, f = sphere_mesh(subdiv, n_vertices)
     rho = np.linspace(0.0, 1.6, 321)
     vals = np.stack([_figure_sdf(u * r, limbs) for r in rho], axis=1)  # N x S
     sign = vals > 0
@@ -225,13 +246,14 @@ def figure_mesh(subdiv=6):
     return v, f, limbs
 
 
-def figure(subdiv=6, T=100, M=20000, noise_rel=0.003, seed=0, t_key=None, amp_deg=60.0):
+def figure(subdiv=6, T=100, M=20000, noise_rel=0.003, seed=0, t_key=None, amp_deg=60.0,
+           n_vertices=None):
     """Capsule figure animated by linear blend skinning: each limb rotates
     about its proximal joint by amp sin(2 pi f t~ + phi) about a random axis
     (amp <= amp_deg, f in {1, 2}); skinning weights softmax(-d_k^2 / s^2) over
     the distances to the capsule segments; plus a slow global sway."""
     rng = np.random.default_rng(seed)
-    v, f, limbs = figure_mesh(subdiv)
+    v, f, limbs = figure_mesh(subdiv, n_vertices)
     n_l = len(limbs)
     d2 = np.stack([_seg_dist(v, a, b) ** 2 for a, b, _ in limbs], axis=1)
     s2 = 0.08 ** 2
@@ -323,6 +345,24 @@ def preset(name):
                     res=linear_resolutions(4, 16, 64), F=4, H=64, D=3, slope=0.01, iters=500,
                     w_iso=1.0)
     raise KeyError(name)
+
+
+def batch_specs(n=16, seed=0):
+    """Sizes of the uneven-sequence batch: N ~ U[5000, 50000] vertices (Fibonacci
+    spheres), T ~ U[50, 500] frames, M ~ U[5000, 30000] points per frame; even
+    sequences use the sphere-blob generator, odd ones the capsule figure."""
+    rng = np.random.default_rng(seed)
+    return [dict(gen="sphere_blob" if s % 2 == 0 else "figure",
+                 n_vertices=int(rng.integers(5000, 50001)), T=int(rng.integers(50, 501)),
+                 M=int(rng.integers(5000, 30001)), seed=1000 + s) for s in range(n)]
+
+
+def make_batch_sequence(spec):
+    if spec["gen"] == "sphere_blob":
+        return sphere_blob(T=spec["T"], M=spec["M"], noise=0.005, seed=spec["seed"],
+                           n_vertices=spec["n_vertices"])
+    return figure(T=spec["T"], M=spec["M"], noise_rel=0.003, seed=spec["seed"],
+                  n_vertices=spec["n_vertices"])
 
 
 def make_sequence(p, seed=0):

@@ -102,6 +102,9 @@ _SIG = {
     "npg_timing_read": (_i, [_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "npg_launch_count": (C.c_longlong, [_vp]),
     "npg_search_stats": (_i, [_vp, C.POINTER(C.c_longlong)]),
+    "npg_batch_create": (_i, [C.POINTER(_vp), _i, C.POINTER(_vp), _vp]),
+    "npg_batch_iteration": (_i, [_vp, _vp]),
+    "npg_batch_destroy": (_i, [_vp]),
 }
 for _name, (_res, _args) in _SIG.items():
     _f = getattr(_lib, _name)
@@ -196,6 +199,23 @@ def npg_backprop(ctx, dxhat=None):
 
 def npg_iteration(ctx, loss_out=None):
     _check(_lib.npg_iteration(ctx, _ptr(loss_out)), ctx)
+
+
+def npg_batch_create(ctxs, stream):
+    """ctxs: context handles, each created with its own non-default stream."""
+    arr = (C.c_void_p * len(ctxs))(*ctxs)
+    out = C.c_void_p()
+    _check(_lib.npg_batch_create(C.byref(out), len(ctxs), arr, _stream_handle(stream)))
+    return out.value
+
+
+def npg_batch_iteration(batch, loss_out=None):
+    """loss_out: host float64 array of S x 3, or None."""
+    _check(_lib.npg_batch_iteration(batch, _ptr(loss_out)))
+
+
+def npg_batch_destroy(batch):
+    _check(_lib.npg_batch_destroy(batch))
 
 
 def npg_set_points(ctx, points, frame_offsets):
