@@ -1,0 +1,149 @@
+"""Differentiation stress case: N = 100000 vertices (Fibonacci-sphere capsule
+figure), T = 200 frames, M = 100000 points per frame (Chamfer-dominated),
+plain FP32, 8-level grid 16 -> 256.
+
+At this size every buffer of one iteration (20 M vertex-frames, 20 M points)
+fits in HBM at once, so no per-frame recomputation is needed. Checks, as for
+the benchmark workload, on what the oracle can compute one by one:
+  search        sampled queries of both directions bit-exact against brute
+                force on the GPU's own x-hat
+  loss          cd_t and L re-formed in FP64 from the GPU's indices
+  reverse pass  a dL/dx-hat nonzero on 16 vertices (all 200 frames) against
+                the oracle's reverse pass on those vertices
+  gradient      central differences of the GPU loss (steps 1e-3 / 1e-4) along
+                the gradient and along random-sign combinations of its 64
+                largest entries, grid and MLP, against the hand-written adjoint
+The context runs at e = e_max (all confidence weights 1) with w_iso = 0, where
+the paper's stop-gradient inputs are constant, so that finite differences and
+the adjoint differentiate the same function.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_22212_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+N, T, M = 100000, 200, 100000
+
+
+@pytest.fixture(scope="module")
+def npg():
+    from paper_2602_22212_gb300 import build
+    build.build()
+    from paper_2602_22212_gb300 import npg as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def stress(npg):
+    import torch
+    seq = I.figure(T=T, M=M, noise_rel=0.003, seed=11, n_vertices=N)
+    res = I.linear_resolutions(8, 16, 256)
+    ocfg = O.make_cfg(L=8, res=res, F=4, H=64, D=3, slope=0.01, w_iso=0.0)
+    rng = np.random.default_rng(12)
+    grid = rng.normal(scale=0.3, size=O.grid_len(ocfg)).astype(np.float32)
+    mlp = I.mlp_init(O.k_in(ocfg), 64, 3, O.n_out(ocfg), seed=13, zero_last=False)
+    mlp[-(O.n_out(ocfg) * 64 + O.n_out(ocfg)):] *= 0.5
+    e_max = 200
+    cfg = npg.make_config(8, res, 4, 64, 3, slope=0.01, e_max=e_max, w_iso=0.0)
+    ctx = npg.Context(cfg, seq, mlp, device_inputs=True)
+    npg.npg_set_epoch(ctx.h, e_max)
+    fn = npg.npg_loss_fn()
+    dev = torch.device("cuda")
+    g = torch.tensor(grid, device=dev, requires_grad=True)
+    m = torch.tensor(mlp, device=dev, requires_grad=True)
+    loss = fn.apply(g, m, ctx.h)
+    loss.backward()
+    st = dict(seq=seq, ocfg=ocfg, ctx=ctx, fn=fn, grid=grid, mlp=mlp, loss=float(loss),
+              gg=g.grad.double().cpu().numpy(), gm=m.grad.double().cpu().numpy(),
+              xhat=ctx.get(npg.BUF_XHAT).reshape(T, N, 3), nnx=ctx.get(npg.BUF_NN_X).reshape(T, N),
+              nnp=ctx.get(npg.BUF_NN_P), cd=ctx.get(npg.BUF_CD))
+    yield st
+    ctx.close()
+
+
+def test_search_sampled_queries_bit_exact(stress):
+    seq, xh = stress["seq"], stress["xhat"]
+    rng = np.random.default_rng(14)
+    pts = seq.points.astype(np.float64)
+    for t in rng.choice(T, size=4, replace=False):
+        a, b = int(seq.offsets[t]), int(seq.offsets[t + 1])
+        P, X = pts[a:b], xh[t].astype(np.float64)
+        qi = rng.choice(N, size=100, replace=False)
+        np.testing.assert_array_equal(stress["nnx"][t, qi], O.nn(X[qi], P, decide_f32=True)[0])
+        qj = rng.choice(b - a, size=100, replace=False)
+        np.testing.assert_array_equal(stress["nnp"][a + qj], O.nn(P[qj], X, decide_f32=True)[0])
+
+
+def test_loss_from_gpu_indices(stress):
+    seq, xh = stress["seq"], stress["xhat"]
+    pts = seq.points.astype(np.float64)
+    cd = np.zeros(T)
+    for t in range(T):
+        a, b = int(seq.offsets[t]), int(seq.offsets[t + 1])
+        P, X = pts[a:b], xh[t].astype(np.float64)
+        cd[t] = (np.sum((X - P[stress["nnx"][t]]) ** 2, axis=1).mean() +
+                 np.sum((P - X[stress["nnp"][a:b]]) ** 2, axis=1).mean())
+    np.testing.assert_allclose(stress["cd"], cd, rtol=1e-5)
+    # e = e_max: every confidence weight is 1, w_iso = 0: L = mean_t cd_t
+    assert abs(stress["loss"] - cd.mean()) <= 1e-5 * cd.mean()
+
+
+def test_reverse_pass_of_sampled_vertices(stress, npg):
+    import torch
+    seq, ocfg, ctx = stress["seq"], stress["ocfg"], stress["ctx"]
+    rng = np.random.default_rng(15)
+    S = np.sort(rng.choice(N, size=16, replace=False))
+    gs = rng.normal(scale=1e-3, size=(T, len(S), 3)).astype(np.float32)
+    gx = np.zeros((T, N, 3), np.float32)
+    gx[:, S] = gs
+    ctx.set(npg.BUF_GRID, stress["grid"])
+    ctx.set(npg.BUF_MLP, stress["mlp"])
+    ctx.forward()
+    npg.npg_backprop(ctx.h, torch.from_numpy(gx.reshape(-1)).cuda())
+    gg = ctx.get(npg.BUF_GRID_GRAD).astype(np.float64)
+    gm = ctx.get(npg.BUF_MLP_GRAD).astype(np.float64)
+    sub = O.Problem(ocfg, seq.x[S], seq.n[S], np.zeros((0, 3), np.int32), np.zeros((1, 3)),
+                    np.array([0] + [1] * T), seq.t_key)
+    want_g, want_m = O.backprop(sub, stress["grid"].astype(np.float64),
+                                stress["mlp"].astype(np.float64), gs.astype(np.float64))
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(gm, want_m) <= 1e-4, rel(gm, want_m)
+    for l in range(ocfg.L + 1):
+        a = O.level_offset(ocfg, l)
+        b = O.level_offset(ocfg, l + 1) if l < ocfg.L else O.grid_len(ocfg)
+        assert rel(gg[a:b], want_g[a:b]) <= 1e-4, (l, rel(gg[a:b], want_g[a:b]))
+
+
+def test_gradient_matches_central_differences(stress):
+    import torch
+    fn, ctx = stress["fn"], stress["ctx"]
+    dev = torch.device("cuda")
+    grid0, mlp0 = stress["grid"].astype(np.float64), stress["mlp"].astype(np.float64)
+
+    def L(g, m):
+        with torch.no_grad():
+            return float(fn.apply(torch.tensor(g, dtype=torch.float32, device=dev),
+                                  torch.tensor(m, dtype=torch.float32, device=dev), ctx.h))
+
+    rng = np.random.default_rng(16)
+    for name, g0, gvec in (("grid", grid0, stress["gg"]), ("mlp", mlp0, stress["gm"])):
+        eps = 1e-3 if name == "grid" else 1e-4
+
+        def Ld(d):
+            if name == "grid":
+                return (L(g0 + eps * d, mlp0) - L(g0 - eps * d, mlp0)) / (2 * eps)
+            return (L(grid0, g0 + eps * d) - L(grid0, g0 - eps * d)) / (2 * eps)
+
+        gn = np.linalg.norm(gvec)
+        fd = Ld(gvec / gn)
+        assert abs(fd - gn) <= 2e-3 * gn, (name, fd, gn)
+        top = np.argsort(-np.abs(gvec))[:64]
+        for k in range(2):
+            d = np.zeros_like(g0)
+            d[top] = rng.choice([-1.0, 1.0], size=len(top))
+            d /= np.linalg.norm(d)
+            fd, an = Ld(d), float(gvec @ d)
+            assert abs(fd - an) <= 1e-2 * abs(an) + 2e-3 * gn, (name, k, fd, an)
