@@ -56,7 +56,7 @@ def stress(npg):
     m = torch.tensor(mlp, device=dev, requires_grad=True)
     loss = fn.apply(g, m, ctx.h)
     loss.backward()
-    st = dict(seq=seq, ocfg=ocfg, ctx=ctx, fn=fn, grid=grid, mlp=mlp, loss=float(loss),
+    st = dict(seq=seq, ocfg=ocfg, ctx=ctx, fn=fn, grid=grid, mlp=mlp, loss=float(loss.detach()),
               gg=g.grad.double().cpu().numpy(), gm=m.grad.double().cpu().numpy(),
               xhat=ctx.get(npg.BUF_XHAT).reshape(T, N, 3), nnx=ctx.get(npg.BUF_NN_X).reshape(T, N),
               nnp=ctx.get(npg.BUF_NN_P), cd=ctx.get(npg.BUF_CD))
