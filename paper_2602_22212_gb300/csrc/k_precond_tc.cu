@@ -17,7 +17,17 @@
 // columns as MN-major tiles, and one thread issues 12 MMAs per 128-row block
 // into one of two TMEM accumulators while the epilogue warps drain the other
 // with coalesced rotated stores (float4 for F = 4).
+//
+// Between the passes of one preconditioner call the data stays split: a pass
+// may store its output as the hi and lo BF16 arrays (the same bytes as FP32,
+// rows padded to a multiple of 8 elements), and the next pass then loads its
+// input tiles with TMA straight into the swizzled operand layout, so that its
+// producer warps move no data through registers. Only the first pass reads
+// (and splits) FP32 and only the last one writes FP32.
+#include <cuda.h>  // CUtensorMap and its encoder's types (the encoder is fetched at run time)
 #include <cuda_bf16.h>
+
+#include <mutex>
 
 #include "npg_internal.cuh"
 #include "tc_sm100.cuh"
@@ -61,6 +71,21 @@ __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// hi = bf16(x), lo = bf16(x - hi) of 4 values, packed in pairs.
+__device__ __forceinline__ void split4(float4 x, uint2& hi, uint2& lo) {
+  const float v[4] = {x.x, x.y, x.z, x.w};
+  uint32_t h[2], l[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const __nv_bfloat16 a = __float2bfloat16_rn(v[2 * j]);
+    const __nv_bfloat16 b = __float2bfloat16_rn(v[2 * j + 1]);
+    h[j] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+    l[j] = tc::pack_bf16(v[2 * j] - __bfloat162float(a), v[2 * j + 1] - __bfloat162float(b));
+  }
+  hi = make_uint2(h[0], h[1]);
+  lo = make_uint2(l[0], l[1]);
+}
+
 // Bounded wait shared by every role; gives up (and flags the CTA) once any
 // thread of the CTA has timed out.
 __device__ __forceinline__ bool pc_wait(uint64_t* bar, uint32_t phase, volatile int* abort,
@@ -80,10 +105,16 @@ __device__ __forceinline__ bool pc_wait(uint64_t* bar, uint32_t phase, volatile 
 // warp 8 issues the MMAs into one of two TMEM accumulators, warps 4-7 drain
 // the other accumulator to global memory. CTAs loop over column tiles of 128.
 // tabs: pre-swizzled chunks [kc][hi m0, hi m1, lo m0, lo m1] of 16 KB each.
-template <bool SCALE>
+// IN_SPLIT: the input is hi / lo BF16 rows loaded by TMA (tm_hi, tm_lo, boxes
+// of 64 rows x 64 columns, 128B swizzle); else FP32 `in`, split by the
+// producers. OUT_SPLIT: the output goes to hi / lo BF16 arrays `ohi`, `olo`
+// with row pitch `pitch`; else FP32 `out`.
+template <bool SCALE, bool IN_SPLIT, bool OUT_SPLIT>
 __global__ void __launch_bounds__(THREADS, 1) dct_pass_tc_kernel(
     const float* __restrict__ in, float* __restrict__ out, const uint8_t* __restrict__ tabs,
-    const float* __restrict__ mu, int r, int F, float lambda, int* err) {
+    const float* __restrict__ mu, int r, int F, float lambda, int* err,
+    const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+    __nv_bfloat16* __restrict__ ohi, __nv_bfloat16* __restrict__ olo, long long pitch) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + PcSmem::BAR);
@@ -135,13 +166,25 @@ __global__ void __launch_bounds__(THREADS, 1) dct_pass_tc_kernel(
         const uint32_t s = u & 1u, ph = (u >> 1) & 1u;
         if (!pc_wait(empty + s, ph ^ 1u, abort, err)) goto producers_done;
         uint8_t* st = sm + s * PcSmem::STAGE;
+        uint8_t* sb = st + 4 * TILE_A;
         if (tid == 0) {
-          tc::mbar_arrive_expect_tx(full + s, a_bytes);
+          tc::mbar_arrive_expect_tx(full + s, a_bytes + (IN_SPLIT ? 4 * ATOM_B : 0u));
           tc::bulk_g2s(st, tabs + (size_t)kc * a_bytes, a_bytes, full + s);
+          if (IN_SPLIT) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              tc::tma_load_2d(sb + h * ATOM_B, &tm_hi, (int)(col0 + 64 * h), kc * 64, full + s);
+              tc::tma_load_2d(sb + (2 + h) * ATOM_B, &tm_lo, (int)(col0 + 64 * h), kc * 64,
+                              full + s);
+            }
+          }
           last_copy = u;
           copied = true;
         }
-        uint8_t* sb = st + 4 * TILE_A;
+        if (IN_SPLIT) {
+          tc::mbar_arrive(full + s);
+          continue;
+        }
         // 64 K-rows x 16 groups of 8 columns; all loads issued before any store.
         constexpr int PER = 64 * 16 / PRODUCERS;
         float x[PER][8];
@@ -236,6 +279,11 @@ __global__ void __launch_bounds__(THREADS, 1) dct_pass_tc_kernel(
       if (!pc_wait(acc_full + acc, aph, abort, err)) break;
       tc::fence_after_sync();
       const long long col0 = tile * 128;
+      // (pa, pb): the two untransformed axes of the tile's first column
+      // (F = 4); later columns step pb, carrying into pa (32-bit, no division
+      // per element)
+      const int p0 = (int)(col0 >> 2);
+      const int pa0 = p0 / r, pb0 = p0 - pa0 * r;
       for (int mt = 0; mt < nM; ++mt) {
         const int k = mt * 128 + et;
         const uint32_t lane = tmem + acc * acc_cols + mt * 128 + qlane;
@@ -245,34 +293,62 @@ __global__ void __launch_bounds__(THREADS, 1) dct_pass_tc_kernel(
           tc::tmem_ld_wait();
           if (k >= r) continue;
           if (F == 4) {
+            int pa = pa0, pb = pb0 + (cg >> 2);
+            while (pb >= r) {
+              pb -= r;
+              ++pa;
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+              if (q > 0 && ++pb == r) {
+                pb = 0;
+                ++pa;
+              }
               const long long col = col0 + cg + 4 * q;
               if (col >= ncol) break;
-              const long long p = col >> 2;
               float sc = 1.f;
               if (SCALE) {
-                const float dd = 1.f + lambda * (smu[p / r] + smu[p % r] + smu[k]);
+                const float dd = 1.f + lambda * (smu[pa] + smu[pb] + smu[k]);
                 sc = 1.f / (dd * dd);
               }
-              __stcs(reinterpret_cast<float4*>(out + p * rF + (long long)k * 4),
-                     make_float4(__uint_as_float(v[4 * q]) * sc, __uint_as_float(v[4 * q + 1]) * sc,
-                                 __uint_as_float(v[4 * q + 2]) * sc,
-                                 __uint_as_float(v[4 * q + 3]) * sc));
+              const float x0 = __uint_as_float(v[4 * q]) * sc;
+              const float x1 = __uint_as_float(v[4 * q + 1]) * sc;
+              const float x2 = __uint_as_float(v[4 * q + 2]) * sc;
+              const float x3 = __uint_as_float(v[4 * q + 3]) * sc;
+              if (OUT_SPLIT) {
+                const long long o = (long long)pa * pitch + (long long)pb * rF + (long long)k * 4;
+                uint2 hi, lo;
+                split4(make_float4(x0, x1, x2, x3), hi, lo);
+                __stcs(reinterpret_cast<uint2*>(ohi + o), hi);
+                __stcs(reinterpret_cast<uint2*>(olo + o), lo);
+              } else {
+                const long long o = ((long long)pa * r + pb) * rF + (long long)k * 4;
+                __stcs(reinterpret_cast<float4*>(out + o), make_float4(x0, x1, x2, x3));
+              }
             }
           } else {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const long long col = col0 + cg + j;
               if (col >= ncol) break;
-              const long long p = col / F;
-              const int c = (int)(col - p * F);
+              const int pi = (int)col / F;
+              const int c = (int)col - pi * F;
+              const int pa = pi / r, pb = pi - pa * r;
               float sc = 1.f;
               if (SCALE) {
-                const float dd = 1.f + lambda * (smu[p / r] + smu[p % r] + smu[k]);
+                const float dd = 1.f + lambda * (smu[pa] + smu[pb] + smu[k]);
                 sc = 1.f / (dd * dd);
               }
-              out[p * rF + (long long)k * F + c] = __uint_as_float(v[j]) * sc;
+              const float x = __uint_as_float(v[j]) * sc;
+              if (OUT_SPLIT) {
+                const long long o =
+                    (long long)pa * pitch + (long long)pb * rF + (long long)k * F + c;
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                ohi[o] = h;
+                olo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+              } else {
+                out[(long long)pi * rF + (long long)k * F + c] = x;
+              }
             }
           }
         }
@@ -336,6 +412,53 @@ void dct_tc_tables(int r, const float* Mx, uint16_t* dst) {
       }
 }
 
+// Row pitch (elements) of the split hi / lo intermediates of an r^3 x F level:
+// r^2 F rounded up to 8, so that every row starts 16-byte aligned for TMA.
+long long dct_tc_split_pitch(int r, int F) { return (((long long)r * r * F) + 7) & ~7LL; }
+
+size_t dct_tc_scratch_elems(int r, int F) {
+  // hi + lo BF16 of r rows of `pitch` elements, in units of floats
+  return (size_t)r * (size_t)dct_tc_split_pitch(r, F);
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of one split array: `rows` rows of `cols` BF16 with row pitch
+// `pitch` elements; boxes of 64 x 64, 128-byte swizzle, zero fill outside.
+static bool split_map(CUtensorMap* m, const __nv_bfloat16* base, int rows, long long cols,
+                      long long pitch) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * 2};
+  const cuuint32_t box[2] = {64, 64};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims,
+             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+// t0, t1: scratch of dct_tc_scratch_elems(r, F) floats each, holding the split
+// intermediates (hi then lo BF16 arrays).
 cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float* t1,
                                    const uint16_t* tabC, const uint16_t* tabCt, const float* mu,
                                    int r, int F, float lambda, int* err, cudaStream_t s) {
@@ -345,25 +468,47 @@ cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float*
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(dct_pass_tc_kernel<false>,
+    cudaError_t e = cudaFuncSetAttribute(dct_pass_tc_kernel<false, false, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(dct_pass_tc_kernel<true>,
+      e = cudaFuncSetAttribute(dct_pass_tc_kernel<false, true, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(dct_pass_tc_kernel<true, true, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(dct_pass_tc_kernel<false, true, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const long long ncol = (long long)r * r * F;
+  const long long pitch = dct_tc_split_pitch(r, F);
   const long long tiles = (ncol + 127) / 128;
   const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
   const uint8_t* C = reinterpret_cast<const uint8_t*>(tabC);
   const uint8_t* Ct = reinterpret_cast<const uint8_t*>(tabCt);
-  dct_pass_tc_kernel<false><<<grid, THREADS, smem, s>>>(g, t0, C, mu, r, F, lambda, err);
-  dct_pass_tc_kernel<false><<<grid, THREADS, smem, s>>>(t0, t1, C, mu, r, F, lambda, err);
-  dct_pass_tc_kernel<true><<<grid, THREADS, smem, s>>>(t1, t0, C, mu, r, F, lambda, err);
-  dct_pass_tc_kernel<false><<<grid, THREADS, smem, s>>>(t0, t1, Ct, mu, r, F, lambda, err);
-  dct_pass_tc_kernel<false><<<grid, THREADS, smem, s>>>(t1, t0, Ct, mu, r, F, lambda, err);
-  dct_pass_tc_kernel<false><<<grid, THREADS, smem, s>>>(t0, out, Ct, mu, r, F, lambda, err);
+  __nv_bfloat16* h0 = reinterpret_cast<__nv_bfloat16*>(t0);
+  __nv_bfloat16* l0 = h0 + (long long)r * pitch;
+  __nv_bfloat16* h1 = reinterpret_cast<__nv_bfloat16*>(t1);
+  __nv_bfloat16* l1 = h1 + (long long)r * pitch;
+  CUtensorMap mh0, ml0, mh1, ml1;
+  if (!split_map(&mh0, h0, r, ncol, pitch) || !split_map(&ml0, l0, r, ncol, pitch) ||
+      !split_map(&mh1, h1, r, ncol, pitch) || !split_map(&ml1, l1, r, ncol, pitch))
+    return cudaErrorInvalidValue;
+  // g -> t0 (split) -> t1 -> t0 (scaled) -> t1 -> t0 -> out (FP32)
+  dct_pass_tc_kernel<false, false, true><<<grid, THREADS, smem, s>>>(
+      g, nullptr, C, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch);
+  dct_pass_tc_kernel<false, true, true><<<grid, THREADS, smem, s>>>(
+      nullptr, nullptr, C, mu, r, F, lambda, err, mh0, ml0, h1, l1, pitch);
+  dct_pass_tc_kernel<true, true, true><<<grid, THREADS, smem, s>>>(
+      nullptr, nullptr, C, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch);
+  dct_pass_tc_kernel<false, true, true><<<grid, THREADS, smem, s>>>(
+      nullptr, nullptr, Ct, mu, r, F, lambda, err, mh0, ml0, h1, l1, pitch);
+  dct_pass_tc_kernel<false, true, true><<<grid, THREADS, smem, s>>>(
+      nullptr, nullptr, Ct, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch);
+  dct_pass_tc_kernel<false, true, false><<<grid, THREADS, smem, s>>>(
+      nullptr, out, Ct, mu, r, F, lambda, err, mh0, ml0, nullptr, nullptr, pitch);
   return cudaGetLastError();
 }
 

@@ -340,6 +340,8 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
     flat += lv.n;
     c->max_r = std::max(c->max_r, lv.r);
     c->max_level_n = std::max(c->max_level_n, lv.n);
+    if (cfg->precond_mode == NPG_PRECOND_TC && lv.r >= PRECOND_TC_MIN_R)
+      c->max_level_n = std::max(c->max_level_n, (long long)dct_tc_scratch_elems(lv.r, lv.F));
   }
   c->grid_dev_len = off;
   c->grid_flat_len = flat;
@@ -1202,8 +1204,9 @@ extern "C" int npg_precondition_tc(const float* g, float* out, int r, int F, flo
   float *t0 = nullptr, *t1 = nullptr, *dmu = nullptr;
   uint16_t* dtt = nullptr;
   int* derr = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&t0, sizeof(float) * n, s);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&t1, sizeof(float) * n, s);
+  const long long nt = std::max(n, (long long)dct_tc_scratch_elems(r, F));
+  cudaError_t e = cudaMallocAsync((void**)&t0, sizeof(float) * nt, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&t1, sizeof(float) * nt, s);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&dmu, sizeof(float) * r, s);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&dtt, sizeof(uint16_t) * tt.size(), s);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&derr, sizeof(int), s);

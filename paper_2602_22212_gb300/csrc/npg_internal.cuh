@@ -173,6 +173,9 @@ cudaError_t launch_step_prepare(const int* epoch, float b1, float b2, float* cc,
 cudaError_t launch_step_finish(int* epoch, cudaStream_t s);
 void dct_tables(int r, float* C, float* Ct, float* mu);
 size_t dct_tc_table_elems(int r);
+// Scratch (floats, per buffer) the tensor-core preconditioner needs for an
+// r^3 x F level: its split hi / lo intermediates with padded rows.
+size_t dct_tc_scratch_elems(int r, int F);
 void dct_tc_tables(int r, const float* Mx, uint16_t* dst);
 cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float* t1,
                                    const uint16_t* tabC, const uint16_t* tabCt, const float* mu,

@@ -76,6 +76,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// 2D tiled tensor load (TMA) of one box at element coordinates (x innermost,
+// y) into shared memory, completing on an mbarrier as transaction bytes.
+// tmap: generic address of a CUtensorMap (kernel parameter or global).
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // ----------------------------------------------------------------- TMEM
 // Warp-collective; ncols a power of two >= 32. The TMEM address is written
 // to *dst (shared memory).
