@@ -38,7 +38,16 @@ namespace {
 constexpr uint32_t TILE_A = 128 * 128;  // [128][64] BF16, 128B-swizzled
 constexpr uint32_t ATOM_B = 64 * 128;   // MN-major atom: 64 K-rows x 64 columns BF16
 constexpr uint32_t WAIT = 1u << 22;
-constexpr int PRODUCERS = 128, EPILOGUE = 128, THREADS = PRODUCERS + EPILOGUE + 32;
+// Warp roles: producers [0, PW), epilogue [PW, PW + EW), the MMA warp PW + EW.
+// A pass that splits FP32 input needs 4 producer warps; one whose input comes
+// by TMA needs one thread to issue it, and gives the warps to the epilogue
+// (two per TMEM lane quarter, each draining half of the tile's columns).
+template <bool IN_SPLIT> struct Roles {
+  static constexpr int PW = IN_SPLIT ? 1 : 4, EW = IN_SPLIT ? 8 : 4;
+  static constexpr int PRODUCERS = PW * 32, EPILOGUE = EW * 32, MMA_WARP = PW + EW;
+  static constexpr int THREADS = (PW + EW + 1) * 32;
+};
+constexpr int PRODUCERS = Roles<false>::PRODUCERS;
 
 // Per stage: A chunk [hi m0, hi m1, lo m0, lo m1] (a straight copy of the
 // pre-swizzled table chunk), B chunk [hi (2 atoms), lo (2 atoms)].
@@ -110,7 +119,7 @@ __device__ __forceinline__ bool pc_wait(uint64_t* bar, uint32_t phase, volatile 
 // producers. OUT_SPLIT: the output goes to hi / lo BF16 arrays `ohi`, `olo`
 // with row pitch `pitch`; else FP32 `out`.
 template <bool SCALE, bool IN_SPLIT, bool OUT_SPLIT>
-__global__ void __launch_bounds__(THREADS, 1) dct_pass_tc_kernel(
+__global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kernel(
     const float* __restrict__ in, float* __restrict__ out, const uint8_t* __restrict__ tabs,
     const float* __restrict__ mu, int r, int F, float lambda, int* err,
     const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
@@ -133,19 +142,20 @@ __global__ void __launch_bounds__(THREADS, 1) dct_pass_tc_kernel(
   const uint32_t tm_cols = nM == 2 ? 512u : 256u;
   const long long ncol = (long long)r * r * F;
   const long long ntiles = (ncol + 127) / 128;
-  for (int k = tid; k < r; k += THREADS) smu[k] = mu[k];
+  using RL = Roles<IN_SPLIT>;
+  for (int k = tid; k < r; k += RL::THREADS) smu[k] = mu[k];
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(full + b, PRODUCERS + 1);
+      tc::mbar_init(full + b, RL::PRODUCERS + 1);
       tc::mbar_init(empty + b, 1);
       tc::mbar_init(acc_full + b, 1);
-      tc::mbar_init(acc_empty + b, EPILOGUE);
+      tc::mbar_init(acc_empty + b, RL::EPILOGUE);
     }
     tc::mbar_init(fin, 1);
     *abort = 0;
     tc::fence_mbar_init();
   }
-  if (warp == 8) {
+  if (warp == RL::MMA_WARP) {
     tc::tmem_alloc(tmem_ptr, tm_cols);
     tc::tmem_relinquish();
   }
@@ -154,7 +164,7 @@ __global__ void __launch_bounds__(THREADS, 1) dct_pass_tc_kernel(
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_ptr;
 
-  if (warp < 4) {
+  if (warp < RL::PW) {
     // ------------------------------------------------------------ producers
     // Thread 0 arrives with the table copy's transaction count when it issues
     // it; every producer arrives once its share of the input chunk is stored.
@@ -220,7 +230,7 @@ __global__ void __launch_bounds__(THREADS, 1) dct_pass_tc_kernel(
   producers_done:
     // Do not leave with a table copy in flight (bounded).
     if (tid == 0 && copied) tc::mbar_wait(full + (last_copy & 1u), (last_copy >> 1) & 1u, WAIT);
-  } else if (warp == 8) {
+  } else if (warp == RL::MMA_WARP) {
     // ------------------------------------------------------------ MMA issuer
     // The whole warp follows the barriers; lane 0 issues.
     const bool leader = (tid & 31) == 0;
@@ -270,7 +280,10 @@ __global__ void __launch_bounds__(THREADS, 1) dct_pass_tc_kernel(
     tc::mbar_wait(fin, 0, WAIT);
   } else {
     // ------------------------------------------------------------ epilogue
-    const int et = tid - PRODUCERS;  // 0..127 = TMEM lane
+    const int et = 32 * (warp & 3) + (tid & 31);  // TMEM lane of this thread
+    // column range of the tile this warp drains
+    const int cg_lo = RL::EW == 8 ? 64 * ((warp - RL::PW) >> 2) : 0;
+    const int cg_hi = RL::EW == 8 ? cg_lo + 64 : 128;
     const uint32_t qlane = (uint32_t)((warp & 3) * 32) << 16;
     const long long rF = (long long)r * F;
     uint32_t lt = 0;
@@ -287,7 +300,7 @@ __global__ void __launch_bounds__(THREADS, 1) dct_pass_tc_kernel(
       for (int mt = 0; mt < nM; ++mt) {
         const int k = mt * 128 + et;
         const uint32_t lane = tmem + acc * acc_cols + mt * 128 + qlane;
-        for (int cg = 0; cg < 128; cg += 16) {
+        for (int cg = cg_lo; cg < cg_hi; cg += 16) {
           uint32_t v[16];
           tc::tmem_ld16(lane + cg, v);
           tc::tmem_ld_wait();
@@ -360,7 +373,7 @@ __global__ void __launch_bounds__(THREADS, 1) dct_pass_tc_kernel(
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 8) {
+  if (warp == RL::MMA_WARP) {
     __syncwarp();
     tc::tmem_dealloc(tmem, tm_cols);
   }
@@ -497,17 +510,18 @@ cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float*
       !split_map(&mh1, h1, r, ncol, pitch) || !split_map(&ml1, l1, r, ncol, pitch))
     return cudaErrorInvalidValue;
   // g -> t0 (split) -> t1 -> t0 (scaled) -> t1 -> t0 -> out (FP32)
-  dct_pass_tc_kernel<false, false, true><<<grid, THREADS, smem, s>>>(
+  constexpr int T0 = Roles<false>::THREADS, T1 = Roles<true>::THREADS;
+  dct_pass_tc_kernel<false, false, true><<<grid, T0, smem, s>>>(
       g, nullptr, C, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch);
-  dct_pass_tc_kernel<false, true, true><<<grid, THREADS, smem, s>>>(
+  dct_pass_tc_kernel<false, true, true><<<grid, T1, smem, s>>>(
       nullptr, nullptr, C, mu, r, F, lambda, err, mh0, ml0, h1, l1, pitch);
-  dct_pass_tc_kernel<true, true, true><<<grid, THREADS, smem, s>>>(
+  dct_pass_tc_kernel<true, true, true><<<grid, T1, smem, s>>>(
       nullptr, nullptr, C, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch);
-  dct_pass_tc_kernel<false, true, true><<<grid, THREADS, smem, s>>>(
+  dct_pass_tc_kernel<false, true, true><<<grid, T1, smem, s>>>(
       nullptr, nullptr, Ct, mu, r, F, lambda, err, mh0, ml0, h1, l1, pitch);
-  dct_pass_tc_kernel<false, true, true><<<grid, THREADS, smem, s>>>(
+  dct_pass_tc_kernel<false, true, true><<<grid, T1, smem, s>>>(
       nullptr, nullptr, Ct, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch);
-  dct_pass_tc_kernel<false, true, false><<<grid, THREADS, smem, s>>>(
+  dct_pass_tc_kernel<false, true, false><<<grid, T1, smem, s>>>(
       nullptr, out, Ct, mu, r, F, lambda, err, mh0, ml0, nullptr, nullptr, pitch);
   return cudaGetLastError();
 }
