@@ -123,7 +123,7 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- algorithmic work
 
-def stage_work(p, N, T, MT, mlp_dims, precond="fp32", precision="fp32"):
+def stage_work(p, N, T, MT, mlp_dims, precond="fp32", precision="fp32", mlp_len=0):
     """Algorithmic bytes / FLOPs per launch of each stage (documented in the design doc)."""
     H, D, K, Z, NO = mlp_dims
     L, F = p["L"], p["F"]
@@ -140,8 +140,12 @@ def stage_work(p, N, T, MT, mlp_dims, precond="fp32", precision="fp32"):
         "nn_p": ("alu", None, "FLOP"),
         "decode": (mlp_kind, fwd_row * rows, "FLOP"),
         "mlp_bwd": (mlp_kind, bwd_row * rows, "FLOP"),
-        "precond": ("hbm", dct_bytes, "B") if precond == "tc" else ("alu", dct_flops, "FLOP"),
-        "adam": ("hbm", 28 * n_params, "B"),
+        # the grid levels' Adam steps run inside the preconditioner stage (each
+        # level's DCT passes and Adam on one of four concurrent stream lanes);
+        # the adam stage is the MLP's
+        "precond": (("hbm", dct_bytes + 28 * n_params, "B") if precond == "tc"
+                    else ("alu", dct_flops, "FLOP")),
+        "adam": ("hbm", 28 * mlp_len, "B"),
         "encode": ("hbm", N * (8 * L * F + 8 * 2) * 4 + N * 16 * 2, "B"),
         "scatter": ("hbm", N * (8 * L * F + 8 * 2) * 4 * 2, "B"),
     }
@@ -462,7 +466,7 @@ def main():
     e2e_value = world * N * T * e2e_steps / t_e2e
 
     peaks = load_peaks()
-    work = stage_work(p, N, T, MT, (H, D, K, Z, NO), precond, args.precision)
+    work = stage_work(p, N, T, MT, (H, D, K, Z, NO), precond, args.precision, mlp.size)
     # search work: 8 FLOP per candidate pair (3 sub, 1 mul, 2 fma, compare)
     work["nn_x"] = ("alu", 8 * search["cand_per_query_x"] * N * T, "FLOP")
     work["nn_p"] = ("alu", 8 * search["cand_per_query_p"] * MT, "FLOP")

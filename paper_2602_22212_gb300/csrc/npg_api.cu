@@ -80,7 +80,7 @@ static void* dev_alloc(npg_ctx* c, size_t bytes) {
     cudaGetLastError();
     p = nullptr;
   }
-  if (p && c->n_allocs < 64) c->allocs[c->n_allocs++] = p;
+  if (p && c->n_allocs < 128) c->allocs[c->n_allocs++] = p;
   return p;
 }
 
@@ -296,6 +296,15 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
   if (cudaGetDevice(&c->dev) != cudaSuccess) return fail(cuda_fail(c, cudaGetLastError(), "cudaGetDevice"));
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev);
   if (c->num_sms <= 0) c->num_sms = 148;
+  c->lane[0] = c->stream;
+  {
+    cudaError_t e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    for (int j = 0; j < npg_ctx::NLANE && e == cudaSuccess; ++j) {
+      if (j > 0) e = cudaStreamCreateWithFlags(&c->lane[j], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join[j], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) return fail(cuda_fail(c, e, "lane streams"));
+  }
 
   MlpDims& md = c->md;
   md.H = cfg->H;
@@ -425,6 +434,33 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
   ok &= alloc_n(c, c->mlp, c->mlp_len) && alloc_n(c, c->g_mlp, c->mlp_len) &&
         alloc_n(c, c->m_mlp, c->mlp_len) && alloc_n(c, c->v_mlp, c->mlp_len);
   ok &= alloc_n(c, c->pc_tmp0, c->max_level_n) && alloc_n(c, c->pc_tmp1, c->max_level_n);
+  ok &= alloc_n(c, c->nnq_p.counters, 4) && alloc_n(c, c->nnq_p.items, c->MT_cap);
+  c->nnq_p.far_blocks = c->num_sms * 16;
+  // levels to lanes, largest first onto the least loaded lane; each lane's
+  // scratch holds its largest level
+  {
+    long long load[npg_ctx::NLANE] = {}, need[npg_ctx::NLANE] = {};
+    int order[NPG_MAX_LEVELS + 1];
+    for (int l = 0; l < c->nlev; ++l) order[l] = l;
+    std::sort(order, order + c->nlev, [&](int a, int b) { return c->lev[a].n > c->lev[b].n; });
+    for (int i = 0; i < c->nlev; ++i) {
+      const int l = order[i];
+      int best = 0;
+      for (int j = 1; j < npg_ctx::NLANE; ++j)
+        if (load[j] < load[best]) best = j;
+      c->level_lane[l] = best;
+      load[best] += c->lev[l].n;
+      long long n = c->lev[l].n;
+      if (cfg->precond_mode == NPG_PRECOND_TC && c->lev[l].r >= PRECOND_TC_MIN_R)
+        n = std::max(n, (long long)dct_tc_scratch_elems(c->lev[l].r, c->lev[l].F));
+      need[best] = std::max(need[best], n);
+    }
+    c->lane_tmp[0][0] = c->pc_tmp0;
+    c->lane_tmp[0][1] = c->pc_tmp1;
+    for (int j = 1; j < npg_ctx::NLANE; ++j)
+      if (need[j] > 0)
+        ok &= alloc_n(c, c->lane_tmp[j][0], need[j]) && alloc_n(c, c->lane_tmp[j][1], need[j]);
+  }
   long long dct_len = 0;
   for (int l = 0; l < c->nlev; ++l) {
     c->dct_off[l] = dct_len;
@@ -533,18 +569,37 @@ static int forward_launch(npg_ctx* c) {
   return NPG_OK;
 }
 
+// Lanes 1..n-1 start after everything issued so far on the main stream.
+static cudaError_t lanes_fork(npg_ctx* c, int n) {
+  cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
+  for (int j = 1; j < n && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->lane[j], c->ev_fork, 0);
+  return e;
+}
+
+// The main stream continues after everything issued on lanes 1..n-1.
+static cudaError_t lanes_join(npg_ctx* c, int n) {
+  cudaError_t e = cudaSuccess;
+  for (int j = 1; j < n && e == cudaSuccess; ++j) {
+    e = cudaEventRecord(c->ev_join[j], c->lane[j]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join[j], 0);
+  }
+  return e;
+}
+
 static int loss_launch(npg_ctx* c) {
   const long long NT = (long long)c->N * c->T;
   CK(c, bucket_build(c->xhat, nullptr, c->N, c->T, NT, c->xb.G, c->xb, c->stream));
   mark(c, 3);
   // vertex -> point (queries in x-hat bucket order for coherent warps)
   const bool count = c->tev && !c->capturing && c->t_cur >= 0;
+  // point -> vertex on lane 1, concurrently with vertex -> point on the main stream
+  CK(c, lanes_fork(c, 2));
+  CK(c, launch_nn(c->pb.sorted, 0, c->p_off, c->T, c->MT, c->xb, nullptr, c->N, c->nn_p, c->d_p,
+                  c->nnq_p, c->lane[1], count ? c->d_nnstats + 2 : nullptr, true));
   CK(c, launch_nn(c->xb.sorted, c->N, nullptr, c->T, NT, c->pb, c->p_off, 0, c->nn_x, c->d_x,
                   c->nnq, c->stream, count ? c->d_nnstats : nullptr, true));
   mark(c, 4);
-  // point -> vertex
-  CK(c, launch_nn(c->pb.sorted, 0, c->p_off, c->T, c->MT, c->xb, nullptr, c->N, c->nn_p, c->d_p,
-                  c->nnq, c->stream, count ? c->d_nnstats + 2 : nullptr, true));
+  CK(c, lanes_join(c, 2));
   mark(c, 5);
   CK(c, launch_loss(c));
   mark(c, 6);
@@ -577,26 +632,30 @@ static int backward_launch(npg_ctx* c) {
 static int step_launch(npg_ctx* c) {
   const npg_config& f = c->cfg;
   CK(c, launch_step_prepare(c->d_epoch, f.adam_beta1, f.adam_beta2, c->d_adam_c, c->stream));
+  // each grid level's preconditioner and Adam step on its lane (levels are
+  // independent), the lanes joined back before the epoch advances
+  CK(c, lanes_fork(c, npg_ctx::NLANE));
   for (int l = 0; l < c->nlev; ++l) {
     const Level& lv = c->lev[l];
+    const int j = c->level_lane[l];
+    cudaStream_t ls = c->lane[j];
     const float* tab = c->dct + c->dct_off[l];
     const long long rr = (long long)lv.r * lv.r;
     if (c->cfg.precond_mode == NPG_PRECOND_TC && lv.r >= PRECOND_TC_MIN_R)
-      CK(c, launch_precondition_tc(c->g_grid + lv.off, c->g_pc + lv.off, c->pc_tmp0, c->pc_tmp1,
-                                   c->dct_tc + c->dct_tc_off[l][0],
+      CK(c, launch_precondition_tc(c->g_grid + lv.off, c->g_pc + lv.off, c->lane_tmp[j][0],
+                                   c->lane_tmp[j][1], c->dct_tc + c->dct_tc_off[l][0],
                                    c->dct_tc + c->dct_tc_off[l][1], tab + 2 * rr, lv.r, lv.F,
-                                   lv.lambda, c->d_err, c->stream));
+                                   lv.lambda, c->d_err, ls));
     else
-      CK(c, launch_precondition(c->g_grid + lv.off, c->g_pc + lv.off, c->pc_tmp0, c->pc_tmp1,
-                                tab, tab + rr, tab + 2 * rr, lv.r, lv.F, lv.lambda, c->stream));
-  }
-  mark(c, 10);
-  for (int l = 0; l < c->nlev; ++l) {
-    const Level& lv = c->lev[l];
+      CK(c, launch_precondition(c->g_grid + lv.off, c->g_pc + lv.off, c->lane_tmp[j][0],
+                                c->lane_tmp[j][1], tab, tab + rr, tab + 2 * rr, lv.r, lv.F,
+                                lv.lambda, ls));
     CK(c, launch_adam(c->grid + lv.off, c->g_pc + lv.off, c->m_grid + lv.off,
                       c->v_grid + lv.off, lv.n, lv.lr, f.adam_beta1, f.adam_beta2, f.adam_eps,
-                      c->d_adam_c, c->stream));
+                      c->d_adam_c, ls));
   }
+  CK(c, lanes_join(c, npg_ctx::NLANE));
+  mark(c, 10);
   CK(c, launch_adam(c->mlp, c->g_mlp, c->m_mlp, c->v_mlp, c->mlp_len, f.lr_mlp, f.adam_beta1,
                     f.adam_beta2, f.adam_eps, c->d_adam_c, c->stream));
   CK(c, launch_step_finish(c->d_epoch, c->stream));
@@ -1118,6 +1177,14 @@ extern "C" int npg_batch_iteration(npg_batch* b, double* loss_out) {
 extern "C" int npg_destroy(npg_ctx* c) {
   if (!c) return NPG_OK;
   if (c->stream || true) cudaStreamSynchronize(c->stream);
+  for (int j = 1; j < npg_ctx::NLANE; ++j)
+    if (c->lane[j]) {
+      cudaStreamSynchronize(c->lane[j]);
+      cudaStreamDestroy(c->lane[j]);
+    }
+  for (int j = 0; j < npg_ctx::NLANE; ++j)
+    if (c->ev_join[j]) cudaEventDestroy(c->ev_join[j]);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   free_timing(c);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);

@@ -120,6 +120,16 @@ struct npg_ctx {
   float* pc_tmp0 = nullptr;
   float* pc_tmp1 = nullptr;
 
+  // Stream lanes: the grid levels' preconditioner + Adam, and the two search
+  // directions, run concurrently on the main stream (lane 0) and auxiliary
+  // streams forked from it and joined back (also inside a captured graph).
+  static constexpr int NLANE = 4;
+  cudaStream_t lane[NLANE] = {};   // lane[0] = stream
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[NLANE] = {};
+  float* lane_tmp[NLANE][2] = {};  // preconditioner scratch of each lane
+  int level_lane[NPG_MAX_LEVELS + 1] = {};
+
   // per-stage timing (event ring) and launch accounting
   cudaEvent_t* tev = nullptr;  // t_slots x (NPG_NUM_STAGES + 1)
   unsigned* t_mask = nullptr;  // per slot: which marks were recorded
@@ -127,13 +137,14 @@ struct npg_ctx {
   int capturing = 0;
   long long launches = 0;
   unsigned long long* d_nnstats = nullptr;  // per direction: candidates, cell rows (timing mode)
-  npg::NnQueue nnq;
+  npg::NnQueue nnq;    // vertex -> point search
+  npg::NnQueue nnq_p;  // point -> vertex search (runs concurrently)
   long long graph_launches = 0;  // kernels in one replay of the captured graph
   int* d_epoch = nullptr;  // device copy of e (read by graph-captured kernels)
   float* d_adam_c = nullptr;  // 1 - beta1^s, 1 - beta2^s of the current step
   int* d_err = nullptr;       // set by a kernel whose bounded wait gave up
   float* xhat3 = nullptr;     // T x N x 3 staging for npg_get
-  void* allocs[64];
+  void* allocs[128];
   int n_allocs = 0;
   int phase = 0;  // 0 ready, 1 forward done, 2 loss done, 3 backward done
   int e = 0;
