@@ -12,8 +12,13 @@ MLP 3 x 64 LeakyReLU; synthetic, seeded. Its per-iteration working set (grid,
 gradient, moments: ~3 GB) is far larger than L2, so no L2 flush is needed
 between steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
                   [--graph|--no-graph] [--impl npg|reference]
+
+The default form is the metric's headline: BF16 tensor-core MLP, tensor-core
+preconditioner, the iteration replayed from a CUDA graph (`value`); the plain
+FP32 per-sequence form (FP32 SIMT MLP and preconditioner, eager) is timed on
+the same sequence and state beside it (`plain_fp32`, with the ratio).
 
 With N > 1 (torchrun, one rank per GPU) every rank optimises its own sequence
 (independent problems: weak scaling, no data-path collective); value counts
@@ -341,7 +346,11 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="npg", choices=["npg", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"],
+                    help="bf16: the batched BF16 graph-captured form (headline); fp32: the "
+                         "plain FP32 per-sequence form")
+    ap.add_argument("--no-fp32-leg", action="store_true",
+                    help="skip timing the plain FP32 form beside the BF16 form")
     ap.add_argument("--graph", dest="graph", action="store_true", default=None)
     ap.add_argument("--no-graph", dest="graph", action="store_false")
     ap.add_argument("--workload", default="paper", choices=["paper", "tiny", "profile"])
@@ -491,6 +500,35 @@ def main():
     roof["kernel"] = dom
     roof["ms_per_launch"] = stages[dom]
 
+    # the plain FP32 per-sequence form on the same sequence, for the ratio the
+    # metric names (eager, FP32 preconditioner, from the same initial state)
+    plain = None
+    if args.precision == "bf16" and not args.no_fp32_leg:
+        cfg3 = make_cfg(npg, p, "fp32", False, stream, e_max, "fp32")
+        pctx = npg.Context(cfg3, seq, mlp, device_inputs=True)
+        for _ in range(args.warmup):
+            pctx.iteration()
+        npg.npg_set_state(pctx.h, state0)
+        steps3 = max(3, min(args.steps, 20))
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps3):
+            npg.npg_iteration(pctx.h, None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms3 = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms3], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms3 = float(t.item())
+        v3 = world * N * T * steps3 / (ms3 * 1e-3)
+        plain = {"value": v3, "unit": UNIT, "ms_per_step": ms3 / steps3, "steps": steps3,
+                 "form": "plain FP32 per-sequence (eager, FP32 preconditioner)",
+                 "ratio_bf16_over_fp32": value / v3}
+        pctx.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, s, desc = oracle_sample(p, seq, frames=2)
@@ -514,6 +552,7 @@ def main():
             "roofline": roof,
             "stages_ms": {k: round(v, 4) for k, v in stages.items()},
             "search": {k: round(v, 2) for k, v in search.items()},
+            "plain_fp32": plain,
             "cpu_baseline": cpu,
             "clocks": clocks,
         }
