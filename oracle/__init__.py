@@ -98,6 +98,7 @@ def lib():
                 "or_adam": (None, [l, pd, pd, pd, pd, d, d, d, d, i]),
                 "or_iteration": (d, [cfg, i, pd, pd, i, pi64, pd, l, pi32, i, i, i, pd, pd, pd,
                                      pd, pd, pd, pd, d, pd, d, d, d, i, d, pd, pd, pd, pd]),
+                "or_evaluate": (None, [i, i, pd, pd, i, pi32, d, pd]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -435,3 +436,20 @@ def iteration(prob: Problem, st: State, e_max, lr_grid, lr_mlp, lam, b1=0.9, b2=
                            int(bool(decide_f32)), float(cg_tol), pcd, pgg, pgp, pgm)
     st.e += 1
     return dict(loss=float(L), cd=cd, g_grid=gg, g_grid_pc=gp, g_mlp=gm)
+
+
+EVAL_FIELDS = ("cd", "precision", "recall", "fscore", "nc", "corr")
+
+
+def evaluate(xhat, gt, faces, tau_rel=0.005):
+    """Sec. 4 evaluation metrics per frame (reading in npg_oracle.c): T x 6
+    {cd, precision, recall, fscore, nc, corr}; xhat and gt are T x N x 3 with
+    the reference mesh's connectivity."""
+    xhat = np.ascontiguousarray(xhat, dtype=np.float64)
+    T, N = xhat.shape[0], xhat.shape[1]
+    x, px = _d(xhat)
+    g, pg = _d(gt)
+    f, pf = _i32(faces)
+    out, po = _out_d(6 * T)
+    lib().or_evaluate(T, N, px, pg, len(faces), pf, float(tau_rel), po)
+    return out[: 6 * T].reshape(T, 6)

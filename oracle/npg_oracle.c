@@ -836,3 +836,98 @@ double or_iteration(const or_cfg* c, int N, const double* x, const double* n, in
   free(gm);
   return L;
 }
+
+/* ---------------------------------- Sec. 4: evaluation metrics */
+
+/* Area-weighted vertex normals of one frame (sum of the incident faces'
+ * cross products, normalised; a vertex without area gets (0, 0, 0)). */
+static void vertex_normals(int N, const double* v, int F_tri, const int32_t* faces, double* nrm) {
+  for (long i = 0; i < 3L * N; ++i) nrm[i] = 0.0;
+  for (int f = 0; f < F_tri; ++f) {
+    const int32_t* t = faces + 3L * f;
+    const double* a = v + 3L * t[0];
+    const double* b = v + 3L * t[1];
+    const double* c = v + 3L * t[2];
+    const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const double w[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    const double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2],
+                         u[0] * w[1] - u[1] * w[0]};
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) nrm[3L * t[k] + d] += n[d];
+  }
+  for (int i = 0; i < N; ++i) {
+    double* p = nrm + 3L * i;
+    const double l = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    if (l > 0.0)
+      for (int d = 0; d < 3; ++d) p[d] /= l;
+  }
+}
+
+/* Per frame t, the reconstruction xhat (reference connectivity) against the
+ * ground truth gt (same connectivity, known trajectories), both T x N x 3:
+ *   cd        mean_i min_j |xh_i - g_j|^2 + mean_j min_i |g_j - xh_i|^2
+ *   precision fraction of xh_i with min_j |xh_i - g_j| < tau
+ *   recall    fraction of g_j with min_i |g_j - xh_i| < tau
+ *   fscore    2 P R / (P + R), 0 when P + R = 0
+ *   nc        (mean_i |n_i . n_g(nn(i))| + mean_j |n_g,j . n(nn(j))|) / 2
+ *   corr      mean_i |xh_i - g_i|
+ * with tau = tau_rel x the diagonal of frame t's ground-truth bounding box
+ * and area-weighted vertex normals. out: T x 6 in that order. */
+void or_evaluate(int T, int N, const double* xhat, const double* gt, int F_tri,
+                 const int32_t* faces, double tau_rel, double* out) {
+  double* nx = (double*)malloc(sizeof(double) * 3 * N);
+  double* ng = (double*)malloc(sizeof(double) * 3 * N);
+  int32_t* ix = (int32_t*)malloc(sizeof(int32_t) * N);
+  int32_t* ig = (int32_t*)malloc(sizeof(int32_t) * N);
+  double* dx = (double*)malloc(sizeof(double) * N);
+  double* dg = (double*)malloc(sizeof(double) * N);
+  for (int t = 0; t < T; ++t) {
+    const double* X = xhat + 3L * N * t;
+    const double* G = gt + 3L * N * t;
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) lo[d] = hi[d] = G[d];
+    for (int i = 0; i < N; ++i)
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = fmin(lo[d], G[3L * i + d]);
+        hi[d] = fmax(hi[d], G[3L * i + d]);
+      }
+    const double diag = sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                             (hi[2] - lo[2]) * (hi[2] - lo[2]));
+    const double tau = tau_rel * diag;
+    vertex_normals(N, X, F_tri, faces, nx);
+    vertex_normals(N, G, F_tri, faces, ng);
+    or_nn(N, X, N, G, 0, ix, dx);
+    or_nn(N, G, N, X, 0, ig, dg);
+    double sx = 0, sg = 0, cx = 0, cg = 0, nsx = 0, nsg = 0, sc = 0;
+    for (int i = 0; i < N; ++i) {
+      sx += dx[i];
+      sg += dg[i];
+      if (dx[i] < tau * tau) cx += 1;
+      if (dg[i] < tau * tau) cg += 1;
+      const double* a = nx + 3L * i;
+      const double* b = ng + 3L * ix[i];
+      nsx += fabs(a[0] * b[0] + a[1] * b[1] + a[2] * b[2]);
+      const double* c = ng + 3L * i;
+      const double* e = nx + 3L * ig[i];
+      nsg += fabs(c[0] * e[0] + c[1] * e[1] + c[2] * e[2]);
+      const double* p = X + 3L * i;
+      const double* q = G + 3L * i;
+      sc += sqrt((p[0] - q[0]) * (p[0] - q[0]) + (p[1] - q[1]) * (p[1] - q[1]) +
+                 (p[2] - q[2]) * (p[2] - q[2]));
+    }
+    double* o = out + 6L * t;
+    const double P = cx / N, R = cg / N;
+    o[0] = sx / N + sg / N;
+    o[1] = P;
+    o[2] = R;
+    o[3] = P + R > 0 ? 2 * P * R / (P + R) : 0.0;
+    o[4] = 0.5 * (nsx / N + nsg / N);
+    o[5] = sc / N;
+  }
+  free(nx);
+  free(ng);
+  free(ix);
+  free(ig);
+  free(dx);
+  free(dg);
+}

@@ -385,3 +385,67 @@ def test_iteration_decreases_chamfer():
     cds = [O.iteration(prob, st, 20, lr, 1e-3, lam)["cd"].mean() for _ in range(8)]
     assert cds[-1] < cds[0]
     assert st.e == 8
+
+
+# ---------------------------------------------------------------- Sec. 4 metrics
+
+def test_evaluation_metrics_invariants():
+    """Identity: (cd, P, R, F, NC, corr) = (0, 1, 1, 1, 1, 0). A uniform shift s
+    smaller than half the vertex spacing keeps every nearest pair on the same
+    vertex: cd = 2 |s|^2, corr = |s|, NC = 1, and F = 1 below the threshold,
+    0 above it. Scaling both meshes by k scales cd by k^2 and corr by k and
+    leaves the rest (the threshold is relative to the bounding box)."""
+    v, f = I.icosphere(3)
+    rng = np.random.default_rng(0)
+    gt = np.stack([v, v * 1.2 + 0.1])
+    m = O.evaluate(gt, gt, f)
+    np.testing.assert_array_equal(m, [[0, 1, 1, 1, 1, 0]] * 2)
+    tau = 0.005 * np.linalg.norm(gt[0].max(0) - gt[0].min(0))
+    for mag in (0.5 * tau, 3.0 * tau):
+        s = _unit3(rng) * mag
+        m = O.evaluate(gt[:1] + s, gt[:1], f)[0]
+        np.testing.assert_allclose(m[0], 2 * mag ** 2, rtol=1e-9)
+        np.testing.assert_allclose(m[5], mag, rtol=1e-9)
+        np.testing.assert_allclose(m[4], 1.0, rtol=1e-12)
+        assert m[3] == (1.0 if mag < tau else 0.0)
+    xh = gt + rng.normal(scale=0.01, size=gt.shape)
+    a, b = O.evaluate(xh, gt, f), O.evaluate(3.0 * xh, 3.0 * gt, f)
+    np.testing.assert_allclose(b[:, 0], 9.0 * a[:, 0], rtol=1e-9)
+    np.testing.assert_allclose(b[:, 5], 3.0 * a[:, 5], rtol=1e-9)
+    np.testing.assert_allclose(b[:, 1:5], a[:, 1:5], rtol=1e-9)
+
+
+def _unit3(rng):
+    u = rng.normal(size=3)
+    return u / np.linalg.norm(u)
+
+
+def test_evaluation_metrics_match_kdtree_and_numpy_normals():
+    """Against an independent computation: scipy cKDTree nearest neighbours
+    and normals accumulated with numpy (np.add.at over face cross products)."""
+    from scipy.spatial import cKDTree
+    seq = I.sphere_blob(subdiv=3, T=3, M=500, seed=3)
+    rng = np.random.default_rng(1)
+    gt = seq.gt_frames
+    xh = gt + rng.normal(scale=0.02, size=gt.shape)
+    f = seq.faces
+    got = O.evaluate(xh, gt, f, tau_rel=0.01)
+
+    def normals(v):
+        n = np.cross(v[f[:, 1]] - v[f[:, 0]], v[f[:, 2]] - v[f[:, 0]])
+        acc = np.zeros_like(v)
+        for k in range(3):
+            np.add.at(acc, f[:, k], n)
+        return acc / np.linalg.norm(acc, axis=1, keepdims=True)
+
+    for t in range(gt.shape[0]):
+        X, G = xh[t], gt[t]
+        dx, ix = cKDTree(G).query(X)
+        dg, ig = cKDTree(X).query(G)
+        tau = 0.01 * np.linalg.norm(G.max(0) - G.min(0))
+        P, R = np.mean(dx < tau), np.mean(dg < tau)
+        nx, ng = normals(X), normals(G)
+        nc = 0.5 * (np.mean(np.abs(np.sum(nx * ng[ix], 1))) + np.mean(np.abs(np.sum(ng * nx[ig], 1))))
+        want = [np.mean(dx ** 2) + np.mean(dg ** 2), P, R, 2 * P * R / (P + R), nc,
+                np.mean(np.linalg.norm(X - G, axis=1))]
+        np.testing.assert_allclose(got[t], want, rtol=1e-9, atol=1e-15)
