@@ -193,6 +193,27 @@ NPG_API int npg_step(npg_ctx* ctx);
 NPG_API int npg_iteration(npg_ctx* ctx, double* loss_out);
 
 /*
+ * Reconstruction quality (the evaluation metrics of Sec. 4) of the x-hat of
+ * the last npg_forward against ground-truth vertex positions gt_xyz (T x N x 3
+ * FP32, host or device per on_device, the reference mesh's connectivity, so
+ * vertex i of every frame is the same material point). Per frame t:
+ *   cd        mean_i min_j |x_i - g_j|^2 + mean_j min_i |g_j - x_i|^2
+ *   precision fraction of x_i with min_j |x_i - g_j| < tau, recall likewise
+ *             for g_j, fscore = 2 P R / (P + R) (0 when both are 0)
+ *   nc        (mean_i |n_i . n_g(nn(i))| + mean_j |n_g,j . n(nn(j))|) / 2 with
+ *             area-weighted vertex normals
+ *   corr      mean_i |x_i - g_i| (correspondence error along trajectories)
+ * tau = tau_rel x the diagonal of frame t's ground-truth bounding box (the
+ * paper's F-score threshold is 0.5%: tau_rel = 0.005). The paper names these
+ * metrics without formulas; the definitions above are this library's reading.
+ * out (host): (T + 1) x 6 doubles {cd, precision, recall, fscore, nc, corr}
+ * per frame, then their mean over frames. Allocates its scratch with
+ * cudaMallocAsync on the context's stream and synchronizes.
+ */
+NPG_API int npg_evaluate(npg_ctx* ctx, const float* gt_xyz, int on_device, float tau_rel,
+                         double* out);
+
+/*
  * Batch of independent sequences (many sequences of uneven vertex, frame and
  * point counts optimised together). The caller creates one context per
  * sequence with npg_create, each with its own non-default stream, distinct

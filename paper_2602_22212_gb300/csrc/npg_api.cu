@@ -368,6 +368,7 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
   std::vector<std::pair<int, int>> ev;
   ev.reserve(3 * (size_t)F_tri);
   const int32_t* hf = reinterpret_cast<const int32_t*>(hfaces.data());
+  c->faces_h.assign(hf, hf + 3 * (size_t)F_tri);
   for (int f = 0; f < F_tri; ++f)
     for (int k = 0; k < 3; ++k) {
       int a = hf[3 * f + k], b = hf[3 * f + (k + 1) % 3];
@@ -1032,6 +1033,116 @@ extern "C" int npg_timing_read(npg_ctx* c, int stage, double* total_ms, int* n_i
 }
 
 extern "C" long long npg_launch_count(const npg_ctx* c) { return c ? c->launches : 0; }
+
+// ----------------------------------------------------------------- evaluation
+extern "C" int npg_evaluate(npg_ctx* c, const float* gt_xyz, int on_device, float tau_rel,
+                            double* out) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (!gt_xyz || !out || !(tau_rel > 0.f))
+    return set_err(c, NPG_EINVAL, "npg_evaluate: gt_xyz and out non-NULL, tau_rel > 0");
+  if (c->phase < 1) return set_err(c, NPG_ESTATE, "npg_evaluate needs a preceding npg_forward");
+  const int N = c->N, T = c->T;
+  const long long NT = (long long)N * T;
+  const long long F_tri = (long long)c->faces_h.size() / 3;
+  cudaStream_t s = c->stream;
+  if (!c->d_faces && F_tri > 0) {  // vertex -> face lists, built once
+    std::vector<int> off(N + 1, 0), vf(3 * F_tri);
+    for (long long f = 0; f < F_tri; ++f)
+      for (int k = 0; k < 3; ++k) off[c->faces_h[3 * f + k] + 1]++;
+    for (int i = 0; i < N; ++i) off[i + 1] += off[i];
+    std::vector<int> fill(off.begin(), off.end() - 1);
+    for (long long f = 0; f < F_tri; ++f)
+      for (int k = 0; k < 3; ++k) vf[fill[c->faces_h[3 * f + k]]++] = (int)f;
+    if (!alloc_n(c, c->d_faces, F_tri) || !alloc_n(c, c->d_vf_off, N + 1) ||
+        !alloc_n(c, c->d_vf, 3 * F_tri))
+      return set_err(c, NPG_ENOMEM, "device allocation failed");
+    if ((rc = copy_in(c, c->d_faces, c->faces_h.data(), sizeof(int32_t) * 3 * F_tri, 0)) ||
+        (rc = copy_in(c, c->d_vf_off, off.data(), sizeof(int) * (N + 1), 0)) ||
+        (rc = copy_in(c, c->d_vf, vf.data(), sizeof(int) * 3 * F_tri, 0)))
+      return rc;
+  }
+  const int G = auto_cells(N, T);
+  const long long G3 = (long long)G * G * G;
+  const int split = eval_split(), terms = eval_terms();
+  float4 *g4 = nullptr, *nx = nullptr, *ng = nullptr;
+  float *gstage = nullptr, *d_x = nullptr, *d_g = nullptr, *tau2 = nullptr;
+  int *idx_x = nullptr, *idx_g = nullptr;
+  double* part = nullptr;
+  Buckets xs, gs;
+  NnQueue q;
+  q.far_blocks = c->num_sms * 16;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t b) {
+    if (e == cudaSuccess) e = cudaMallocAsync(p, b, s);
+  };
+  A((void**)&g4, sizeof(float4) * NT);
+  if (!on_device) A((void**)&gstage, sizeof(float) * 3 * NT);
+  A((void**)&nx, sizeof(float4) * NT);
+  A((void**)&ng, sizeof(float4) * NT);
+  A((void**)&idx_x, sizeof(int) * NT);
+  A((void**)&idx_g, sizeof(int) * NT);
+  A((void**)&d_x, sizeof(float) * NT);
+  A((void**)&d_g, sizeof(float) * NT);
+  A((void**)&tau2, sizeof(float) * T);
+  A((void**)&part, sizeof(double) * T * split * terms);
+  for (Buckets* b : {&xs, &gs}) {
+    b->G = G;
+    b->nsets = T;
+    A((void**)&b->cell_start, sizeof(int) * T * (G3 + 1));
+    A((void**)&b->counts, sizeof(int) * T * G3);
+    A((void**)&b->slot, sizeof(int) * NT);
+    A((void**)&b->sorted, sizeof(float4) * NT);
+  }
+  A((void**)&q.counters, sizeof(int) * 2);
+  A((void**)&q.items, sizeof(int4) * NT);
+  const float* gsrc = gt_xyz;
+  if (e == cudaSuccess && !on_device) {
+    e = cudaMemcpyAsync(gstage, gt_xyz, sizeof(float) * 3 * NT, cudaMemcpyHostToDevice, s);
+    gsrc = gstage;
+  }
+  if (e == cudaSuccess) e = launch_points_to_float4(gsrc, g4, NT, s);
+  if (e == cudaSuccess) e = launch_eval_tau(g4, N, T, tau_rel, tau2, s);
+  if (e == cudaSuccess)
+    e = launch_eval_normals(c->xhat, c->d_faces, c->d_vf_off, c->d_vf, N, NT, nx, s);
+  if (e == cudaSuccess) e = launch_eval_normals(g4, c->d_faces, c->d_vf_off, c->d_vf, N, NT, ng, s);
+  if (e == cudaSuccess) e = bucket_build(c->xhat, nullptr, N, T, NT, G, xs, s);
+  if (e == cudaSuccess) e = bucket_build(g4, nullptr, N, T, NT, G, gs, s);
+  if (e == cudaSuccess)
+    e = launch_nn(xs.sorted, N, nullptr, T, NT, gs, nullptr, N, idx_x, d_x, q, s);
+  if (e == cudaSuccess)
+    e = launch_nn(gs.sorted, N, nullptr, T, NT, xs, nullptr, N, idx_g, d_g, q, s);
+  if (e == cudaSuccess)
+    e = launch_eval_frames(c->xhat, g4, nx, ng, idx_x, d_x, idx_g, d_g, tau2, N, T, part, s);
+  std::vector<double> hp((size_t)T * split * terms);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s);
+  for (void* p : {(void*)g4, (void*)gstage, (void*)nx, (void*)ng, (void*)idx_x, (void*)idx_g,
+                  (void*)d_x, (void*)d_g, (void*)tau2, (void*)part, (void*)q.counters,
+                  (void*)q.items, (void*)xs.cell_start, (void*)xs.counts, (void*)xs.slot,
+                  (void*)xs.sorted, (void*)gs.cell_start, (void*)gs.counts, (void*)gs.slot,
+                  (void*)gs.sorted})
+    if (p) cudaFreeAsync(p, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "npg_evaluate");
+  double mean[6] = {0, 0, 0, 0, 0, 0};
+  for (int t = 0; t < T; ++t) {
+    double sum[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < split; ++b)
+      for (int m = 0; m < terms; ++m) sum[m] += hp[((size_t)t * split + b) * terms + m];
+    double* o = out + 6 * (size_t)t;
+    const double P = sum[2] / N, R = sum[3] / N;
+    o[0] = (sum[0] + sum[1]) / N;
+    o[1] = P;
+    o[2] = R;
+    o[3] = P + R > 0 ? 2 * P * R / (P + R) : 0.0;
+    o[4] = 0.5 * (sum[4] + sum[5]) / N;
+    o[5] = sum[6] / N;
+    for (int m = 0; m < 6; ++m) mean[m] += o[m] / T;
+  }
+  for (int m = 0; m < 6; ++m) out[6 * (size_t)T + m] = mean[m];
+  return NPG_OK;
+}
 
 // ----------------------------------------------------------------- batch
 struct npg_batch {

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/npg.h"
 
@@ -153,6 +154,11 @@ struct npg_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   cudaGraph_t graph = nullptr;
   std::string err;
+  // evaluation metrics: faces (host copy) and, once built, their device form
+  std::vector<int32_t> faces_h;
+  int3* d_faces = nullptr;
+  int* d_vf_off = nullptr;  // vertex -> incident faces, CSR
+  int* d_vf = nullptr;
 };
 
 namespace npg {
@@ -196,6 +202,18 @@ cudaError_t launch_points_to_float4(const float* src, float4* dst, long long n, 
 cudaError_t launch_xhat_out(const float4* xhat, float* out, long long n, cudaStream_t s);
 
 int auto_cells(long long points_per_set, int nsets);
+
+// evaluation metrics (k_eval.cu)
+cudaError_t launch_eval_normals(const float4* v, const int3* faces, const int* vf_off,
+                                const int* vf, int N, long long NT, float4* nrm, cudaStream_t s);
+cudaError_t launch_eval_tau(const float4* g, int N, int T, float tau_rel, float* tau2,
+                            cudaStream_t s);
+cudaError_t launch_eval_frames(const float4* x, const float4* g, const float4* nx,
+                               const float4* ng, const int* idx_x, const float* d_x,
+                               const int* idx_g, const float* d_g, const float* tau2, int N,
+                               int T, double* part, cudaStream_t s);
+int eval_split();
+int eval_terms();
 // records a message for npg_last_error(NULL) and returns code
 int set_error_message(int code, const char* fmt, ...);
 bool decode_fp32_supported(int H, int D);

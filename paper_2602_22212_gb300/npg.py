@@ -102,6 +102,7 @@ _SIG = {
     "npg_timing_read": (_i, [_vp, _i, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "npg_launch_count": (C.c_longlong, [_vp]),
     "npg_search_stats": (_i, [_vp, C.POINTER(C.c_longlong)]),
+    "npg_evaluate": (_i, [_vp, _vp, _i, C.c_float, _vp]),
     "npg_batch_create": (_i, [C.POINTER(_vp), _i, C.POINTER(_vp), _vp]),
     "npg_batch_iteration": (_i, [_vp, _vp]),
     "npg_batch_destroy": (_i, [_vp]),
@@ -199,6 +200,22 @@ def npg_backprop(ctx, dxhat=None):
 
 def npg_iteration(ctx, loss_out=None):
     _check(_lib.npg_iteration(ctx, _ptr(loss_out)), ctx)
+
+
+EVAL_FIELDS = ("cd", "precision", "recall", "fscore", "nc", "corr")
+
+
+def npg_evaluate(ctx, gt_xyz, tau_rel=0.005):
+    """Sec. 4 metrics of the last forward's x-hat against ground-truth vertices
+    (T x N x 3, host array or CUDA tensor): (T + 1) x 6 array, the last row the
+    mean over frames; columns EVAL_FIELDS."""
+    T = int(gt_xyz.shape[0])
+    out = np.zeros((T + 1, 6))
+    if not _on_device(gt_xyz):
+        gt_xyz = np.ascontiguousarray(gt_xyz, dtype=np.float32)
+    _check(_lib.npg_evaluate(ctx, _ptr(gt_xyz), int(_on_device(gt_xyz)), float(tau_rel),
+                             out.ctypes.data), ctx)
+    return out
 
 
 def npg_batch_create(ctxs, stream):
