@@ -43,6 +43,10 @@ class OrCfg(C.Structure):
         ("slope", C.c_double),
         ("alpha", C.c_double),
         ("w_iso", C.c_double),
+        ("time_enc", C.c_int),
+        ("time_B", C.c_double * 8),
+        ("conf_delta", C.c_int),
+        ("conf_omega", C.c_int),
     ]
 
 
@@ -99,6 +103,7 @@ def lib():
                 "or_iteration": (d, [cfg, i, pd, pd, i, pi64, pd, l, pi32, i, i, i, pd, pd, pd,
                                      pd, pd, pd, pd, d, pd, d, d, d, i, d, pd, pd, pd, pd]),
                 "or_evaluate": (None, [i, i, pd, pd, i, pi32, d, pd]),
+                "or_conf_weights_mode": (None, [i, pd, i, d, d, i, i, pd]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -136,7 +141,8 @@ def _out_i32(n):
 
 
 def make_cfg(L, res, F, Fn=2, rn=4, H=64, D=3, rot_mode=0, n_freq=4, slope=0.01,
-             alpha=0.1, w_iso=100.0) -> OrCfg:
+             alpha=0.1, w_iso=100.0, time_enc=0, time_B=None, conf_delta=0,
+             conf_omega=0) -> OrCfg:
     c = OrCfg()
     c.L = int(L)
     for k, r in enumerate(res):
@@ -144,6 +150,9 @@ def make_cfg(L, res, F, Fn=2, rn=4, H=64, D=3, rot_mode=0, n_freq=4, slope=0.01,
     c.F, c.Fn, c.rn, c.H, c.D = int(F), int(Fn), int(rn), int(H), int(D)
     c.rot_mode, c.n_freq = int(rot_mode), int(n_freq)
     c.slope, c.alpha, c.w_iso = float(slope), float(alpha), float(w_iso)
+    c.time_enc, c.conf_delta, c.conf_omega = int(time_enc), int(conf_delta), int(conf_omega)
+    for j, b in enumerate(time_B if time_B is not None else []):
+        c.time_B[j] = float(b)
     return c
 
 
@@ -255,12 +264,13 @@ def chamfer(xhat, off, pts, decide_f32=False):
     return (nnx.reshape(T, N), dx.reshape(T, N), nnp[:MT], dp[:MT], cd)
 
 
-def conf_weights(cd, t_key, e, e_max):
-    """Sec. 3.5, Eq. 11-12."""
+def conf_weights(cd, t_key, e, e_max, delta_mode=0, omega_mode=0):
+    """Sec. 3.5, Eq. 11-12 (modes: the stability ablation's variants)."""
     T = len(cd)
     cd, pcd = _d(cd)
     w, pw = _out_d(T)
-    lib().or_conf_weights(T, pcd, int(t_key), float(e), float(e_max), pw)
+    lib().or_conf_weights_mode(T, pcd, int(t_key), float(e), float(e_max), int(delta_mode),
+                               int(omega_mode), pw)
     return w
 
 

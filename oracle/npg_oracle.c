@@ -58,6 +58,15 @@ typedef struct {
   double slope;            /* LeakyReLU negative slope                       */
   double alpha;            /* translation squashing factor (Eq. 6)           */
   double w_iso;            /* isometry weight (Eq. 8)                        */
+  /* variants of the ablations (Sec. 4): 0 is the method itself */
+  int time_enc;            /* time encoding: 0 Fourier (Eq. 3), 1 polynomial,
+                              2 Gaussian Fourier with frequencies time_B     */
+  double time_B[8];        /* Gaussian Fourier frequencies B_j (j < n_freq)  */
+  int conf_delta;          /* catch-up delta: 0 1 - sqrt(e~), 1 constant 1,
+                              2 linear 1 - e~, 3 exp(-5 e~), 4 interpolated  */
+  int conf_omega;          /* 0 cumulative product of omega (Eq. 11-12);
+                              direct w = omega(t)^delta with omega 1 constant,
+                              2 one half, 3 the single-frame omega(t)        */
 } or_cfg;
 
 /* ------------------------------------------------------------------ sizes */
@@ -135,15 +144,25 @@ void or_encode(const or_cfg* c, int N, const double* x, const double* n,
 
 /* ------------------------------------- Sec. 3.3, Eq. 3: time embedding */
 
+/* Sec. 3.3, Eq. 3 (and the ablation's variants): time_enc 1 is the
+ * polynomial basis gamma_j = t~^j, j = 1..2M; time_enc 2 the Gaussian Fourier
+ * mapping (sin(2 pi B_j t~), cos(2 pi B_j t~)) with given B, interleaved
+ * like Eq. 3. */
 void or_time_embedding(const or_cfg* c, int T, double* gamma) {
   const double pi = 3.14159265358979323846;
   int M = c->n_freq;
   for (int t = 0; t < T; ++t) {
     double tt = T > 1 ? (double)t / (double)(T - 1) : 0.0;
+    double* g = gamma + (long)t * 2 * M;
+    if (c->time_enc == 1) {
+      for (int j = 0; j < 2 * M; ++j) g[j] = pow(tt, (double)(j + 1));
+      continue;
+    }
     for (int j = 0; j < M; ++j) {
-      double nu = ldexp(1.0, j); /* nu_j = 2^(j-1) for 1-based j */
-      gamma[(long)t * 2 * M + 2 * j] = sin(pi * nu * tt);
-      gamma[(long)t * 2 * M + 2 * j + 1] = cos(pi * nu * tt);
+      double a = c->time_enc == 2 ? 2.0 * c->time_B[j] * tt
+                                  : ldexp(1.0, j) * tt; /* nu_j = 2^(j-1), 1-based */
+      g[2 * j] = sin(pi * a);
+      g[2 * j + 1] = cos(pi * a);
     }
   }
 }
@@ -419,21 +438,45 @@ void or_chamfer(int T, int N, const double* xhat, const int64_t* off, const doub
 /* w(t) = prod_{tau between t_key and t, inclusive} omega(tau)^delta,
  * omega(tau) = 1 / (1 + max(0, cd_tau - cd_tkey)), delta = 1 - sqrt(e / e_max)
  * with e / e_max clamped to [0, 1]. */
-void or_conf_weights(int T, const double* cd, int t_key, double e, double e_max, double* w) {
+/* The ablation's schedules (Sec. 4, stability function): delta_mode picks
+ * the catch-up variable (0: 1 - sqrt(e~), the method; 1: 1; 2: 1 - e~;
+ * 3: exp(-5 e~); 4: interpolated, w = (1 - e~) W(t) + e~ with W(t) the
+ * weight at delta = 1), omega_mode the temporal weighting (0: the cumulative
+ * product of Eq. 11-12; 1, 2, 3: direct w = omega(t)^delta with omega = 1,
+ * 0.5, or 1 / (1 + max(0, cd_t - cd_key))). */
+void or_conf_weights_mode(int T, const double* cd, int t_key, double e, double e_max,
+                          int delta_mode, int omega_mode, double* w) {
   double eb = e_max > 0 ? e / e_max : 1.0;
   if (eb < 0) eb = 0;
   if (eb > 1) eb = 1;
   double delta = 1.0 - sqrt(eb);
+  if (delta_mode == 1 || delta_mode == 4) delta = 1.0;
+  if (delta_mode == 2) delta = 1.0 - eb;
+  if (delta_mode == 3) delta = exp(-5.0 * eb);
   for (int t = 0; t < T; ++t) {
-    int lo = t < t_key ? t : t_key, hi = t < t_key ? t_key : t;
-    double prod = 1.0;
-    for (int tau = lo; tau <= hi; ++tau) {
-      double ex = cd[tau] - cd[t_key];
-      double om = 1.0 / (1.0 + (ex > 0 ? ex : 0.0));
-      prod *= pow(om, delta);
+    double wt;
+    if (omega_mode == 0) {
+      int lo = t < t_key ? t : t_key, hi = t < t_key ? t_key : t;
+      double prod = 1.0;
+      for (int tau = lo; tau <= hi; ++tau) {
+        double ex = cd[tau] - cd[t_key];
+        double om = 1.0 / (1.0 + (ex > 0 ? ex : 0.0));
+        prod *= pow(om, delta);
+      }
+      wt = prod;
+    } else {
+      double ex = cd[t] - cd[t_key];
+      double om = omega_mode == 1 ? 1.0
+                : omega_mode == 2 ? 0.5
+                                  : 1.0 / (1.0 + (ex > 0 ? ex : 0.0));
+      wt = pow(om, delta);
     }
-    w[t] = prod;
+    w[t] = delta_mode == 4 ? (1.0 - eb) * wt + eb : wt;
   }
+}
+
+void or_conf_weights(int T, const double* cd, int t_key, double e, double e_max, double* w) {
+  or_conf_weights_mode(T, cd, t_key, e, e_max, 0, 0, w);
 }
 
 /* ------------------------------------------------------ mesh edges */
@@ -695,7 +738,7 @@ double or_loss_full(const or_cfg* c, int N, const double* x, const double* n, in
   double* w = (double*)malloc(sizeof(double) * T);
   double* lref = (double*)malloc(sizeof(double) * (E > 0 ? E : 1));
   or_chamfer(T, N, xhat, off, pts, decide_f32, nn_x, d_x, nn_p, d_p, cd);
-  or_conf_weights(T, cd, t_key, e, e_max, w);
+  or_conf_weights_mode(T, cd, t_key, e, e_max, c->conf_delta, c->conf_omega, w);
   or_edge_lengths(N, xhat, t_key, E, edges, lref);
   double L = or_loss_grad(c, N, x, n, T, off, pts, E, edges, grid, mlp, w, lref, decide_f32,
                           g_grid, g_mlp, xhat_out, cd_out, parts, nn_x_out, nn_p_out, gx_out);

@@ -449,3 +449,45 @@ def test_evaluation_metrics_match_kdtree_and_numpy_normals():
         want = [np.mean(dx ** 2) + np.mean(dg ** 2), P, R, 2 * P * R / (P + R), nc,
                 np.mean(np.linalg.norm(X - G, axis=1))]
         np.testing.assert_allclose(got[t], want, rtol=1e-9, atol=1e-15)
+
+
+# ---------------------------------------------------------------- ablation variants
+
+def test_time_encoding_variants():
+    """Polynomial basis t~^j (j = 1..2M) and Gaussian Fourier mapping
+    sin / cos(2 pi B_j t~), against hand values."""
+    cfg = O.make_cfg(L=2, res=(4, 5), F=2, n_freq=2, time_enc=1)
+    g = O.time_embedding(cfg, 5)  # t~ = 0, 1/4, 1/2, 3/4, 1
+    np.testing.assert_allclose(g[1], [0.25, 0.0625, 0.015625, 0.00390625], rtol=1e-15)
+    np.testing.assert_array_equal(g[0], 0.0)
+    np.testing.assert_array_equal(g[4], 1.0)
+    cfg = O.make_cfg(L=2, res=(4, 5), F=2, n_freq=2, time_enc=2, time_B=(1.0, 0.5))
+    g = O.time_embedding(cfg, 5)
+    np.testing.assert_allclose(g[0], [0, 1, 0, 1], atol=1e-15)
+    # t~ = 1/4: B = 1 -> (sin pi/2, cos pi/2); B = 1/2 -> (sin pi/4, cos pi/4)
+    np.testing.assert_allclose(g[1], [1, 0, 0.5 ** 0.5, 0.5 ** 0.5], atol=1e-15)
+    # t~ = 1: B = 1 -> (0, 1); B = 1/2 -> (0, -1)
+    np.testing.assert_allclose(g[4], [0, 1, 0, -1], atol=1e-15)
+
+
+def test_stability_schedule_variants():
+    """The confidence weights of the stability ablation on a hand-worked
+    example: cd = (2, 1, 1.5, 3), keyframe 1, so omega = (1/2, 1, 2/3, 1/3)."""
+    cd = np.array([2.0, 1.0, 1.5, 3.0])
+    cum1 = np.array([0.5, 1.0, 2 / 3, 2 / 9])        # cumulative products, delta = 1
+    single = np.array([0.5, 1.0, 2 / 3, 1 / 3])      # omega(t) alone
+    w = lambda e, d, o: O.conf_weights(cd, 1, e, 4, d, o)
+    # e~ = 0: every schedule has delta = 1
+    for d in (0, 1, 2, 3, 4):
+        np.testing.assert_allclose(w(0, d, 0), cum1, rtol=1e-14)
+    # e~ = 1/4: delta = 1/2 (sqrt), 1 (constant), 3/4 (linear), exp(-5/4)
+    for d, delta in ((0, 0.5), (1, 1.0), (2, 0.75), (3, np.exp(-1.25))):
+        np.testing.assert_allclose(w(1, d, 0), cum1 ** delta, rtol=1e-14)
+        np.testing.assert_allclose(w(1, d, 3), single ** delta, rtol=1e-14)
+        np.testing.assert_allclose(w(1, d, 1), np.ones(4), rtol=0)
+        np.testing.assert_allclose(w(1, d, 2), np.full(4, 0.5 ** delta), rtol=1e-14)
+    np.testing.assert_allclose(w(1, 4, 0), 0.75 * cum1 + 0.25, rtol=1e-14)
+    np.testing.assert_allclose(w(1, 4, 3), 0.75 * single + 0.25, rtol=1e-14)
+    # e~ = 1: the method's delta is 0 (all weights 1), and so is the linear one
+    for d in (0, 2, 4):
+        np.testing.assert_allclose(w(4, d, 0), np.ones(4), rtol=1e-14)
