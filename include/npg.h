@@ -48,6 +48,7 @@ extern "C" {
 #endif
 
 #define NPG_MAX_LEVELS 16
+#define NPG_MAX_FREQ 8  /* time-encoding frequencies M <= 8 */
 
 /* status codes */
 #define NPG_OK 0
@@ -67,6 +68,18 @@ extern "C" {
 #define NPG_PRECOND_TC 1
 
 /* arithmetic of the MLP decode and its backward pass */
+#define NPG_TIME_FOURIER 0
+#define NPG_TIME_POLY 1
+#define NPG_TIME_GAUSS 2
+#define NPG_DELTA_SQRT 0
+#define NPG_DELTA_CONST 1
+#define NPG_DELTA_LINEAR 2
+#define NPG_DELTA_EXP 3
+#define NPG_DELTA_INTERP 4
+#define NPG_OMEGA_CUMULATIVE 0
+#define NPG_OMEGA_CONST 1
+#define NPG_OMEGA_HALF 2
+#define NPG_OMEGA_SINGLE 3
 #define NPG_FP32 0     /* FP32 SIMT                                          */
 #define NPG_BF16_MLP 1 /* BF16 operands, FP32 accumulation on tcgen05 tensor cores */
 
@@ -80,7 +93,7 @@ typedef struct npg_ctx npg_ctx; /* opaque; owns all device memory it allocates *
  *                    (1..8), nodes per axis of the normal grid (Sec. 3.2).
  *   H, depth         hidden width and number of hidden layers (Sec. 3.3);
  *                    NPG_FP32 supports H in {16, 32, 64}, NPG_BF16_MLP
- *                    H in {64, 128}; depth 1..8.
+ *                    H = 64 with depth 3; depth 1..8.
  *   leaky_slope      LeakyReLU negative slope (0 = ReLU).
  *   rot_mode         NPG_ROT_QUAT or NPG_ROT_EXPMAP.
  *   n_freq           Fourier frequencies M (Eq. 3; 1..8).
@@ -99,6 +112,19 @@ typedef struct npg_ctx npg_ctx; /* opaque; owns all device memory it allocates *
  *                    cores in split BF16 (hi + lo, three products, FP32
  *                    accumulation; ~1e-5 relative) for levels with r >= 24.
  *   use_graph        npg_iteration replays one captured CUDA graph.
+ *   time_enc         time encoding gamma(t) (Sec. 3.3 and its ablation, Sec. 4):
+ *                    NPG_TIME_FOURIER (Eq. 3, the method), NPG_TIME_POLY
+ *                    (t~^j, j = 1..2M), NPG_TIME_GAUSS (sin / cos(2 pi B_j t~)
+ *                    with the caller's frequencies time_B[0..M-1], e.g. drawn
+ *                    from N(0, 1)).
+ *   conf_delta       catch-up variable of the confidence weights (Eq. 11-12 and
+ *                    the stability ablation): NPG_DELTA_SQRT (1 - sqrt(e~), the
+ *                    method), _CONST (1), _LINEAR (1 - e~), _EXP (exp(-5 e~)),
+ *                    _INTERP (w = (1 - e~) W(t) + e~, W the weight at delta 1).
+ *   conf_omega       temporal weighting: NPG_OMEGA_CUMULATIVE (Eq. 12, the
+ *                    method) or a direct w = omega(t)^delta with omega = 1
+ *                    (_CONST), 0.5 (_HALF) or 1 / (1 + max(0, cd_t - cd_key))
+ *                    (_SINGLE).
  *   stream           cudaStream_t for all device work.
  *   alloc/free/user  optional device allocator (e.g. PyTorch's caching
  *                    allocator); NULL = cudaMalloc / cudaFree.
@@ -131,13 +157,18 @@ typedef struct npg_config {
   void* (*alloc)(size_t bytes, void* user);
   void (*free)(void* ptr, void* user);
   void* alloc_user;
+  int time_enc;
+  float time_B[NPG_MAX_FREQ];
+  int conf_delta;
+  int conf_omega;
 } npg_config;
 
 /* Paper defaults (Sec. 3.2-3.5): resolutions r_l = round(r_min + (r_max -
  * r_min)(l-1)/(L-1)), F_n = 2, res_n = 4, LeakyReLU 0.01, quaternions, M = 4,
  * alpha = 0.1, lr_mlp = 1e-3, lr_l = 0.005 * 2.5^(l-1), lambda_l = 0.4 *
  * 1.5^(l-1) (l = 1 coarsest; the normal grid takes the level-1 values), Adam
- * (0.9, 0.999, 1e-8), w_iso = 100, e_max = 1000, FP32. */
+ * (0.9, 0.999, 1e-8), w_iso = 100, e_max = 1000, FP32, Fourier time encoding,
+ * the cumulative confidence weights with delta = 1 - sqrt(e~). */
 NPG_API int npg_config_default(npg_config* cfg, int L, int r_min, int r_max, int F_p, int H, int depth);
 
 /*

@@ -20,6 +20,7 @@ struct BwdArgs {
   const float* z;
   const float4* xr;
   const float4* dxhat;
+  const float* gamma;  // T x 2M time encoding
   float* g_mlp;
   float* dz;
   int N, T, K, Z, M, D, NO;
@@ -122,7 +123,9 @@ __global__ void __launch_bounds__(128, 1) mlp_bwd_fp32_kernel(BwdArgs a) {
       const int v = k / Z, q = k % Z;
       Ys[k] = (i0 + v < a.N) ? a.z[(long long)(i0 + v) * Z + q] : 0.f;
     }
-    if (tid < 8) time_embedding(min(t0 + tid, a.T - 1), a.T, M, Ys + 8 * Z + tid * 2 * M);
+    if (tid < 8)
+      for (int k = 0; k < 2 * M; ++k)
+        Ys[8 * Z + tid * 2 * M + k] = a.gamma[(long long)min(t0 + tid, a.T - 1) * 2 * M + k];
 
     // ---- forward recompute
     float h[H];
@@ -360,6 +363,7 @@ static cudaError_t mlp_bwd_h(npg_ctx* c) {
   a.K = c->md.K;
   a.Z = c->md.Z;
   a.M = c->md.M;
+  a.gamma = c->gamma;
   a.D = c->md.D;
   a.NO = c->md.NO;
   a.slope = c->md.slope;

@@ -592,25 +592,39 @@ __global__ void loss_combine_kernel(const double* __restrict__ part,
 // The per-frame factors (one FP64 power each) are computed in parallel; one
 // thread then forms the products outward from the keyframe; the sums use the
 // block's fixed-order reduction.
+// Variants (the stability ablation): delta_mode NPG_DELTA_* picks the
+// catch-up variable, omega_mode NPG_OMEGA_* replaces the cumulative product by
+// a direct weight omega(t)^delta; NPG_DELTA_INTERP blends the delta = 1
+// weight W(t) as (1 - e~) W(t) + e~.
 __global__ void __launch_bounds__(256) loss_final_kernel(
     const double* __restrict__ cd, const double* __restrict__ iso_t, const int* __restrict__ epoch,
-    int e_max, int T, int t_key, int E, double w_iso, double* __restrict__ w,
-    double* __restrict__ loss) {
+    int e_max, int T, int t_key, int E, double w_iso, int delta_mode, int omega_mode,
+    double* __restrict__ w, double* __restrict__ loss) {
   __shared__ double sh[32];
   double eb = e_max > 0 ? (double)(*epoch) / (double)e_max : 1.0;
   eb = fmin(fmax(eb, 0.0), 1.0);
-  const double delta = 1.0 - sqrt(eb);
+  double delta = 1.0 - sqrt(eb);
+  if (delta_mode == NPG_DELTA_CONST || delta_mode == NPG_DELTA_INTERP) delta = 1.0;
+  if (delta_mode == NPG_DELTA_LINEAR) delta = 1.0 - eb;
+  if (delta_mode == NPG_DELTA_EXP) delta = exp(-5.0 * eb);
   const double ck = cd[t_key];
   for (int t = threadIdx.x; t < T; t += blockDim.x) {
     const double ex = cd[t] - ck;
-    w[t] = t == t_key ? 1.0 : pow(1.0 / (1.0 + (ex > 0 ? ex : 0.0)), delta);
+    const double om = omega_mode == NPG_OMEGA_CONST  ? 1.0
+                      : omega_mode == NPG_OMEGA_HALF ? 0.5
+                                                     : 1.0 / (1.0 + (ex > 0 ? ex : 0.0));
+    w[t] = (t == t_key && omega_mode == NPG_OMEGA_CUMULATIVE) ? 1.0 : pow(om, delta);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && omega_mode == NPG_OMEGA_CUMULATIVE) {
     for (int t = t_key + 1; t < T; ++t) w[t] *= w[t - 1];
     for (int t = t_key - 1; t >= 0; --t) w[t] *= w[t + 1];
   }
   __syncthreads();
+  if (delta_mode == NPG_DELTA_INTERP) {
+    for (int t = threadIdx.x; t < T; t += blockDim.x) w[t] = (1.0 - eb) * w[t] + eb;
+    __syncthreads();
+  }
   double ld = 0.0, li = 0.0;
   for (int t = threadIdx.x; t < T; t += blockDim.x) {
     ld += w[t] * cd[t];
@@ -634,7 +648,8 @@ cudaError_t launch_loss(npg_ctx* c) {
   loss_combine_kernel<<<(c->T + 127) / 128, 128, 0, c->stream>>>(c->loss_part, c->p_off, c->N,
                                                                  c->T, c->cd, c->iso_t);
   loss_final_kernel<<<1, 256, 0, c->stream>>>(c->cd, c->iso_t, c->d_epoch, c->cfg.e_max,
-                                             c->T, c->t_key, c->E, (double)c->cfg.w_iso, c->wconf,
+                                             c->T, c->t_key, c->E, (double)c->cfg.w_iso,
+                                             c->cfg.conf_delta, c->cfg.conf_omega, c->wconf,
                                              c->loss);
   return cudaGetLastError();
 }

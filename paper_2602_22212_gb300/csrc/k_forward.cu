@@ -120,12 +120,21 @@ cudaError_t launch_encode(npg_ctx* c) {
 }
 
 // ----------------------------------------------------------------- time modulation
+// gamma(t) of every frame (T x 2M), once per context: the encoding is fixed.
+struct TimeFreqs {
+  float B[NPG_MAX_FREQ];
+};
+
+__global__ void time_table_kernel(float* gamma, int T, int M, int mode, TimeFreqs f) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < T) time_embedding_mode(t, T, M, mode, f.B, gamma + (long long)t * 2 * M);
+}
+
 // V_t = W1[:, Z:] gamma(t) (Eq. 2-3; the bias lives in U).
-__global__ void time_mod_kernel(const float* mlp, float* V, int T, int H, int K, int Z, int M) {
+__global__ void time_mod_kernel(const float* mlp, const float* gamma, float* V, int T, int H,
+                                int K, int Z, int M) {
   const int t = blockIdx.x;
-  __shared__ float g[2 * NPG_MAX_FREQ];
-  if (threadIdx.x == 0) time_embedding(t, T, M, g);
-  __syncthreads();
+  const float* g = gamma + (long long)t * 2 * M;
   for (int j = threadIdx.x; j < H; j += blockDim.x) {
     float s = 0.f;
     for (int k = 0; k < 2 * M; ++k) s = fmaf(mlp[(long long)j * K + Z + k], g[k], s);
@@ -133,9 +142,17 @@ __global__ void time_mod_kernel(const float* mlp, float* V, int T, int H, int K,
   }
 }
 
+cudaError_t launch_time_table(npg_ctx* c) {
+  TimeFreqs f;
+  for (int j = 0; j < NPG_MAX_FREQ; ++j) f.B[j] = c->cfg.time_B[j];
+  time_table_kernel<<<(c->T + 127) / 128, 128, 0, c->stream>>>(c->gamma, c->T, c->md.M,
+                                                               c->cfg.time_enc, f);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_time_mod(npg_ctx* c) {
-  time_mod_kernel<<<c->T, 128, 0, c->stream>>>(c->mlp, c->V, c->T, c->md.H, c->md.K, c->md.Z,
-                                              c->md.M);
+  time_mod_kernel<<<c->T, 128, 0, c->stream>>>(c->mlp, c->gamma, c->V, c->T, c->md.H, c->md.K,
+                                              c->md.Z, c->md.M);
   return cudaGetLastError();
 }
 

@@ -69,6 +69,7 @@ struct TcArgs {
   float4* disp;
   const float4* dxhat;
   const float* z;
+  const float* gamma;  // T x 2M time encoding
   float* g_mlp;
   float* dz;
   int* err;
@@ -248,6 +249,7 @@ static TcArgs tc_args(npg_ctx* c) {
   a.K = c->md.K;
   a.Z = c->md.Z;
   a.M = c->md.M;
+  a.gamma = c->gamma;
   a.NO = c->md.NO;
   a.slope = c->md.slope;
   a.alpha = c->cfg.alpha;
@@ -533,13 +535,8 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
 #pragma unroll
       for (int k = 0; k < 8; ++k)
         if (k < Z) st_bf16(sm + BwdSmem::Y, row, k, valid ? zs[k] : 0.f);
-      const float tt = a.T > 1 ? (float)(valid ? t : 0) / (float)(a.T - 1) : 0.f;
-      for (int j = 0; j < M; ++j) {
-        float sn, cs;
-        sincospif(ldexpf(tt, j), &sn, &cs);
-        st_bf16(sm + BwdSmem::Y, row, Z + 2 * j, sn);
-        st_bf16(sm + BwdSmem::Y, row, Z + 2 * j + 1, cs);
-      }
+      const float* gt = a.gamma + (long long)(valid ? t : 0) * 2 * M;
+      for (int k = 0; k < 2 * M; ++k) st_bf16(sm + BwdSmem::Y, row, Z + k, gt[k]);
     }
     // ---- forward: layer 2
     if (!(ok = tc_sync_ok(ok, a.err))) break;

@@ -183,6 +183,12 @@ static int validate(const npg_config* c, char* why, size_t n) {
     return snprintf(why, n, "depth=%d out of 1..8", c->depth), 0;
   if (c->n_freq < 1 || c->n_freq > NPG_MAX_FREQ)
     return snprintf(why, n, "n_freq=%d out of 1..8", c->n_freq), 0;
+  if (c->time_enc < NPG_TIME_FOURIER || c->time_enc > NPG_TIME_GAUSS)
+    return snprintf(why, n, "time_enc=%d", c->time_enc), 0;
+  if (c->conf_delta < NPG_DELTA_SQRT || c->conf_delta > NPG_DELTA_INTERP)
+    return snprintf(why, n, "conf_delta=%d", c->conf_delta), 0;
+  if (c->conf_omega < NPG_OMEGA_CUMULATIVE || c->conf_omega > NPG_OMEGA_SINGLE)
+    return snprintf(why, n, "conf_omega=%d", c->conf_omega), 0;
   if (c->rot_mode != NPG_ROT_QUAT && c->rot_mode != NPG_ROT_EXPMAP)
     return snprintf(why, n, "rot_mode=%d", c->rot_mode), 0;
   if (!(c->leaky_slope >= 0.f)) return snprintf(why, n, "leaky_slope must be >= 0"), 0;
@@ -419,6 +425,7 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
         alloc_n(c, c->xb.slot, NT) && alloc_n(c, c->xb.sorted, NT);
   ok &= alloc_n(c, c->z, (long long)N * md.Z) && alloc_n(c, c->U, (long long)N * md.H) &&
         alloc_n(c, c->V, (long long)T * md.H) && alloc_n(c, c->xhat, NT) &&
+        alloc_n(c, c->gamma, (long long)T * 2 * md.M) &&
         alloc_n(c, c->disp, NT) &&
         alloc_n(c, c->dxhat, NT) && alloc_n(c, c->nn_x, NT) && alloc_n(c, c->d_x, NT) &&
         alloc_n(c, c->nn_p, c->MT_cap) && alloc_n(c, c->d_p, c->MT_cap) &&
@@ -536,6 +543,7 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
   CK(c, cudaMemsetAsync(c->d_epoch, 0, sizeof(int), c->stream));
   CK(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
   CK(c, cudaMemsetAsync(c->d_nnstats, 0, sizeof(unsigned long long) * 4, c->stream));
+  CK(c, launch_time_table(c));
   // no nearest-neighbour seeds before the first search
   CK(c, cudaMemsetAsync(c->nn_x, 0xff, sizeof(int) * NT, c->stream));
   CK(c, cudaMemsetAsync(c->nn_p, 0xff, sizeof(int) * c->MT_cap, c->stream));

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include "../../include/npg.h"
 
 namespace npg {
 
@@ -214,6 +215,31 @@ __device__ __forceinline__ void time_embedding(int t, int T, int M, float* g) {
     const float a = ldexpf(tt, j);
     float s, c;
     sincospif(a, &s, &c);
+    g[2 * j] = s;
+    g[2 * j + 1] = c;
+  }
+}
+
+// gamma(t) of the chosen encoding (NPG_TIME_*): Eq. 3, the polynomial basis
+// t~^j (j = 1..2M), or the Gaussian Fourier mapping sin / cos(2 pi B_j t~).
+__device__ __forceinline__ void time_embedding_mode(int t, int T, int M, int mode,
+                                                    const float* B, float* g) {
+  if (mode == NPG_TIME_FOURIER) {
+    time_embedding(t, T, M, g);
+    return;
+  }
+  const float tt = T > 1 ? (float)t / (float)(T - 1) : 0.f;
+  if (mode == NPG_TIME_POLY) {
+    float p = 1.f;
+    for (int j = 0; j < 2 * M; ++j) {
+      p *= tt;
+      g[j] = p;
+    }
+    return;
+  }
+  for (int j = 0; j < M; ++j) {
+    float s, c;
+    sincospif(2.f * B[j] * tt, &s, &c);
     g[2 * j] = s;
     g[2 * j + 1] = c;
   }

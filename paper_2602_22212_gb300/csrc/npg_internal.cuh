@@ -12,7 +12,6 @@
 #define NPG_MAX_F 32
 #define NPG_MAX_FN 8
 #define NPG_MAX_Z (NPG_MAX_F + NPG_MAX_FN)
-#define NPG_MAX_FREQ 8
 #define NPG_MAX_K (NPG_MAX_Z + 2 * NPG_MAX_FREQ)
 #define NPG_MAX_DEPTH 8
 
@@ -86,6 +85,7 @@ struct npg_ctx {
   float* z = nullptr;      // N x Z
   float* U = nullptr;      // N x H
   float* V = nullptr;      // T x H
+  float* gamma = nullptr;  // T x 2M time encoding gamma(t)
   float4* xhat = nullptr;  // T x N deformed vertices
   float4* disp = nullptr;  // T x N displacements x-hat - x
   float4* dxhat = nullptr; // T x N
@@ -165,6 +165,7 @@ namespace npg {
 
 // kernels (launchers return cudaGetLastError())
 cudaError_t launch_encode(npg_ctx* c);
+cudaError_t launch_time_table(npg_ctx* c);
 cudaError_t launch_time_mod(npg_ctx* c);
 cudaError_t launch_decode_fp32(npg_ctx* c);
 cudaError_t launch_decode_bf16(npg_ctx* c);

@@ -24,6 +24,10 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 MAX_LEVELS = 16
+MAX_FREQ = 8
+TIME_FOURIER, TIME_POLY, TIME_GAUSS = 0, 1, 2
+DELTA_SQRT, DELTA_CONST, DELTA_LINEAR, DELTA_EXP, DELTA_INTERP = 0, 1, 2, 3, 4
+OMEGA_CUMULATIVE, OMEGA_CONST, OMEGA_HALF, OMEGA_SINGLE = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
 ROT_QUAT, ROT_EXPMAP = 0, 1
 FP32, BF16_MLP = 0, 1
@@ -69,6 +73,10 @@ class npg_config(C.Structure):
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_user", C.c_void_p),
+        ("time_enc", C.c_int),
+        ("time_B", C.c_float * MAX_FREQ),
+        ("conf_delta", C.c_int),
+        ("conf_omega", C.c_int),
     ]
 
 
@@ -339,7 +347,8 @@ def npg_precondition_static(g, out, r, F, lam, stream=None):
 def make_config(L, res, F_p, H, depth, *, F_n=2, res_n=4, slope=0.01, rot_mode=ROT_QUAT,
                 precision=FP32, e_max=1000, w_iso=100.0, lr_mlp=1e-3, lr_grid=None,
                 lam=None, n_freq=4, alpha=0.1, nn_cells=0, use_graph=False, stream=None,
-                precond_mode=PRECOND_FP32):
+                precond_mode=PRECOND_FP32, time_enc=TIME_FOURIER, time_B=None,
+                conf_delta=DELTA_SQRT, conf_omega=OMEGA_CUMULATIVE):
     """npg_config with the paper's defaults (Sec. 3.2-3.5) and explicit resolutions."""
     cfg = npg_config_default(L, 2, 2, F_p, H, depth)
     for k, r in enumerate(res):
@@ -351,6 +360,9 @@ def make_config(L, res, F_p, H, depth, *, F_n=2, res_n=4, slope=0.01, rot_mode=R
     cfg.n_freq, cfg.alpha, cfg.nn_cells, cfg.use_graph = int(n_freq), float(alpha), int(
         nn_cells), int(bool(use_graph))
     cfg.precond_mode = int(precond_mode)
+    cfg.time_enc, cfg.conf_delta, cfg.conf_omega = int(time_enc), int(conf_delta), int(conf_omega)
+    for j, b in enumerate(time_B if time_B is not None else []):
+        cfg.time_B[j] = float(b)
     if lr_grid is not None:
         for k, v in enumerate(lr_grid):
             cfg.lr_grid[k] = float(v)

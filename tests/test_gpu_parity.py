@@ -536,3 +536,47 @@ def test_set_points_and_uneven_frames(npg):
     loss2, _ = ctx.loss()
     assert abs(loss2[0] - ref2["loss"]) <= LOSS_RTOL * ref2["loss"]
     ctx.close()
+
+
+VARIANTS = [  # (time_enc, B, conf_delta, conf_omega): the ablation's variants
+    (1, None, 0, 0), (2, (0.7, -1.3, 0.4, 2.1), 1, 3), (0, None, 2, 2), (0, None, 3, 1),
+    (1, None, 4, 0), (2, (1.1, 0.3, -0.6, 1.7), 4, 3)]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_ablation_variants_parity(npg, variant):
+    """Time encodings (polynomial, Gaussian Fourier) and stability schedules
+    (catch-up and temporal-weighting variants): loss, cd_t and confidence
+    weights at e = 3 of 10, and the parameter gradients from the same
+    dL/dx-hat (linear activation, so no ReLU kink decisions)."""
+    import torch
+    te, B, cdm, com = variant
+    seq = I.sphere_blob(subdiv=4, T=8, M=4096, noise=0.005, seed=1)
+    res = (8, 27, 45, 64)
+    ocfg = O.make_cfg(L=4, res=res, F=2, H=64, D=2, slope=1.0, time_enc=te, time_B=B,
+                      conf_delta=cdm, conf_omega=com)
+    prob = O.Problem(ocfg, seq.x, seq.n, seq.faces, seq.points, seq.offsets, seq.t_key)
+    grid, mlp = random_state(ocfg)
+    ref = O.loss_full(prob, f32(grid), f32(mlp), 3, 10, decide_f32=True)
+    cfg = npg.make_config(4, res, 2, 64, 2, slope=1.0, e_max=10, time_enc=te, time_B=B,
+                          conf_delta=cdm, conf_omega=com)
+    ctx = npg.Context(cfg, seq, mlp)
+    ctx.set(npg.BUF_GRID, grid)
+    npg.npg_set_epoch(ctx.h, 3)
+    ctx.forward()
+    loss, cd = ctx.loss()
+    np.testing.assert_allclose(cd, ref["cd"], rtol=LOSS_RTOL)
+    np.testing.assert_allclose(ctx.get(npg.BUF_WCONF), ref["w"], rtol=LOSS_RTOL)
+    for k, key in enumerate(("loss", "L_def", "L_iso")):
+        assert abs(loss[k] - ref[key]) <= LOSS_RTOL * abs(ref[key]), key
+    gx32 = ref["g_xhat"].astype(np.float32)
+    want_g, want_m = O.backprop(prob, f32(grid), f32(mlp), f32(gx32))
+    npg.npg_backprop(ctx.h, torch.from_numpy(gx32.reshape(-1)).cuda())
+    gg = ctx.get(npg.BUF_GRID_GRAD).astype(np.float64)
+    gm = ctx.get(npg.BUF_MLP_GRAD).astype(np.float64)
+    rng = np.random.default_rng(9)
+    gb, mb = blocks_of(ocfg)
+    for name, sl in gb + mb:
+        check_grad_block(name, (gg if name.startswith("grid") else gm)[sl],
+                         (want_g if name.startswith("grid") else want_m)[sl], rng)
+    ctx.close()
