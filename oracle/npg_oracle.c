@@ -53,7 +53,8 @@ typedef struct {
   int rn;                  /* nodes per axis of the normal grid              */
   int H;                   /* hidden width                                   */
   int D;                   /* number of hidden layers                        */
-  int rot_mode;            /* 0: quaternion (Eq. 5), 1: exponential map      */
+  int rot_mode;            /* 0: quaternion (Eq. 5), 1: exponential map,
+                              2: Cayley transform                            */
   int n_freq;              /* Fourier frequencies M (Eq. 3)                  */
   double slope;            /* LeakyReLU negative slope                       */
   double alpha;            /* translation squashing factor (Eq. 6)           */
@@ -245,6 +246,22 @@ static void expmap_coeffs(double th, double* A, double* B, double* dA, double* d
   }
 }
 
+/* Cayley transform (the rotation-representation ablation, Sec. 4):
+ * R = (I - K)^-1 (I + K) with K = [w]x, in closed form I + c (K + K^2),
+ * c = 2 / (1 + |w|^2); as for the exponential map, dA = dB = (dc/d|w|) / |w|. */
+static void cayley_coeffs(double th, double* A, double* B, double* dA, double* dB) {
+  const double cc = 2.0 / (1.0 + th * th);
+  *A = *B = cc;
+  *dA = *dB = -cc * cc;
+}
+
+static void rot_coeffs(int rot_mode, double th, double* A, double* B, double* dA, double* dB) {
+  if (rot_mode == 2)
+    cayley_coeffs(th, A, B, dA, dB);
+  else
+    expmap_coeffs(th, A, B, dA, dB);
+}
+
 static void skew(const double* w, double* K) {
   K[0] = 0; K[1] = -w[2]; K[2] = w[1];
   K[3] = w[2]; K[4] = 0; K[5] = -w[0];
@@ -260,10 +277,10 @@ static void matmul3(const double* A, const double* B, double* C) {
     }
 }
 
-static void expmap_R(const double* w, double* R) {
+static void expmap_R(int rot_mode, const double* w, double* R) {
   double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
   double A, B, dA, dB, K[9], K2[9];
-  expmap_coeffs(th, &A, &B, &dA, &dB);
+  rot_coeffs(rot_mode, th, &A, &B, &dA, &dB);
   skew(w, K);
   matmul3(K, K, K2);
   for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0 ? 1.0 : 0.0) + A * K[i] + B * K2[i];
@@ -282,7 +299,7 @@ void or_rotation_translation(const or_cfg* c, const double* o, double* R, double
     quat_to_R(q, R);
     for (int a = 0; a < 3; ++a) d[a] = tanh(c->alpha * o[4 + a]);
   } else {
-    expmap_R(o, R);
+    expmap_R(c->rot_mode, o, R);
     for (int a = 0; a < 3; ++a) d[a] = tanh(c->alpha * o[3 + a]);
   }
 }
@@ -329,7 +346,7 @@ static void transform_row_backward(const or_cfg* c, const double* o, const doubl
     const double* w = o;
     double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
     double A, B, dA, dB, K[9], K2[9];
-    expmap_coeffs(th, &A, &B, &dA, &dB);
+    rot_coeffs(c->rot_mode, th, &A, &B, &dA, &dB);
     skew(w, K);
     matmul3(K, K, K2);
     for (int k = 0; k < 3; ++k) {

@@ -177,10 +177,37 @@ def test_expmap_rotation_matches_scipy_and_quaternion():
             np.testing.assert_allclose(R, Rq, atol=2e-15)
 
 
+def test_cayley_rotation_matches_its_definition():
+    """Rotation ablation (Sec. 4): the Cayley transform R = (I - K)^-1 (I + K),
+    K = [w]x, here by a linear solve, against the oracle's closed form; R is
+    orthonormal with det 1, the identity at w = 0, and a rotation by
+    2 atan(|w|) about w (the Cayley transform's angle)."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(9)
+    cc = small_cfg(rot_mode=2)
+    R0, _ = O.rotation_translation(cc, np.zeros(6))
+    np.testing.assert_array_equal(R0, np.eye(3))
+    for scale in (1e-6, 0.1, 1.0, 5.0):
+        for _ in range(10):
+            w = rng.normal(size=3)
+            w *= scale / np.linalg.norm(w)
+            o = np.concatenate([w, rng.normal(size=3)])
+            R, d = O.rotation_translation(cc, o)
+            K = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+            want = np.linalg.solve(np.eye(3) - K, np.eye(3) + K)
+            np.testing.assert_allclose(R, want, atol=1e-14)
+            np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-14)
+            assert abs(np.linalg.det(R) - 1.0) < 1e-13
+            ang = 2 * np.arctan(np.linalg.norm(w))
+            rv = w / np.linalg.norm(w) * ang
+            np.testing.assert_allclose(R, Rotation.from_rotvec(rv).as_matrix(), atol=1e-13)
+            np.testing.assert_allclose(d, np.tanh(0.1 * o[3:]), atol=1e-16)
+
+
 def test_identity_at_initialisation():
     """Sec. 3.1: zero grids and a zeroed last layer give x-hat == x exactly."""
     seq = I.random_cloud_sequence(T=3)
-    for rot in (0, 1):
+    for rot in (0, 1, 2):
         cfg = small_cfg(rot_mode=rot)
         grid = np.zeros(O.grid_len(cfg))
         mlp = I.mlp_init(O.k_in(cfg), cfg.H, cfg.D, O.n_out(cfg), seed=0)
@@ -276,7 +303,7 @@ def _fd_problem(rot_mode, seed=0):
     return prob, grid, mlp
 
 
-@pytest.mark.parametrize("rot_mode", [0, 1])
+@pytest.mark.parametrize("rot_mode", [0, 1, 2])
 def test_gradient_matches_central_differences(rot_mode):
     """Hand-written reverse mode == central FD of the same loss (FP64,
     stop-grad inputs held fixed as Eq. 11-13 prescribe)."""
