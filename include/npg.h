@@ -62,6 +62,8 @@ extern "C" {
 /* rotation parameterisation of the decoder output */
 #define NPG_ROT_QUAT 0   /* Eq. 5: q = (1 + o0, o1, o2, o3) / norm, d = o4..6 */
 #define NPG_ROT_EXPMAP 1 /* exponential map: omega = o0..2, d = o3..5        */
+#define NPG_ROT_CAYLEY 2 /* Cayley transform (I - K)^-1 (I + K), K = [o0..2]x, d = o3..5
+                            (the rotation-representation ablation, Sec. 4)  */
 
 /* arithmetic of the preconditioner's DCT passes */
 #define NPG_PRECOND_FP32 0
@@ -95,7 +97,7 @@ typedef struct npg_ctx npg_ctx; /* opaque; owns all device memory it allocates *
  *                    NPG_FP32 supports H in {16, 32, 64}, NPG_BF16_MLP
  *                    H = 64 with depth 3; depth 1..8.
  *   leaky_slope      LeakyReLU negative slope (0 = ReLU).
- *   rot_mode         NPG_ROT_QUAT or NPG_ROT_EXPMAP.
+ *   rot_mode         NPG_ROT_QUAT, NPG_ROT_EXPMAP or NPG_ROT_CAYLEY.
  *   n_freq           Fourier frequencies M (Eq. 3; 1..8).
  *   alpha            translation squashing factor (Eq. 6).
  *   lr_mlp           Adam learning rate of the MLP.

@@ -380,12 +380,17 @@ static cudaError_t mlp_bwd_h(npg_ctx* c) {
 }
 
 cudaError_t launch_mlp_backward_fp32(npg_ctx* c) {
-  const bool q = c->cfg.rot_mode == NPG_ROT_QUAT;
+  const int rm = c->cfg.rot_mode;
+#define NPG_BWD_H(HH)                                                                       \
+  case HH:                                                                                  \
+    return rm == NPG_ROT_QUAT ? mlp_bwd_h<HH, 0>(c)                                         \
+                              : rm == NPG_ROT_EXPMAP ? mlp_bwd_h<HH, 1>(c) : mlp_bwd_h<HH, 2>(c);
   switch (c->md.H) {
-    case 16: return q ? mlp_bwd_h<16, 0>(c) : mlp_bwd_h<16, 1>(c);
-    case 32: return q ? mlp_bwd_h<32, 0>(c) : mlp_bwd_h<32, 1>(c);
-    case 64: return q ? mlp_bwd_h<64, 0>(c) : mlp_bwd_h<64, 1>(c);
+    NPG_BWD_H(16)
+    NPG_BWD_H(32)
+    NPG_BWD_H(64)
   }
+#undef NPG_BWD_H
   return cudaErrorInvalidValue;
 }
 

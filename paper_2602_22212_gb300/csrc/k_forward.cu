@@ -262,10 +262,16 @@ static cudaError_t decode_fp32_h(npg_ctx* c) {
 
 cudaError_t launch_decode_fp32(npg_ctx* c) {
   const int H = c->md.H;
-  const bool q = c->cfg.rot_mode == NPG_ROT_QUAT;
-  if (H == 16) return q ? decode_fp32_h<16, 0>(c) : decode_fp32_h<16, 1>(c);
-  if (H == 32) return q ? decode_fp32_h<32, 0>(c) : decode_fp32_h<32, 1>(c);
-  if (H == 64) return q ? decode_fp32_h<64, 0>(c) : decode_fp32_h<64, 1>(c);
+  const int rm = c->cfg.rot_mode;
+#define NPG_DECODE_H(HH)                                                                    \
+  if (H == HH)                                                                              \
+    return rm == NPG_ROT_QUAT     ? decode_fp32_h<HH, 0>(c)                                 \
+           : rm == NPG_ROT_EXPMAP ? decode_fp32_h<HH, 1>(c)                                 \
+                                  : decode_fp32_h<HH, 2>(c);
+  NPG_DECODE_H(16)
+  NPG_DECODE_H(32)
+  NPG_DECODE_H(64)
+#undef NPG_DECODE_H
   return cudaErrorInvalidValue;
 }
 

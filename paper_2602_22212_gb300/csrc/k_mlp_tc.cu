@@ -258,7 +258,9 @@ static TcArgs tc_args(npg_ctx* c) {
 
 cudaError_t launch_decode_bf16(npg_ctx* c) {
   const size_t smem = DecodeSmem::TOTAL + 1024;
-  auto k = c->cfg.rot_mode == NPG_ROT_QUAT ? decode_tc_kernel<0> : decode_tc_kernel<1>;
+  auto k = c->cfg.rot_mode == NPG_ROT_QUAT     ? decode_tc_kernel<0>
+           : c->cfg.rot_mode == NPG_ROT_EXPMAP ? decode_tc_kernel<1>
+                                               : decode_tc_kernel<2>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long tiles = ((long long)c->N * c->T + TC_ROWS - 1) / TC_ROWS;
@@ -743,7 +745,9 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
 
 cudaError_t launch_mlp_backward_bf16(npg_ctx* c) {
   const size_t smem = BwdSmem::TOTAL + 1024;
-  auto k = c->cfg.rot_mode == NPG_ROT_QUAT ? mlp_bwd_tc_kernel<0> : mlp_bwd_tc_kernel<1>;
+  auto k = c->cfg.rot_mode == NPG_ROT_QUAT     ? mlp_bwd_tc_kernel<0>
+           : c->cfg.rot_mode == NPG_ROT_EXPMAP ? mlp_bwd_tc_kernel<1>
+                                               : mlp_bwd_tc_kernel<2>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long tiles = (long long)((c->N + 15) / 16) * ((c->T + 7) / 8);

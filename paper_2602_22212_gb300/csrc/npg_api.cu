@@ -189,7 +189,8 @@ static int validate(const npg_config* c, char* why, size_t n) {
     return snprintf(why, n, "conf_delta=%d", c->conf_delta), 0;
   if (c->conf_omega < NPG_OMEGA_CUMULATIVE || c->conf_omega > NPG_OMEGA_SINGLE)
     return snprintf(why, n, "conf_omega=%d", c->conf_omega), 0;
-  if (c->rot_mode != NPG_ROT_QUAT && c->rot_mode != NPG_ROT_EXPMAP)
+  if (c->rot_mode != NPG_ROT_QUAT && c->rot_mode != NPG_ROT_EXPMAP &&
+      c->rot_mode != NPG_ROT_CAYLEY)
     return snprintf(why, n, "rot_mode=%d", c->rot_mode), 0;
   if (!(c->leaky_slope >= 0.f)) return snprintf(why, n, "leaky_slope must be >= 0"), 0;
   for (int l = 0; l <= c->L; ++l)

@@ -56,7 +56,25 @@ __device__ __forceinline__ void expmap_coeffs(float th, float& A, float& B, floa
   }
 }
 
-// Rotation R (row-major) and translation d from one decoder output row.
+// Cayley transform R = (I - K)^-1 (I + K) = I + c (K + K^2), c = 2 / (1 + |w|^2):
+// the same form as the exponential map with A = B = c and
+// dA = dB = (dc/d|w|) / |w| = -c^2.
+__device__ __forceinline__ void cayley_coeffs(float th, float& A, float& B, float& dA, float& dB) {
+  const float c = 2.f / (1.f + th * th);
+  A = B = c;
+  dA = dB = -c * c;
+}
+
+template <int ROT>
+__device__ __forceinline__ void rot_coeffs(float th, float& A, float& B, float& dA, float& dB) {
+  if (ROT == 2)
+    cayley_coeffs(th, A, B, dA, dB);
+  else
+    expmap_coeffs(th, A, B, dA, dB);
+}
+
+// Rotation R (row-major) and translation d from one decoder output row
+// (ROT: NPG_ROT_QUAT, NPG_ROT_EXPMAP or NPG_ROT_CAYLEY).
 template <int ROT>
 __device__ __forceinline__ void rot_trans(const float* o, float alpha, float* R, float* d) {
   if (ROT == 0) {
@@ -79,7 +97,7 @@ __device__ __forceinline__ void rot_trans(const float* o, float alpha, float* R,
     const float wx = o[0], wy = o[1], wz = o[2];
     const float th = sqrtf(wx * wx + wy * wy + wz * wz);
     float A, B, dA, dB;
-    expmap_coeffs(th, A, B, dA, dB);
+    rot_coeffs<ROT>(th, A, B, dA, dB);
     // K = [w]x, K^2 = w w^T - |w|^2 I
     const float xx = wx * wx, yy = wy * wy, zz = wz * wz, xy = wx * wy, xz = wx * wz, yz = wy * wz;
     R[0] = 1.f + B * (-(yy + zz)); R[1] = -A * wz + B * xy;       R[2] = A * wy + B * xz;
@@ -164,7 +182,7 @@ __device__ __forceinline__ void transform_backward(const float* o, float alpha, 
     const float w[3] = {o[0], o[1], o[2]};
     const float th = sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
     float A, B, dA, dB;
-    expmap_coeffs(th, A, B, dA, dB);
+    rot_coeffs<ROT>(th, A, B, dA, dB);
     float K[9] = {0.f, -w[2], w[1], w[2], 0.f, -w[0], -w[1], w[0], 0.f};
     float K2[9];
 #pragma unroll

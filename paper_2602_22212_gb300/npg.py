@@ -29,7 +29,7 @@ TIME_FOURIER, TIME_POLY, TIME_GAUSS = 0, 1, 2
 DELTA_SQRT, DELTA_CONST, DELTA_LINEAR, DELTA_EXP, DELTA_INTERP = 0, 1, 2, 3, 4
 OMEGA_CUMULATIVE, OMEGA_CONST, OMEGA_HALF, OMEGA_SINGLE = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
-ROT_QUAT, ROT_EXPMAP = 0, 1
+ROT_QUAT, ROT_EXPMAP, ROT_CAYLEY = 0, 1, 2
 FP32, BF16_MLP = 0, 1
 PRECOND_FP32, PRECOND_TC = 0, 1
 (BUF_GRID, BUF_MLP, BUF_GRID_GRAD, BUF_GRID_PC, BUF_MLP_GRAD, BUF_XHAT, BUF_NN_X, BUF_NN_P,

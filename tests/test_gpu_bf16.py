@@ -56,7 +56,7 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("rot_mode", [0, 1])
+@pytest.mark.parametrize("rot_mode", [0, 1, 2])
 def test_bf16_decode_tracks_fp32(npg, rot_mode):
     seq, ocfg, prob = setup(rot_mode)
     grid, mlp = rand_params(ocfg)
@@ -84,7 +84,7 @@ def test_bf16_identity_initialisation_exact(npg):
     ctx.close()
 
 
-@pytest.mark.parametrize("rot_mode", [0, 1])
+@pytest.mark.parametrize("rot_mode", [0, 1, 2])
 def test_bf16_backprop_vs_oracle(npg, rot_mode):
     import torch
     seq, ocfg, prob = setup(rot_mode)

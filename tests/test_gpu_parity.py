@@ -221,7 +221,7 @@ def ambiguous_rows(prob, ref, nnx, nnp, margin=2e-5):
     return bad
 
 
-@pytest.mark.parametrize("rot_mode", [0, 1])
+@pytest.mark.parametrize("rot_mode", [0, 1, 2])
 def test_forward_and_loss_parity(npg, rot_mode):
     seq, ocfg, prob = tiny_setup(rot_mode=rot_mode, seed=1)
     grid, mlp = random_state(ocfg)
@@ -353,7 +353,7 @@ def test_backprop_parity(npg, rot_mode, precond):
     ctx.close()
 
 
-@pytest.mark.parametrize("rot_mode", [0, 1])
+@pytest.mark.parametrize("rot_mode", [0, 1, 2])
 @pytest.mark.parametrize("w_iso", [100.0, 0.0])
 def test_backprop_parity_without_activation_kinks(npg, rot_mode, w_iso):
     """With slope 1 the activation has no kink, so the reverse pass is a smooth
