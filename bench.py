@@ -479,26 +479,38 @@ def main():
     # search work: 8 FLOP per candidate pair (3 sub, 1 mul, 2 fma, compare)
     work["nn_x"] = ("alu", 8 * search["cand_per_query_x"] * N * T, "FLOP")
     work["nn_p"] = ("alu", 8 * search["cand_per_query_p"] * MT, "FLOP")
-    dom = max((s for s in stages if s in work), key=lambda s: stages[s])
-    kind, amount, u = work[dom][:3]
-    dur = stages[dom] * 1e-3
-    if kind == "hbm":
-        ach = amount / dur / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm"], "unit": "GB/s",
-                "frac": ach / peaks["hbm"], "traffic": None,
-                "peak_source": f"{peaks['src']} copy bandwidth"}
-    elif kind == "tensor":
+    def roofline(stage):
+        kind, amount, _ = work[stage][:3]
+        dur = stages[stage] * 1e-3
+        if kind == "hbm":
+            ach = amount / dur / 1e9
+            return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm"], "traffic": None,
+                    "peak_source": f"{peaks['src']} copy bandwidth"}
+        if kind == "tensor":
+            ach = amount / dur / 1e12
+            return {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_sus"],
+                    "unit": "TFLOP/s", "frac": ach / peaks["bf16_sus"], "traffic": None,
+                    "peak_source": f"{peaks['src']} BF16 dense, sustained"}
         ach = amount / dur / 1e12
-        roof = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_sus"], "unit": "TFLOP/s",
-                "frac": ach / peaks["bf16_sus"], "traffic": None,
-                "peak_source": f"{peaks['src']} BF16 dense, sustained"}
-    else:
-        ach = amount / dur / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP32_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+        return {"bound": "alu", "achieved": ach, "peak": FP32_TFLOPS_NOMINAL, "unit": "TFLOP/s",
                 "frac": ach / FP32_TFLOPS_NOMINAL, "traffic": None,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
-    roof["kernel"] = dom
+
+    # the dominant kernel: the longest stage that is one kernel launch (the
+    # preconditioner stage is 6 passes x levels plus Adam on concurrent lanes,
+    # the search stages two kernels per direction); every stage's position is
+    # listed in stage_rooflines
+    kernels = {"mlp_bwd": "mlp_bwd_tc_kernel" if args.precision == "bf16" else "mlp_bwd_fp32_kernel",
+               "decode": "decode_tc_kernel" if args.precision == "bf16" else "decode_fp32_kernel",
+               "encode": "encode_kernel", "scatter": "scatter_kernel"}
+    dom = max(kernels, key=lambda s: stages.get(s, 0.0))
+    roof = roofline(dom)
+    roof["kernel"] = kernels[dom]
     roof["ms_per_launch"] = stages[dom]
+    stage_roofs = {s: {k: v for k, v in roofline(s).items() if k in ("bound", "achieved", "unit",
+                                                                    "frac")}
+                   for s in stages if s in work and stages[s] > 0}
 
     # the plain FP32 per-sequence form on the same sequence, for the ratio the
     # metric names (eager, FP32 preconditioner, from the same initial state)
@@ -550,6 +562,7 @@ def main():
                     "d2h_bytes_per_step": 24},
             "gpu_launches": int(launches),
             "roofline": roof,
+            "stage_rooflines": stage_roofs,
             "stages_ms": {k: round(v, 4) for k, v in stages.items()},
             "search": {k: round(v, 2) for k, v in search.items()},
             "plain_fp32": plain,
