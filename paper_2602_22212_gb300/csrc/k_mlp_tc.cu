@@ -284,17 +284,21 @@ cudaError_t launch_decode_bf16(npg_ctx* c) {
 // lanes 32 (w % 4) .. + 31 (its tile rows) and the 16-column quarter
 // c = w / 4 of every 64-wide activation, so each thread converts, masks and
 // stores 16 values per layer. Per-row scalar work is spread over the
-// quarters: c = 0 forms dL/do, c = 1 writes the y row. The next tile's inputs
+// quarters and overlapped in one phase: while c = 0 forms dL/do, c = 1 writes
+// the y row and c >= 2 sums and adds the previous tile's dL/dz partials. The
+// output-bias gradient stays in per-thread FP32 registers until the CTA ends.
+// The next tile's inputs
 // (U, V, z, x, dL/dx-hat rows) are copied into a second shared staging
 // buffer with cp.async while the current tile computes, and its h1 is written
 // while the last weight-gradient MMA of the current tile runs.
 struct BwdStage {  // inputs of one tile, FP32
-  static constexpr uint32_t U = 0;            // [16 vertices][64]
-  static constexpr uint32_t V = 4096;         // [8 frames][64]
-  static constexpr uint32_t X = 6144;         // [16] float4 x_i
-  static constexpr uint32_t G = 6400;         // [8][16] float4 dL/dx-hat
-  static constexpr uint32_t Z = 8448;         // [16][Z] z_i (Z <= 8)
-  static constexpr uint32_t BYTES = 9216;
+  static constexpr uint32_t U_PITCH = 272;    // 256 B + 16: the 16 vertex rows hit distinct banks
+  static constexpr uint32_t U = 0;            // [16 vertices][64], rows U_PITCH apart
+  static constexpr uint32_t V = 4352;         // [8 frames][64]
+  static constexpr uint32_t X = 6400;         // [16] float4 x_i
+  static constexpr uint32_t G = 6656;         // [8][16] float4 dL/dx-hat
+  static constexpr uint32_t Z = 8704;         // [16][Z] z_i (Z <= 8)
+  static constexpr uint32_t BYTES = 9216 + 256;
 };
 struct BwdSmem {
   // B operands of the forward and dh MMAs (K-major)
@@ -303,10 +307,10 @@ struct BwdSmem {
   // [h2 | h1 | y | h3] then [gO | dpre3 | dpre2], 16 KB tiles
   static constexpr uint32_t H2 = 43008, H1 = H2 + TC_TILE, Y = H1 + TC_TILE, H3 = Y + TC_TILE;
   static constexpr uint32_t GO = H3 + TC_TILE, DP3 = GO + TC_TILE, DP2 = DP3 + TC_TILE;
-  static constexpr uint32_t W1F = DP2 + TC_TILE;                // FP32 W1 (64 x K <= 64 x 15)
-  static constexpr uint32_t BIAS = W1F + 64 * 16 * 4;           // b2, b3, bo FP32
-  static constexpr uint32_t DZP = BIAS + (64 + 64 + 16) * 4;    // FP32 [4][8][128 rows]
-  static constexpr uint32_t STG = DZP + 128 * 4 * 8 * 4;        // 2 x BwdStage
+  static constexpr uint32_t BIAS = DP2 + TC_TILE;               // b2, b3, bo FP32
+  static constexpr uint32_t W1Z = BIAS + (64 + 64 + 16) * 4;    // FP32 [8][64]: W1[:, :Z]^T
+  static constexpr uint32_t DZP = W1Z + 8 * 64 * 4;             // FP32 [4 c][8 qz][64]
+  static constexpr uint32_t STG = DZP + 4 * 8 * 64 * 4;         // 2 x BwdStage
   static constexpr uint32_t DBO = STG + 2 * BwdStage::BYTES;    // FP32 [8] output-bias gradient
   static constexpr uint32_t BAR = DBO + 8 * 4;  // MMA completion, final drain
   static constexpr uint32_t TMEMP = BAR + 16;
@@ -383,8 +387,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Issue the copies of one tile's inputs into a staging buffer (one commit group).
-__device__ void bwd_stage(const TcArgs& a, long long tile, int n_tb, uint8_t* stg) {
-  const int i0 = (int)(tile / n_tb) * 16, t0 = (int)(tile % n_tb) * 8;
+__device__ void bwd_stage(const TcArgs& a, int i0, int t0, uint8_t* stg) {
   const uint32_t zbytes = 16u * (uint32_t)a.Z * 4u;
   const long long zend = (long long)a.N * a.Z * 4;  // bytes of the whole z array
   for (int e = threadIdx.x; e < 256 + 128 + 16 + 128 + 32; e += BWD_THREADS) {
@@ -393,7 +396,7 @@ __device__ void bwd_stage(const TcArgs& a, long long tile, int n_tb, uint8_t* st
     uint32_t n = 16u;
     if (e < 256) {
       const int v = e >> 4, ch = e & 15, i = i0 + v;
-      dst = stg + BwdStage::U + v * 256 + ch * 16;
+      dst = stg + BwdStage::U + v * BwdStage::U_PITCH + ch * 16;
       if (i < a.N) src = a.U + (long long)i * TC_H + ch * 4; else n = 0u;
     } else if (e < 384) {
       const int f = (e - 256) >> 4, ch = (e - 256) & 15, t = t0 + f;
@@ -432,8 +435,8 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + BwdSmem::BAR);
   uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + BwdSmem::TMEMP);
   float* bias = reinterpret_cast<float*>(sm + BwdSmem::BIAS);
-  float* w1f = reinterpret_cast<float*>(sm + BwdSmem::W1F);
   float* dzp = reinterpret_cast<float*>(sm + BwdSmem::DZP);
+  float* w1z = reinterpret_cast<float*>(sm + BwdSmem::W1Z);
   float* dbo = reinterpret_cast<float*>(sm + BwdSmem::DBO);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q4 = warp & 3, c = warp >> 2;  // lane quarter, column quarter
@@ -460,7 +463,10 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
       *reinterpret_cast<uint4*>(sm + (e < TC_TILE / 16 ? BwdSmem::GO : BwdSmem::Y) + off) = zero;
     }
   }
-  for (int e = tid; e < 64 * K; e += BWD_THREADS) w1f[e] = a.mlp[e];
+  for (int e = tid; e < 8 * 64; e += BWD_THREADS) {
+    const int qz = e >> 6, m = e & 63;
+    w1z[e] = qz < Z ? a.mlp[m * K + qz] : 0.f;
+  }
   for (int k = tid; k < 64; k += BWD_THREADS) {
     bias[k] = p2[H * H + k];
     bias[64 + k] = p3[H * H + k];
@@ -475,10 +481,17 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
     tc::tmem_alloc(tmem_ptr, 512);
     tc::tmem_relinquish();
   }
-  const int n_ib = (a.N + 15) / 16, n_tb = (a.T + 7) / 8;
-  const long long ntiles = (long long)n_ib * n_tb;
-  long long tile = blockIdx.x;
-  if (tile < ntiles) bwd_stage(a, tile, n_tb, sm + BwdSmem::STG);
+  // tile = ib n_tb + tb covers vertices 16 ib.. and frames 8 tb.. (the host
+  // checks that the tile count fits an int)
+  const int n_tb = (a.T + 7) / 8;
+  const int ntiles = ((a.N + 15) / 16) * n_tb;
+  int tile = blockIdx.x;
+  int i0 = 0, t0 = 0;  // first vertex and frame of `tile`
+  if (tile < ntiles) {
+    i0 = tile / n_tb * 16;
+    t0 = (tile - i0 / 16 * n_tb) * 8;
+    bwd_stage(a, i0, t0, sm + BwdSmem::STG);
+  }
   cp_async_wait_all();
   __syncthreads();  // zeroed y before its column 15 is set
   if (c == 1) st_bf16(sm + BwdSmem::Y, row, 15, 1.f);
@@ -497,7 +510,8 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
 
   // h1 of the tile staged in `stg`: act' mask and the H1 store
   auto put_h1 = [&](const uint8_t* stg, bool valid) {
-    const float4* u4 = reinterpret_cast<const float4*>(stg + BwdStage::U + il * 256 + 64 * c);
+    const float4* u4 =
+        reinterpret_cast<const float4*>(stg + BwdStage::U + il * BwdStage::U_PITCH + 64 * c);
     const float4* v4 = reinterpret_cast<const float4*>(stg + BwdStage::V + tl * 256 + 64 * c);
     float v[16];
 #pragma unroll
@@ -514,32 +528,41 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
     st_row16(sm + BwdSmem::H1, row, 16 * c, v);
     return m;
   };
-  auto tile_valid = [&](long long tl_) {
-    const int i = (int)(tl_ / n_tb) * 16 + il, t = (int)(tl_ % n_tb) * 8 + tl;
-    return i < a.N && t < a.T;
-  };
+  auto row_valid = [&](int i0_, int t0_) { return i0_ + il < a.N && t0_ + tl < a.T; };
 
   uint32_t m1 = 0u;
   int buf = 0;
-  if (tile < ntiles) m1 = put_h1(sm + BwdSmem::STG, tile_valid(tile));
+  int dz_i0 = -1;  // first vertex of the tile whose dL/dz partials wait in dzp
+  float dbo_acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  // dL/dz of the tile whose partials are in dzp: sum over its 8 frames (two
+  // per warp, pre-summed) and the 4 column quarters, one global add per value
+  auto flush_dz = [&](int e0, int stride) {
+    for (int e = e0; e < 16 * Z; e += stride) {
+      const int vi = e & 15, qz = e >> 4;
+      if (dz_i0 + vi >= a.N) continue;
+      float s = 0.f;
+#pragma unroll
+      for (int cq = 0; cq < 4; ++cq)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s += dzp[(cq * 8 + qz) * 64 + q * 16 + vi];
+      atomicAdd(a.dz + (long long)(dz_i0 + vi) * Z + qz, s);
+    }
+  };
+  if (tile < ntiles) m1 = put_h1(sm + BwdSmem::STG, row_valid(i0, t0));
   // `ok` leaves the loop only through tc_sync_ok, so every thread breaks at
   // the same barrier
   for (; tile < ntiles; tile += gridDim.x) {
-    const long long next = tile + gridDim.x;
-    uint8_t* stg = sm + BwdSmem::STG + buf * BwdStage::BYTES;
-    const int t = (int)(tile % n_tb) * 8 + tl;
-    const bool valid = tile_valid(tile);
-    // the next tile's inputs copy while this tile computes
-    if (next < ntiles) bwd_stage(a, next, n_tb, sm + BwdSmem::STG + (buf ^ 1) * BwdStage::BYTES);
-    // y row (quarter 1): z_i, gamma_t in columns 0..Z+2M-1
-    if (c == 1) {
-      const float* zs = reinterpret_cast<const float*>(stg + BwdStage::Z) + il * Z;
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (k < Z) st_bf16(sm + BwdSmem::Y, row, k, valid ? zs[k] : 0.f);
-      const float* gt = a.gamma + (long long)(valid ? t : 0) * 2 * M;
-      for (int k = 0; k < 2 * M; ++k) st_bf16(sm + BwdSmem::Y, row, Z + k, gt[k]);
+    const int next = tile + (int)gridDim.x;
+    int ni0 = 0, nt0 = 0;
+    if (next < ntiles) {
+      ni0 = next / n_tb * 16;
+      nt0 = (next - ni0 / 16 * n_tb) * 8;
     }
+    uint8_t* stg = sm + BwdSmem::STG + buf * BwdStage::BYTES;
+    const int t = t0 + tl;
+    const bool valid = row_valid(i0, t0);
+    // the next tile's inputs copy while this tile computes
+    if (next < ntiles) bwd_stage(a, ni0, nt0, sm + BwdSmem::STG + (buf ^ 1) * BwdStage::BYTES);
     // ---- forward: layer 2
     if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
@@ -599,18 +622,25 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
       // output-bias gradient: summed in FP32 (rows cancel strongly; a BF16
       // rounding of each row's dL/do would dominate the sum)
 #pragma unroll
-      for (int j = 0; j < 7; ++j) {
-        float sj = go[j];
-#pragma unroll
-        for (int o2 = 16; o2 > 0; o2 >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o2);
-        if (lane == 0 && j < NO) atomicAdd(dbo + j, sj);
-      }
+      for (int j = 0; j < 7; ++j) dbo_acc[j] += go[j];
       uint4 q0;
       q0.x = tc::pack_bf16(go[0], go[1]);
       q0.y = tc::pack_bf16(go[2], go[3]);
       q0.z = tc::pack_bf16(go[4], go[5]);
       q0.w = tc::pack_bf16(NO > 6 ? go[6] : 0.f, 0.f);
       *reinterpret_cast<uint4*>(sm + BwdSmem::GO + tc::sw128_off(row, 0)) = q0;
+    } else if (c == 1) {
+      // y row: z_i, gamma_t in columns 0..K-1, zeros, 1 in column 15 (first
+      // read by the ACC_W MMA, after the dh2 step)
+      const float* zs = reinterpret_cast<const float*>(stg + BwdStage::Z) + il * Z;
+      const float* gt = a.gamma + (long long)(valid ? t : 0) * 2 * M;
+      float y[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        y[k] = k == 15 ? 1.f : k < Z ? (valid ? zs[k] : 0.f) : k < K ? gt[k - Z] : 0.f;
+      st_row16(sm + BwdSmem::Y, row, 0, y);
+    } else if (dz_i0 >= 0) {
+      flush_dz(tid - 256, 256);
     }
     // ---- backward: dh3 = gO Wo (K = 16)
     if (!(ok = tc_sync_ok(ok, a.err))) break;
@@ -655,12 +685,25 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
 #pragma unroll
       for (int k = 0; k < 16; ++k) v[k] *= ((m1 >> k) & 1u) ? 1.f : a.slope;
       st_row16(sm + BwdSmem::DP3, row, 16 * c, v);  // dpre1 (ACC_W has consumed dpre3)
-      // dL/dz partial over this quarter's 16 hidden units, FP32
-      for (int qz = 0; qz < Z; ++qz) {
-        float s = 0.f;
+      // dL/dz partial over this quarter's 16 hidden units, FP32, summed with
+      // lane ^ 16 (the same vertex, the other frame of the warp's two)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) s = fmaf(w1f[(16 * c + j) * K + qz], v[j], s);
-        dzp[(c * 8 + qz) * 128 + row] = valid ? s : 0.f;
+      for (int qz = 0; qz < 8; ++qz) {
+        if (qz < Z) {
+          const float4* w4 = reinterpret_cast<const float4*>(w1z + qz * 64 + 16 * c);
+          float s = 0.f;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float4 w = w4[j];
+            s = fmaf(w.x, v[4 * j + 0], s);
+            s = fmaf(w.y, v[4 * j + 1], s);
+            s = fmaf(w.z, v[4 * j + 2], s);
+            s = fmaf(w.w, v[4 * j + 3], s);
+          }
+          s = valid ? s : 0.f;
+          s += __shfl_xor_sync(0xffffffffu, s, 16);
+          if (lane < 16) dzp[(c * 8 + qz) * 64 + q4 * 16 + lane] = s;
+        }
       }
     }
     // the next tile's staged inputs must have landed before the barrier
@@ -672,25 +715,26 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
       tc::mma_commit(bar);
     }
     first = false;
-    // dL/dz of the tile's 16 vertices: sum over its 8 frames and 4 quarters
-    {
-      const int i0 = (int)(tile / n_tb) * 16;
-      for (int e = tid; e < 16 * Z; e += BWD_THREADS) {
-        const int vi = e & 15, qz = e >> 4;
-        if (i0 + vi >= a.N) continue;
-        float s = 0.f;
-#pragma unroll
-        for (int tt = 0; tt < 8; ++tt)
-#pragma unroll
-          for (int cq = 0; cq < 4; ++cq) s += dzp[(cq * 8 + qz) * 128 + tt * 16 + vi];
-        atomicAdd(a.dz + (long long)(i0 + vi) * Z + qz, s);
-      }
-    }
+    dz_i0 = i0;
     // the next tile's h1 goes to H1, which ACC_X does not read
     buf ^= 1;
-    if (next < ntiles) m1 = put_h1(sm + BwdSmem::STG + buf * BwdStage::BYTES, tile_valid(next));
+    if (next < ntiles) m1 = put_h1(sm + BwdSmem::STG + buf * BwdStage::BYTES, row_valid(ni0, nt0));
+    i0 = ni0;
+    t0 = nt0;
     // ACC_X reads y, h3, gO and dpre1: wait before the next tile writes them
     tc_wait(bar, phase, ok);
+  }
+  // the last tile's dL/dz partials; the output-bias gradient of quarter 0
+  ok = tc_sync_ok(ok, a.err);
+  if (ok && dz_i0 >= 0) flush_dz(tid, BWD_THREADS);
+  if (c == 0) {
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      float sj = dbo_acc[j];
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o2);
+      if (lane == 0 && j < NO) atomicAdd(dbo + j, sj);
+    }
   }
   // ---- accumulators -> global gradient (parameter layout), once per CTA
   ok = tc_sync_ok(ok, a.err);
@@ -751,6 +795,7 @@ cudaError_t launch_mlp_backward_bf16(npg_ctx* c) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long tiles = (long long)((c->N + 15) / 16) * ((c->T + 7) / 8);
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;  // tile indices are ints
   k<<<tc_blocks(c, tiles, 1), BWD_THREADS, smem, c->stream>>>(tc_args(c));
   return cudaGetLastError();
 }

@@ -156,9 +156,9 @@ __device__ __forceinline__ void transform_backward(const float* o, float alpha, 
     const float qw = 1.f + o[0], qx = o[1], qy = o[2], qz = o[3];
     const float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
     if (n2 > 0.f) {
-      const float nq = __fsqrt_rn(n2), inv = __fdiv_rn(1.f, nq);
-      const float w = __fdiv_rn(qw, nq), X = __fdiv_rn(qx, nq), Y = __fdiv_rn(qy, nq),
-                  Z = __fdiv_rn(qz, nq);
+      // a gradient, not a decision: one reciprocal square root suffices
+      const float inv = rsqrtf(n2);
+      const float w = qw * inv, X = qx * inv, Y = qy * inv, Z = qz * inv;
       float gq0 = 2.f * (-Z * G[1] + Y * G[2] + Z * G[3] - X * G[5] - Y * G[6] + X * G[7]);
       float gq1 = 2.f * (Y * G[1] + Z * G[2] + Y * G[3] - 2.f * X * G[4] - w * G[5] + Z * G[6] +
                          w * G[7] - 2.f * X * G[8]);
