@@ -129,7 +129,9 @@ typedef struct npg_ctx npg_ctx; /* opaque; owns all device memory it allocates *
  *                    (_SINGLE).
  *   stream           cudaStream_t for all device work.
  *   alloc/free/user  optional device allocator (e.g. PyTorch's caching
- *                    allocator); NULL = cudaMalloc / cudaFree.
+ *                    allocator); NULL = cudaMalloc / cudaFree. Blocks must be
+ *                    16-byte aligned (a misaligned block fails with
+ *                    NPG_ENOMEM).
  */
 typedef struct npg_config {
   int L;

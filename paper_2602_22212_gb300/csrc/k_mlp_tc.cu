@@ -278,7 +278,7 @@ cudaError_t launch_decode_bf16(npg_ctx* c) {
 //     ACC_X += [gO | dpre1]^T [y | h3]           (M 128, N 128)
 //   where y = (z_i, gamma_t, 0.., 1 at column 15): the diagonal blocks are
 //   dW3, dW2 and dW_out, dW1, the column of ones gives the bias gradients.
-//   dL/dz_i = W1[:, :Z]^T dpre1 in FP32, summed over the tile's frames.
+//   dL/dz rows = dpre1 W1[:, :Z] (an N = 16 MMA), summed over the tile's frames.
 //
 // A CTA of 512 threads (16 warps) owns one tile at a time: warp w serves TMEM
 // lanes 32 (w % 4) .. + 31 (its tile rows) and the 16-column quarter
@@ -287,10 +287,10 @@ cudaError_t launch_decode_bf16(npg_ctx* c) {
 // quarters and overlapped in one phase: while c = 0 forms dL/do, c = 1 writes
 // the y row and c >= 2 sums and adds the previous tile's dL/dz partials. The
 // output-bias gradient stays in per-thread FP32 registers until the CTA ends.
-// The next tile's inputs
-// (U, V, z, x, dL/dx-hat rows) are copied into a second shared staging
-// buffer with cp.async while the current tile computes, and its h1 is written
-// while the last weight-gradient MMA of the current tile runs.
+// One warp issues the bulk copies of the next tile's inputs (U, V, x, dL/dx-hat,
+// z and gamma rows) into a second shared staging buffer while the current
+// tile computes; the next tile's h1 is written while the current tile's last
+// weight-gradient MMA runs, which the next tile's first MMA commit covers.
 struct BwdStage {  // inputs of one tile, FP32
   static constexpr uint32_t U_PITCH = 272;    // 256 B + 16: the 16 vertex rows hit distinct banks
   static constexpr uint32_t U = 0;            // [16 vertices][64], rows U_PITCH apart
@@ -298,7 +298,8 @@ struct BwdStage {  // inputs of one tile, FP32
   static constexpr uint32_t X = 6400;         // [16] float4 x_i
   static constexpr uint32_t G = 6656;         // [8][16] float4 dL/dx-hat
   static constexpr uint32_t Z = 8704;         // [16][Z] z_i (Z <= 8)
-  static constexpr uint32_t BYTES = 9216 + 256;
+  static constexpr uint32_t GAM = 9216;       // [8 frames][2M] gamma_t (2M <= 16)
+  static constexpr uint32_t BYTES = 9728;
 };
 struct BwdSmem {
   // B operands of the forward and dh MMAs (K-major)
@@ -307,16 +308,17 @@ struct BwdSmem {
   // [h2 | h1 | y | h3] then [gO | dpre3 | dpre2], 16 KB tiles
   static constexpr uint32_t H2 = 43008, H1 = H2 + TC_TILE, Y = H1 + TC_TILE, H3 = Y + TC_TILE;
   static constexpr uint32_t GO = H3 + TC_TILE, DP3 = GO + TC_TILE, DP2 = DP3 + TC_TILE;
-  static constexpr uint32_t BIAS = DP2 + TC_TILE;               // b2, b3, bo FP32
-  static constexpr uint32_t W1Z = BIAS + (64 + 64 + 16) * 4;    // FP32 [8][64]: W1[:, :Z]^T
-  static constexpr uint32_t DZP = W1Z + 8 * 64 * 4;             // FP32 [4 c][8 qz][64]
-  static constexpr uint32_t STG = DZP + 4 * 8 * 64 * 4;         // 2 x BwdStage
+  static constexpr uint32_t W1Z = DP2 + TC_TILE;  // BF16 K-major [16][64]: W1[:, :Z]^T, rows >= Z zero
+  static constexpr uint32_t BIAS = W1Z + 2048;                  // b2, b3, bo FP32
+  static constexpr uint32_t DZP = BIAS + (64 + 64 + 16) * 4;    // FP32 [8 qz][4 q4][16 vertices]
+  static constexpr uint32_t STG = DZP + 8 * 64 * 4;             // 2 x BwdStage
   static constexpr uint32_t DBO = STG + 2 * BwdStage::BYTES;    // FP32 [8] output-bias gradient
-  static constexpr uint32_t BAR = DBO + 8 * 4;  // MMA completion, final drain
-  static constexpr uint32_t TMEMP = BAR + 16;
+  // mbarriers: chain MMAs, final drain, dL/dz MMA, staging buffer 0 and 1
+  static constexpr uint32_t BAR = DBO + 8 * 4;
+  static constexpr uint32_t TMEMP = BAR + 5 * 8;
   static constexpr uint32_t TOTAL = TMEMP + 8;
 };
-constexpr uint32_t ACC_W_COL = 0, ACC_X_COL = 256, WORK_COL = 384;
+constexpr uint32_t ACC_W_COL = 0, ACC_X_COL = 256, WORK_COL = 384, DZ_COL = 448;
 constexpr int BWD_THREADS = 512;
 
 bool backward_bf16_supported(int K, int Z) { return K <= 15 && Z <= 8; }
@@ -373,59 +375,52 @@ __device__ __forceinline__ void mma_rows(uint32_t d, uint32_t a_smem, uint32_t b
                  (first && ks == 0) ? 0u : 1u);
 }
 
-// 16-byte global -> shared copy; src_bytes < 16 zero-fills the rest (0: no read).
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(dst)),
-               "l"(src), "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
-
-// Issue the copies of one tile's inputs into a staging buffer (one commit group).
-__device__ void bwd_stage(const TcArgs& a, int i0, int t0, uint8_t* stg) {
-  const uint32_t zbytes = 16u * (uint32_t)a.Z * 4u;
-  const long long zend = (long long)a.N * a.Z * 4;  // bytes of the whole z array
-  for (int e = threadIdx.x; e < 256 + 128 + 16 + 128 + 32; e += BWD_THREADS) {
-    const void* src = a.U;
-    uint8_t* dst;
-    uint32_t n = 16u;
-    if (e < 256) {
-      const int v = e >> 4, ch = e & 15, i = i0 + v;
-      dst = stg + BwdStage::U + v * BwdStage::U_PITCH + ch * 16;
-      if (i < a.N) src = a.U + (long long)i * TC_H + ch * 4; else n = 0u;
-    } else if (e < 384) {
-      const int f = (e - 256) >> 4, ch = (e - 256) & 15, t = t0 + f;
-      dst = stg + BwdStage::V + f * 256 + ch * 16;
-      if (t < a.T) src = a.V + (long long)t * TC_H + ch * 4; else n = 0u;
-    } else if (e < 400) {
-      const int v = e - 384, i = i0 + v;
-      dst = stg + BwdStage::X + v * 16;
-      if (i < a.N) src = a.xr + i; else n = 0u;
-    } else if (e < 528) {
-      const int f = (e - 400) >> 4, v = (e - 400) & 15, i = i0 + v, t = t0 + f;
-      dst = stg + BwdStage::G + (f * 16 + v) * 16;
-      if (i < a.N && t < a.T) src = a.dxhat + (long long)t * a.N + i; else n = 0u;
-    } else {
-      const uint32_t off = (uint32_t)(e - 528) * 16u;
-      if (off >= zbytes) continue;
-      dst = stg + BwdStage::Z + off;
-      const long long g = (long long)i0 * a.Z * 4 + off;  // byte offset in z
-      const long long left = zend - g;
-      if (left > 0) {
-        src = reinterpret_cast<const uint8_t*>(a.z) + g;
-        n = left < 16 ? (uint32_t)left : 16u;
-      } else {
-        n = 0u;
-      }
-    }
-    cp_async16(dst, src, n);
+// Issue the bulk copies of one tile's inputs into a staging buffer. The 28
+// pieces (16 U rows, 8 dL/dx-hat frame rows, V, x, z, gamma) are spread over
+// STAGE_WARPS warps, lane l of part p taking piece p + STAGE_WARPS l; each
+// warp announces its own bytes on *sbar (initialised with one arrival per
+// warp). Vertices past N and frames past T are not copied: their staging rows
+// keep stale (or never written) values, which every reader replaces by zero
+// through a select. The z and gamma copies round up to 16 B; those arrays
+// carry 16 B of padding.
+constexpr int STAGE_WARPS = 4, STAGE_PIECES = 28;
+__device__ void bwd_stage(const TcArgs& a, int i0, int t0, uint8_t* stg, uint64_t* sbar,
+                          int part, int lane) {
+  const int nv = min(16, a.N - i0), nf = min(8, a.T - t0);
+  const uint32_t zb = ((uint32_t)(nv * a.Z * 4) + 15u) & ~15u;
+  const uint32_t gb = ((uint32_t)(nf * 2 * a.M * 4) + 15u) & ~15u;
+  // bytes of piece k (0: not copied)
+  auto piece_bytes = [&](int k) -> uint32_t {
+    if (k < 16) return k < nv ? 256u : 0u;
+    if (k < 24) return k - 16 < nf ? (uint32_t)nv * 16u : 0u;
+    if (k == 24) return (uint32_t)nf * 256u;
+    if (k == 25) return (uint32_t)nv * 16u;
+    return k == 26 ? zb : gb;
+  };
+  if (lane == 0) {
+    uint32_t total = 0u;
+    for (int k = part; k < STAGE_PIECES; k += STAGE_WARPS) total += piece_bytes(k);
+    tc::mbar_arrive_expect_tx(sbar, total);
   }
-  cp_async_commit();
+  __syncwarp();
+  const int k = part + STAGE_WARPS * lane;
+  if (k >= STAGE_PIECES) return;
+  const uint32_t n = piece_bytes(k);
+  if (n == 0u) return;
+  if (k < 16)
+    tc::bulk_g2s(stg + BwdStage::U + k * BwdStage::U_PITCH, a.U + (long long)(i0 + k) * TC_H, n,
+                 sbar);
+  else if (k < 24)
+    tc::bulk_g2s(stg + BwdStage::G + (k - 16) * 256, a.dxhat + (long long)(t0 + k - 16) * a.N + i0,
+                 n, sbar);
+  else if (k == 24)
+    tc::bulk_g2s(stg + BwdStage::V, a.V + (long long)t0 * TC_H, n, sbar);
+  else if (k == 25)
+    tc::bulk_g2s(stg + BwdStage::X, a.xr + i0, n, sbar);
+  else if (k == 26)
+    tc::bulk_g2s(stg + BwdStage::Z, a.z + (long long)i0 * a.Z, n, sbar);
+  else
+    tc::bulk_g2s(stg + BwdStage::GAM, a.gamma + (long long)t0 * 2 * a.M, n, sbar);
 }
 
 template <int ROT>
@@ -436,12 +431,12 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
   uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + BwdSmem::TMEMP);
   float* bias = reinterpret_cast<float*>(sm + BwdSmem::BIAS);
   float* dzp = reinterpret_cast<float*>(sm + BwdSmem::DZP);
-  float* w1z = reinterpret_cast<float*>(sm + BwdSmem::W1Z);
   float* dbo = reinterpret_cast<float*>(sm + BwdSmem::DBO);
+  uint64_t* sbar = bar + 3;  // staging buffers
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q4 = warp & 3, c = warp >> 2;  // lane quarter, column quarter
   const int row = 32 * q4 + lane, il = row & 15, tl = row >> 4;
-  const int H = TC_H, K = a.K, Z = a.Z, M = a.M, NO = a.NO;
+  const int H = TC_H, K = a.K, Z = a.Z, NO = a.NO;
   if (tid < 8) dbo[tid] = 0.f;
 
   const float* p2 = a.mlp + H * K + H;
@@ -463,9 +458,9 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
       *reinterpret_cast<uint4*>(sm + (e < TC_TILE / 16 ? BwdSmem::GO : BwdSmem::Y) + off) = zero;
     }
   }
-  for (int e = tid; e < 8 * 64; e += BWD_THREADS) {
+  for (int e = tid; e < 16 * 64; e += BWD_THREADS) {
     const int qz = e >> 6, m = e & 63;
-    w1z[e] = qz < Z ? a.mlp[m * K + qz] : 0.f;
+    st_bf16(sm + BwdSmem::W1Z, qz, m, qz < Z ? a.mlp[m * K + qz] : 0.f);
   }
   for (int k = tid; k < 64; k += BWD_THREADS) {
     bias[k] = p2[H * H + k];
@@ -473,8 +468,8 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
   }
   if (tid < 16) bias[128 + tid] = tid < NO ? po[NO * H + tid] : 0.f;
   if (tid == 0) {
-    tc::mbar_init(bar, 1);
-    tc::mbar_init(bar + 1, 1);
+    for (int b = 0; b < 3; ++b) tc::mbar_init(bar + b, 1);
+    for (int b = 3; b < 5; ++b) tc::mbar_init(bar + b, STAGE_WARPS);
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -490,12 +485,26 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
   if (tile < ntiles) {
     i0 = tile / n_tb * 16;
     t0 = (tile - i0 / 16 * n_tb) * 8;
-    bwd_stage(a, i0, t0, sm + BwdSmem::STG);
   }
-  cp_async_wait_all();
-  __syncthreads();  // zeroed y before its column 15 is set
+  __syncthreads();  // zeroed y before its column 15 is set; barriers initialised
   if (c == 1) st_bf16(sm + BwdSmem::Y, row, 15, 1.f);
   bool ok = tc_sync_ok(true, a.err);
+  // staging: warps 16 - STAGE_WARPS .. 15 issue a tile's copies, every thread
+  // waits on the buffer's barrier before its first read (parity and in-flight
+  // bit per buffer)
+  uint32_t sphase = 0u, pending = 0u;
+  auto stage_issue = [&](int b, int i0_, int t0_) {
+    const int part = warp - (16 - STAGE_WARPS);
+    if (part >= 0)
+      bwd_stage(a, i0_, t0_, sm + BwdSmem::STG + b * BwdStage::BYTES, sbar + b, part, lane);
+    pending |= 1u << b;
+  };
+  auto stage_wait = [&](int b) {
+    ok = ok && tc::mbar_wait(sbar + b, (sphase >> b) & 1u, WAIT_TRIES);
+    sphase ^= 1u << b;
+    pending &= ~(1u << b);
+  };
+  if (tile < ntiles) stage_issue(0, i0, t0);
   const uint32_t tmem = *tmem_ptr;
   const uint32_t lane_addr = tmem + ((uint32_t)(q4 * 32) << 16);
   auto sa = [&](uint32_t off) { return tc::smem_u32(sm + off); };
@@ -503,7 +512,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
   constexpr uint32_t ID16 = tc::idesc_bf16(128, 16, false, false);
   constexpr uint32_t IDW = tc::idesc_bf16(128, 144, true, true);
   constexpr uint32_t IDX = tc::idesc_bf16(128, 128, true, true);
-  uint32_t phase = 0;
+  uint32_t phase = 0, phase_dz = 0;
   bool first = true;
   const float* b2 = bias + 16 * c;
   const float* b3 = bias + 64 + 16 * c;
@@ -535,20 +544,21 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
   int dz_i0 = -1;  // first vertex of the tile whose dL/dz partials wait in dzp
   float dbo_acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   // dL/dz of the tile whose partials are in dzp: sum over its 8 frames (two
-  // per warp, pre-summed) and the 4 column quarters, one global add per value
+  // per warp quarter, pre-summed), one global add per value
   auto flush_dz = [&](int e0, int stride) {
     for (int e = e0; e < 16 * Z; e += stride) {
       const int vi = e & 15, qz = e >> 4;
       if (dz_i0 + vi >= a.N) continue;
       float s = 0.f;
 #pragma unroll
-      for (int cq = 0; cq < 4; ++cq)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) s += dzp[(cq * 8 + qz) * 64 + q * 16 + vi];
+      for (int q = 0; q < 4; ++q) s += dzp[(qz * 4 + q) * 16 + vi];
       atomicAdd(a.dz + (long long)(dz_i0 + vi) * Z + qz, s);
     }
   };
-  if (tile < ntiles) m1 = put_h1(sm + BwdSmem::STG, row_valid(i0, t0));
+  if (tile < ntiles) {
+    stage_wait(0);
+    m1 = put_h1(sm + BwdSmem::STG, row_valid(i0, t0));
+  }
   // `ok` leaves the loop only through tc_sync_ok, so every thread breaks at
   // the same barrier
   for (; tile < ntiles; tile += gridDim.x) {
@@ -559,16 +569,16 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
       nt0 = (next - ni0 / 16 * n_tb) * 8;
     }
     uint8_t* stg = sm + BwdSmem::STG + buf * BwdStage::BYTES;
-    const int t = t0 + tl;
     const bool valid = row_valid(i0, t0);
-    // the next tile's inputs copy while this tile computes
-    if (next < ntiles) bwd_stage(a, ni0, nt0, sm + BwdSmem::STG + (buf ^ 1) * BwdStage::BYTES);
     // ---- forward: layer 2
     if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
       mma_k64(tmem + WORK_COL, sa(BwdSmem::H1), sa(BwdSmem::W2), ID64);
       tc::mma_commit(bar);
     }
+    // the next tile's inputs copy while this tile computes (the buffer's last
+    // readers, the previous tile's dL/do and y row, are behind several barriers)
+    if (next < ntiles) stage_issue(buf ^ 1, ni0, nt0);
     tc_wait(bar, phase, ok);
     uint32_t m2 = 0u, m3 = 0u;
     {
@@ -633,14 +643,14 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
       // y row: z_i, gamma_t in columns 0..K-1, zeros, 1 in column 15 (first
       // read by the ACC_W MMA, after the dh2 step)
       const float* zs = reinterpret_cast<const float*>(stg + BwdStage::Z) + il * Z;
-      const float* gt = a.gamma + (long long)(valid ? t : 0) * 2 * M;
+      const float* gt = reinterpret_cast<const float*>(stg + BwdStage::GAM) + tl * (K - Z);
       float y[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k)
-        y[k] = k == 15 ? 1.f : k < Z ? (valid ? zs[k] : 0.f) : k < K ? gt[k - Z] : 0.f;
+        y[k] = k == 15 ? 1.f : !valid ? 0.f : k < Z ? zs[k] : k < K ? gt[k - Z] : 0.f;
       st_row16(sm + BwdSmem::Y, row, 0, y);
     } else if (dz_i0 >= 0) {
-      flush_dz(tid - 256, 256);
+      flush_dz(tid - 256, 256);  // 16 Z <= 128 values: warps 8..11
     }
     // ---- backward: dh3 = gO Wo (K = 16)
     if (!(ok = tc_sync_ok(ok, a.err))) break;
@@ -685,43 +695,45 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
 #pragma unroll
       for (int k = 0; k < 16; ++k) v[k] *= ((m1 >> k) & 1u) ? 1.f : a.slope;
       st_row16(sm + BwdSmem::DP3, row, 16 * c, v);  // dpre1 (ACC_W has consumed dpre3)
-      // dL/dz partial over this quarter's 16 hidden units, FP32, summed with
-      // lane ^ 16 (the same vertex, the other frame of the warp's two)
-#pragma unroll
-      for (int qz = 0; qz < 8; ++qz) {
-        if (qz < Z) {
-          const float4* w4 = reinterpret_cast<const float4*>(w1z + qz * 64 + 16 * c);
-          float s = 0.f;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const float4 w = w4[j];
-            s = fmaf(w.x, v[4 * j + 0], s);
-            s = fmaf(w.y, v[4 * j + 1], s);
-            s = fmaf(w.z, v[4 * j + 2], s);
-            s = fmaf(w.w, v[4 * j + 3], s);
-          }
-          s = valid ? s : 0.f;
-          s += __shfl_xor_sync(0xffffffffu, s, 16);
-          if (lane < 16) dzp[(c * 8 + qz) * 64 + q4 * 16 + lane] = s;
-        }
-      }
     }
-    // the next tile's staged inputs must have landed before the barrier
-    cp_async_wait_all();
-    // ---- ACC_X += [gO | dpre1]^T [y | h3]
+    // the next tile's h1 (ACC_W, the last reader of H1, has completed); the
+    // current m1 is used up
+    if (next < ntiles) {
+      stage_wait(buf ^ 1);
+      m1 = put_h1(sm + BwdSmem::STG + (buf ^ 1) * BwdStage::BYTES, row_valid(ni0, nt0));
+    }
+    // ---- dL/dz rows = dpre1 W1[:, :Z] (N = 16); ACC_X += [gO | dpre1]^T [y | h3]
     if (!(ok = tc_sync_ok(ok, a.err))) break;
+    // ACC_X is not waited for here: the next tile's first commit also covers
+    // it, and nothing before that wait writes a tile ACC_X reads
     if (tid == 0) {
+      mma_k64(tmem + DZ_COL, sa(BwdSmem::DP3), sa(BwdSmem::W1Z), ID16);
+      tc::mma_commit(bar + 2);
       mma_rows(tmem + ACC_X_COL, sa(BwdSmem::GO), sa(BwdSmem::Y), IDX, first);
-      tc::mma_commit(bar);
     }
     first = false;
     dz_i0 = i0;
-    // the next tile's h1 goes to H1, which ACC_X does not read
+    // dL/dz partials (quarter 1; warp 0 is issuing), summed with lane ^ 16
+    // (the same vertex, the warp's other frame)
+    if (c == 1) {
+      tc_wait(bar + 2, phase_dz, ok);
+      float r[16];
+      ld_col16(lane_addr + DZ_COL, r);
+#pragma unroll
+      for (int qz = 0; qz < 8; ++qz) {
+        if (qz < Z) {
+          const float s = r[qz] + __shfl_xor_sync(0xffffffffu, r[qz], 16);
+          if (lane < 16) dzp[(qz * 4 + q4) * 16 + lane] = s;
+        }
+      }
+    }
     buf ^= 1;
-    if (next < ntiles) m1 = put_h1(sm + BwdSmem::STG + buf * BwdStage::BYTES, row_valid(ni0, nt0));
     i0 = ni0;
     t0 = nt0;
-    // ACC_X reads y, h3, gO and dpre1: wait before the next tile writes them
+  }
+  // the last ACC_X
+  if (!first) {
+    if (tid == 0) tc::mma_commit(bar);
     tc_wait(bar, phase, ok);
   }
   // the last tile's dL/dz partials; the output-bias gradient of quarter 0
@@ -771,12 +783,15 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
       }
     } else if (c == 0) {
       ld_col16(lane_addr + ACC_X_COL, v);
-      for (int k = 0; k < K; ++k) atomicAdd(gW1 + (row - 64) * K + k, v[k]);
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (k < K) atomicAdd(gW1 + (row - 64) * K + k, v[k]);
       atomicAdd(gb1 + (row - 64), v[15]);
     }
   }
   // drain (bounded): no copy or MMA of this CTA may be in flight when it exits
-  cp_async_wait_all();
+  for (int b = 0; b < 2; ++b)
+    if (pending & (1u << b)) tc::mbar_wait(sbar + b, (sphase >> b) & 1u, WAIT_TRIES);
   if (tid == 0) {
     tc::mma_commit(bar + 1);
     tc::mbar_wait(bar + 1, 0, WAIT_TRIES);

@@ -80,6 +80,10 @@ static void* dev_alloc(npg_ctx* c, size_t bytes) {
     cudaGetLastError();
     p = nullptr;
   }
+  if (p && ((uintptr_t)p & 15u) != 0) {  // bulk and vector copies need 16-byte alignment
+    if (c->cfg.free) c->cfg.free(p, c->cfg.alloc_user);
+    return nullptr;
+  }
   if (p && c->n_allocs < 128) c->allocs[c->n_allocs++] = p;
   return p;
 }
@@ -424,9 +428,11 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
         alloc_n(c, c->pb.slot, c->MT_cap) && alloc_n(c, c->pb.sorted, c->MT_cap);
   ok &= alloc_n(c, c->xb.cell_start, T * (Gx3 + 1)) && alloc_n(c, c->xb.counts, T * Gx3) &&
         alloc_n(c, c->xb.slot, NT) && alloc_n(c, c->xb.sorted, NT);
-  ok &= alloc_n(c, c->z, (long long)N * md.Z) && alloc_n(c, c->U, (long long)N * md.H) &&
+  // z and gamma carry 16 B of padding: the BF16 backward stages them with
+  // bulk copies rounded up to 16 B
+  ok &= alloc_n(c, c->z, (long long)N * md.Z + 4) && alloc_n(c, c->U, (long long)N * md.H) &&
         alloc_n(c, c->V, (long long)T * md.H) && alloc_n(c, c->xhat, NT) &&
-        alloc_n(c, c->gamma, (long long)T * 2 * md.M) &&
+        alloc_n(c, c->gamma, (long long)T * 2 * md.M + 4) &&
         alloc_n(c, c->disp, NT) &&
         alloc_n(c, c->dxhat, NT) && alloc_n(c, c->nn_x, NT) && alloc_n(c, c->d_x, NT) &&
         alloc_n(c, c->nn_p, c->MT_cap) && alloc_n(c, c->d_p, c->MT_cap) &&
