@@ -39,18 +39,6 @@ __device__ __forceinline__ void st_bf16(uint8_t* tile, int row, int col, float v
   *reinterpret_cast<__nv_bfloat16*>(tile + tc::sw128_off(row, col)) = __float2bfloat16_rn(v);
 }
 
-// 64 FP32 accumulator columns of this thread's lane, starting at column c0.
-__device__ __forceinline__ void ld_row64(uint32_t tmem_lane, uint32_t c0, float* v) {
-  uint32_t r[16];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    tc::tmem_ld16(tmem_lane + c0 + 16 * q, r);
-    tc::tmem_ld_wait();
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[16 * q + j] = __uint_as_float(r[j]);
-  }
-}
-
 // Issue D = A * B^T with K = 64 (4 steps of 16), K-major operands.
 __device__ __forceinline__ void mma_k64(uint32_t d, uint32_t a_smem, uint32_t b_smem,
                                         uint32_t idesc) {
@@ -140,12 +128,17 @@ __global__ void __launch_bounds__(128) decode_tc_kernel(TcArgs a) {
   constexpr uint32_t ID64 = tc::idesc_bf16(128, 64, false, false);
   constexpr uint32_t ID16 = tc::idesc_bf16(128, 16, false, false);
   uint32_t phase = 0;
-  bool ok = true;
+  bool ok = true, run = true;
   const long long rows = (long long)a.N * a.T;
   const long long ntiles = (rows + TC_ROWS - 1) / TC_ROWS;
   uint8_t* act = sm + DecodeSmem::ACT;
 
-  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+  // One barrier per layer: it publishes the activation tile to the tensor
+  // core, orders every lane's TMEM reads of the previous layer before the
+  // next MMA overwrites the accumulator, and agrees on the waits' outcome.
+  // A thread writes the next activation into `act` right after its own wait
+  // (the MMA that read `act` has completed).
+  for (long long tile = blockIdx.x; tile < ntiles && run; tile += gridDim.x) {
     const long long row = tile * TC_ROWS + tid;
     const bool valid = row < rows;
     const int t = valid ? (int)(row / a.N) : 0;
@@ -172,8 +165,9 @@ __global__ void __launch_bounds__(128) decode_tc_kernel(TcArgs a) {
     for (int layer = 0; layer < 3; ++layer) {
       tc::fence_async_smem();
       tc::fence_before_sync();
-      __syncthreads();
+      run = __syncthreads_and(ok) != 0;
       tc::fence_after_sync();
+      if (!run) break;
       if (tid == 0) {
         if (layer < 2)
           mma_k64(tmem, s_act, layer == 0 ? s_w2 : s_w3, ID64);
@@ -181,24 +175,18 @@ __global__ void __launch_bounds__(128) decode_tc_kernel(TcArgs a) {
           mma_k64(tmem, s_act, s_wo, ID16);
         tc::mma_commit(bar);
       }
-      {
-        bool w = tc::mbar_wait(bar, phase, WAIT_TRIES);
-        phase ^= 1u;
-        w = __syncthreads_and(w) != 0;
-        if (!w) {
-          if (tid == 0) atomicExch(a.err, 1);
-          ok = false;
-          break;
-        }
-        tc::fence_after_sync();
+      if (!tc::mbar_wait(bar, phase, WAIT_TRIES)) {
+        ok = false;
+        atomicExch(a.err, 1);
       }
+      phase ^= 1u;
+      tc::fence_after_sync();
       if (layer < 2) {
-        ld_row64(lane, 0, v);
+        uint32_t r[64];
+        tc::tmem_ld64_wait(lane, r);
         const float* b = bias + 64 * layer;
 #pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = leaky(v[k] + b[k], a.slope);
-        tc::fence_before_sync();
-        __syncthreads();  // every lane has read TMEM before the next MMA overwrites it
+        for (int k = 0; k < 64; ++k) v[k] = leaky(__uint_as_float(r[k]) + b[k], a.slope);
         st_row64(act, tid, v);
       } else {
         uint32_t r[16];
@@ -213,11 +201,10 @@ __global__ void __launch_bounds__(128) decode_tc_kernel(TcArgs a) {
           a.xhat[row] = xh;
           a.disp[row] = dl;
         }
-        tc::fence_before_sync();
-        __syncthreads();
       }
     }
   }
+  // every lane's TMEM reads are complete before the columns are freed
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
