@@ -47,6 +47,34 @@ METRIC = "fwd+bwd+step vertex-frames/s at T=100, N=40962; batched BF16 vs plain 
 UNIT = "vertex-frames/s"
 FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e-3  # SMs x FP32 lanes x FMA x max GHz -> TFLOP/s
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
+# kernel at the default workload, from a one-pass ncu capture, with the
+# SHA-256 of the sources that define the kernel at capture time: a changed
+# source reports null traffic until the counters are taken again.
+KERNEL_SOURCES = {
+    "mlp_bwd_tc_kernel": ("k_mlp_tc.cu", "tc_sm100.cuh", "npg_device.cuh", "npg_internal.cuh"),
+}
+MEASURED_TRAFFIC = {
+    ("mlp_bwd_tc_kernel", "paper"): {"bytes": None, "sha256": None},
+}
+
+
+def sources_sha(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2602_22212_gb300", "csrc")
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel, workload):
+    rec = MEASURED_TRAFFIC.get((kernel, workload))
+    if not rec or rec["bytes"] is None or kernel not in KERNEL_SOURCES:
+        return None
+    return rec["bytes"] if sources_sha(kernel) == rec["sha256"] else None
+
 
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -508,6 +536,7 @@ def main():
     roof = roofline(dom)
     roof["kernel"] = kernels[dom]
     roof["ms_per_launch"] = stages[dom]
+    roof["traffic"] = measured_traffic(kernels[dom], args.workload)
     stage_roofs = {s: {k: v for k, v in roofline(s).items() if k in ("bound", "achieved", "unit",
                                                                     "frac")}
                    for s in stages if s in work and stages[s] > 0}

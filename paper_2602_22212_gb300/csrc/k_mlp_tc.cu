@@ -549,12 +549,6 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
   // `ok` leaves the loop only through tc_sync_ok, so every thread breaks at
   // the same barrier
   for (; tile < ntiles; tile += gridDim.x) {
-    const int next = tile + (int)gridDim.x;
-    int ni0 = 0, nt0 = 0;
-    if (next < ntiles) {
-      ni0 = next / n_tb * 16;
-      nt0 = (next - ni0 / 16 * n_tb) * 8;
-    }
     uint8_t* stg = sm + BwdSmem::STG + buf * BwdStage::BYTES;
     const bool valid = row_valid(i0, t0);
     // ---- forward: layer 2
@@ -562,6 +556,13 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
     if (tid == 0) {
       mma_k64(tmem + WORK_COL, sa(BwdSmem::H1), sa(BwdSmem::W2), ID64);
       tc::mma_commit(bar);
+    }
+    // the next tile's coordinates, while the MMA runs
+    const int next = tile + (int)gridDim.x;
+    int ni0 = 0, nt0 = 0;
+    if (next < ntiles) {
+      ni0 = next / n_tb * 16;
+      nt0 = (next - ni0 / 16 * n_tb) * 8;
     }
     // the next tile's inputs copy while this tile computes (the buffer's last
     // readers, the previous tile's dL/do and y row, are behind several barriers)

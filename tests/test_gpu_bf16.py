@@ -31,9 +31,10 @@ def npg():
     return mod
 
 
-def setup(rot_mode=0, seed=1, T=8, M=4096):
+def setup(rot_mode=0, seed=1, T=8, M=4096, Fn=2, n_freq=4):
     seq = I.sphere_blob(subdiv=4, T=T, M=M, noise=0.005, seed=seed)
-    ocfg = O.make_cfg(L=4, res=(8, 27, 45, 64), F=4, H=64, D=3, rot_mode=rot_mode, slope=0.01)
+    ocfg = O.make_cfg(L=4, res=(8, 27, 45, 64), F=4, Fn=Fn, H=64, D=3, rot_mode=rot_mode,
+                      slope=0.01, n_freq=n_freq)
     prob = O.Problem(ocfg, seq.x, seq.n, seq.faces, seq.points, seq.offsets, seq.t_key)
     return seq, ocfg, prob
 
@@ -84,16 +85,14 @@ def test_bf16_identity_initialisation_exact(npg):
     ctx.close()
 
 
-@pytest.mark.parametrize("rot_mode", [0, 1, 2])
-def test_bf16_backprop_vs_oracle(npg, rot_mode):
+def _backprop_vs_oracle(npg, seq, ocfg, prob, **kw):
     import torch
-    seq, ocfg, prob = setup(rot_mode)
     grid, mlp = rand_params(ocfg)
     f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
     ref = O.loss_full(prob, f32(grid), f32(mlp), 3, 10, decide_f32=True)
     gx32 = ref["g_xhat"].astype(np.float32)
     want_g, want_m = O.backprop(prob, f32(grid), f32(mlp), f32(gx32))
-    ctx = npg.Context(cfg_of(npg, ocfg, npg.BF16_MLP), seq, mlp)
+    ctx = npg.Context(cfg_of(npg, ocfg, npg.BF16_MLP, **kw), seq, mlp)
     ctx.set(npg.BUF_GRID, grid)
     npg.npg_set_epoch(ctx.h, 3)
     ctx.forward()
@@ -111,6 +110,22 @@ def test_bf16_backprop_vs_oracle(npg, rot_mode):
         b = O.level_offset(ocfg, l + 1) if l < ocfg.L else O.grid_len(ocfg)
         assert rel(gg[a:b], want_g[a:b]) <= 1e-1, (l, rel(gg[a:b], want_g[a:b]))
     ctx.close()
+
+
+@pytest.mark.parametrize("rot_mode", [0, 1, 2])
+def test_bf16_backprop_vs_oracle(npg, rot_mode):
+    seq, ocfg, prob = setup(rot_mode)
+    _backprop_vs_oracle(npg, seq, ocfg, prob)
+
+
+def test_bf16_backprop_ragged_tiles(npg):
+    """Tiles cut by both ends: N = 2562 leaves 2 vertices in the last block of
+    16, T = 5 fills 5 of the 8 frames, and Z = 5, 2M = 6 make the last
+    block's z run (2 x 5 floats) and every gamma run (5 x 6 floats) miss a
+    16-byte multiple, so the staged copies take their rounded, padded form."""
+    seq, ocfg, prob = setup(0, T=5, Fn=1, n_freq=3)
+    assert seq.N % 16 == 2 and O.k_in(ocfg) == 11
+    _backprop_vs_oracle(npg, seq, ocfg, prob, F_n=1, n_freq=3)
 
 
 _FINAL_RUNS = 8
