@@ -5,8 +5,11 @@ BF16 keeps 8 significand bits, so each rounded activation or weight carries
 a relative error up to 2^-9 = 2e-3; a 64-term dot product of such terms lands
 within a few 1e-3 of its FP32 value. Tolerances:
   x-hat                 5e-3 absolute against the FP32 path (coordinates O(1))
-  MLP gradients         3e-2 relative per block against the oracle, from the
-                        same dL/dx-hat
+  MLP gradients         3e-2 relative per weight block against the oracle,
+                        from the same dL/dx-hat; 5e-2 per bias block: a bias
+                        gradient sums one term per row over all vertex-frames,
+                        and those terms largely cancel, which magnifies the
+                        rounding of each
   grid gradients        1e-1 relative per level: every grid node sums the
                         contributions of many vertex-frames that largely cancel
                         (the coarsest level most), which magnifies the BF16
@@ -103,7 +106,8 @@ def _backprop_vs_oracle(npg, seq, ocfg, prob, **kw):
     off = 0
     for name, n in [("W1", H * K), ("b1", H), ("W2", H * H), ("b2", H), ("W3", H * H),
                     ("b3", H), ("Wo", NO * H), ("bo", NO)]:
-        assert rel(gm[off:off + n], want_m[off:off + n]) <= 3e-2, name
+        bound = 5e-2 if name.startswith("b") else 3e-2
+        assert rel(gm[off:off + n], want_m[off:off + n]) <= bound, (name, rel(gm[off:off + n], want_m[off:off + n]))
         off += n
     for l in range(ocfg.L + 1):
         a = O.level_offset(ocfg, l)
