@@ -274,10 +274,11 @@ cudaError_t launch_decode_bf16(npg_ctx* c) {
 // quarters and overlapped in one phase: while c = 0 forms dL/do, c = 1 writes
 // the y row and c >= 2 sums and adds the previous tile's dL/dz partials. The
 // output-bias gradient stays in per-thread FP32 registers until the CTA ends.
-// One warp issues the bulk copies of the next tile's inputs (U, V, x, dL/dx-hat,
-// z and gamma rows) into a second shared staging buffer while the current
-// tile computes; the next tile's h1 is written while the current tile's last
-// weight-gradient MMA runs, which the next tile's first MMA commit covers.
+// Warps 2..15 issue the bulk copies of the next tile's inputs (U, V, x,
+// dL/dx-hat, z and gamma rows) into a second shared staging buffer during the
+// current tile's first MMA. The next tile's h1 is written before the current
+// tile's last barrier, and the last weight-gradient MMA is not waited for:
+// the next tile's first MMA commit covers it.
 struct BwdStage {  // inputs of one tile, FP32
   static constexpr uint32_t U_PITCH = 272;    // 256 B + 16: the 16 vertex rows hit distinct banks
   static constexpr uint32_t U = 0;            // [16 vertices][64], rows U_PITCH apart
@@ -370,7 +371,7 @@ __device__ __forceinline__ void mma_rows(uint32_t d, uint32_t a_smem, uint32_t b
 // keep stale (or never written) values, which every reader replaces by zero
 // through a select. The z and gamma copies round up to 16 B; those arrays
 // carry 16 B of padding.
-constexpr int STAGE_WARPS = 4, STAGE_PIECES = 28;
+constexpr int STAGE_WARPS = 14, STAGE_PIECES = 28;
 __device__ void bwd_stage(const TcArgs& a, int i0, int t0, uint8_t* stg, uint64_t* sbar,
                           int part, int lane) {
   const int nv = min(16, a.N - i0), nf = min(8, a.T - t0);
@@ -476,9 +477,9 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
   __syncthreads();  // zeroed y before its column 15 is set; barriers initialised
   if (c == 1) st_bf16(sm + BwdSmem::Y, row, 15, 1.f);
   bool ok = tc_sync_ok(true, a.err);
-  // staging: warps 16 - STAGE_WARPS .. 15 issue a tile's copies, every thread
-  // waits on the buffer's barrier before its first read (parity and in-flight
-  // bit per buffer)
+  // staging: warps 16 - STAGE_WARPS .. 15 (two pieces each; warp 0 issues the
+  // MMAs) issue a tile's copies, every thread waits on the buffer's barrier
+  // before its first read (parity and in-flight bit per buffer)
   uint32_t sphase = 0u, pending = 0u;
   auto stage_issue = [&](int b, int i0_, int t0_) {
     const int part = warp - (16 - STAGE_WARPS);
