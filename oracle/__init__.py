@@ -104,6 +104,7 @@ def lib():
                                      pd, pd, pd, pd, d, pd, d, d, d, i, d, pd, pd, pd, pd]),
                 "or_evaluate": (None, [i, i, pd, pd, i, pi32, d, pd]),
                 "or_conf_weights_mode": (None, [i, pd, i, d, d, i, i, pd]),
+                "or_select_keyframe": (i, [i, pi64, pd, d, pd]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -463,3 +464,16 @@ def evaluate(xhat, gt, faces, tau_rel=0.005):
     out, po = _out_d(6 * T)
     lib().or_evaluate(T, N, px, pg, len(faces), pf, float(tau_rel), po)
     return out[: 6 * T].reshape(T, 6)
+
+
+def select_keyframe(points, offsets, bias=1.0):
+    """Sec. 3.1 keyframe selection (reading in npg_oracle.c): (t_key, extents)
+    for concatenated clouds points (off[T] x 3) with frame offsets (T + 1)."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    T = len(off) - 1
+    p, pp = _d(np.asarray(points, np.float64).reshape(-1, 3))
+    o, po = _out_d(T)
+    t_key = lib().or_select_keyframe(T, off.ctypes.data_as(C.POINTER(C.c_int64)), pp,
+                                     float(bias), po)
+    return int(t_key), o[:T].copy()
+

@@ -991,3 +991,41 @@ void or_evaluate(int T, int N, const double* xhat, const double* gt, int F_tri,
   free(dx);
   free(dg);
 }
+
+/* Keyframe selection (Sec. 3.1, Initialization): each frame's point cloud is
+ * rated by its spatial extent, weighted by a term that favours the temporal
+ * midpoint, and the best-rated frame becomes t_key. The paper defers the
+ * formula to an earlier method; the reading taken here:
+ *   e_t = sqrt( mean_j |p_j - c_t|^2 ),  c_t = mean_j p_j   (RMS radius of P_t)
+ *   w_t = 1 - bias |t~ - 1/2|,  t~ = t / (T - 1)  (t~ = 1/2 when T = 1)
+ *   t_key = argmax_t w_t e_t, the lowest t on ties.
+ * Two passes per frame (centroid, then squared distances), FP64, points in
+ * input order. pts: off[T] x 3; extent (T, nullable) receives e_t. */
+int or_select_keyframe(int T, const int64_t* off, const double* pts, double bias,
+                       double* extent) {
+  int best = 0;
+  double best_s = -1.0;
+  for (int t = 0; t < T; ++t) {
+    const int64_t a = off[t], b = off[t + 1];
+    const double n = (double)(b - a);
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = a; j < b; ++j)
+      for (int d = 0; d < 3; ++d) c[d] += pts[3 * j + d];
+    for (int d = 0; d < 3; ++d) c[d] /= n;
+    double s2 = 0.0;
+    for (int64_t j = a; j < b; ++j)
+      for (int d = 0; d < 3; ++d) {
+        const double u = pts[3 * j + d] - c[d];
+        s2 += u * u;
+      }
+    const double e = sqrt(s2 / n);
+    if (extent) extent[t] = e;
+    const double tt = T > 1 ? (double)t / (double)(T - 1) : 0.5;
+    const double s = (1.0 - bias * fabs(tt - 0.5)) * e;
+    if (s > best_s) {
+      best_s = s;
+      best = t;
+    }
+  }
+  return best;
+}

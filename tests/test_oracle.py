@@ -518,3 +518,37 @@ def test_stability_schedule_variants():
     # e~ = 1: the method's delta is 0 (all weights 1), and so is the linear one
     for d in (0, 2, 4):
         np.testing.assert_allclose(w(4, d, 0), np.ones(4), rtol=1e-14)
+
+
+def _frames(clouds):
+    off = np.cumsum([0] + [len(c) for c in clouds])
+    return np.concatenate(clouds), off
+
+
+def test_keyframe_extent_closed_forms():
+    """The RMS radius of an octahedron's six vertices about any centre is its
+    circumradius; the radius scales with the cloud and ignores translation."""
+    rng = np.random.default_rng(3)
+    octa = np.concatenate([np.eye(3), -np.eye(3)])
+    clouds = [0.7 * octa + np.array([0.1, -0.2, 0.3]), 0.25 * octa]
+    base = rng.normal(size=(97, 3))
+    clouds += [base, 2.5 * base + np.array([0.4, 0.0, -0.1])]
+    _, e = O.select_keyframe(*_frames(clouds), bias=0.0)
+    np.testing.assert_allclose(e[:2], [0.7, 0.25], rtol=1e-15)
+    np.testing.assert_allclose(e[3], 2.5 * e[2], rtol=1e-13)
+
+
+def test_keyframe_choice_and_midpoint_bias():
+    """Without bias the widest frame wins (the first one on exact ties); equal
+    frames go to the middle one; a wider edge frame beats the middle frame
+    exactly when its weighted extent is larger: T = 3, extents (1.5, 1, 1),
+    weights (1 - b/2, 1, 1 - b/2) give frame 0 for b < 2/3 and frame 1 above."""
+    octa = np.concatenate([np.eye(3), -np.eye(3)])
+    pts, off = _frames([s * octa for s in (0.5, 0.9, 0.3, 0.9)])
+    assert O.select_keyframe(pts, off, 0.0)[0] == 1
+    for T in (1, 3, 5, 9):
+        pts, off = _frames([octa] * T)
+        assert O.select_keyframe(pts, off, 1.0)[0] == (T - 1) // 2
+    pts, off = _frames([1.5 * octa, octa, octa])
+    for b, want in ((0.0, 0), (0.5, 0), (0.6, 0), (0.7, 1), (1.0, 1)):
+        assert O.select_keyframe(pts, off, b)[0] == want, b
