@@ -368,6 +368,27 @@ NPG_API int npg_nearest(const float* q, int nq, const float* c, int nc, int32_t*
                 int cells, void* stream);
 
 /*
+ * Keyframe selection (Sec. 3.1, Initialization): every frame's point cloud is
+ * rated by its spatial extent, weighted toward the temporal midpoint, and the
+ * best-rated frame is returned as t_key (the frame whose cloud the caller
+ * turns into the reference mesh). The paper defers the formula to an earlier
+ * method; this library's reading:
+ *   e_t = sqrt(mean_j |p_j - c_t|^2), c_t = mean_j p_j   (RMS radius, FP64)
+ *   w_t = 1 - bias |t / (T - 1) - 1/2|                   (T = 1: t_key = 0)
+ *   t_key = argmax_t w_t e_t, the lowest t on ties.
+ * points: concatenated clouds, frame_offsets[T] x 3 FP32; frame_offsets: T + 1
+ * int64, frame_offsets[0] = 0, every frame non-empty. Both are device pointers
+ * when on_device, else host pointers; the caller keeps them. 0 <= bias <= 1.
+ * extent_out (host, T doubles, nullable) receives e_t, t_key_out (host) the
+ * choice. Allocates its scratch with cudaMallocAsync on stream and
+ * synchronizes the stream before returning. Bad arguments and invalid offsets
+ * return NPG_EINVAL before any device work.
+ */
+NPG_API int npg_select_keyframe(const float* points, const int64_t* frame_offsets, int T,
+                                int on_device, double bias, double* extent_out, int* t_key_out,
+                                void* stream);
+
+/*
  * Standalone Sobolev preconditioner (Eq. 9) of one r^3 x F block:
  * out = (I + lambda L)^-2 g per channel, L the 6-neighbour lattice Laplacian
  * with natural (Neumann) boundary. g and out are device pointers (r^3 x F

@@ -5,7 +5,8 @@
 // box, normal consistency of nearest pairs (area-weighted vertex normals),
 // and the mean correspondence error |x-hat_i - g_i|. The nearest neighbours
 // come from the exact bucketed search (k_chamfer.cu); the per-frame sums are
-// FP64 partials in a fixed order.
+// FP64 partials in a fixed order. Also the per-frame spatial extent that
+// keyframe selection rates (Sec. 3.1).
 #include <float.h>
 
 #include "npg_internal.cuh"
@@ -142,6 +143,41 @@ cudaError_t launch_eval_frames(const float4* x, const float4* g, const float4* n
                                int T, double* part, cudaStream_t s) {
   eval_frame_kernel<<<dim3(T, EVAL_SPLIT), 256, 0, s>>>(x, g, nx, ng, idx_x, d_x, idx_g, d_g,
                                                         tau2, N, part);
+  return cudaGetLastError();
+}
+
+// Keyframe selection (Sec. 3.1): one block per frame computes the RMS radius
+// of the frame's points about their centroid in FP64, in two passes (the
+// centroid, then the squared distances), each a strided per-thread sum and a
+// block reduction. off: T + 1 offsets into pts (x, y, z per point).
+__global__ void __launch_bounds__(256) keyframe_extent_kernel(const float* __restrict__ pts,
+                                                              const long long* __restrict__ off,
+                                                              double* __restrict__ extent) {
+  __shared__ double sh[32];
+  __shared__ double cen[3];
+  const long long a = off[blockIdx.x], b = off[blockIdx.x + 1];
+  const double n = (double)(b - a);
+  double s[3] = {0.0, 0.0, 0.0};
+  for (long long j = a + threadIdx.x; j < b; j += blockDim.x)
+    for (int d = 0; d < 3; ++d) s[d] += (double)pts[3 * j + d];
+  for (int d = 0; d < 3; ++d) {
+    const double r = eval_block_sum(s[d], sh);
+    if (threadIdx.x == 0) cen[d] = r / n;
+  }
+  __syncthreads();
+  double s2 = 0.0;
+  for (long long j = a + threadIdx.x; j < b; j += blockDim.x)
+    for (int d = 0; d < 3; ++d) {
+      const double u = (double)pts[3 * j + d] - cen[d];
+      s2 += u * u;
+    }
+  const double r = eval_block_sum(s2, sh);
+  if (threadIdx.x == 0) extent[blockIdx.x] = sqrt(r / n);
+}
+
+cudaError_t launch_keyframe_extent(const float* pts, const long long* off, int T, double* extent,
+                                   cudaStream_t s) {
+  keyframe_extent_kernel<<<T, 256, 0, s>>>(pts, off, extent);
   return cudaGetLastError();
 }
 

@@ -1382,6 +1382,66 @@ extern "C" int npg_nearest(const float* q, int nq, const float* cand, int nc, in
   return NPG_OK;
 }
 
+extern "C" int npg_select_keyframe(const float* points, const int64_t* frame_offsets, int T,
+                                   int on_device, double bias, double* extent_out,
+                                   int* t_key_out, void* stream) {
+  if (T < 1 || !points || !frame_offsets || !t_key_out || !(bias >= 0.0 && bias <= 1.0))
+    return set_err(nullptr, NPG_EINVAL, "npg_select_keyframe: bad arguments (T=%d)", T);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<long long> off(T + 1);
+  cudaError_t e = cudaSuccess;
+  if (on_device) {
+    e = cudaMemcpyAsync(off.data(), frame_offsets, sizeof(long long) * (T + 1),
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "npg_select_keyframe");
+  } else {
+    for (int t = 0; t <= T; ++t) off[t] = frame_offsets[t];
+  }
+  if (off[0] != 0) return set_err(nullptr, NPG_EINVAL, "frame_offsets[0] must be 0");
+  for (int t = 0; t < T; ++t)
+    if (off[t + 1] - off[t] < 1)
+      return set_err(nullptr, NPG_EINVAL, "frame %d has no points (every frame needs one)", t);
+  const long long MT = off[T];
+  const float* d_pts = on_device ? points : nullptr;
+  float* own_pts = nullptr;
+  long long* d_off = nullptr;
+  double* d_ext = nullptr;
+  if (!on_device) {
+    e = cudaMallocAsync((void**)&own_pts, sizeof(float) * 3 * MT, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(own_pts, points, sizeof(float) * 3 * MT, cudaMemcpyHostToDevice, s);
+    d_pts = own_pts;
+  }
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_off, sizeof(long long) * (T + 1), s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_ext, sizeof(double) * T, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * (T + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_keyframe_extent(d_pts, d_off, T, d_ext, s);
+  std::vector<double> ext(T);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ext.data(), d_ext, sizeof(double) * T, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(own_pts, s);
+  cudaFreeAsync(d_off, s);
+  cudaFreeAsync(d_ext, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "npg_select_keyframe");
+  // rating and choice on the host, in FP64 (lowest frame on ties)
+  int best = 0;
+  double best_s = -1.0;
+  for (int t = 0; t < T; ++t) {
+    const double tt = T > 1 ? (double)t / (double)(T - 1) : 0.5;
+    const double sc = (1.0 - bias * fabs(tt - 0.5)) * ext[t];
+    if (sc > best_s) {
+      best_s = sc;
+      best = t;
+    }
+    if (extent_out) extent_out[t] = ext[t];
+  }
+  *t_key_out = best;
+  return NPG_OK;
+}
+
 extern "C" int npg_precondition_tc(const float* g, float* out, int r, int F, float lambda,
                                    void* stream) {
   if (!g || !out || r < 2 || r > 256 || F < 1 || F > NPG_MAX_F || !(lambda >= 0.f))

@@ -213,6 +213,8 @@ cudaError_t launch_eval_frames(const float4* x, const float4* g, const float4* n
                                const float4* ng, const int* idx_x, const float* d_x,
                                const int* idx_g, const float* d_g, const float* tau2, int N,
                                int T, double* part, cudaStream_t s);
+cudaError_t launch_keyframe_extent(const float* pts, const long long* off, int T, double* extent,
+                                   cudaStream_t s);
 int eval_split();
 int eval_terms();
 // records a message for npg_last_error(NULL) and returns code

@@ -103,6 +103,7 @@ _SIG = {
     "npg_destroy": (_i, [_vp]),
     "npg_last_error": (C.c_char_p, [_vp]),
     "npg_nearest": (_i, [_vp, _i, _vp, _i, _vp, _vp, _i, _vp]),
+    "npg_select_keyframe": (_i, [_vp, _vp, _i, _i, C.c_double, _vp, C.POINTER(C.c_int), _vp]),
     "npg_precondition": (_i, [_vp, _vp, _i, _i, C.c_float, _vp]),
     "npg_precondition_static": (_i, [_vp, _vp, _i, _i, C.c_float, _vp]),
     "npg_precondition_tc": (_i, [_vp, _vp, _i, _i, C.c_float, _vp]),
@@ -323,6 +324,20 @@ def npg_nearest(q, cand, idx, dist=None, cells=0, stream=None):
     """Device tensors: q (nq x 3), cand (nc x 3) FP32; idx (nq) int32; dist (nq) FP32."""
     _check(_lib.npg_nearest(_ptr(q), int(q.shape[0]), _ptr(cand), int(cand.shape[0]), _ptr(idx),
                             _ptr(dist), int(cells), _stream_handle(stream)))
+
+
+def npg_select_keyframe(points, frame_offsets, bias=1.0, stream=None):
+    """Keyframe selection (Sec. 3.1): (t_key, per-frame extents). points
+    (M_total x 3 FP32) and frame_offsets (T + 1 int64) are both numpy arrays
+    (host) or both CUDA tensors (device)."""
+    on_device = not isinstance(points, np.ndarray)
+    T = int(frame_offsets.shape[0]) - 1
+    ext = np.zeros(max(T, 1), np.float64)
+    t_key = C.c_int(-1)
+    _check(_lib.npg_select_keyframe(_ptr(points), _ptr(frame_offsets), T, int(on_device),
+                                    float(bias), ext.ctypes.data, C.byref(t_key),
+                                    _stream_handle(stream)))
+    return t_key.value, ext[:T]
 
 
 def npg_precondition(g, out, r, F, lam, stream=None):

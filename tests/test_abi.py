@@ -98,6 +98,17 @@ def test_invalid_arguments_are_rejected_before_any_device_work(npg):
     # standalone ops validate their sizes
     assert npg._lib.npg_nearest(None, -1, None, 0, None, None, 0, None) == npg.EINVAL
     assert npg._lib.npg_precondition(None, None, 1, 1, 0.4, None) == npg.EINVAL
+    # keyframe selection validates sizes, bias and host offsets before any device work
+    pts = np.zeros((4, 3), np.float32)
+    tk = C.c_int(-1)
+    sel = lambda off, bias, T: npg._lib.npg_select_keyframe(
+        pts.ctypes.data, off.ctypes.data, T, 0, bias, None, C.byref(tk), None)
+    assert sel(np.array([0, 2, 4], np.int64), 1.0, 0) == npg.EINVAL
+    assert sel(np.array([0, 2, 4], np.int64), 1.5, 2) == npg.EINVAL
+    assert sel(np.array([1, 2, 4], np.int64), 1.0, 2) == npg.EINVAL
+    assert sel(np.array([0, 2, 2], np.int64), 1.0, 2) == npg.EINVAL
+    assert "no points" in npg.npg_last_error()
+    assert tk.value == -1
 
 
 def test_mlp_and_grid_lengths(npg):

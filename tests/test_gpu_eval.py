@@ -70,3 +70,36 @@ def test_metrics_match_oracle(npg, rot_mode):
         np.testing.assert_allclose(got[:T, 3], want[:, 3], atol=4.0 / N)
         assert np.all(want[:, 3] > 0) or tau_rel == 0.005
     ctx.close()
+
+
+def test_keyframe_selection_matches_oracle(npg):
+    """Keyframe selection (npg_select_keyframe) against oracle.select_keyframe
+    on the same FP32 clouds, from host and from device memory: extents within
+    1e-12 relative (FP64 sums in another order), the same frame unless two
+    weighted extents agree within that tolerance."""
+    import torch
+    rng = np.random.default_rng(11)
+    seq = I.figure(subdiv=3, T=13, M=2500, noise_rel=0.003, seed=4)
+    sizes = rng.integers(1, 3000, size=9)
+    sizes[3] = 1
+    ragged = [(rng.normal(size=(n, 3)) * rng.uniform(0.2, 0.9)).astype(np.float32) for n in sizes]
+    cases = [(seq.points.astype(np.float32), seq.offsets.astype(np.int64)),
+             (np.concatenate(ragged), np.cumsum([0] + list(sizes)).astype(np.int64)),
+             (ragged[0], np.array([0, len(ragged[0])], np.int64))]
+    for pts, off in cases:
+        for bias in (0.0, 0.5, 1.0):
+            want_t, want_e = O.select_keyframe(pts.astype(np.float64), off, bias)
+            T = len(off) - 1
+            tt = np.arange(T) / (T - 1) if T > 1 else np.full(1, 0.5)
+            w = 1.0 - bias * np.abs(tt - 0.5)
+            for dev in (False, True):
+                if dev:
+                    got_t, got_e = npg.npg_select_keyframe(torch.from_numpy(pts).cuda(),
+                                                           torch.from_numpy(off).cuda(), bias)
+                else:
+                    got_t, got_e = npg.npg_select_keyframe(pts, off, bias)
+                np.testing.assert_allclose(got_e, want_e, rtol=1e-12)
+                if got_t != want_t:
+                    s = w * want_e
+                    assert abs(s[got_t] - s[want_t]) <= 1e-12 * s[want_t], (got_t, want_t)
+
