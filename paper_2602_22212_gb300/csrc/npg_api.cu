@@ -626,11 +626,15 @@ static int loss_launch(npg_ctx* c) {
 static int backprop_launch(npg_ctx* c) {
   CK(c, cudaMemsetAsync(c->g_mlp, 0, sizeof(float) * c->mlp_len, c->stream));
   CK(c, cudaMemsetAsync(c->dz, 0, sizeof(float) * (size_t)c->N * c->md.Z, c->stream));
-  CK(c, cudaMemsetAsync(c->g_grid, 0, sizeof(float) * c->grid_dev_len, c->stream));
+  // the grid gradient (every level; 0.6 GB at the paper's sizes) is cleared on
+  // lane 1 while the MLP backward, which neither reads nor writes it, runs
+  CK(c, lanes_fork(c, 2));
+  CK(c, cudaMemsetAsync(c->g_grid, 0, sizeof(float) * c->grid_dev_len, c->lane[1]));
   if (c->cfg.precision == NPG_BF16_MLP)
     CK(c, launch_mlp_backward_bf16(c));
   else
     CK(c, launch_mlp_backward_fp32(c));
+  CK(c, lanes_join(c, 2));
   mark(c, 8);
   CK(c, launch_scatter(c));
   mark(c, 9);
