@@ -76,6 +76,24 @@ def measured_traffic(kernel, workload):
     return rec["bytes"] if sources_sha(kernel) == rec["sha256"] else None
 
 
+def max_over_ranks(x, dist):
+    """The maximum of a per-rank scalar over all ranks (x itself without a
+    process group); on the process group's device (CUDA for NCCL)."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, N, T, steps, seconds):
+    """Whole-job vertex-frames/s: every rank processes its own N x T sequence
+    (weak scaling), timed by the slowest rank."""
+    return world * N * T * steps / seconds
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -452,11 +470,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     clocks = sampler.stop()
     launches = npg.npg_launch_count(ctx.h) - launches0
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N * T * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist)
+    value = job_throughput(world, N, T, args.steps, ms * 1e-3)
 
     # per-stage attribution: the same iteration, eager, with CUDA events per stage
     sctx = ctx
@@ -496,11 +511,8 @@ def main():
         npg.npg_set_points(ctx.h, pts_pin, off_pin)
         npg.npg_iteration(ctx.h, loss_out)
     t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_value = world * N * T * e2e_steps / t_e2e
+    t_e2e = max_over_ranks(t_e2e, dist)
+    e2e_value = job_throughput(world, N, T, e2e_steps, t_e2e)
 
     peaks = load_peaks()
     work = stage_work(p, N, T, MT, (H, D, K, Z, NO), precond, args.precision, mlp.size)
@@ -560,11 +572,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms3 = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms3], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms3 = float(t.item())
-        v3 = world * N * T * steps3 / (ms3 * 1e-3)
+        ms3 = max_over_ranks(ms3, dist)
+        v3 = job_throughput(world, N, T, steps3, ms3 * 1e-3)
         plain = {"value": v3, "unit": UNIT, "ms_per_step": ms3 / steps3, "steps": steps3,
                  "form": "plain FP32 per-sequence (eager, FP32 preconditioner)",
                  "ratio_bf16_over_fp32": value / v3}
