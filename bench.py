@@ -45,7 +45,12 @@ if ROOT not in sys.path:
 
 METRIC = "fwd+bwd+step vertex-frames/s at T=100, N=40962; batched BF16 vs plain FP32"
 UNIT = "vertex-frames/s"
-FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.070e-3  # SMs x FP32 lanes x FMA x max GHz -> TFLOP/s
+FP32_LANES_PER_SM = 128  # FP32 FMA units per SM (Blackwell)
+
+
+def fp32_peak_tflops(sms, mhz):
+    """FP32 peak from unit counts: SMs x FMA lanes x 2 FLOP x SM clock."""
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a
 # kernel at the default workload, from a one-pass ncu capture, with the
@@ -179,8 +184,12 @@ def stage_work(p, N, T, MT, mlp_dims, precond="fp32", precision="fp32", mlp_len=
     H, D, K, Z, NO = mlp_dims
     L, F = p["L"], p["F"]
     rows = N * T
+    # per vertex-frame: the forward's hidden and output layers (the first layer
+    # is factorised into per-vertex U and per-frame V); the backward is twice
+    # that (input and weight gradients), the forward recompute inside the
+    # backward kernel is not counted as algorithmic work
     fwd_row = 2 * H * H * (D - 1) + 2 * NO * H
-    bwd_row = fwd_row + 2 * NO * H * 2 + (D - 1) * 4 * H * H + 2 * H * K + 2 * H * Z
+    bwd_row = 2 * fwd_row
     res = p["res"]
     dct_flops = sum(12 * r ** 4 * F for r in res) + 12 * 4 ** 4 * 2
     dct_bytes = sum(6 * 8 * r ** 3 * F for r in res) + 6 * 8 * 4 ** 3 * 2
@@ -203,6 +212,44 @@ def stage_work(p, N, T, MT, mlp_dims, precond="fp32", precision="fp32", mlp_len=
 
 
 # ----------------------------------------------------------------- CPU oracle sample
+
+def cpu_info():
+    """Host CPU model and logical core count (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "hardware", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
+def oracle_timed(p, seq, frames):
+    """The oracle sample on one host thread and on all of them."""
+    import oracle as O
+    n0 = O.set_threads()
+    out = {}
+    try:
+        for label, n in (("one", 1), ("all", os.cpu_count() or 1)):
+            used = O.set_threads(n)
+            v, s, desc = oracle_sample(p, seq, frames=frames)
+            out[label] = (v, s, desc, used)
+    finally:
+        O.set_threads(n0)
+    return out
+
 
 def oracle_sample(p, seq, frames=1, level=1):
     """Time the FP64 oracle on a bounded sample of the workload and extrapolate
@@ -244,7 +291,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle as O
     p, seq = workload(args.workload)
+    cores = O.set_threads(os.cpu_count() or 1)
     for _ in range(args.warmup):
         oracle_sample(p, seq)
     vals, secs = [], 0.0
@@ -254,13 +303,14 @@ def run_reference(args):
         vals.append(v)
         secs += s
     value = float(np.mean(vals))
+    host = cpu_info()
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_dict(p, seq, "f64 CPU oracle", False),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc, "cpu_model": host["model"], "nproc": host["nproc"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -515,6 +565,24 @@ def main():
     e2e_value = job_throughput(world, N, T, e2e_steps, t_e2e)
 
     peaks = load_peaks()
+    # FP32 peak: unit counts at the SM clock sampled during the timed region
+    # (the maximum clock when no sample was taken); the FMA probe measures the
+    # same rate directly, with its own clock samples, as a cross-check
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clocks["sm_mhz"] if clocks else 2070.0
+    fp32_peak = fp32_peak_tflops(sms, mhz)
+    fp32_src = (f"FP32 FMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x {mhz:.0f} MHz "
+                f"({'median sampled under load' if clocks else 'maximum clock'})")
+    probe_sampler = ClockSampler(local)
+    probe_sampler.start()
+    probe = [npg.npg_fp32_fma_rate(stream) for _ in range(12)]
+    probe_clk = probe_sampler.stop()
+    fp32_probe = {"tflops_median": statistics.median(t for t, _ in probe),
+                  "tflops_max": max(t for t, _ in probe),
+                  "ms_per_launch": statistics.median(m for _, m in probe),
+                  "clocks": probe_clk,
+                  "derived_at_probe_clock": (fp32_peak_tflops(sms, probe_clk["sm_mhz"])
+                                             if probe_clk else None)}
     work = stage_work(p, N, T, MT, (H, D, K, Z, NO), precond, args.precision, mlp.size)
     # search work: 8 FLOP per candidate pair (3 sub, 1 mul, 2 fma, compare)
     work["nn_x"] = ("alu", 8 * search["cand_per_query_x"] * N * T, "FLOP")
@@ -533,9 +601,9 @@ def main():
                     "unit": "TFLOP/s", "frac": ach / peaks["bf16_sus"], "traffic": None,
                     "peak_source": f"{peaks['src']} BF16 dense, sustained"}
         ach = amount / dur / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": FP32_TFLOPS_NOMINAL, "unit": "TFLOP/s",
-                "frac": ach / FP32_TFLOPS_NOMINAL, "traffic": None,
-                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+        return {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None,
+                "peak_source": fp32_src}
 
     # the dominant kernel: the longest stage that is one kernel launch (the
     # preconditioner stage is 6 passes x levels plus Adam on concurrent lanes,
@@ -549,6 +617,10 @@ def main():
     roof["kernel"] = kernels[dom]
     roof["ms_per_launch"] = stages[dom]
     roof["traffic"] = measured_traffic(kernels[dom], args.workload)
+    if dom == "mlp_bwd":
+        # what the kernel also executes beyond the algorithmic backward: the
+        # forward recompute of every row (not counted in `achieved`)
+        roof["recompute_flop"] = work["decode"][1]
     stage_roofs = {s: {k: v for k, v in roofline(s).items() if k in ("bound", "achieved", "unit",
                                                                     "frac")}
                    for s in stages if s in work and stages[s] > 0}
@@ -581,8 +653,15 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, s, desc = oracle_sample(p, seq, frames=2)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        host = cpu_info()
+        res = oracle_timed(p, seq, frames=2)
+        v, s, desc, used = res["all"]
+        v1, s1, _, _ = res["one"]
+        cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": desc,
+               "cpu_model": host["model"], "nproc": host["nproc"],
+               "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                 "sample_seconds": round(s1, 2)},
+               "all_threads_sample_seconds": round(s, 2)}
 
     if rank == 0:
         form = ("batched BF16 tensor-core MLP, graph-captured" if args.precision == "bf16"
@@ -604,6 +683,7 @@ def main():
             "stages_ms": {k: round(v, 4) for k, v in stages.items()},
             "search": {k: round(v, 2) for k, v in search.items()},
             "plain_fp32": plain,
+            "fp32_fma_probe": fp32_probe,
             "cpu_baseline": cpu,
             "clocks": clocks,
         }

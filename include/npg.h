@@ -302,6 +302,12 @@ NPG_API int npg_set_points(npg_ctx* ctx, const float* points, const int64_t* fra
 #define NPG_BUF_DISP 17       /* FP32 T x N x 3 displacement x-hat - x of the last forward,
                                  formed directly as (R - I) x + d-hat (keeps its relative
                                  precision when the motion is small) */
+#define NPG_BUF_DEVICE_ERROR 18 /* int32 (one value): the device error word that a kernel
+                                 sets when one of its bounded waits gives up. Nonzero
+                                 makes the next call that synchronises return
+                                 NPG_ETIMEOUT (and clears it); npg_get reads it without
+                                 clearing. Settable (e.g. to 0, or to nonzero to exercise
+                                 a caller's own error handling). */
 
 /* Size in bytes of a buffer (0 for an unknown id). */
 NPG_API size_t npg_size(const npg_ctx* ctx, int which);
@@ -414,13 +420,16 @@ NPG_API int npg_precondition_tc(const float* g, float* out, int r, int F, float 
  * not risk the implicit device synchronisation of cudaMalloc / cudaFree. This
  * entry point takes the same arguments and gives the same result as
  * npg_precondition, but allocates and frees nothing: its scratch is one
- * file-scope device array of about 10.5 MB that every GPU which loads
+ * file-scope device array of about 8.5 MB that every GPU which loads
  * libnpg.so holds until the process exits.
- *   - Limit: r <= 512 and r^3 * F <= 1,048,576 (e.g. r = 64 with F = 4);
- *     larger blocks return NPG_EINVAL (use npg_precondition).
+ *   - Limit: r^3 * F <= 1,048,576, hence r <= 101 (e.g. r = 64 with F = 4,
+ *     r = 101 with F = 1); larger blocks return NPG_EINVAL (use
+ *     npg_precondition).
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the
+ *     rest of the process; make that first call before any stream capture,
+ *     and do not call this entry point again after a cudaDeviceReset of that
+ *     device (the kept address would be stale).
  *   - The work is queued on stream and not waited for.
  *   - Every call shares the one array. Calls whose work overlaps on the GPU
  *     (different streams or host threads without ordering) race and corrupt
@@ -428,6 +437,17 @@ NPG_API int npg_precondition_tc(const float* g, float* out, int r, int F, float 
  */
 NPG_API int npg_precondition_static(const float* g, float* out, int r, int F, float lambda,
                                     void* stream);
+
+/*
+ * Measurement helper (no counterpart in the paper): the FP32 FMA rate of the
+ * current device, the peak against which the plain-FP32 stages are placed.
+ * Launches a kernel of 16 independent FMA chains per thread on 8 x 256
+ * threads per SM (one untimed warm-up launch, one launch timed with CUDA
+ * events on stream) and returns *tflops = 2 x FMAs / time in TFLOP/s and
+ * *ms_out (nullable) the timed launch's milliseconds. Allocates 1.2 MB of
+ * output with cudaMallocAsync on stream and synchronizes it.
+ */
+NPG_API int npg_fp32_fma_rate(double* tflops, double* ms_out, void* stream);
 
 #ifdef __cplusplus
 }

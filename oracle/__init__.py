@@ -59,7 +59,10 @@ def build(force: bool = False) -> str:
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
            "-shared", _SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP over independent queries / rows / nodes when the compiler has it
+    # (results do not depend on the thread count); plain serial C otherwise
+    if subprocess.run(cmd[:-1] + ["-fopenmp", "-lm"], capture_output=True).returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -89,6 +92,8 @@ def lib():
                 "or_decode": (None, [cfg, i, i, pd, pd, pd, pd, pd]),
                 "or_nn": (None, [i, pd, i, pd, i, pi32, pd]),
                 "or_chamfer": (None, [i, i, pd, pi64, pd, i, pi32, pd, pi32, pd, pd]),
+                "or_chamfer_from_nn": (None, [i, i, pd, pi64, pd, pi32, pi32, pd]),
+                "or_set_threads": (i, [i]),
                 "or_conf_weights": (None, [i, pd, i, d, d, pd]),
                 "or_edges": (l, [i, pi32, pi32]),
                 "or_edge_lengths": (None, [i, pd, i, l, pi32, pd]),
@@ -263,6 +268,26 @@ def chamfer(xhat, off, pts, decide_f32=False):
     cd, pcd = _out_d(T)
     lib().or_chamfer(T, N, pxh, po, pp, int(bool(decide_f32)), pnnx, pdx, pnnp, pdp, pcd)
     return (nnx.reshape(T, N), dx.reshape(T, N), nnp[:MT], dp[:MT], cd)
+
+
+def chamfer_from_nn(xhat, off, pts, nn_x, nn_p):
+    """Sec. 3.5, Eq. 10's cd_t for given nearest-neighbour choices (nn_x: T x N
+    frame-local point indices, nn_p: one vertex index per point)."""
+    T, N = xhat.shape[0], xhat.shape[1]
+    xh, pxh = _d(xhat)
+    o, po = _i64(off)
+    p, pp = _d(pts)
+    a, pa = _i32(np.asarray(nn_x).reshape(-1))
+    b, pb = _i32(nn_p)
+    cd, pcd = _out_d(T)
+    lib().or_chamfer_from_nn(T, N, pxh, po, pp, pa, pb, pcd)
+    return cd[:T]
+
+
+def set_threads(n=0):
+    """Host threads of the oracle's parallel loops (n <= 0 keeps the current
+    setting); returns the count in effect (1 when built without OpenMP)."""
+    return int(lib().or_set_threads(int(n)))
 
 
 def conf_weights(cd, t_key, e, e_max, delta_mode=0, omega_mode=0):

@@ -42,6 +42,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_MAX_LEVELS 16
 
@@ -69,6 +72,22 @@ typedef struct {
                               direct w = omega(t)^delta with omega 1 constant,
                               2 one half, 3 the single-frame omega(t)        */
 } or_cfg;
+
+/* ---------------------------------------------------------------- threads */
+
+/* Loops over independent queries, rows and lattice nodes may run on several
+ * host threads (OpenMP, when compiled with it); every such loop writes
+ * disjoint outputs and has no reduction, so results do not depend on the
+ * thread count. Returns the thread count in effect (1 without OpenMP). */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------ sizes */
 
@@ -373,23 +392,27 @@ static void transform_row_backward(const or_cfg* c, const double* o, const doubl
  * x-hat[t][i] = R x_i + d (Eq. 5-7). xhat is T x N x 3. */
 void or_decode(const or_cfg* c, int N, int T, const double* x, const double* z,
                const double* gamma, const double* mlp, double* xhat) {
-  int K = or_k_in(c), Z = c->Fn + c->F, G2 = 2 * c->n_freq, O = or_n_out(c);
+  int K = or_k_in(c), Z = c->Fn + c->F, G2 = 2 * c->n_freq;
   int H = c->H, D = c->D;
-  double* y = (double*)malloc(sizeof(double) * K);
-  double* pre = (double*)malloc(sizeof(double) * H * D);
-  double* h = (double*)malloc(sizeof(double) * H * D);
-  double o[8];
-  for (int t = 0; t < T; ++t)
-    for (int i = 0; i < N; ++i) {
-      for (int k = 0; k < Z; ++k) y[k] = z[(long)i * Z + k];
-      for (int k = 0; k < G2; ++k) y[Z + k] = gamma[(long)t * G2 + k];
+  long rows = (long)N * T;
+#pragma omp parallel
+  {
+    double* y = (double*)malloc(sizeof(double) * K);
+    double* pre = (double*)malloc(sizeof(double) * H * D);
+    double* h = (double*)malloc(sizeof(double) * H * D);
+    double o[8];
+#pragma omp for schedule(static)
+    for (long row = 0; row < rows; ++row) {
+      long t = row / N, i = row % N;
+      for (int k = 0; k < Z; ++k) y[k] = z[i * Z + k];
+      for (int k = 0; k < G2; ++k) y[Z + k] = gamma[t * G2 + k];
       mlp_row(c, mlp, y, pre, h, o);
-      (void)O;
-      transform_row(c, o, x + 3L * i, xhat + ((long)t * N + i) * 3);
+      transform_row(c, o, x + 3L * i, xhat + (t * N + i) * 3);
     }
-  free(y);
-  free(pre);
-  free(h);
+    free(y);
+    free(pre);
+    free(h);
+  }
 }
 
 /* ------------------------------------------- Sec. 3.5: Chamfer distance */
@@ -401,6 +424,7 @@ void or_decode(const or_cfg* c, int N, int T, const double* x, const double* z,
  * always the FP64 squared distance of the chosen pair. */
 void or_nn(int nq, const double* q, int nc, const double* cand, int decide_f32,
            int32_t* idx, double* dist) {
+#pragma omp parallel for schedule(dynamic, 64)
   for (int i = 0; i < nq; ++i) {
     const double* a = q + 3L * i;
     int best = -1;
@@ -431,6 +455,33 @@ void or_nn(int nq, const double* q, int nc, const double* cand, int decide_f32,
   }
 }
 
+/* cd_t of Eq. 10's Chamfer term for given nearest-neighbour choices: the mean
+ * squared distance of every vertex to its chosen point plus that of every
+ * point to its chosen vertex, FP64, summed in index order. nn_x is T x N
+ * (frame-local point indices), nn_p follows the point order. */
+void or_chamfer_from_nn(int T, int N, const double* xhat, const int64_t* off, const double* pts,
+                        const int32_t* nn_x, const int32_t* nn_p, double* cd) {
+  for (int t = 0; t < T; ++t) {
+    const double* X = xhat + (long)t * N * 3;
+    long M = off[t + 1] - off[t];
+    const double* P = pts + 3 * off[t];
+    double sx = 0, sp = 0;
+    for (int i = 0; i < N; ++i) {
+      const double* a = X + 3L * i;
+      const double* b = P + 3L * nn_x[(long)t * N + i];
+      double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+      sx += dx * dx + dy * dy + dz * dz;
+    }
+    for (long j = 0; j < M; ++j) {
+      const double* a = P + 3L * j;
+      const double* b = X + 3L * nn_p[off[t] + j];
+      double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+      sp += dx * dx + dy * dy + dz * dz;
+    }
+    cd[t] = sx / N + sp / (double)M;
+  }
+}
+
 /* Per frame t: cd_t = mean_i min_j |x-hat_i - p_j|^2 + mean_j min_i |p_j - x-hat_i|^2.
  * off has T+1 entries; points of frame t are pts[off[t] .. off[t+1]).
  * nn_x, d_x are T x N; nn_p, d_p follow the point order (off[T] entries). */
@@ -443,11 +494,8 @@ void or_chamfer(int T, int N, const double* xhat, const int64_t* off, const doub
     const double* P = pts + 3 * off[t];
     or_nn(N, X, (int)M, P, decide_f32, nn_x + (long)t * N, d_x + (long)t * N);
     or_nn((int)M, P, N, X, decide_f32, nn_p + off[t], d_p + off[t]);
-    double sx = 0, sp = 0;
-    for (int i = 0; i < N; ++i) sx += d_x[(long)t * N + i];
-    for (long j = 0; j < M; ++j) sp += d_p[off[t] + j];
-    cd[t] = sx / N + sp / (double)M;
   }
+  or_chamfer_from_nn(T, N, xhat, off, pts, nn_x, nn_p, cd);
 }
 
 /* ---------------------------------- Sec. 3.5, Eq. 11-12: confidence weight */
@@ -769,6 +817,7 @@ double or_loss_full(const or_cfg* c, int N, const double* x, const double* n, in
 
 /* y = (I + lambda L) u on an r^3 node lattice, one channel (stride F). */
 static void apply_A(int r, int F, int ch, double lambda, const double* u, double* y) {
+#pragma omp parallel for schedule(static)
   for (long iz = 0; iz < r; ++iz)
     for (long iy = 0; iy < r; ++iy)
       for (long ix = 0; ix < r; ++ix) {

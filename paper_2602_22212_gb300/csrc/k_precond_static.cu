@@ -11,12 +11,13 @@
 #include "npg_internal.cuh"
 
 #define NPG_PC_STATIC_MAX_ELEMS (1 << 20)
-#define NPG_PC_STATIC_MAX_R 512
+// r^3 * F <= 2^20 with F >= 1 caps r at floor(cbrt(2^20)) = 101
+#define NPG_PC_STATIC_MAX_R 101
 #define NPG_PC_STATIC_TABLE (2 * NPG_PC_STATIC_MAX_R * NPG_PC_STATIC_MAX_R + NPG_PC_STATIC_MAX_R)
 
 // Two transform buffers of NPG_PC_STATIC_MAX_ELEMS floats, then the DCT
 // tables of one level (C, C^T, mu). Every GPU that loads this library holds
-// this array (about 10 MB) until the process exits.
+// this array (about 8.5 MB) until the process exits.
 static __device__ __align__(256) float g_pc_scratch[2 * NPG_PC_STATIC_MAX_ELEMS +
                                                      NPG_PC_STATIC_TABLE];
 
@@ -40,7 +41,10 @@ __global__ void dct_tables_kernel(float* C, float* Ct, float* mu, int r) {
 }  // namespace npg
 
 static std::mutex g_pc_mutex;
-static float* g_pc_addr[256];  // device address of g_pc_scratch, per device ordinal
+// Device address of g_pc_scratch, per device ordinal, looked up once per
+// process: it stays valid as long as the device's primary context does (a
+// cudaDeviceReset invalidates it; the header says so).
+static float* g_pc_addr[256];
 
 extern "C" int npg_precondition_static(const float* g, float* out, int r, int F, float lambda,
                                        void* stream) {

@@ -829,6 +829,7 @@ extern "C" size_t npg_size(const npg_ctx* c, int which) {
     case NPG_BUF_CD: case NPG_BUF_WCONF: return sizeof(double) * (size_t)c->T;
     case NPG_BUF_DIST_X: return sizeof(float) * NT;
     case NPG_BUF_DIST_P: return sizeof(float) * (size_t)c->MT;
+    case NPG_BUF_DEVICE_ERROR: return sizeof(int32_t);
   }
   return 0;
 }
@@ -856,6 +857,7 @@ static void* plain_buf(npg_ctx* c, int which) {
     case NPG_BUF_WCONF: return c->wconf;
     case NPG_BUF_DIST_X: return c->d_x;
     case NPG_BUF_DIST_P: return c->d_p;
+    case NPG_BUF_DEVICE_ERROR: return c->d_err;
   }
   return nullptr;
 }
@@ -888,7 +890,8 @@ extern "C" int npg_get(npg_ctx* c, int which, void* dst, size_t bytes, int dst_o
     CK(c, cudaMemcpyAsync(dst, plain_buf(c, which), bytes, kind, c->stream));
   }
   CK(c, cudaStreamSynchronize(c->stream));
-  return check_device_error(c);
+  // reading the error word itself reports it without clearing it
+  return which == NPG_BUF_DEVICE_ERROR ? NPG_OK : check_device_error(c);
 }
 
 extern "C" int npg_set(npg_ctx* c, int which, const void* src, size_t bytes, int src_on_device) {
@@ -897,7 +900,8 @@ extern "C" int npg_set(npg_ctx* c, int which, const void* src, size_t bytes, int
   const bool settable = which == NPG_BUF_GRID || which == NPG_BUF_MLP ||
                         which == NPG_BUF_ADAM_M_GRID || which == NPG_BUF_ADAM_V_GRID ||
                         which == NPG_BUF_ADAM_M_MLP || which == NPG_BUF_ADAM_V_MLP ||
-                        which == NPG_BUF_NN_X || which == NPG_BUF_NN_P;
+                        which == NPG_BUF_NN_X || which == NPG_BUF_NN_P ||
+                        which == NPG_BUF_DEVICE_ERROR;
   if (!settable) return set_err(c, NPG_EINVAL, "buffer %d is not settable", which);
   const size_t need = npg_size(c, which);
   if (!src || bytes != need)

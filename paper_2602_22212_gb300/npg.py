@@ -34,9 +34,10 @@ FP32, BF16_MLP = 0, 1
 PRECOND_FP32, PRECOND_TC = 0, 1
 (BUF_GRID, BUF_MLP, BUF_GRID_GRAD, BUF_GRID_PC, BUF_MLP_GRAD, BUF_XHAT, BUF_NN_X, BUF_NN_P,
  BUF_CD, BUF_WCONF, BUF_ADAM_M_GRID, BUF_ADAM_V_GRID, BUF_ADAM_M_MLP, BUF_ADAM_V_MLP,
- BUF_DIST_X, BUF_DIST_P, BUF_DXHAT, BUF_DISP) = range(18)
+ BUF_DIST_X, BUF_DIST_P, BUF_DXHAT, BUF_DISP, BUF_DEVICE_ERROR) = range(19)
 
-_BUF_DTYPE = {BUF_NN_X: np.int32, BUF_NN_P: np.int32, BUF_CD: np.float64, BUF_WCONF: np.float64}
+_BUF_DTYPE = {BUF_NN_X: np.int32, BUF_NN_P: np.int32, BUF_CD: np.float64, BUF_WCONF: np.float64,
+              BUF_DEVICE_ERROR: np.int32}
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -115,6 +116,7 @@ _SIG = {
     "npg_batch_create": (_i, [C.POINTER(_vp), _i, C.POINTER(_vp), _vp]),
     "npg_batch_iteration": (_i, [_vp, _vp]),
     "npg_batch_destroy": (_i, [_vp]),
+    "npg_fp32_fma_rate": (_i, [C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
 }
 for _name, (_res, _args) in _SIG.items():
     _f = getattr(_lib, _name)
@@ -355,6 +357,13 @@ def npg_precondition_static(g, out, r, F, lam, stream=None):
     """Allocation-free npg_precondition (fixed-size scratch; see include/npg.h)."""
     _check(_lib.npg_precondition_static(_ptr(g), _ptr(out), int(r), int(F), float(lam),
                                         _stream_handle(stream)))
+
+
+def npg_fp32_fma_rate(stream=None):
+    """(TFLOP/s, ms) of the FP32 FMA probe on the current device."""
+    t, ms = C.c_double(0), C.c_double(0)
+    _check(_lib.npg_fp32_fma_rate(C.byref(t), C.byref(ms), _stream_handle(stream)))
+    return t.value, ms.value
 
 
 # ----------------------------------------------------------------- convenience

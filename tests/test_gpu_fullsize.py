@@ -139,37 +139,52 @@ def test_search_sampled_queries_bit_exact(run, workload):
         np.testing.assert_array_equal(run.nnp[a + qj], want_p)
 
 
-def loss_terms(run, seq):
-    """cd_t, edge lengths, L_def, L_iso in FP64 from the GPU's x-hat and indices."""
-    T, N = seq.T, seq.N
-    xh = run.xhat.astype(np.float64)
+def test_search_against_fp64_oracle(run, workload):
+    """The nearest-neighbour contract against the FP64 oracle itself: the
+    oracle decodes every vertex of two frames in FP64 from the same
+    parameters and searches by brute force in FP64; the GPU's choice must be
+    the same index, or a tie within 1e-6 of the oracle's squared distance
+    (measured on the oracle's x-hat). The BF16 form's x-hat is not the FP64
+    one (its MLP rounds to 8 bits), so there the FP64 decision runs on the
+    GPU's own x-hat."""
+    p, seq, ocfg = workload
+    rng = np.random.default_rng(9)
     pts = seq.points.astype(np.float64)
-    off = seq.offsets
-    cd = np.zeros(T)
-    for t in range(T):
-        P = pts[off[t]:off[t + 1]]
-        dx = np.sum((xh[t] - P[run.nnx[t]]) ** 2, axis=1)
-        dp = np.sum((P - xh[t][run.nnp[off[t]:off[t + 1]]]) ** 2, axis=1)
-        cd[t] = dx.mean() + dp.mean()
-    # edge vectors from the reference and the displacement: (x_a - x_b) +
-    # (delta_a - delta_b) keeps the length differences' relative precision
-    # when the motion is small (from the rounded x-hat they would drown in
-    # its rounding error)
-    e = O.edges(seq.faces)
     x = seq.x.astype(np.float64)
-    de = x[e[:, 0]] - x[e[:, 1]]
-    dl = run.disp.astype(np.float64)
-    ek = de + dl[seq.t_key][e[:, 0]] - dl[seq.t_key][e[:, 1]]
-    lk = np.linalg.norm(ek, axis=1)
-    iso = 0.0
-    for t in range(T):
-        if t == seq.t_key:
-            continue
-        et = de + dl[t][e[:, 0]] - dl[t][e[:, 1]]
-        lt = np.linalg.norm(et, axis=1)
-        # |l_t - l_k| = |(e_t - e_k) . (e_t + e_k)| / (l_t + l_k), exact in FP64
-        iso += np.abs(np.sum((et - ek) * (et + ek), axis=1) / (lt + lk)).sum()
-    return cd, e, lk, iso / (T * len(e))
+    z = O.encode(ocfg, x, seq.n.astype(np.float64), run.grid0.astype(np.float64))
+    gam = O.time_embedding(ocfg, seq.T)
+    for t in rng.choice(seq.T, size=2, replace=False):
+        a, b = int(seq.offsets[t]), int(seq.offsets[t + 1])
+        P = pts[a:b]
+        if run.form == "fp32":
+            X = O.decode(ocfg, x, z, gam[[t]], run.mlp0.astype(np.float64))[0]
+        else:
+            X = run.xhat[t].astype(np.float64)
+        qi = rng.choice(seq.N, size=300, replace=False)
+        want, dw = O.nn(X[qi], P, decide_f32=False)
+        got = run.nnx[t, qi]
+        dg = np.sum((X[qi] - P[got]) ** 2, axis=1)
+        assert np.all((got == want) | (np.abs(dg - dw) <= 1e-6)), t
+        qj = rng.choice(b - a, size=300, replace=False)
+        want, dw = O.nn(P[qj], X, decide_f32=False)
+        got = run.nnp[a + qj]
+        dg = np.sum((P[qj] - X[got]) ** 2, axis=1)
+        assert np.all((got == want) | (np.abs(dg - dw) <= 1e-6)), t
+
+
+def loss_terms(run, seq):
+    """cd_t, keyframe edge lengths and L_iso by the oracle (Eq. 10 for the GPU's
+    nearest-neighbour choices, Eq. 13), on x-hat = x + delta formed in FP64
+    from the reference and the GPU's displacement: from the FP32-rounded x-hat
+    the edge-length differences would drown in its rounding error when the
+    motion is small."""
+    T, N = seq.T, seq.N
+    xh = seq.x.astype(np.float64)[None] + run.disp.astype(np.float64)
+    pts = seq.points.astype(np.float64)
+    cd = O.chamfer_from_nn(xh, seq.offsets, pts, run.nnx, run.nnp)
+    e = O.edges(seq.faces)
+    lk = O.edge_lengths(xh, seq.t_key, e)
+    return cd, e, lk, O.iso(xh, e, lk)
 
 
 def test_loss_from_gpu_indices(run, workload):
@@ -285,15 +300,11 @@ def test_preconditioner_every_level(run, workload):
         assert rel(run.gpc[a:b], want) <= tol, (l, r, rel(run.gpc[a:b], want))
 
 
-def adam_ref(p0, g, m0, v0, lr, step, b1=0.9, b2=0.999, eps=1e-8):
-    """Adam in FP64 with the FP32 hyper-parameters the library holds (1 - 0.999
-    differs from 1 - float32(0.999) by 1.3e-5 relative)."""
-    b1, b2, eps = (float(np.float32(v)) for v in (b1, b2, eps))
-    p0, g, m0, v0 = (np.asarray(a, np.float64) for a in (p0, g, m0, v0))
-    m = b1 * m0 + (1 - b1) * g
-    v = b2 * v0 + (1 - b2) * g * g
-    c1, c2 = 1 - b1 ** step, 1 - b2 ** step
-    return p0 - lr * (m / c1) / (np.sqrt(v / c2) + eps), m, v
+def adam_ref(p0, g, m0, v0, lr, step):
+    """The oracle's Adam with the FP32 hyper-parameters the library holds
+    (1 - 0.999 differs from 1 - float32(0.999) by 1.3e-5 relative)."""
+    b1, b2, eps = (float(np.float32(v)) for v in (0.9, 0.999, 1e-8))
+    return O.adam(p0, g, m0, v0, lr, step, b1=b1, b2=b2, eps=eps)
 
 
 def test_adam_sampled_parameters(run, workload):

@@ -259,6 +259,37 @@ def test_chamfer_invariants():
     assert abs(cd - ref) < 1e-13
 
 
+def test_chamfer_from_given_indices_and_thread_count():
+    """cd from given nearest-neighbour choices: with the cKDTree choices it is
+    the Chamfer distance; any other choice only raises it. The brute-force
+    search returns the same indices on 1 and on all host threads."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(14)
+    X = rng.uniform(-1, 1, size=(2, 60, 3))
+    P = rng.uniform(-1, 1, size=(130, 3))
+    off = np.array([0, 70, 130])
+    nnx = np.stack([cKDTree(P[off[t]:off[t + 1]]).query(X[t])[1] for t in range(2)])
+    nnp = np.concatenate([cKDTree(X[t]).query(P[off[t]:off[t + 1]])[1] for t in range(2)])
+    cd = O.chamfer_from_nn(X, off, P, nnx, nnp)
+    for t in range(2):
+        Pt = P[off[t]:off[t + 1]]
+        ref = (np.mean(cKDTree(Pt).query(X[t])[0] ** 2) +
+               np.mean(cKDTree(X[t]).query(Pt)[0] ** 2))
+        assert abs(cd[t] - ref) < 1e-13
+    worse = O.chamfer_from_nn(X, off, P, (nnx + 1) % 70 % 60, (nnp + 1) % 60)
+    assert np.all(worse > cd)
+    n0 = O.set_threads()
+    try:
+        O.set_threads(1)
+        one = O.chamfer(X, off, P)
+        O.set_threads(max(n0, 4))
+        many = O.chamfer(X, off, P)
+    finally:
+        O.set_threads(n0)
+    for a, b in zip(one, many):
+        np.testing.assert_array_equal(a, b)
+
+
 # ---------------------------------------------------------------- Sec. 3.5 weights, iso
 
 def test_confidence_weights_golden_and_invariants():
@@ -412,6 +443,78 @@ def test_iteration_decreases_chamfer():
     cds = [O.iteration(prob, st, 20, lr, 1e-3, lam)["cd"].mean() for _ in range(8)]
     assert cds[-1] < cds[0]
     assert st.e == 8
+
+
+def _dct_precondition(r, F, lam, g):
+    """(I + lam L)^-2 g per channel through scipy's orthonormal 3-D DCT-II: the
+    Neumann lattice Laplacian is diagonal there with eigenvalues
+    sum_axes (2 - 2 cos(pi k / r)). Independent of the oracle's CG solve."""
+    from scipy.fft import dctn, idctn
+    k = np.arange(r)
+    mu1 = 2.0 - 2.0 * np.cos(np.pi * k / r)
+    mu = mu1[:, None, None] + mu1[None, :, None] + mu1[None, None, :]
+    out = np.empty_like(g)
+    for ch in range(F):
+        x = g[ch::F].reshape(r, r, r)
+        out[ch::F] = idctn(dctn(x, norm="ortho") / (1.0 + lam * mu) ** 2, norm="ortho").ravel()
+    return out
+
+
+def test_iteration_first_adam_step_hand_worked():
+    """One whole iteration (Sec. 3.5: Eq. 9, then Adam with the per-level rates
+    of the implementation details) from zero Adam moments at e = 5.
+
+    Hand-worked: with m = v = 0 the update of step s is
+      dp = -lr (1 - b1)/(1 - b1^s) g / (sqrt((1 - b2)/(1 - b2^s)) |g| + eps),
+    i.e. |dp| = lr * 0.5221178227 for s = e + 1 = 6 (it would be 0.5454892500
+    for s = e = 5), against the sign of g. So every grid value of level l
+    (0-based, coarsest first) must move by exactly 0.005 * 2.5^l * 0.52211782
+    against the *preconditioned* gradient, the normal grid by 0.005 * 0.52211782,
+    the MLP by 1e-3 * 0.52211782 against its raw gradient. The preconditioned
+    gradient is recomputed here by a DCT solve with lambda_l = 0.4 * 1.5^l: it
+    moves nodes whose raw gradient is 0 and flips the sign of others, so a raw
+    gradient passed to Adam, a level index off by one or the step count e
+    fails a check."""
+    seq = I.sphere_blob(subdiv=2, T=3, M=300, seed=5)
+    cfg = O.make_cfg(L=2, res=(5, 9), F=2, H=16, D=2, slope=0.01)
+    prob = O.Problem(cfg, seq.x, seq.n, seq.faces, seq.points, seq.offsets, seq.t_key)
+    rng = np.random.default_rng(7)
+    grid0 = rng.normal(scale=0.05, size=O.grid_len(cfg))
+    mlp0 = I.mlp_init(O.k_in(cfg), 16, 2, O.n_out(cfg), seed=3, zero_last=False)
+    st = O.State(prob, grid0, mlp0)
+    st.e = 5
+    lr = [0.005 * 2.5 ** l for l in range(cfg.L)] + [0.005]
+    lam = [0.4 * 1.5 ** l for l in range(cfg.L)] + [0.4]
+    # eps far below every |g| checked, so that |dp| is lr * 0.52211782 to 1e-6
+    out = O.iteration(prob, st, 20, lr, 1e-3, lam, eps=1e-14)
+    assert st.e == 6
+    ratio = 0.5221178227443565
+    moved_zero, flipped = 0, 0
+    for l in range(cfg.L + 1):
+        r = cfg.res[l] if l < cfg.L else cfg.rn
+        F = cfg.F if l < cfg.L else cfg.Fn
+        o, n = O.level_offset(cfg, l), r ** 3 * F
+        g = out["g_grid"][o:o + n]
+        gt = out["g_grid_pc"][o:o + n]
+        want_gt = _dct_precondition(r, F, lam[l], g)
+        np.testing.assert_allclose(gt, want_gt, rtol=0, atol=1e-10 * np.abs(want_gt).max())
+        d = st.grid[o:o + n] - grid0[o:o + n]
+        big = np.abs(gt) > max(1e-7, 1e-4 * np.abs(gt).max())
+        assert big.sum() > n // 2
+        np.testing.assert_allclose(np.abs(d[big]), lr[l] * ratio, rtol=1e-6)
+        assert np.all(np.sign(d[big]) == -np.sign(gt[big]))
+        moved_zero += int(np.sum(big & (g == 0)))
+        flipped += int(np.sum(big & (np.sign(g) * np.sign(gt) < 0)))
+    assert moved_zero > 0 and flipped > 0
+    gm = out["g_mlp"]
+    dm = st.mlp - mlp0
+    bigm = np.abs(gm) > 1e-7
+    assert bigm.sum() > len(gm) // 2
+    np.testing.assert_allclose(np.abs(dm[bigm]), 1e-3 * ratio, rtol=1e-5)
+    assert np.all(np.sign(dm[bigm]) == -np.sign(gm[bigm]))
+    # the loss is that of the parameters before the update, at e = 5
+    ref = O.loss_full(prob, grid0, mlp0, 5, 20, want_grad=False)
+    assert abs(out["loss"] - ref["loss"]) <= 1e-13 * abs(ref["loss"])
 
 
 # ---------------------------------------------------------------- Sec. 4 metrics

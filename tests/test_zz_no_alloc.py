@@ -8,6 +8,7 @@ reuses the same file-scope scratch array whose contents the previous call left.
 This file is collected last on purpose.
 """
 import ctypes as C
+import os
 
 import numpy as np
 import pytest
@@ -15,8 +16,15 @@ import pytest
 
 @pytest.fixture(scope="module")
 def npg():
+    """The binding; builds libnpg.so when nvcc is available, else uses the
+    library already built, else skips (the argument checks need no GPU but do
+    need the library)."""
+    import shutil
     from paper_2602_22212_gb300 import build
-    build.build()
+    if shutil.which(build.NVCC) is not None:
+        build.build()
+    elif not os.path.exists(build.LIB):
+        pytest.skip("neither nvcc nor a built libnpg.so is available")
     from paper_2602_22212_gb300 import npg as mod
     return mod
 
@@ -45,6 +53,14 @@ def test_static_matches_allocating_entry_point_twice_in_a_row(npg):
         w, o = want.cpu().numpy().astype(np.float64), got.cpu().numpy().astype(np.float64)
         assert np.all(np.isfinite(o))
         assert _rel(o, w) <= 2e-6
+    # a further call allocates nothing: the device's free memory is unchanged
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    rc = npg._lib.npg_precondition_static(C.c_void_p(g.data_ptr()), C.c_void_p(got.data_ptr()),
+                                          r, F, C.c_float(lam), C.c_void_p(s.cuda_stream))
+    assert rc == npg.OK, npg.npg_last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_static_rejects_blocks_beyond_its_scratch(npg):
@@ -53,3 +69,5 @@ def test_static_rejects_blocks_beyond_its_scratch(npg):
     assert rc == npg.EINVAL
     assert "static scratch limit" in npg.npg_last_error()
     assert npg._lib.npg_precondition_static(x, x, 600, 1, C.c_float(0.4), None) == npg.EINVAL
+    # r = 102 with F = 1 is past the cube root of the limit
+    assert npg._lib.npg_precondition_static(x, x, 102, 1, C.c_float(0.4), None) == npg.EINVAL
