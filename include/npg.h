@@ -94,8 +94,9 @@ typedef struct npg_ctx npg_ctx; /* opaque; owns all device memory it allocates *
  *   F_p, F_n, res_n  features per position node (1..32), per normal node
  *                    (1..8), nodes per axis of the normal grid (Sec. 3.2).
  *   H, depth         hidden width and number of hidden layers (Sec. 3.3);
- *                    NPG_FP32 supports H in {16, 32, 64}, NPG_BF16_MLP
- *                    H = 64 with depth 3; depth 1..8.
+ *                    NPG_FP32 supports H in {16, 32, 64} and multiples of 32
+ *                    in (64, 512] (the paper's own network is 512 wide),
+ *                    NPG_BF16_MLP H in {64, 128} with depth 3; depth 1..8.
  *   leaky_slope      LeakyReLU negative slope (0 = ReLU).
  *   rot_mode         NPG_ROT_QUAT, NPG_ROT_EXPMAP or NPG_ROT_CAYLEY.
  *   n_freq           Fourier frequencies M (Eq. 3; 1..8).

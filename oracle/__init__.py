@@ -103,6 +103,7 @@ def lib():
                 "or_loss_full": (d, [cfg, i, pd, pd, i, pi64, pd, l, pi32, i, d, d, pd, pd, i,
                                      pd, pd, pd, pd, pd, pd, pi32, pi32, pd]),
                 "or_backprop": (None, [cfg, i, pd, pd, i, pd, pd, pd, pd, pd]),
+                "or_backprop_magnitude": (None, [cfg, i, pd, pd, i, pd, pd, pd, pd, pd]),
                 "or_precondition": (i, [i, i, d, pd, pd, d, i]),
                 "or_adam": (None, [l, pd, pd, pd, pd, d, d, d, d, i]),
                 "or_iteration": (d, [cfg, i, pd, pd, i, pi64, pd, l, pi32, i, i, i, pd, pd, pd,
@@ -397,9 +398,13 @@ def loss_full(prob: Problem, grid, mlp, e, e_max, decide_f32=False, want_grad=Tr
                 nn_p=nnp[:MT], g_xhat=gx.reshape(T, N, 3))
 
 
-def backprop(prob: Problem, grid, mlp, g_xhat):
+def backprop(prob: Problem, grid, mlp, g_xhat, magnitude=False):
     """Parameter gradient of a given dL/dx-hat (T x N x 3): the reverse pass
-    through Eq. 7-5, Eq. 4, Eq. 2 and Eq. 1."""
+    through Eq. 7-5, Eq. 4, Eq. 2 and Eq. 1. magnitude=True returns instead
+    the sums of the absolute values of the products that make up each
+    gradient value (dL/do, weights, activations and inputs taken by absolute
+    value): the scale against which rounding errors of the operands are
+    bounded."""
     c, N, T = prob.cfg, prob.N, prob.T
     _, px = _d(prob.x)
     _, pn = _d(prob.n)
@@ -408,7 +413,8 @@ def backprop(prob: Problem, grid, mlp, g_xhat):
     gx, pgx = _d(np.asarray(g_xhat).reshape(-1))
     gg, pgg = _out_d(grid_len(c))
     gm, pgm = _out_d(mlp_len(c))
-    lib().or_backprop(C.byref(c), N, px, pn, T, pg, pm, pgx, pgg, pgm)
+    fn = lib().or_backprop_magnitude if magnitude else lib().or_backprop
+    fn(C.byref(c), N, px, pn, T, pg, pm, pgx, pgg, pgm)
     return gg, gm
 
 

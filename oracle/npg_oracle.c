@@ -606,10 +606,15 @@ double or_iso(int T, int N, const double* xhat, long E, const int32_t* edges,
 
 /* Reverse pass from a given dL/dx-hat (T x N x 3): back through Eq. 7-5, the
  * MLP (Eq. 4), the input vector (Eq. 2), the trilinear lookups and the level
- * mean (Eq. 1). g_grid and g_mlp (nullable) are overwritten. */
-void or_backprop(const or_cfg* c, int N, const double* x, const double* n, int T,
-                 const double* grid, const double* mlp, const double* gx, double* g_grid,
-                 double* g_mlp) {
+ * mean (Eq. 1). g_grid and g_mlp (nullable) are overwritten.
+ * With mag != 0 the same pass runs on magnitudes: dL/do, the weights, the
+ * activations and the inputs enter by their absolute values, so every output
+ * is the sum of |each product| that makes up the true gradient (the usual
+ * companion computation of a forward rounding-error bound: an operand rounding
+ * of relative size u perturbs each gradient value by at most u times it). */
+static void backprop_impl(const or_cfg* c, int N, const double* x, const double* n, int T,
+                          const double* grid, const double* mlp, const double* gx,
+                          double* g_grid, double* g_mlp, int mag) {
   int F = c->F, Fn = c->Fn, Z = Fn + F, G2 = 2 * c->n_freq, K = or_k_in(c);
   int H = c->H, D = c->D, O = or_n_out(c);
   double* z = (double*)malloc(sizeof(double) * (size_t)N * Z);
@@ -625,12 +630,18 @@ void or_backprop(const or_cfg* c, int N, const double* x, const double* n, int T
   double* dh = (double*)malloc(sizeof(double) * H);
   double* dp = (double*)malloc(sizeof(double) * H);
   double o[8], go[8];
+#define W(idx) (mag ? fabs(mlp[idx]) : mlp[idx])
   for (int t = 0; t < T; ++t)
     for (int i = 0; i < N; ++i) {
       for (int k = 0; k < Z; ++k) y[k] = z[(long)i * Z + k];
       for (int k = 0; k < G2; ++k) y[Z + k] = gamma[(long)t * G2 + k];
       mlp_row(c, mlp, y, pre, h, o);
       transform_row_backward(c, o, x + 3L * i, gx + ((long)t * N + i) * 3, go);
+      if (mag) {
+        for (int j = 0; j < O; ++j) go[j] = fabs(go[j]);
+        for (int k = 0; k < H * D; ++k) h[k] = fabs(h[k]);
+        for (int k = 0; k < K; ++k) y[k] = fabs(y[k]);
+      }
       /* layer offsets in the flat parameter vector */
       long offW0 = 0, offb0 = (long)H * K;
       long offHid = offb0 + H; /* hidden layer k>=1 at offHid + (k-1)(H*H+H) */
@@ -642,7 +653,7 @@ void or_backprop(const or_cfg* c, int N, const double* x, const double* n, int T
         gm[offbo + j] += go[j];
         for (int k = 0; k < H; ++k) {
           gm[offWo + (long)j * H + k] += go[j] * hl[k];
-          dh[k] += mlp[offWo + (long)j * H + k] * go[j];
+          dh[k] += W(offWo + (long)j * H + k) * go[j];
         }
       }
       /* hidden layers D-1 .. 1 */
@@ -655,7 +666,7 @@ void or_backprop(const or_cfg* c, int N, const double* x, const double* n, int T
           gm[offb + j] += dp[j];
           for (int k = 0; k < H; ++k) {
             gm[offW + (long)j * H + k] += dp[j] * hin[k];
-            dh[k] += mlp[offW + (long)j * H + k] * dp[j];
+            dh[k] += W(offW + (long)j * H + k) * dp[j];
           }
         }
       }
@@ -664,9 +675,10 @@ void or_backprop(const or_cfg* c, int N, const double* x, const double* n, int T
       for (int j = 0; j < H; ++j) {
         gm[offb0 + j] += dp[j];
         for (int k = 0; k < K; ++k) gm[offW0 + (long)j * K + k] += dp[j] * y[k];
-        for (int k = 0; k < Z; ++k) gz[(long)i * Z + k] += mlp[offW0 + (long)j * K + k] * dp[j];
+        for (int k = 0; k < Z; ++k) gz[(long)i * Z + k] += W(offW0 + (long)j * K + k) * dp[j];
       }
     }
+#undef W
   if (g_mlp) memcpy(g_mlp, gm, sizeof(double) * (size_t)or_mlp_len(c));
 
   /* back through the trilinear lookups and the level mean (Eq. 1) */
@@ -689,6 +701,19 @@ void or_backprop(const or_cfg* c, int N, const double* x, const double* n, int T
     }
   }
   free(gm); free(gz); free(y); free(pre); free(h); free(dh); free(dp); free(z); free(gamma);
+}
+
+void or_backprop(const or_cfg* c, int N, const double* x, const double* n, int T,
+                 const double* grid, const double* mlp, const double* gx, double* g_grid,
+                 double* g_mlp) {
+  backprop_impl(c, N, x, n, T, grid, mlp, gx, g_grid, g_mlp, 0);
+}
+
+/* The magnitude companion of or_backprop (see backprop_impl). */
+void or_backprop_magnitude(const or_cfg* c, int N, const double* x, const double* n, int T,
+                           const double* grid, const double* mlp, const double* gx,
+                           double* g_grid, double* g_mlp) {
+  backprop_impl(c, N, x, n, T, grid, mlp, gx, g_grid, g_mlp, 1);
 }
 
 /* L = L_def + w_iso L_iso (Eq. 8, 10, 13) with the stop-grad quantities held

@@ -380,6 +380,7 @@ static cudaError_t mlp_bwd_h(npg_ctx* c) {
 }
 
 cudaError_t launch_mlp_backward_fp32(npg_ctx* c) {
+  if (c->md.H > 64) return launch_mlp_backward_fp32_wide(c);
   const int rm = c->cfg.rot_mode;
 #define NPG_BWD_H(HH)                                                                       \
   case HH:                                                                                  \

@@ -262,6 +262,7 @@ static cudaError_t decode_fp32_h(npg_ctx* c) {
 
 cudaError_t launch_decode_fp32(npg_ctx* c) {
   const int H = c->md.H;
+  if (H > 64) return launch_decode_fp32_wide(c);
   const int rm = c->cfg.rot_mode;
 #define NPG_DECODE_H(HH)                                                                    \
   if (H == HH)                                                                              \

@@ -7,20 +7,14 @@
 // thread t owns row t of the tile and TMEM lane t. One elected thread issues
 // the MMAs; completion is tracked by an mbarrier whose waits are bounded: a
 // wait that gives up sets *err and the CTA frees its TMEM and exits.
-#include <cuda_bf16.h>
-
-#include "npg_device.cuh"
-#include "npg_internal.cuh"
-#include "tc_sm100.cuh"
+#include "mlp_tc_common.cuh"
 
 namespace npg {
 
 constexpr int TC_H = 64;
-constexpr int TC_ROWS = 128;
-constexpr uint32_t TC_TILE = TC_ROWS * 128;  // bytes of one [128][64] BF16 swizzled tile
-constexpr uint32_t WAIT_TRIES = 1u << 24;
 
-bool decode_bf16_supported(int H, int D) { return H == TC_H && D == 3; }
+// Hidden width 64 here, 128 in k_mlp_tc128.cu; three hidden layers.
+bool decode_bf16_supported(int H, int D) { return (H == TC_H || H == 128) && D == 3; }
 
 // Write 64 FP32 values of one row as BF16 into a K-major swizzled tile.
 __device__ __forceinline__ void st_row64(uint8_t* tile, int row, const float* v) {
@@ -35,10 +29,6 @@ __device__ __forceinline__ void st_row64(uint8_t* tile, int row, const float* v)
   }
 }
 
-__device__ __forceinline__ void st_bf16(uint8_t* tile, int row, int col, float v) {
-  *reinterpret_cast<__nv_bfloat16*>(tile + tc::sw128_off(row, col)) = __float2bfloat16_rn(v);
-}
-
 // Issue D = A * B^T with K = 64 (4 steps of 16), K-major operands.
 __device__ __forceinline__ void mma_k64(uint32_t d, uint32_t a_smem, uint32_t b_smem,
                                         uint32_t idesc) {
@@ -47,23 +37,6 @@ __device__ __forceinline__ void mma_k64(uint32_t d, uint32_t a_smem, uint32_t b_
     tc::mma_bf16(d, tc::kmajor_sw128(a_smem + 32 * ks), tc::kmajor_sw128(b_smem + 32 * ks),
                  idesc, ks > 0);
 }
-
-struct TcArgs {
-  const float* mlp;
-  const float* U;
-  const float* V;
-  const float4* xr;
-  float4* xhat;
-  float4* disp;
-  const float4* dxhat;
-  const float* z;
-  const float* gamma;  // T x 2M time encoding
-  float* g_mlp;
-  float* dz;
-  int* err;
-  int N, T, K, Z, M, NO;
-  float slope, alpha;
-};
 
 // Shared layout of the decode kernel (offsets from a 1024-byte aligned base).
 struct DecodeSmem {
@@ -211,39 +184,8 @@ __global__ void __launch_bounds__(128) decode_tc_kernel(TcArgs a) {
   if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
-static int tc_blocks(npg_ctx* c, long long tiles, int per_sm) {
-  long long b = (long long)c->num_sms * per_sm;
-  if (b > tiles) b = tiles;
-  if (b < 1) b = 1;
-  return (int)b;
-}
-
-static TcArgs tc_args(npg_ctx* c) {
-  TcArgs a;
-  a.mlp = c->mlp;
-  a.U = c->U;
-  a.V = c->V;
-  a.xr = c->xr;
-  a.xhat = c->xhat;
-  a.disp = c->disp;
-  a.dxhat = c->dxhat;
-  a.z = c->z;
-  a.g_mlp = c->g_mlp;
-  a.dz = c->dz;
-  a.err = c->d_err;
-  a.N = c->N;
-  a.T = c->T;
-  a.K = c->md.K;
-  a.Z = c->md.Z;
-  a.M = c->md.M;
-  a.gamma = c->gamma;
-  a.NO = c->md.NO;
-  a.slope = c->md.slope;
-  a.alpha = c->cfg.alpha;
-  return a;
-}
-
 cudaError_t launch_decode_bf16(npg_ctx* c) {
+  if (c->md.H == 128) return launch_decode_bf16_h128(c);
   const size_t smem = DecodeSmem::TOTAL + 1024;
   auto k = c->cfg.rot_mode == NPG_ROT_QUAT     ? decode_tc_kernel<0>
            : c->cfg.rot_mode == NPG_ROT_EXPMAP ? decode_tc_kernel<1>
@@ -251,7 +193,7 @@ cudaError_t launch_decode_bf16(npg_ctx* c) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long tiles = ((long long)c->N * c->T + TC_ROWS - 1) / TC_ROWS;
-  k<<<tc_blocks(c, tiles, 6), 128, smem, c->stream>>>(tc_args(c));
+  k<<<tc_grid(c, tiles, 6), 128, smem, c->stream>>>(make_tc_args(c));
   return cudaGetLastError();
 }
 
@@ -311,26 +253,6 @@ constexpr int BWD_THREADS = 512;
 
 bool backward_bf16_supported(int K, int Z) { return K <= 15 && Z <= 8; }
 
-// Every thread polls the barrier; the outcome is folded into the next
-// CTA-wide barrier (tc_sync_ok), so a wait that gives up ends the kernel
-// uniformly without an extra barrier per wait.
-__device__ __forceinline__ void tc_wait(uint64_t* bar, uint32_t& phase, bool& ok) {
-  ok = ok && tc::mbar_wait(bar, phase, WAIT_TRIES);
-  phase ^= 1u;
-  tc::fence_after_sync();
-}
-
-// Shared-memory writes -> async proxy, TMEM reads complete, then a CTA
-// barrier that also agrees on `ok`.
-__device__ __forceinline__ bool tc_sync_ok(bool ok, int* err) {
-  tc::fence_async_smem();
-  tc::fence_before_sync();
-  ok = __syncthreads_and(ok) != 0;
-  tc::fence_after_sync();
-  if (!ok && threadIdx.x == 0) atomicExch(err, 1);
-  return ok;
-}
-
 // 16 FP32 values as BF16 into columns [c0, c0 + 16) of a row of a K-major tile.
 __device__ __forceinline__ void st_row16(uint8_t* tile, int row, int c0, const float* v) {
 #pragma unroll
@@ -342,14 +264,6 @@ __device__ __forceinline__ void st_row16(uint8_t* tile, int row, int c0, const f
     q.w = tc::pack_bf16(v[8 * h + 6], v[8 * h + 7]);
     *reinterpret_cast<uint4*>(tile + tc::sw128_off(row, c0 + 8 * h)) = q;
   }
-}
-
-__device__ __forceinline__ void ld_col16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  tc::tmem_ld16(taddr, r);
-  tc::tmem_ld_wait();
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // D (128 x N) += A^T B with A, B MN-major [128 rows][64] tiles placed 16 KB
@@ -792,6 +706,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
 }
 
 cudaError_t launch_mlp_backward_bf16(npg_ctx* c) {
+  if (c->md.H == 128) return launch_mlp_backward_bf16_h128(c);
   const size_t smem = BwdSmem::TOTAL + 1024;
   auto k = c->cfg.rot_mode == NPG_ROT_QUAT     ? mlp_bwd_tc_kernel<0>
            : c->cfg.rot_mode == NPG_ROT_EXPMAP ? mlp_bwd_tc_kernel<1>
@@ -800,7 +715,7 @@ cudaError_t launch_mlp_backward_bf16(npg_ctx* c) {
   if (e != cudaSuccess) return e;
   const long long tiles = (long long)((c->N + 15) / 16) * ((c->T + 7) / 8);
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;  // tile indices are ints
-  k<<<tc_blocks(c, tiles, 1), BWD_THREADS, smem, c->stream>>>(tc_args(c));
+  k<<<tc_grid(c, tiles, 1), BWD_THREADS, smem, c->stream>>>(make_tc_args(c));
   return cudaGetLastError();
 }
 

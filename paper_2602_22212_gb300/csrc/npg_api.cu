@@ -330,15 +330,17 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
   if ((long long)mlp_len != c->mlp_len)
     return fail(set_err(c, NPG_EINVAL, "mlp_len %zu != expected %lld", mlp_len, c->mlp_len));
   if (cfg->precision == NPG_FP32) {
-    if (!decode_fp32_supported(md.H, md.D))
-      return fail(set_err(c, NPG_ENOTIMPL, "FP32 path supports H in {16,32,64}, got %d", md.H));
-    if (mlp_bwd_fp32_smem(md) > 227 * 1024)
+    if (!decode_fp32_supported(md.H, md.D) && !wide_fp32_supported(md.H))
+      return fail(set_err(c, NPG_ENOTIMPL,
+                          "FP32 path supports H in {16,32,64} or a multiple of 32 in (64, 512], "
+                          "got %d", md.H));
+    if (md.H <= 64 && mlp_bwd_fp32_smem(md) > 227 * 1024)
       return fail(set_err(c, NPG_ENOTIMPL, "FP32 backward needs %zu B shared memory (H=%d depth=%d)",
                           mlp_bwd_fp32_smem(md), md.H, md.D));
   } else if (cfg->precision == NPG_BF16_MLP) {
     if (!decode_bf16_supported(md.H, md.D) || !backward_bf16_supported(md.K, md.Z))
       return fail(set_err(c, NPG_ENOTIMPL,
-                          "BF16 path supports H = 64, depth 3, F_n + F_p + 2 n_freq <= 15; "
+                          "BF16 path supports H in {64, 128}, depth 3, F_n + F_p + 2 n_freq <= 15; "
                           "got H=%d depth=%d K=%d", md.H, md.D, md.K));
   } else {
     return fail(set_err(c, NPG_EINVAL, "precision=%d", cfg->precision));
@@ -449,6 +451,8 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
   ok &= alloc_n(c, c->mlp, c->mlp_len) && alloc_n(c, c->g_mlp, c->mlp_len) &&
         alloc_n(c, c->m_mlp, c->mlp_len) && alloc_n(c, c->v_mlp, c->mlp_len);
   ok &= alloc_n(c, c->pc_tmp0, c->max_level_n) && alloc_n(c, c->pc_tmp1, c->max_level_n);
+  if (cfg->precision == NPG_FP32 && md.H > 64)
+    ok &= alloc_n(c, c->wide, wide_fp32_scratch_floats(md.H, md.D, md.K, NT, &c->wide_rows));
   ok &= alloc_n(c, c->nnq_p.counters, 4) && alloc_n(c, c->nnq_p.items, c->MT_cap);
   c->nnq_p.far_blocks = c->num_sms * 16;
   // levels to lanes, largest first onto the least loaded lane; each lane's

@@ -112,6 +112,8 @@ struct npg_ctx {
   float* m_mlp = nullptr;
   float* v_mlp = nullptr;
   float* mlp_bf16 = nullptr;  // packed tensor-core weights (BF16 path)
+  float* wide = nullptr;      // FP32 path with H > 64: per-chunk activations and gradients
+  long long wide_rows = 0;    // rows per chunk of that path
 
   // preconditioner tables and scratch
   float* dct = nullptr;          // per level: C (r x r) then C^T (r x r) then mu (r)
@@ -169,6 +171,7 @@ cudaError_t launch_time_table(npg_ctx* c);
 cudaError_t launch_time_mod(npg_ctx* c);
 cudaError_t launch_decode_fp32(npg_ctx* c);
 cudaError_t launch_decode_bf16(npg_ctx* c);
+cudaError_t launch_decode_bf16_h128(npg_ctx* c);
 
 cudaError_t bucket_build(const float4* pts, const long long* d_off, long long uniform_count,
                          int nsets, long long total, int G, Buckets& b, cudaStream_t s);
@@ -180,7 +183,16 @@ cudaError_t launch_nn(const float4* queries_sorted, long long q_uniform, const l
 cudaError_t launch_loss(npg_ctx* c);
 cudaError_t launch_dxhat(npg_ctx* c);
 cudaError_t launch_mlp_backward_fp32(npg_ctx* c);
+// FP32 MLP for hidden widths beyond 64 (k_mlp_fp32_wide.cu): rows in chunks of
+// at most WIDE_CHUNK, layer by layer through a scratch area of
+// wide_fp32_scratch_floats() floats (c->wide, c->wide_rows rows per chunk).
+constexpr long long WIDE_CHUNK = 262144;
+bool wide_fp32_supported(int H);
+long long wide_fp32_scratch_floats(int H, int D, int K, long long rows, long long* chunk_rows);
+cudaError_t launch_decode_fp32_wide(npg_ctx* c);
+cudaError_t launch_mlp_backward_fp32_wide(npg_ctx* c);
 cudaError_t launch_mlp_backward_bf16(npg_ctx* c);
+cudaError_t launch_mlp_backward_bf16_h128(npg_ctx* c);
 cudaError_t launch_scatter(npg_ctx* c);
 cudaError_t launch_precondition(const float* g, float* out, float* tmp0, float* tmp1,
                                 const float* C, const float* Ct, const float* mu, int r, int F,

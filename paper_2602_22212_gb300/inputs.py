@@ -340,6 +340,10 @@ def preset(name):
         return dict(gen="figure", subdiv=6, T=100, M=20000, noise_rel=0.003, L=8,
                     res=linear_resolutions(8, 16, 256), F=4, H=64, D=3, slope=0.01, iters=500,
                     w_iso=1.0)
+    if name == "long":      # 20000 vertices, 1000 frames, 10000 points per frame, MLP 3 x 128
+        return dict(gen="figure", n_vertices=20000, T=1000, M=10000, noise_rel=0.003, L=8,
+                    res=linear_resolutions(8, 16, 256), F=4, H=128, D=3, slope=0.01, iters=300,
+                    w_iso=1.0)
     if name == "profile":   # 10242 vertices, 10 frames, 20000 points: search kernels at moderate size
         return dict(gen="figure", subdiv=5, T=10, M=20000, noise_rel=0.003, L=4,
                     res=linear_resolutions(4, 16, 64), F=4, H=64, D=3, slope=0.01, iters=500,
@@ -368,4 +372,5 @@ def make_batch_sequence(spec):
 def make_sequence(p, seed=0):
     if p["gen"] == "sphere_blob":
         return sphere_blob(subdiv=p["subdiv"], T=p["T"], M=p["M"], noise=p["noise"], seed=seed)
-    return figure(subdiv=p["subdiv"], T=p["T"], M=p["M"], noise_rel=p["noise_rel"], seed=seed)
+    return figure(subdiv=p.get("subdiv", 6), T=p["T"], M=p["M"], noise_rel=p["noise_rel"],
+                  seed=seed, n_vertices=p.get("n_vertices"))

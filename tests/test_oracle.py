@@ -369,6 +369,30 @@ def test_gradient_matches_central_differences(rot_mode):
     assert np.linalg.norm(gg) > 0 and np.linalg.norm(gm) > 0
 
 
+def test_backprop_magnitude_bounds_the_gradient():
+    """The magnitude companion of the reverse pass sums |each product|: it
+    bounds every gradient value from above (triangle inequality), equals it
+    where a value is made of one product (the output bias of a single row), and
+    scales with |dL/dx-hat|."""
+    prob, grid, mlp = _fd_problem(0)
+    rng = np.random.default_rng(21)
+    gx = rng.normal(size=(prob.T, prob.N, 3))
+    gg, gm = O.backprop(prob, grid, mlp, gx)
+    mg, mm = O.backprop(prob, grid, mlp, gx, magnitude=True)
+    assert np.all(np.abs(gg) <= mg * (1 + 1e-12) + 1e-300)
+    assert np.all(np.abs(gm) <= mm * (1 + 1e-12) + 1e-300)
+    assert np.sum(mm) > 1.5 * np.sum(np.abs(gm))  # the sums do cancel
+    mg2, mm2 = O.backprop(prob, grid, mlp, -3.0 * gx, magnitude=True)
+    np.testing.assert_allclose(mg2, 3.0 * mg, rtol=1e-12)
+    np.testing.assert_allclose(mm2, 3.0 * mm, rtol=1e-12)
+    one = np.zeros_like(gx)
+    one[1, 2] = gx[1, 2]
+    _, gm1 = O.backprop(prob, grid, mlp, one)
+    _, mm1 = O.backprop(prob, grid, mlp, one, magnitude=True)
+    NO = O.n_out(prob.cfg)
+    np.testing.assert_allclose(mm1[-NO:], np.abs(gm1[-NO:]), rtol=1e-14)
+
+
 # ---------------------------------------------------------------- Eq. 9
 
 def _lattice_laplacian(r):
