@@ -707,6 +707,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 1) mlp_bwd_tc_kernel(TcArgs a) {
 
 cudaError_t launch_mlp_backward_bf16(npg_ctx* c) {
   if (c->md.H == 128) return launch_mlp_backward_bf16_h128(c);
+  if (c->md.H == 64) return launch_mlp_backward_bf16_h64(c);
   const size_t smem = BwdSmem::TOTAL + 1024;
   auto k = c->cfg.rot_mode == NPG_ROT_QUAT     ? mlp_bwd_tc_kernel<0>
            : c->cfg.rot_mode == NPG_ROT_EXPMAP ? mlp_bwd_tc_kernel<1>

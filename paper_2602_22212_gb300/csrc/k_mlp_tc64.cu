@@ -1,0 +1,515 @@
+// BF16 tensor-core MLP backward (reverse of Sec. 3.3-3.4) for hidden width 64
+// and 3 hidden layers, sized so that two CTAs share an SM: while one waits on
+// its MMAs or its barriers the other runs its epilogues, which is what the
+// chain of dependent MMA -> TMEM -> CUDA-core steps of one tile cannot do by
+// itself. Each CTA takes 97 KB of shared memory and 256 TMEM columns.
+//
+// Tile = 16 vertices x 8 frames = 128 rows (row r = tl 16 + il); 256 threads:
+// warp w serves TMEM lanes 32 (w % 4) .. + 31 (its rows) and the 32-column
+// half c = w / 4 of every 64-wide activation. Three [128][64] activation
+// tiles X[a], X[b], X[c] rotate roles from tile to tile (see k_mlp_tc128.cu
+// for the step list); a fourth tile YG holds y = (z_i, gamma_t, 0.., 1) in
+// columns 0..15 and dL/do in columns 16..22. The weight gradients accumulate
+// in TMEM over all of a CTA's tiles as M = 64 MMAs whose 64 accumulator rows
+// sit in lanes 16 q .. 16 q + 15 of each 32-lane quarter q:
+//   ACC_3 = dpre3^T [h2 | y]   dW3 in columns 0..63, db3 in column 79 (y's 1)
+//   ACC_2 = dpre2^T [h1 | y]   dW2, db2 likewise
+//   ACC_O = h3^T dL/do         dWo^T
+//   ACC_1 = dpre1^T y          dW1 in columns 0..K-1, db1 in column 15
+// ([h | y] is one MN-major operand whose second 64-column block is YG: the
+// descriptor's leading-byte offset is the distance from the h tile to YG).
+#include "mlp_tc_common.cuh"
+
+namespace npg {
+
+namespace {
+constexpr int H64 = 64;
+
+struct Bwd64Stage {  // inputs of one tile, FP32
+  static constexpr uint32_t U_PITCH = 272;  // 256 B + 16: the 16 vertex rows hit distinct banks
+  static constexpr uint32_t U = 0;          // [16 vertices][64]
+  static constexpr uint32_t V = 16 * U_PITCH;   // [8 frames][64]
+  static constexpr uint32_t X = V + 8 * 256;    // [16] float4
+  static constexpr uint32_t G = X + 256;        // [8][16] float4
+  static constexpr uint32_t Z = G + 2048;       // [16][Z] (Z <= 8)
+  static constexpr uint32_t GAM = Z + 512;      // [8][2M] (2M <= 16)
+  static constexpr uint32_t BYTES = GAM + 512;
+};
+struct Bwd64Smem {
+  static constexpr uint32_t W2 = 0, W3 = W2 + TC_TILE / 2;  // [64][64] K-major, 8 KB each
+  static constexpr uint32_t XB = W3 + TC_TILE / 2;          // X[0..2], 16 KB each
+  static constexpr uint32_t YG = XB + 3 * TC_TILE;          // y | dL/do
+  static constexpr uint32_t WO = YG + TC_TILE;              // [16][64] K-major
+  static constexpr uint32_t W1Z = WO + 2048;                // [16][64]: W1[:, :Z]^T
+  static constexpr uint32_t STG = W1Z + 2048;
+  static constexpr uint32_t BIAS = STG + Bwd64Stage::BYTES;    // b2, b3 (64 each), bo (16)
+  static constexpr uint32_t DZP = BIAS + (64 + 64 + 16) * 4;   // [8 qz][4 q4][16 vertices]
+  static constexpr uint32_t DBO = DZP + 8 * 64 * 4;
+  static constexpr uint32_t BAR = DBO + 8 * 4;  // chain, drain, dL/dz, staged U/V, staged rest
+  static constexpr uint32_t TMEMP = BAR + 5 * 8;
+  static constexpr uint32_t TOTAL = TMEMP + 8;
+};
+static_assert(2 * (Bwd64Smem::TOTAL + 1024) <= 226 * 1024, "two CTAs per SM");
+constexpr uint32_t C_WORK = 0, C_ACC3 = 64, C_ACC2 = 144, C_ACCO = 224, C_ACC1 = 240;
+constexpr int BWD64_THREADS = 256;
+
+// 32 FP32 values as BF16 into columns [c0, c0 + 32) of one row of a [128][64] tile.
+__device__ __forceinline__ void st_row32h(uint8_t* tile, int row, int c0, const float* v) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h) st_bf16x8(tile, row, c0 + 8 * h, v + 8 * h);
+}
+
+__device__ void load_weight64(uint8_t* tile, const float* W, int rows, int valid_rows) {
+  for (int e = threadIdx.x; e < rows * 64; e += BWD64_THREADS) {
+    const int r = e >> 6, k = e & 63;
+    st_bf16(tile, r, k, r < valid_rows ? W[r * 64 + k] : 0.f);
+  }
+}
+
+// M 128 x N (= idesc) over K = 64 features: K-major A and B ([rows][64]).
+__device__ __forceinline__ void mma_f64(uint32_t d, uint32_t a, uint32_t b, uint32_t idesc) {
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks)
+    tc::mma_bf16(d, tc::kmajor_sw128(a + 32 * ks), tc::kmajor_sw128(b + 32 * ks), idesc, ks > 0);
+}
+
+// M 128 x N 64 = A W over K = 64 (the weight's output rows): W a K-major
+// [64 out][64 in] tile read as the MN-major operand.
+__device__ __forceinline__ void mma_w64T(uint32_t d, uint32_t a, uint32_t w, uint32_t idesc) {
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks)
+    tc::mma_bf16(d, tc::kmajor_sw128(a + 32 * ks), tc::mnmajor_sw128(w + 2048 * ks, 0, 1024),
+                 idesc, ks > 0);
+}
+
+// M 64 x N (+)= A^T B over K = the 128 rows of a tile, A and B MN-major; B's
+// second 64-column block lies lbo bytes after its first.
+__device__ __forceinline__ void mma_rows64(uint32_t d, uint32_t a, uint32_t b, uint32_t lbo,
+                                           uint32_t idesc, bool first) {
+#pragma unroll
+  for (int ks = 0; ks < 8; ++ks)
+    tc::mma_bf16(d, tc::mnmajor_sw128(a + 2048 * ks, 0, 1024),
+                 tc::mnmajor_sw128(b + 2048 * ks, lbo, 1024), idesc,
+                 (first && ks == 0) ? 0u : 1u);
+}
+
+// One of the two staged groups of a tile (part 0: the U rows and V, 17
+// pieces; part 1: dL/dx-hat rows, x, z, gamma, 11 pieces), issued by the
+// lanes of one warp; lane 0 announces the group's bytes (one arrival).
+__device__ void bwd64_stage(const TcArgs& a, int i0, int t0, uint8_t* stg, uint64_t* sbar,
+                            int part, int lane) {
+  const int nv = min(16, a.N - i0), nf = min(8, a.T - t0);
+  const uint32_t zb = ((uint32_t)(nv * a.Z * 4) + 15u) & ~15u;
+  const uint32_t gb = ((uint32_t)(nf * 2 * a.M * 4) + 15u) & ~15u;
+  auto bytes = [&](int k) -> uint32_t {
+    if (part == 0) {
+      if (k < 16) return k < nv ? 256u : 0u;
+      return k == 16 ? (uint32_t)nf * 256u : 0u;
+    }
+    if (k < 8) return k < nf ? (uint32_t)nv * 16u : 0u;
+    if (k == 8) return (uint32_t)nv * 16u;
+    if (k == 9) return zb;
+    return k == 10 ? gb : 0u;
+  };
+  if (lane == 0) {
+    uint32_t total = 0u;
+    for (int k = 0; k < 17; ++k) total += bytes(k);
+    tc::mbar_arrive_expect_tx(sbar, total);
+  }
+  __syncwarp();
+  const uint32_t n = lane < 17 ? bytes(lane) : 0u;
+  if (n == 0u) return;
+  const int k = lane;
+  if (part == 0) {
+    if (k < 16)
+      tc::bulk_g2s(stg + Bwd64Stage::U + k * Bwd64Stage::U_PITCH, a.U + (long long)(i0 + k) * H64,
+                   n, sbar);
+    else
+      tc::bulk_g2s(stg + Bwd64Stage::V, a.V + (long long)t0 * H64, n, sbar);
+  } else {
+    if (k < 8)
+      tc::bulk_g2s(stg + Bwd64Stage::G + k * 256, a.dxhat + (long long)(t0 + k) * a.N + i0, n,
+                   sbar);
+    else if (k == 8)
+      tc::bulk_g2s(stg + Bwd64Stage::X, a.xr + i0, n, sbar);
+    else if (k == 9)
+      tc::bulk_g2s(stg + Bwd64Stage::Z, a.z + (long long)i0 * a.Z, n, sbar);
+    else
+      tc::bulk_g2s(stg + Bwd64Stage::GAM, a.gamma + (long long)t0 * 2 * a.M, n, sbar);
+  }
+}
+}  // namespace
+
+template <int ROT>
+__global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + Bwd64Smem::BAR);
+  uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + Bwd64Smem::TMEMP);
+  float* bias = reinterpret_cast<float*>(sm + Bwd64Smem::BIAS);
+  float* dzp = reinterpret_cast<float*>(sm + Bwd64Smem::DZP);
+  float* dbo = reinterpret_cast<float*>(sm + Bwd64Smem::DBO);
+  uint64_t* sbar = bar + 3;
+  uint8_t* stg = sm + Bwd64Smem::STG;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q4 = warp & 3, c = warp >> 2;
+  const int row = 32 * q4 + lane, il = row & 15, tl = row >> 4;
+  const int H = H64, K = a.K, Z = a.Z, NO = a.NO;
+  const int c0 = 32 * c;
+  if (tid < 8) dbo[tid] = 0.f;
+
+  const float* p2 = a.mlp + H * K + H;
+  const float* p3 = p2 + H * H + H;
+  const float* po = p3 + H * H + H;
+  load_weight64(sm + Bwd64Smem::W2, p2, 64, 64);
+  load_weight64(sm + Bwd64Smem::W3, p3, 64, 64);
+  load_weight64(sm + Bwd64Smem::WO, po, 16, NO);
+  for (int e = tid; e < 16 * 64; e += BWD64_THREADS) {
+    const int qz = e >> 6, m = e & 63;
+    st_bf16(sm + Bwd64Smem::W1Z, qz, m, qz < Z ? a.mlp[m * K + qz] : 0.f);
+  }
+  {  // YG starts zero; its columns >= 23 stay zero, column 15 stays 1
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    for (int e = tid; e < TC_TILE / 16; e += BWD64_THREADS)
+      *reinterpret_cast<uint4*>(sm + Bwd64Smem::YG + (uint32_t)e * 16u) = zero;
+  }
+  for (int k = tid; k < 64; k += BWD64_THREADS) {
+    bias[k] = p2[H * H + k];
+    bias[64 + k] = p3[H * H + k];
+  }
+  if (tid < 16) bias[128 + tid] = tid < NO ? po[NO * H + tid] : 0.f;
+  if (tid == 0) {
+    for (int b = 0; b < 5; ++b) tc::mbar_init(bar + b, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_ptr, 256);
+    tc::tmem_relinquish();
+  }
+  const int n_tb = (a.T + 7) / 8;
+  const int ntiles = ((a.N + 15) / 16) * n_tb;
+  int tile = blockIdx.x;
+  int i0 = 0, t0 = 0;
+  if (tile < ntiles) {
+    i0 = tile / n_tb * 16;
+    t0 = (tile - i0 / 16 * n_tb) * 8;
+  }
+  __syncthreads();
+  if (c == 1) st_bf16(sm + Bwd64Smem::YG, row, 15, 1.f);
+  bool ok = tc_sync_ok(true, a.err);
+  uint32_t sphase = 0u, pending = 0u;
+  auto stage_issue = [&](int part, int i0_, int t0_) {
+    if (warp == 1 + part) bwd64_stage(a, i0_, t0_, stg, sbar + part, part, lane);
+    pending |= 1u << part;
+  };
+  auto stage_wait = [&](int part) {
+    ok = ok && tc::mbar_wait(sbar + part, (sphase >> part) & 1u, WAIT_TRIES);
+    sphase ^= 1u << part;
+    pending &= ~(1u << part);
+  };
+  if (tile < ntiles) {
+    stage_issue(0, i0, t0);
+    stage_issue(1, i0, t0);
+  }
+  const uint32_t tmem = *tmem_ptr;
+  const uint32_t lane_addr = tmem + ((uint32_t)(q4 * 32) << 16);
+  auto sa = [&](uint32_t off) { return tc::smem_u32(sm + off); };
+  constexpr uint32_t ID64 = tc::idesc_bf16(128, 64, false, false);
+  constexpr uint32_t ID16 = tc::idesc_bf16(128, 16, false, false);
+  constexpr uint32_t IDW = tc::idesc_bf16(128, 64, false, true);    // A K-major, B MN-major
+  constexpr uint32_t IDR80 = tc::idesc_bf16(64, 80, true, true);    // A^T B over rows
+  constexpr uint32_t IDR16 = tc::idesc_bf16(64, 16, true, true);
+  uint32_t phase = 0, phase_dz = 0;
+  bool first = true;
+  const float* b2 = bias + c0;
+  const float* b3 = bias + 64 + c0;
+  auto xbuf = [&](int k) { return Bwd64Smem::XB + (uint32_t)k * TC_TILE; };
+  const uint32_t s_yg = sa(Bwd64Smem::YG);
+
+  auto put_h1 = [&](int k, bool valid) {
+    const float4* u4 = reinterpret_cast<const float4*>(stg + Bwd64Stage::U +
+                                                       il * Bwd64Stage::U_PITCH + 4 * c0);
+    const float4* v4 = reinterpret_cast<const float4*>(stg + Bwd64Stage::V + tl * 256 + 4 * c0);
+    float v[32];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 u = u4[q], w = v4[q];
+      v[4 * q + 0] = valid ? leaky(u.x + w.x, a.slope) : 0.f;
+      v[4 * q + 1] = valid ? leaky(u.y + w.y, a.slope) : 0.f;
+      v[4 * q + 2] = valid ? leaky(u.z + w.z, a.slope) : 0.f;
+      v[4 * q + 3] = valid ? leaky(u.w + w.w, a.slope) : 0.f;
+    }
+    uint32_t m = 0u;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) m |= (v[q] > 0.f ? 1u : 0u) << q;
+    st_row32h(sm + xbuf(k), row, c0, v);
+    return m;
+  };
+  auto row_valid = [&](int i0_, int t0_) { return i0_ + il < a.N && t0_ + tl < a.T; };
+
+  int xa = 0, xb = 1, xc = 2;
+  uint32_t m1 = 0u;
+  int dz_i0 = -1;
+  float dbo_acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  auto flush_dz = [&](int e0, int stride) {
+    for (int e = e0; e < 16 * Z; e += stride) {
+      const int vi = e & 15, qz = e >> 4;
+      if (dz_i0 + vi >= a.N) continue;
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s += dzp[(qz * 4 + q) * 16 + vi];
+      atomicAdd(a.dz + (long long)(dz_i0 + vi) * Z + qz, s);
+    }
+  };
+  if (tile < ntiles) {
+    stage_wait(0);
+    m1 = put_h1(xa, row_valid(i0, t0));
+  }
+  for (; tile < ntiles; tile += gridDim.x) {
+    const bool valid = row_valid(i0, t0);
+    const int next = tile + (int)gridDim.x;
+    int ni0 = 0, nt0 = 0;
+    if (next < ntiles) {
+      ni0 = next / n_tb * 16;
+      nt0 = (next - ni0 / 16 * n_tb) * 8;
+    }
+    // ---- 2: h2
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
+    if (tid == 0) {
+      mma_f64(tmem + C_WORK, sa(xbuf(xa)), sa(Bwd64Smem::W2), ID64);
+      tc::mma_commit(bar);
+    }
+    if (next < ntiles) stage_issue(0, ni0, nt0);
+    tc_wait(bar, phase, ok);
+    uint32_t m2 = 0u, m3 = 0u;
+    {
+      float v[32];
+      ld_col32(lane_addr + C_WORK + c0, v);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        v[k] = leaky(v[k] + b2[k], a.slope);
+        m2 |= (v[k] > 0.f ? 1u : 0u) << k;
+      }
+      st_row32h(sm + xbuf(xb), row, c0, v);
+    }
+    // ---- 3: h3
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
+    if (tid == 0) {
+      mma_f64(tmem + C_WORK, sa(xbuf(xb)), sa(Bwd64Smem::W3), ID64);
+      tc::mma_commit(bar);
+    }
+    tc_wait(bar, phase, ok);
+    {
+      float v[32];
+      ld_col32(lane_addr + C_WORK + c0, v);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        v[k] = leaky(v[k] + b3[k], a.slope);
+        m3 |= (v[k] > 0.f ? 1u : 0u) << k;
+      }
+      st_row32h(sm + xbuf(xc), row, c0, v);
+    }
+    // ---- 4: o; dL/do (half 0); y and the previous tile's dL/dz (half 1)
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
+    if (tid == 0) {
+      mma_f64(tmem + C_WORK, sa(xbuf(xc)), sa(Bwd64Smem::WO), ID16);
+      tc::mma_commit(bar);
+    }
+    stage_wait(1);
+    tc_wait(bar, phase, ok);
+    if (c == 0) {
+      float r[16];
+      ld_col16(lane_addr + C_WORK, r);
+      float o[7], go[8];
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        o[j] = r[j] + bias[128 + j];
+        go[j] = 0.f;
+      }
+      go[7] = 0.f;
+      if (valid) {
+        const float4 x = reinterpret_cast<const float4*>(stg + Bwd64Stage::X)[il];
+        const float4 g = reinterpret_cast<const float4*>(stg + Bwd64Stage::G)[tl * 16 + il];
+        transform_backward<ROT>(o, a.alpha, x, g, go);
+      }
+      if (NO < 7) go[6] = 0.f;
+#pragma unroll
+      for (int j = 0; j < 7; ++j) dbo_acc[j] += go[j];
+      st_bf16x8(sm + Bwd64Smem::YG, row, 16, go);
+    } else {
+      const float* zs = reinterpret_cast<const float*>(stg + Bwd64Stage::Z) + il * Z;
+      const float* gt = reinterpret_cast<const float*>(stg + Bwd64Stage::GAM) + tl * (K - Z);
+      float y[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        y[k] = k == 15 ? 1.f : !valid ? 0.f : k < Z ? zs[k] : k < K ? gt[k - Z] : 0.f;
+      st_bf16x8(sm + Bwd64Smem::YG, row, 0, y);
+      st_bf16x8(sm + Bwd64Smem::YG, row, 8, y + 8);
+      if (dz_i0 >= 0) flush_dz(tid - 128, 128);
+    }
+    // ---- 5: dh3 = dL/do Wo, ACC_O += h3^T dL/do
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
+    if (tid == 0) {
+      tc::mma_bf16(tmem + C_WORK, tc::kmajor_sw128(s_yg + 32),
+                   tc::mnmajor_sw128(sa(Bwd64Smem::WO), 0, 1024), IDW, 0u);
+      mma_rows64(tmem + C_ACCO, sa(xbuf(xc)), s_yg + 32, 0, IDR16, first);
+      tc::mma_commit(bar);
+    }
+    if (next < ntiles) stage_issue(1, ni0, nt0);
+    tc_wait(bar, phase, ok);
+    {
+      float v[32];
+      ld_col32(lane_addr + C_WORK + c0, v);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] *= ((m3 >> k) & 1u) ? 1.f : a.slope;
+      st_row32h(sm + xbuf(xc), row, c0, v);  // dpre3
+    }
+    // ---- 6: dh2 = dpre3 W3; ACC_3 += dpre3^T [h2 | y]
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
+    if (tid == 0) {
+      mma_w64T(tmem + C_WORK, sa(xbuf(xc)), sa(Bwd64Smem::W3), IDW);
+      mma_rows64(tmem + C_ACC3, sa(xbuf(xc)), sa(xbuf(xb)), Bwd64Smem::YG - xbuf(xb), IDR80,
+                 first);
+      tc::mma_commit(bar);
+    }
+    tc_wait(bar, phase, ok);
+    {
+      float v[32];
+      ld_col32(lane_addr + C_WORK + c0, v);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] *= ((m2 >> k) & 1u) ? 1.f : a.slope;
+      st_row32h(sm + xbuf(xb), row, c0, v);  // dpre2
+    }
+    // ---- 7: dh1 = dpre2 W2; ACC_2 += dpre2^T [h1 | y]
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
+    if (tid == 0) {
+      mma_w64T(tmem + C_WORK, sa(xbuf(xb)), sa(Bwd64Smem::W2), IDW);
+      mma_rows64(tmem + C_ACC2, sa(xbuf(xb)), sa(xbuf(xa)), Bwd64Smem::YG - xbuf(xa), IDR80,
+                 first);
+      tc::mma_commit(bar);
+    }
+    tc_wait(bar, phase, ok);
+    {
+      float v[32];
+      ld_col32(lane_addr + C_WORK + c0, v);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] *= ((m1 >> k) & 1u) ? 1.f : a.slope;
+      st_row32h(sm + xbuf(xa), row, c0, v);  // dpre1
+    }
+    if (next < ntiles) {
+      stage_wait(0);
+      m1 = put_h1(xb, row_valid(ni0, nt0));
+    }
+    // ---- 8: dL/dz rows = dpre1 W1[:, :Z] (into WORK); ACC_1 += dpre1^T y
+    if (!(ok = tc_sync_ok(ok, a.err))) break;
+    if (tid == 0) {
+      mma_f64(tmem + C_WORK, sa(xbuf(xa)), sa(Bwd64Smem::W1Z), ID16);
+      tc::mma_commit(bar + 2);
+      mma_rows64(tmem + C_ACC1, sa(xbuf(xa)), s_yg, 0, IDR16, first);
+    }
+    first = false;
+    dz_i0 = i0;
+    if (c == 1) {
+      tc_wait(bar + 2, phase_dz, ok);
+      float r[16];
+      ld_col16(lane_addr + C_WORK, r);
+#pragma unroll
+      for (int qz = 0; qz < 8; ++qz) {
+        if (qz < Z) {
+          const float s = r[qz] + __shfl_xor_sync(0xffffffffu, r[qz], 16);
+          if (lane < 16) dzp[(qz * 4 + q4) * 16 + lane] = s;
+        }
+      }
+    }
+    const int t_ = xa;
+    xa = xb;
+    xb = xc;
+    xc = t_;
+    i0 = ni0;
+    t0 = nt0;
+  }
+  if (!first) {
+    if (tid == 0) tc::mma_commit(bar);
+    tc_wait(bar, phase, ok);
+  }
+  ok = tc_sync_ok(ok, a.err);
+  if (ok && dz_i0 >= 0) flush_dz(tid, BWD64_THREADS);
+  if (c == 0) {
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      float sj = dbo_acc[j];
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) sj += __shfl_xor_sync(0xffffffffu, sj, o2);
+      if (lane == 0 && j < NO) atomicAdd(dbo + j, sj);
+    }
+  }
+  ok = tc_sync_ok(ok, a.err);
+  if (ok && !first) {
+    // M = 64 accumulators: feature j = 16 q4 + lane in lanes 0..15 of each quarter
+    float* g = a.g_mlp;
+    float* gW1 = g;
+    float* gb1 = g + H * K;
+    float* gW2 = gb1 + H;
+    float* gb2 = gW2 + H * H;
+    float* gW3 = gb2 + H;
+    float* gb3 = gW3 + H * H;
+    float* gWo = gb3 + H;
+    float* gbo = gWo + NO * H;
+    const int j = 16 * q4 + lane;
+    const bool has = lane < 16;
+    float v[32];
+    ld_col32(lane_addr + C_ACC3 + c0, v);
+    if (has)
+#pragma unroll
+      for (int k = 0; k < 32; ++k) atomicAdd(gW3 + j * H + c0 + k, v[k]);
+    ld_col32(lane_addr + C_ACC2 + c0, v);
+    if (has)
+#pragma unroll
+      for (int k = 0; k < 32; ++k) atomicAdd(gW2 + j * H + c0 + k, v[k]);
+    if (c == 0) {
+      ld_col16(lane_addr + C_ACC3 + 64, v);
+      if (has) atomicAdd(gb3 + j, v[15]);
+      ld_col16(lane_addr + C_ACC2 + 64, v);
+      if (has) atomicAdd(gb2 + j, v[15]);
+      ld_col16(lane_addr + C_ACCO, v);  // row m = j of dWo^T
+      if (has)
+#pragma unroll
+        for (int q = 0; q < 7; ++q)
+          if (q < NO) atomicAdd(gWo + q * H + j, v[q]);
+    } else {
+      ld_col16(lane_addr + C_ACC1, v);
+      if (has) {
+#pragma unroll
+        for (int k = 0; k < 15; ++k)
+          if (k < K) atomicAdd(gW1 + j * K + k, v[k]);
+        atomicAdd(gb1 + j, v[15]);
+      }
+      if (q4 == 0 && lane < NO) atomicAdd(gbo + lane, dbo[lane]);
+    }
+  }
+  for (int b = 0; b < 2; ++b)
+    if (pending & (1u << b)) tc::mbar_wait(sbar + b, (sphase >> b) & 1u, WAIT_TRIES);
+  if (tid == 0) {
+    tc::mma_commit(bar + 1);
+    tc::mbar_wait(bar + 1, 0, WAIT_TRIES);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+cudaError_t launch_mlp_backward_bf16_h64(npg_ctx* c) {
+  const size_t smem = Bwd64Smem::TOTAL + 1024;
+  auto k = c->cfg.rot_mode == NPG_ROT_QUAT     ? mlp_bwd_tc2_kernel<0>
+           : c->cfg.rot_mode == NPG_ROT_EXPMAP ? mlp_bwd_tc2_kernel<1>
+                                               : mlp_bwd_tc2_kernel<2>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (long long)((c->N + 15) / 16) * ((c->T + 7) / 8);
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;  // tile indices are ints
+  k<<<tc_grid(c, tiles, 2), BWD64_THREADS, smem, c->stream>>>(make_tc_args(c));
+  return cudaGetLastError();
+}
+
+}  // namespace npg

@@ -193,6 +193,7 @@ cudaError_t launch_decode_fp32_wide(npg_ctx* c);
 cudaError_t launch_mlp_backward_fp32_wide(npg_ctx* c);
 cudaError_t launch_mlp_backward_bf16(npg_ctx* c);
 cudaError_t launch_mlp_backward_bf16_h128(npg_ctx* c);
+cudaError_t launch_mlp_backward_bf16_h64(npg_ctx* c);
 cudaError_t launch_scatter(npg_ctx* c);
 cudaError_t launch_precondition(const float* g, float* out, float* tmp0, float* tmp1,
                                 const float* C, const float* Ct, const float* mu, int r, int F,
