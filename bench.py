@@ -57,10 +57,11 @@ def fp32_peak_tflops(sms, mhz):
 # SHA-256 of the sources that define the kernel at capture time: a changed
 # source reports null traffic until the counters are taken again.
 KERNEL_SOURCES = {
-    "mlp_bwd_tc_kernel": ("k_mlp_tc.cu", "mlp_tc_common.cuh", "tc_sm100.cuh", "npg_device.cuh"),
+    "mlp_bwd_tc2_kernel": ("k_mlp_tc64.cu", "mlp_tc_common.cuh", "tc_sm100.cuh",
+                           "npg_device.cuh"),
 }
 MEASURED_TRAFFIC = {
-    ("mlp_bwd_tc_kernel", "paper"): {"bytes": None, "sha256": None},
+    ("mlp_bwd_tc2_kernel", "paper"): {"bytes": None, "sha256": None},
 }
 
 
@@ -610,7 +611,7 @@ def main():
     # the search stages two kernels per direction); every stage's position is
     # listed in stage_rooflines
     wide = H > 64
-    kernels = {"mlp_bwd": ("mlp_bwd_tc128_kernel" if wide else "mlp_bwd_tc_kernel")
+    kernels = {"mlp_bwd": ("mlp_bwd_tc128_kernel" if wide else "mlp_bwd_tc2_kernel")
                if args.precision == "bf16" else
                ("wide_gemm_kernel (layered)" if wide else "mlp_bwd_fp32_kernel"),
                "decode": ("decode_tc128_kernel" if wide else "decode_tc_kernel")

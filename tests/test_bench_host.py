@@ -35,13 +35,13 @@ def test_stage_work_at_the_benchmark_size():
 
 
 def test_measured_traffic_follows_the_sources(monkeypatch):
-    rec = bench.MEASURED_TRAFFIC[("mlp_bwd_tc_kernel", "paper")]
+    rec = bench.MEASURED_TRAFFIC[("mlp_bwd_tc2_kernel", "paper")]
     assert rec["bytes"] is None or rec["bytes"] > 0
     if rec["bytes"] is not None:
-        assert bench.measured_traffic("mlp_bwd_tc_kernel", "paper") in (rec["bytes"], None)
+        assert bench.measured_traffic("mlp_bwd_tc2_kernel", "paper") in (rec["bytes"], None)
     monkeypatch.setattr(bench, "sources_sha", lambda kernel: "0" * 64)
-    assert bench.measured_traffic("mlp_bwd_tc_kernel", "paper") is None
-    assert bench.measured_traffic("mlp_bwd_tc_kernel", "profile") is None
+    assert bench.measured_traffic("mlp_bwd_tc2_kernel", "paper") is None
+    assert bench.measured_traffic("mlp_bwd_tc2_kernel", "profile") is None
     assert bench.measured_traffic("decode_tc_kernel", "paper") is None
 
 
@@ -49,12 +49,12 @@ def test_sources_hash_covers_the_kernel_files():
     import hashlib
     csrc = os.path.join(ROOT, "paper_2602_22212_gb300", "csrc")
     h = hashlib.sha256()
-    for f in bench.KERNEL_SOURCES["mlp_bwd_tc_kernel"]:
+    for f in bench.KERNEL_SOURCES["mlp_bwd_tc2_kernel"]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
-    assert bench.sources_sha("mlp_bwd_tc_kernel") == h.hexdigest()
+    assert bench.sources_sha("mlp_bwd_tc2_kernel") == h.hexdigest()
     # the committed record matches the committed sources
-    rec = bench.MEASURED_TRAFFIC[("mlp_bwd_tc_kernel", "paper")]
+    rec = bench.MEASURED_TRAFFIC[("mlp_bwd_tc2_kernel", "paper")]
     if rec["sha256"] is not None:
         assert rec["sha256"] == h.hexdigest()
 
