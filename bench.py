@@ -202,9 +202,13 @@ def stage_work(p, N, T, MT, mlp_dims, precond="fp32", precision="fp32", mlp_len=
         "decode": (mlp_kind, fwd_row * rows, "FLOP"),
         "mlp_bwd": (mlp_kind, bwd_row * rows, "FLOP"),
         # the grid levels' Adam steps run inside the preconditioner stage (each
-        # level's DCT passes and Adam on one of four concurrent stream lanes);
-        # the adam stage is the MLP's
-        "precond": (("hbm", dct_bytes + 28 * n_params, "B") if precond == "tc"
+        # level's DCT passes and Adam on one of four concurrent stream lanes,
+        # Adam in the last pass's epilogue on the tensor-core levels); the adam
+        # stage is the MLP's. Algorithmic bytes per grid parameter: read and
+        # write of the gradient for Eq. 9 (8 B) and Adam's read of p, g~, m, v
+        # and write of p, m, v (28 B). The six DCT passes move 48 B per value
+        # (implementation traffic, `dct_bytes`).
+        "precond": (("hbm", 36 * n_params, "B") if precond == "tc"
                     else ("alu", dct_flops, "FLOP")),
         "adam": ("hbm", 28 * mlp_len, "B"),
         "encode": ("hbm", N * (8 * L * F + 8 * 2) * 4 + N * 16 * 2, "B"),

@@ -47,6 +47,7 @@ class OrCfg(C.Structure):
         ("time_B", C.c_double * 8),
         ("conf_delta", C.c_int),
         ("conf_omega", C.c_int),
+        ("Ht", C.c_int),
     ]
 
 
@@ -87,6 +88,8 @@ def lib():
                 "or_trilinear": (None, [i, pd, pl, pd]),
                 "or_encode": (None, [cfg, i, pd, pd, pd, pd]),
                 "or_time_embedding": (None, [cfg, i, pd]),
+                "or_time_embedding_params": (None, [cfg, pd, i, pd]),
+                "or_time_params": (l, [cfg]),
                 "or_mlp_forward": (None, [cfg, pd, i, pd, pd]),
                 "or_rotation_translation": (None, [cfg, pd, pd, pd]),
                 "or_decode": (None, [cfg, i, i, pd, pd, pd, pd, pd]),
@@ -149,7 +152,7 @@ def _out_i32(n):
 
 def make_cfg(L, res, F, Fn=2, rn=4, H=64, D=3, rot_mode=0, n_freq=4, slope=0.01,
              alpha=0.1, w_iso=100.0, time_enc=0, time_B=None, conf_delta=0,
-             conf_omega=0) -> OrCfg:
+             conf_omega=0, time_hidden=0) -> OrCfg:
     c = OrCfg()
     c.L = int(L)
     for k, r in enumerate(res):
@@ -158,6 +161,7 @@ def make_cfg(L, res, F, Fn=2, rn=4, H=64, D=3, rot_mode=0, n_freq=4, slope=0.01,
     c.rot_mode, c.n_freq = int(rot_mode), int(n_freq)
     c.slope, c.alpha, c.w_iso = float(slope), float(alpha), float(w_iso)
     c.time_enc, c.conf_delta, c.conf_omega = int(time_enc), int(conf_delta), int(conf_omega)
+    c.Ht = int(time_hidden)
     for j, b in enumerate(time_B if time_B is not None else []):
         c.time_B[j] = float(b)
     return c
@@ -205,11 +209,22 @@ def encode(cfg, x, n, grid):
     return z.reshape(N, cfg.Fn + cfg.F)
 
 
-def time_embedding(cfg, T):
-    """Sec. 3.3, Eq. 3: T x 2M, interleaved (sin, cos) per frequency."""
+def time_embedding(cfg, T, mlp=None):
+    """Sec. 3.3, Eq. 3: T x 2M, interleaved (sin, cos) per frequency; the
+    ablation's variants by cfg.time_enc (the learned one, 3, needs the
+    parameter vector mlp, whose tail holds psi_t's weights)."""
     g, pg = _out_d(T * 2 * cfg.n_freq)
-    lib().or_time_embedding(C.byref(cfg), int(T), pg)
+    if mlp is None:
+        lib().or_time_embedding(C.byref(cfg), int(T), pg)
+    else:
+        m, pm = _d(mlp)
+        lib().or_time_embedding_params(C.byref(cfg), pm, int(T), pg)
     return g.reshape(T, 2 * cfg.n_freq)
+
+
+def time_params(cfg) -> int:
+    """Number of psi_t parameters at the tail of the MLP vector (0 unless learned)."""
+    return int(lib().or_time_params(C.byref(cfg)))
 
 
 def mlp_forward(cfg, mlp, y):

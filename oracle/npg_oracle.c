@@ -64,13 +64,16 @@ typedef struct {
   double w_iso;            /* isometry weight (Eq. 8)                        */
   /* variants of the ablations (Sec. 4): 0 is the method itself */
   int time_enc;            /* time encoding: 0 Fourier (Eq. 3), 1 polynomial,
-                              2 Gaussian Fourier with frequencies time_B     */
+                              2 Gaussian Fourier with frequencies time_B,
+                              3 learned: psi_t(t~), a two-layer MLP           */
   double time_B[8];        /* Gaussian Fourier frequencies B_j (j < n_freq)  */
   int conf_delta;          /* catch-up delta: 0 1 - sqrt(e~), 1 constant 1,
                               2 linear 1 - e~, 3 exp(-5 e~), 4 interpolated  */
   int conf_omega;          /* 0 cumulative product of omega (Eq. 11-12);
                               direct w = omega(t)^delta with omega 1 constant,
                               2 one half, 3 the single-frame omega(t)        */
+  int Ht;                  /* hidden width of the learned time embedding
+                              psi_t (time_enc 3)                             */
 } or_cfg;
 
 /* ---------------------------------------------------------------- threads */
@@ -109,10 +112,20 @@ long or_grid_len(const or_cfg* c) {
 
 /* MLP layout: layer 0 W (H x K) row-major then b (H); hidden layers
  * 1..D-1 W (H x H), b (H); output layer W (O x H), b (O). */
-long or_mlp_len(const or_cfg* c) {
+/* Parameters of psi_t (time_enc 3), stored after the decoder's: first layer
+ * a, b (Ht each: h = act(a t~ + b)), then W (2M x Ht, row-major) and c (2M):
+ * gamma = W h + c. Zero for the other encodings. */
+long or_time_params(const or_cfg* c) {
+  long Ht = c->Ht, G2 = 2L * c->n_freq;
+  return c->time_enc == 3 ? 2 * Ht + G2 * Ht + G2 : 0;
+}
+
+static long decoder_len(const or_cfg* c) {
   long K = or_k_in(c), H = c->H, D = c->D, O = or_n_out(c);
   return H * K + H + (D - 1) * (H * H + H) + O * H + O;
 }
+
+long or_mlp_len(const or_cfg* c) { return decoder_len(c) + or_time_params(c); }
 
 /* -------------------------------------------- Sec. 3.2: trilinear lookup */
 
@@ -191,6 +204,30 @@ void or_time_embedding(const or_cfg* c, int T, double* gamma) {
 
 static double act(double s, double slope) { return s > 0.0 ? s : slope * s; }
 static double dact(double s, double slope) { return s > 0.0 ? 1.0 : slope; }
+
+/* The time embedding of every frame from the parameter vector mlp: the
+ * learned one of the ablation (time_enc 3: gamma(t) = psi_t(t~), a two-layer
+ * MLP with Ht hidden units and the decoder's activation, parameters after the
+ * decoder's), else the fixed encodings of or_time_embedding. */
+void or_time_embedding_params(const or_cfg* c, const double* mlp, int T, double* gamma) {
+  if (c->time_enc != 3) {
+    or_time_embedding(c, T, gamma);
+    return;
+  }
+  int Ht = c->Ht, G2 = 2 * c->n_freq;
+  const double* a = mlp + decoder_len(c);
+  const double* b = a + Ht;
+  const double* W = b + Ht;
+  const double* cc = W + (long)G2 * Ht;
+  for (int t = 0; t < T; ++t) {
+    double tt = T > 1 ? (double)t / (double)(T - 1) : 0.0;
+    for (int k = 0; k < G2; ++k) {
+      double s = cc[k];
+      for (int j = 0; j < Ht; ++j) s += W[(long)k * Ht + j] * act(a[j] * tt + b[j], c->slope);
+      gamma[(long)t * G2 + k] = s;
+    }
+  }
+}
 
 /* One row: pre[k*H + j] and h[k*H + j] for hidden layer k, then o (O). */
 static void mlp_row(const or_cfg* c, const double* mlp, const double* y,
@@ -620,7 +657,7 @@ static void backprop_impl(const or_cfg* c, int N, const double* x, const double*
   double* z = (double*)malloc(sizeof(double) * (size_t)N * Z);
   double* gamma = (double*)malloc(sizeof(double) * (size_t)T * G2);
   or_encode(c, N, x, n, grid, z);
-  or_time_embedding(c, T, gamma);
+  or_time_embedding_params(c, mlp, T, gamma);
   /* back through Eq. 7-5, the MLP (Eq. 4) and the input vector (Eq. 2) */
   double* gm = (double*)calloc((size_t)or_mlp_len(c), sizeof(double));
   double* gz = (double*)calloc((size_t)N * Z, sizeof(double));
@@ -629,6 +666,7 @@ static void backprop_impl(const or_cfg* c, int N, const double* x, const double*
   double* h = (double*)malloc(sizeof(double) * H * D);
   double* dh = (double*)malloc(sizeof(double) * H);
   double* dp = (double*)malloc(sizeof(double) * H);
+  double* ggam = (double*)calloc((size_t)T * G2, sizeof(double)); /* dL/dgamma_t */
   double o[8], go[8];
 #define W(idx) (mag ? fabs(mlp[idx]) : mlp[idx])
   for (int t = 0; t < T; ++t)
@@ -676,9 +714,35 @@ static void backprop_impl(const or_cfg* c, int N, const double* x, const double*
         gm[offb0 + j] += dp[j];
         for (int k = 0; k < K; ++k) gm[offW0 + (long)j * K + k] += dp[j] * y[k];
         for (int k = 0; k < Z; ++k) gz[(long)i * Z + k] += W(offW0 + (long)j * K + k) * dp[j];
+        for (int k = 0; k < G2; ++k)
+          ggam[(long)t * G2 + k] += W(offW0 + (long)j * K + Z + k) * dp[j];
       }
     }
+  /* back through the learned time embedding psi_t (time_enc 3) */
+  if (c->time_enc == 3) {
+    int Ht = c->Ht;
+    long oa = decoder_len(c), ob = oa + Ht, oW = ob + Ht, oc = oW + (long)G2 * Ht;
+    for (int t = 0; t < T; ++t) {
+      double tt = T > 1 ? (double)t / (double)(T - 1) : 0.0;
+      const double* gg = ggam + (long)t * G2;
+      for (int j = 0; j < Ht; ++j) {
+        double hp = mlp[oa + j] * tt + mlp[ob + j];
+        double hj = act(hp, c->slope);
+        if (mag) hj = fabs(hj);
+        double dhj = 0.0;
+        for (int k = 0; k < G2; ++k) {
+          gm[oW + (long)k * Ht + j] += gg[k] * hj;
+          dhj += W(oW + (long)k * Ht + j) * gg[k];
+        }
+        double dpj = dhj * dact(hp, c->slope);
+        gm[oa + j] += dpj * tt;
+        gm[ob + j] += dpj;
+      }
+      for (int k = 0; k < G2; ++k) gm[oc + k] += gg[k];
+    }
+  }
 #undef W
+  free(ggam);
   if (g_mlp) memcpy(g_mlp, gm, sizeof(double) * (size_t)or_mlp_len(c));
 
   /* back through the trilinear lookups and the level mean (Eq. 1) */
@@ -734,7 +798,7 @@ double or_loss_grad(const or_cfg* c, int N, const double* x, const double* n, in
   double* gamma = (double*)malloc(sizeof(double) * (size_t)T * G2);
   double* xhat = (double*)malloc(sizeof(double) * (size_t)T * N * 3);
   or_encode(c, N, x, n, grid, z);
-  or_time_embedding(c, T, gamma);
+  or_time_embedding_params(c, mlp, T, gamma);
   or_decode(c, N, T, x, z, gamma, mlp, xhat);
 
   int32_t* nn_x = (int32_t*)malloc(sizeof(int32_t) * (size_t)T * N);
@@ -818,7 +882,7 @@ double or_loss_full(const or_cfg* c, int N, const double* x, const double* n, in
   double* gamma = (double*)malloc(sizeof(double) * (size_t)T * G2);
   double* xhat = (double*)malloc(sizeof(double) * (size_t)T * N * 3);
   or_encode(c, N, x, n, grid, z);
-  or_time_embedding(c, T, gamma);
+  or_time_embedding_params(c, mlp, T, gamma);
   or_decode(c, N, T, x, z, gamma, mlp, xhat);
   int32_t* nn_x = (int32_t*)malloc(sizeof(int32_t) * (size_t)T * N);
   double* d_x = (double*)malloc(sizeof(double) * (size_t)T * N);

@@ -369,6 +369,58 @@ def test_gradient_matches_central_differences(rot_mode):
     assert np.linalg.norm(gg) > 0 and np.linalg.norm(gm) > 0
 
 
+def test_learned_time_embedding_closed_forms():
+    """The learned embedding of the time-encoding ablation (Sec. 4),
+    gamma(t) = psi_t(t~) = W act(a t~ + b) + c with Ht hidden units: with one
+    linear hidden unit (slope 1, a = 1, b = 0) gamma_k = W_k t~ + c_k; with a
+    ReLU unit a = -1, b = 1/2 it is W_k max(0, 1/2 - t~) + c_k."""
+    T, M = 5, 2
+    for slope, a, b, h in ((1.0, 1.0, 0.0, lambda t: t),
+                           (0.0, -1.0, 0.5, lambda t: max(0.0, 0.5 - t))):
+        cfg = O.make_cfg(L=1, res=(3,), F=1, H=4, D=1, n_freq=M, slope=slope, time_enc=3,
+                         time_hidden=1)
+        nt = O.time_params(cfg)
+        assert nt == 2 + 2 * M + 2 * M
+        Wk = np.array([1.0, -2.0, 0.25, 3.0])
+        ck = np.array([0.5, 0.0, -1.0, 2.0])
+        tail = np.concatenate([[a], [b], Wk, ck])
+        mlp = np.concatenate([np.zeros(O.mlp_len(cfg) - nt), tail])
+        g = O.time_embedding(cfg, T, mlp)
+        for t in range(T):
+            np.testing.assert_allclose(g[t], Wk * h(t / (T - 1)) + ck, rtol=0, atol=1e-15)
+
+
+def test_learned_time_embedding_gradient_matches_central_differences():
+    """Reverse mode through psi_t (and through everything else) == central FD
+    of the same loss, every parameter of the decoder and of psi_t."""
+    seq = I.random_cloud_sequence(T=3, M=[25, 31, 18], seed=4)
+    cfg = O.make_cfg(L=2, res=(3, 5), F=2, Fn=2, rn=4, H=8, D=2, slope=0.01, time_enc=3,
+                     time_hidden=6)
+    prob = O.Problem(cfg, seq.x, seq.n, seq.faces, seq.points, seq.offsets, seq.t_key)
+    rng = np.random.default_rng(104)
+    grid = rng.normal(scale=0.3, size=O.grid_len(cfg))
+    nt = O.time_params(cfg)
+    dec = I.mlp_init(O.k_in(cfg), cfg.H, cfg.D, O.n_out(cfg), seed=4, zero_last=False) * 1.5
+    mlp = np.concatenate([dec.astype(np.float64), rng.normal(scale=0.8, size=nt)])
+    assert len(mlp) == O.mlp_len(cfg)
+    full = O.loss_full(prob, grid, mlp, e=3, e_max=10)
+    w = full["w"]
+    lref = O.edge_lengths(full["xhat"], prob.t_key, prob.edges)
+    L0, gg, gm, _ = O.loss_grad(prob, grid, mlp, w, lref)
+    eps = 1e-6
+    num_m = np.zeros_like(mlp)
+    for k in range(len(mlp)):
+        mp, mm = mlp.copy(), mlp.copy()
+        mp[k] += eps
+        mm[k] -= eps
+        num_m[k] = (O.loss_grad(prob, grid, mp, w, lref, want_grad=False)[0] -
+                    O.loss_grad(prob, grid, mm, w, lref, want_grad=False)[0]) / (2 * eps)
+    assert np.linalg.norm(gm - num_m) <= 1e-6 * np.linalg.norm(gm)
+    tail = slice(len(mlp) - nt, len(mlp))
+    assert np.linalg.norm(gm[tail]) > 0
+    assert np.linalg.norm(gm[tail] - num_m[tail]) <= 1e-6 * np.linalg.norm(gm[tail])
+
+
 def test_backprop_magnitude_bounds_the_gradient():
     """The magnitude companion of the reverse pass sums |each product|: it
     bounds every gradient value from above (triangle inequality), equals it
