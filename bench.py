@@ -381,6 +381,9 @@ def run_batch(args):
         ctxs.append(npg.Context(cfg, seq, I.mlp_init(K, p["H"], p["D"], NO, seed=k),
                                 device_inputs=True))
         streams.append(st)
+    # each sequence's launch shapes (search-grid resolutions, decode CTAs per
+    # SM) tuned to its sizes before the batch is captured
+    tuned = [npg.npg_autotune(c.h, 2) for c in ctxs] if not args.no_autotune else None
     main = torch.cuda.Stream()
     batch = npg.npg_batch_create([c.h for c in ctxs], main)
     vf = sum(s.N * s.T for s in seqs)
@@ -424,6 +427,8 @@ def run_batch(args):
                    "sequences": sizes},
         "one_by_one": {"value": vf / (ms1 * 1e-3), "unit": UNIT, "ms_per_step": ms1,
                        "timing": "host clock, each sequence's graph synchronised"},
+        "autotuned": ([dict(vertex_cells=t[0], point_cells=t[1], decode_ctas_per_sm=t[2])
+                       for t in tuned] if tuned else None),
         "gpu_launches": int(launches), "clocks": clocks}))
     for c in ctxs:
         c.close()
@@ -462,6 +467,8 @@ def main():
     ap.add_argument("--batch", type=int, default=0,
                     help="time that many uneven sequences as one batch (npg_batch_*) against "
                          "running them one by one, instead of the single-sequence step")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="--batch: keep every sequence's default launch shapes")
     ap.add_argument("--micro", default=None, choices=["precond_tc", "precond_fp32"],
                     help="time one kernel family alone on a standalone grid instead of the step")
     ap.add_argument("--micro-res", type=int, default=256)

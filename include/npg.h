@@ -73,6 +73,7 @@ extern "C" {
 #define NPG_TIME_FOURIER 0
 #define NPG_TIME_POLY 1
 #define NPG_TIME_GAUSS 2
+#define NPG_TIME_LEARNED 3
 #define NPG_DELTA_SQRT 0
 #define NPG_DELTA_CONST 1
 #define NPG_DELTA_LINEAR 2
@@ -119,7 +120,13 @@ typedef struct npg_ctx npg_ctx; /* opaque; owns all device memory it allocates *
  *                    NPG_TIME_FOURIER (Eq. 3, the method), NPG_TIME_POLY
  *                    (t~^j, j = 1..2M), NPG_TIME_GAUSS (sin / cos(2 pi B_j t~)
  *                    with the caller's frequencies time_B[0..M-1], e.g. drawn
- *                    from N(0, 1)).
+ *                    from N(0, 1)), NPG_TIME_LEARNED (gamma(t) = psi_t(t~), a
+ *                    two-layer MLP with time_hidden hidden units and the
+ *                    decoder's LeakyReLU, trained with the decoder: its
+ *                    parameters a, b (time_hidden each; h = act(a t~ + b)), W
+ *                    (2M x time_hidden), c (2M; gamma = W h + c) follow the
+ *                    decoder's in the MLP vector; NPG_FP32 only).
+ *   time_hidden      hidden width of psi_t (NPG_TIME_LEARNED; 1..256).
  *   conf_delta       catch-up variable of the confidence weights (Eq. 11-12 and
  *                    the stability ablation): NPG_DELTA_SQRT (1 - sqrt(e~), the
  *                    method), _CONST (1), _LINEAR (1 - e~), _EXP (exp(-5 e~)),
@@ -166,6 +173,7 @@ typedef struct npg_config {
   float time_B[NPG_MAX_FREQ];
   int conf_delta;
   int conf_omega;
+  int time_hidden;
 } npg_config;
 
 /* Paper defaults (Sec. 3.2-3.5): resolutions r_l = round(r_min + (r_max -
@@ -189,7 +197,8 @@ NPG_API int npg_config_default(npg_config* cfg, int L, int r_min, int r_max, int
  *                     (H x K, row-major, K = F_n + F_p + 2 n_freq, input order
  *                     (z_n, z_p, gamma)) then b (H); hidden layers W (H x H) + b;
  *                     output W (O x H) + b, O = 7 (quaternion) or 6
- *                     (exponential map). Zeroing the output layer gives the
+ *                     (exponential map); with NPG_TIME_LEARNED the parameters
+ *                     of psi_t after those. Zeroing the output layer gives the
  *                     identity initialisation of Sec. 3.1.
  *   inputs_on_device  0: every input pointer is host memory; 1: device memory.
  * Grids and Adam moments start at zero, e = 0. On failure *out is NULL.
@@ -354,6 +363,22 @@ NPG_API int npg_search_stats(npg_ctx* ctx, long long* out4);
 /* Number of kernels this context has launched (graph replays count every
  * kernel node they contain). */
 NPG_API long long npg_launch_count(const npg_ctx* ctx);
+
+/*
+ * Autotuner of the context's launch shapes (one of the batching tools: each
+ * sequence of a batch gets the shapes that suit its sizes). It times `reps`
+ * forward (+ loss) passes, after one warm-up, for each candidate and keeps the
+ * fastest: the bucket cells per axis of the vertex-side and then of the
+ * point-side search grid (the default resolution times 0.7, 0.85, 1, 1.25;
+ * the search is exact at every resolution), then, for the BF16 form with
+ * H = 64, the decode's CTAs per SM (3, 4, 6 or 8). Parameters, Adam state and
+ * e are unchanged; the nearest-neighbour buffers hold the last search's
+ * (exact) results; the call order restarts before forward, and a captured
+ * iteration graph is captured again at the next npg_iteration.
+ * chosen (host, nullable): 3 ints {vertex-side cells, point-side cells,
+ * decode CTAs per SM}. NPG_EINVAL if cfg.nn_cells fixes the cells. Synchronizes.
+ */
+NPG_API int npg_autotune(npg_ctx* ctx, int reps, int* chosen);
 
 /* Release everything the context owns; NULL is allowed. */
 NPG_API int npg_destroy(npg_ctx* ctx);

@@ -23,6 +23,7 @@ struct BwdArgs {
   const float* gamma;  // T x 2M time encoding
   float* g_mlp;
   float* dz;
+  float* dV;  // T x H, nullable: per-frame sums of dpre1 (learned time embedding)
   int N, T, K, Z, M, D, NO;
   float slope, alpha;
 };
@@ -323,6 +324,15 @@ __global__ void __launch_bounds__(128, 1) mlp_bwd_fp32_kernel(BwdArgs a) {
       for (int j = 0; j < H; ++j) s = fmaf(W1[j * K + q], cur[r * H + j], s);
       dZ[r * Z + q] = s;
     }
+    if (a.dV) {  // per-frame sums over the tile's 8 vertices (rows tl * 8 + il)
+      for (int e = tid; e < 8 * H; e += 128) {
+        const int ft = e / H, j = e % H;
+        if (t0 + ft >= a.T) continue;
+        float s = 0.f;
+        for (int v = 0; v < 8; ++v) s += cur[(ft * 8 + v) * H + j];
+        atomicAdd(a.dV + (long long)(t0 + ft) * H + j, s);
+      }
+    }
     __syncthreads();
     for (int e = tid; e < 8 * Z; e += 128) {
       const int v = e / Z, q = e % Z;
@@ -358,6 +368,7 @@ static cudaError_t mlp_bwd_h(npg_ctx* c) {
   a.dxhat = c->dxhat;
   a.g_mlp = c->g_mlp;
   a.dz = c->dz;
+  a.dV = c->dV;
   a.N = c->N;
   a.T = c->T;
   a.K = c->md.K;

@@ -178,18 +178,19 @@ int auto_cells(long long points_per_set, int nsets) {
 // Two passes balance the work: pass 1 (one thread per query, queries in cell
 // order) searches rings 0..NN_NEAR_RINGS and finishes most queries; a query
 // that is still open is appended to a queue with its best so far. Pass 2
-// (one warp per queued query, lanes splitting each ring's cell rows) finishes
-// the far queries, whose rings hold many (mostly empty) cells.
+// (a group of 8 lanes per queued query, the lanes splitting the cell rows)
+// finishes the far queries, whose rings hold many (mostly empty) cells.
 //
 // Seeded search: when a starting candidate is known (the previous result of
 // an optimisation loop; any index in range will do), its distance bounds the
 // ball that can hold the nearest neighbour. The ball is then covered directly,
 // one row segment per (z, y) cell row within reach, instead of ring by ring:
 // every cell row costs two loads of cell starts, however many cells its
-// segment spans. The result is the same exact nearest neighbour; the seed only
-// changes how much of the grid is visited.
+// segment spans. Balls of up to NN_NEAR_BALL_ROWS rows are covered in pass 1,
+// wider ones in pass 2. The result is the same exact nearest neighbour; the
+// seed only changes how much of the grid is visited.
 constexpr int NN_NEAR_RINGS = 1;
-constexpr int NN_NEAR_BALL_ROWS = 25;  // ball scans up to this many cell rows stay in pass 1
+constexpr int NN_NEAR_BALL_ROWS = 12;  // ball scans up to this many cell rows stay in pass 1
 
 struct NnGeom {
   const float4* qs;
@@ -407,12 +408,30 @@ __global__ void __launch_bounds__(128) nn_near_kernel(NnGeom g) {
   warp_stats(g.stats, n_cand, n_rows);
 }
 
-// warp minimum of (best, index), lowest index on ties
-__device__ __forceinline__ void warp_min(float& best, int& bi) {
+// ----------------------------------------------------------------- far queries, lane groups
+// The queued queries (a seed ball wider than NN_NEAR_BALL_ROWS cell rows, or
+// no seed and still open after rings 0..1) are served by groups of NN_GROUP
+// lanes: a group takes the next item of the queue and deals the cell rows of
+// the seed's ball (nearest rows first: the query's own row, then rows
+// stepping out in z and y alternately) or of each further ring to its lanes,
+// NN_GROUP rows per round, agreeing on the best candidate after every round so
+// that later rows are pruned by it. Groups of one warp proceed independently
+// (their shuffles name only the group's lanes).
+constexpr int NN_GROUP = 8;
+
+// i-th index of [a, b] ordered by distance from c (c, c + 1, c - 1, c + 2, ...).
+__device__ __forceinline__ int center_out(int i, int a, int b, int c) {
+  const int up = b - c, dn = c - a, m = min(up, dn);
+  if (i <= 2 * m) return c + ((i & 1) ? (i + 1) / 2 : -(i / 2));
+  return up > dn ? c + (i - m) : c - (i - m);
+}
+
+// minimum of (best, index) over the group's lanes, lowest index on ties
+__device__ __forceinline__ void group_min(unsigned mask, float& best, int& bi) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+  for (int o = NN_GROUP / 2; o > 0; o >>= 1) {
+    const float ob = __shfl_xor_sync(mask, best, o);
+    const int oi = __shfl_xor_sync(mask, bi, o);
     if (ob < best || (ob == best && oi < bi)) {
       best = ob;
       bi = oi;
@@ -420,38 +439,18 @@ __device__ __forceinline__ void warp_min(float& best, int& bi) {
   }
 }
 
-// Rings NN_NEAR_RINGS + 1 .. for a query with no candidate yet, lanes
-// splitting each ring's cell rows, until no unexplored cell can be closer.
-__device__ __forceinline__ void ring_search_far(const NnGeom& g, const int* st, long long cb,
-                                                float4 q, int cx, int cy, int cz, float h,
-                                                int lane, float& best, int& bi,
-                                                unsigned long long& n_cand,
-                                                unsigned long long& n_rows) {
-  const int G = g.G;
-  for (int ring = NN_NEAR_RINGS + 1; ring < G; ++ring) {
-    const int za = max(cz - ring, 0), zb = min(cz + ring, G - 1);
-    const int ya = max(cy - ring, 0), yb = min(cy + ring, G - 1);
-    const int ny = yb - ya + 1, nrows = (zb - za + 1) * ny;
-    for (int p = lane; p < nrows; p += 32) {
-      const int z = za + p / ny, y = ya + p % ny;
-      n_rows += scan_row(g, st, cb, z, y, cx, cy, cz, ring, q, h, best, bi, n_cand) ? 1 : 0;
-    }
-    warp_min(best, bi);
-    if (ring_done(ring_bound(q, cx, cy, cz, ring, G, h), best)) break;
-  }
-}
-
-__global__ void __launch_bounds__(128) nn_far_kernel(NnGeom g) {
+__global__ void __launch_bounds__(128) nn_far_group_kernel(NnGeom g) {
   const int G = g.G;
   const long long G3 = (long long)G * G * G;
   const float h = 2.f / (float)G;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, gl = lane & (NN_GROUP - 1);
+  const unsigned mask = 0xffu << (lane & ~(NN_GROUP - 1));
   const int nq = *g.qcount;
   unsigned long long n_cand = 0, n_rows = 0;
   while (true) {
     int item = 0;
-    if (lane == 0) item = atomicAdd(g.qcount + 1, 1);
-    item = __shfl_sync(0xffffffffu, item, 0);
+    if (gl == 0) item = atomicAdd(g.qcount + 1, 1);
+    item = __shfl_sync(mask, item, lane & ~(NN_GROUP - 1));
     if (item >= nq) break;
     const int4 it = g.qitems[item];
     const long long k = it.x;
@@ -463,137 +462,39 @@ __global__ void __launch_bounds__(128) nn_far_kernel(NnGeom g) {
     float best = __int_as_float(it.y);
     int bi = it.z;
     if (best < FLT_MAX) {
-      // a candidate is known: cover its ball, lanes splitting the cell rows;
-      // the warp's best is shared after every 32 rows
       int za, zb, ya, yb;
       ball_axis(q.z, best, G, za, zb);
       ball_axis(q.y, best, G, ya, yb);
       const int ny = yb - ya + 1, nrows = (zb - za + 1) * ny;
-      for (int p0 = 0; p0 < nrows; p0 += 32) {
-        const int p = p0 + lane;
-        if (p < nrows)
-          n_rows += ball_row(g, st, cb, za + p / ny, ya + p % ny, q, h, best, bi, n_cand) ? 1 : 0;
-        warp_min(best, bi);
+      for (int p0 = 0; p0 < nrows; p0 += NN_GROUP) {
+        const int p = p0 + gl;
+        if (p < nrows) {
+          const int z = center_out(p / ny, za, zb, cz), y = center_out(p % ny, ya, yb, cy);
+          n_rows += ball_row(g, st, cb, z, y, q, h, best, bi, n_cand) ? 1 : 0;
+        }
+        group_min(mask, best, bi);
       }
     } else {
-      ring_search_far(g, st, cb, q, cx, cy, cz, h, lane, best, bi, n_cand, n_rows);
+      for (int ring = NN_NEAR_RINGS + 1; ring < G; ++ring) {
+        const int za = max(cz - ring, 0), zb = min(cz + ring, G - 1);
+        const int ya = max(cy - ring, 0), yb = min(cy + ring, G - 1);
+        const int ny = yb - ya + 1, nrows = (zb - za + 1) * ny;
+        for (int p = gl; p < nrows; p += NN_GROUP) {
+          const int z = za + p / ny, y = ya + p % ny;
+          n_rows += scan_row(g, st, cb, z, y, cx, cy, cz, ring, q, h, best, bi, n_cand) ? 1 : 0;
+        }
+        group_min(mask, best, bi);
+        if (ring_done(ring_bound(q, cx, cy, cz, ring, G, h), best)) break;
+      }
     }
-    if (lane == 0) {
+    if (gl == 0) {
       const long long ob = set_base(s, g.q_uniform, g.q_off) + __float_as_int(q.w);
       g.out_idx[ob] = bi;
       if (g.out_d) g.out_d[ob] = best;
     }
   }
-  warp_stats(g.stats, n_cand, n_rows);
-}
-
-// ----------------------------------------------------------------- seeded search, lane groups
-// Every query of a seeded search (an optimisation step after the first) is
-// served by a group of NN_GROUP lanes: the cell rows of its seed's ball are
-// dealt to the lanes in rounds of NN_GROUP rows, nearest rows first (the
-// query's own row, then rows stepping out in z and y alternately), and the
-// group agrees on its best candidate after every round, so later rows are
-// pruned by the best found so far. The chain of dependent loads of one query
-// (two cell starts, then the candidates of one row) is thus spread over the
-// group instead of being walked by one thread, and lanes stay busy on the
-// short rows that dominate. A query without a valid seed scans rings 0..1 the
-// same way; queries whose ball spans more than NN_BALL_MAX_ROWS rows, and
-// unseeded queries not settled by rings 0..1, go to the far pass.
-constexpr int NN_GROUP = 8;
-constexpr int NN_BALL_MAX_ROWS = 96;
-
-// i-th index of [a, b] ordered by distance from c (c, c + 1, c - 1, c + 2, ...).
-__device__ __forceinline__ int center_out(int i, int a, int b, int c) {
-  const int up = b - c, dn = c - a, m = min(up, dn);
-  if (i <= 2 * m) return c + ((i & 1) ? (i + 1) / 2 : -(i / 2));
-  return up > dn ? c + (i - m) : c - (i - m);
-}
-
-// minimum of (best, index) over the NN_GROUP lanes of a group, lowest index on ties
-__device__ __forceinline__ void group_min(float& best, int& bi) {
-#pragma unroll
-  for (int o = NN_GROUP / 2; o > 0; o >>= 1) {
-    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ob < best || (ob == best && oi < bi)) {
-      best = ob;
-      bi = oi;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(128) nn_group_kernel(NnGeom g) {
-  const int G = g.G;
-  const long long G3 = (long long)G * G * G;
-  const float h = 2.f / (float)G;
-  const int gl = threadIdx.x & (NN_GROUP - 1);
-  const long long groups = (long long)gridDim.x * (blockDim.x / NN_GROUP);
-  unsigned long long n_cand = 0, n_rows = 0;
-  // every lane of a warp runs the same number of iterations (shuffles below)
-  const long long first = (long long)blockIdx.x * (blockDim.x / NN_GROUP) + threadIdx.x / NN_GROUP;
-  const long long wfirst = first - (threadIdx.x & 31) / NN_GROUP;
-  for (long long kb = wfirst; kb < g.q_total; kb += groups) {
-    const long long k = kb + (threadIdx.x & 31) / NN_GROUP;
-    const bool act = k < g.q_total;
-    const long long kk = act ? k : g.q_total - 1;
-    const int s = set_of(kk, g.q_uniform, g.q_off, g.nsets);
-    const float4 q = g.qs[kk];
-    const long long cb = set_base(s, g.c_uniform, g.c_off);
-    const int* st = g.cstart + s * (G3 + 1);
-    const int cx = cell_axis(q.x, G), cy = cell_axis(q.y, G), cz = cell_axis(q.z, G);
-    const long long ob = set_base(s, g.q_uniform, g.q_off) + __float_as_int(q.w);
-    float best = FLT_MAX;
-    int bi = 0x7fffffff;
-    seed_start(g, ob, cb, set_count(s, g.c_uniform, g.c_off), q, best, bi);
-    int za, zb, ya, yb, zc, yc;
-    bool ring = best == FLT_MAX;
-    if (ring) {  // rings 0..1 around the query's cell
-      za = max(cz - NN_NEAR_RINGS, 0);
-      zb = min(cz + NN_NEAR_RINGS, G - 1);
-      ya = max(cy - NN_NEAR_RINGS, 0);
-      yb = min(cy + NN_NEAR_RINGS, G - 1);
-    } else {
-      ball_axis(q.z, best, G, za, zb);
-      ball_axis(q.y, best, G, ya, yb);
-    }
-    zc = cz;
-    yc = cy;
-    const int ny = yb - ya + 1, nrows = (zb - za + 1) * ny;
-    const bool far = act && !ring && nrows > NN_BALL_MAX_ROWS;
-    // rounds: the group's largest row count decides (lanes of other groups idle)
-    int my_rounds = (act && !far) ? (nrows + NN_GROUP - 1) / NN_GROUP : 0;
-    int rounds = my_rounds;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, o));
-    // without a seed, ring 0 (the query's own cell) first; the ring-1 rows
-    // below then read only ring 1's cells
-    if (ring && act && gl == 0)
-      n_rows += scan_row(g, st, cb, cz, cy, cx, cy, cz, 0, q, h, best, bi, n_cand) ? 1 : 0;
-    group_min(best, bi);
-    for (int r = 0; r < rounds; ++r) {
-      const int p = r * NN_GROUP + gl;
-      if (r < my_rounds && p < nrows) {
-        const int z = center_out(p / ny, za, zb, zc), y = center_out(p % ny, ya, yb, yc);
-        if (ring)
-          n_rows += scan_row(g, st, cb, z, y, cx, cy, cz, NN_NEAR_RINGS, q, h, best, bi, n_cand)
-                        ? 1 : 0;
-        else
-          n_rows += ball_row(g, st, cb, z, y, q, h, best, bi, n_cand) ? 1 : 0;
-      }
-      group_min(best, bi);
-    }
-    if (act && gl == 0) {
-      const bool done = !far && (!ring || ring_done(ring_bound(q, cx, cy, cz, NN_NEAR_RINGS, G, h),
-                                                   best));
-      if (done) {
-        g.out_idx[ob] = bi;
-        if (g.out_d) g.out_d[ob] = best;
-      } else {
-        const int pos = atomicAdd(g.qcount, 1);
-        g.qitems[pos] = make_int4((int)k, __float_as_int(best), bi, 0);
-      }
-    }
-  }
+  // the work counters: every group has left the loop; reduce over the warp
+  __syncwarp();
   warp_stats(g.stats, n_cand, n_rows);
 }
 
@@ -608,11 +509,8 @@ cudaError_t launch_nn(const float4* queries_sorted, long long q_uniform, const l
            cand.src, seeded && cand.src != nullptr};
   cudaError_t e = cudaMemsetAsync(queue.counters, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
-  if (g.seeded)
-    nn_group_kernel<<<grid_blocks(q_total * NN_GROUP, 128), 128, 0, s>>>(g);
-  else
-    nn_near_kernel<<<grid_blocks(q_total, 128), 128, 0, s>>>(g);
-  nn_far_kernel<<<queue.far_blocks, 128, 0, s>>>(g);
+  nn_near_kernel<<<grid_blocks(q_total, 128), 128, 0, s>>>(g);
+  nn_far_group_kernel<<<queue.far_blocks, 128, 0, s>>>(g);
   return cudaGetLastError();
 }
 

@@ -142,7 +142,84 @@ __global__ void time_mod_kernel(const float* mlp, const float* gamma, float* V, 
   }
 }
 
+// Learned time embedding (the time-encoding ablation, Sec. 4): per frame,
+// h = act(a t~ + b) (Ht values), gamma = W h + c (2M values); the parameters
+// follow the decoder's in the MLP vector. One block per frame.
+__global__ void learned_time_kernel(const float* __restrict__ tp, float* __restrict__ gamma,
+                                    int T, int M, int Ht, float slope) {
+  extern __shared__ float hs[];
+  const int t = blockIdx.x;
+  const float tt = T > 1 ? (float)t / (float)(T - 1) : 0.f;
+  const float* a = tp;
+  const float* b = a + Ht;
+  const float* W = b + Ht;
+  const float* cc = W + 2 * M * Ht;
+  for (int j = threadIdx.x; j < Ht; j += blockDim.x) hs[j] = leaky(fmaf(a[j], tt, b[j]), slope);
+  __syncthreads();
+  for (int k = threadIdx.x; k < 2 * M; k += blockDim.x) {
+    float s = cc[k];
+    for (int j = 0; j < Ht; ++j) s = fmaf(W[k * Ht + j], hs[j], s);
+    gamma[(long long)t * 2 * M + k] = s;
+  }
+}
+
+cudaError_t launch_learned_time(npg_ctx* c) {
+  const MlpDims& md = c->md;
+  learned_time_kernel<<<c->T, 64, sizeof(float) * md.Ht, c->stream>>>(
+      c->mlp + md.dec_len, c->gamma, c->T, md.M, md.Ht, md.slope);
+  return cudaGetLastError();
+}
+
+// Reverse of the above, one block per frame: dL/dgamma_t = W1[:, Z:]^T dV_t
+// (dV_t = the sum over vertices of dL/d(first-layer pre-activation) at frame
+// t), then back through gamma = W h + c and h = act(a t~ + b) into psi_t's
+// gradient (atomic adds over frames).
+__global__ void learned_time_backward_kernel(const float* __restrict__ mlp,
+                                             const float* __restrict__ dV,
+                                             float* __restrict__ g_tp, int T, int H, int K, int Z,
+                                             int M, int Ht, long long dec_len, float slope) {
+  __shared__ float gg[2 * NPG_MAX_FREQ];
+  const int t = blockIdx.x;
+  const float tt = T > 1 ? (float)t / (float)(T - 1) : 0.f;
+  const int G2 = 2 * M;
+  for (int k = threadIdx.x; k < G2; k += blockDim.x) {
+    float s = 0.f;
+    for (int j = 0; j < H; ++j) s = fmaf(mlp[(long long)j * K + Z + k], dV[(long long)t * H + j], s);
+    gg[k] = s;
+  }
+  __syncthreads();
+  const float* a = mlp + dec_len;
+  const float* b = a + Ht;
+  const float* W = b + Ht;
+  float* ga = g_tp;
+  float* gb = ga + Ht;
+  float* gW = gb + Ht;
+  float* gc = gW + G2 * Ht;
+  for (int j = threadIdx.x; j < Ht; j += blockDim.x) {
+    const float hp = fmaf(a[j], tt, b[j]);
+    const float h = leaky(hp, slope);
+    float dh = 0.f;
+    for (int k = 0; k < G2; ++k) {
+      atomicAdd(gW + k * Ht + j, gg[k] * h);
+      dh = fmaf(W[k * Ht + j], gg[k], dh);
+    }
+    const float dp = dh * (hp > 0.f ? 1.f : slope);
+    atomicAdd(ga + j, dp * tt);
+    atomicAdd(gb + j, dp);
+  }
+  for (int k = threadIdx.x; k < G2; k += blockDim.x) atomicAdd(gc + k, gg[k]);
+}
+
+cudaError_t launch_learned_time_backward(npg_ctx* c) {
+  const MlpDims& md = c->md;
+  learned_time_backward_kernel<<<c->T, 64, 0, c->stream>>>(c->mlp, c->dV, c->g_mlp + md.dec_len,
+                                                            c->T, md.H, md.K, md.Z, md.M, md.Ht,
+                                                            md.dec_len, md.slope);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_time_table(npg_ctx* c) {
+  if (c->md.Ht > 0) return launch_learned_time(c);
   TimeFreqs f;
   for (int j = 0; j < NPG_MAX_FREQ; ++j) f.B[j] = c->cfg.time_B[j];
   time_table_kernel<<<(c->T + 127) / 128, 128, 0, c->stream>>>(c->gamma, c->T, c->md.M,

@@ -224,6 +224,30 @@ cudaError_t colsum(const float* A, float* out, int rows, int ncol, int lda, cuda
   return cudaGetLastError();
 }
 
+// Per-frame column sums: dV[t][n] += sum of A[m][n] over the chunk's rows m of
+// frame t = (r0 + m) / N (rows are frame-major, so a slice of rows spans few
+// frames; one atomic add per column and frame met).
+__global__ void wide_frame_colsum_kernel(const float* __restrict__ A, float* __restrict__ dV,
+                                         long long r0, int rows, int N, int H) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= H) return;
+  const int per = (rows + gridDim.y - 1) / gridDim.y;
+  const int b = blockIdx.y * per, e = min(rows, b + per);
+  if (b >= e) return;
+  long long t = (r0 + b) / N;
+  float s = 0.f;
+  for (int m = b; m < e; ++m) {
+    const long long tm = (r0 + m) / N;
+    if (tm != t) {
+      atomicAdd(dV + t * H + n, s);
+      s = 0.f;
+      t = tm;
+    }
+    s += A[(long long)m * H + n];
+  }
+  atomicAdd(dV + t * H + n, s);
+}
+
 // y = (z_i, gamma_t) of the chunk's rows, K wide.
 __global__ void wide_y_kernel(const float* __restrict__ z, const float* __restrict__ gamma,
                               float* __restrict__ y, long long r0, int rows, int N, int Z, int K) {
@@ -434,6 +458,11 @@ cudaError_t launch_mlp_backward_fp32_wide(npg_ctx* c) {
       e = gemm<G_TN_ADD>(p, s);
     }
     if (e == cudaSuccess) e = colsum(dp, gb1, n, H, H, s);
+    if (e == cudaSuccess && c->dV) {
+      dim3 grid((H + 127) / 128, (unsigned)std::max(1, std::min(1024, n / 512)));
+      wide_frame_colsum_kernel<<<grid, 128, 0, s>>>(dp, c->dV, r0, n, c->N, H);
+      e = cudaGetLastError();
+    }
     if (e == cudaSuccess) {
       GemmArgs p{};
       p.A = dp;

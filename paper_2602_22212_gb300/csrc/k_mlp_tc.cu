@@ -193,7 +193,7 @@ cudaError_t launch_decode_bf16(npg_ctx* c) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long tiles = ((long long)c->N * c->T + TC_ROWS - 1) / TC_ROWS;
-  k<<<tc_grid(c, tiles, 6), 128, smem, c->stream>>>(make_tc_args(c));
+  k<<<tc_grid(c, tiles, c->dec_per_sm), 128, smem, c->stream>>>(make_tc_args(c));
   return cudaGetLastError();
 }
 

@@ -53,12 +53,6 @@ static_assert(2 * (Bwd64Smem::TOTAL + 1024) <= 226 * 1024, "two CTAs per SM");
 constexpr uint32_t C_WORK = 0, C_ACC3 = 64, C_ACC2 = 144, C_ACCO = 224, C_ACC1 = 240;
 constexpr int BWD64_THREADS = 256;
 
-// 32 FP32 values as BF16 into columns [c0, c0 + 32) of one row of a [128][64] tile.
-__device__ __forceinline__ void st_row32h(uint8_t* tile, int row, int c0, const float* v) {
-#pragma unroll
-  for (int h = 0; h < 4; ++h) st_bf16x8(tile, row, c0 + 8 * h, v + 8 * h);
-}
-
 __device__ void load_weight64(uint8_t* tile, const float* W, int rows, int valid_rows) {
   for (int e = threadIdx.x; e < rows * 64; e += BWD64_THREADS) {
     const int r = e >> 6, k = e & 63;
@@ -226,24 +220,59 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
   auto xbuf = [&](int k) { return Bwd64Smem::XB + (uint32_t)k * TC_TILE; };
   const uint32_t s_yg = sa(Bwd64Smem::YG);
 
+  // (every epilogue below works on 16 columns at a time: fewer live registers)
   auto put_h1 = [&](int k, bool valid) {
-    const float4* u4 = reinterpret_cast<const float4*>(stg + Bwd64Stage::U +
-                                                       il * Bwd64Stage::U_PITCH + 4 * c0);
-    const float4* v4 = reinterpret_cast<const float4*>(stg + Bwd64Stage::V + tl * 256 + 4 * c0);
-    float v[32];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 u = u4[q], w = v4[q];
-      v[4 * q + 0] = valid ? leaky(u.x + w.x, a.slope) : 0.f;
-      v[4 * q + 1] = valid ? leaky(u.y + w.y, a.slope) : 0.f;
-      v[4 * q + 2] = valid ? leaky(u.z + w.z, a.slope) : 0.f;
-      v[4 * q + 3] = valid ? leaky(u.w + w.w, a.slope) : 0.f;
-    }
     uint32_t m = 0u;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) m |= (v[q] > 0.f ? 1u : 0u) << q;
-    st_row32h(sm + xbuf(k), row, c0, v);
+    for (int hh = 0; hh < 2; ++hh) {
+      const float4* u4 = reinterpret_cast<const float4*>(
+          stg + Bwd64Stage::U + il * Bwd64Stage::U_PITCH + 4 * (c0 + 16 * hh));
+      const float4* v4 =
+          reinterpret_cast<const float4*>(stg + Bwd64Stage::V + tl * 256 + 4 * (c0 + 16 * hh));
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 u = u4[q], w = v4[q];
+        v[4 * q + 0] = valid ? leaky(u.x + w.x, a.slope) : 0.f;
+        v[4 * q + 1] = valid ? leaky(u.y + w.y, a.slope) : 0.f;
+        v[4 * q + 2] = valid ? leaky(u.z + w.z, a.slope) : 0.f;
+        v[4 * q + 3] = valid ? leaky(u.w + w.w, a.slope) : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) m |= (v[q] > 0.f ? 1u : 0u) << (16 * hh + q);
+      st_bf16x8(sm + xbuf(k), row, c0 + 16 * hh, v);
+      st_bf16x8(sm + xbuf(k), row, c0 + 16 * hh + 8, v + 8);
+    }
     return m;
+  };
+  // act(WORK + bias) of this thread's 32 columns into tile k; returns the mask
+  auto fwd_epi = [&](const float* bias_c, int k) {
+    uint32_t m = 0u;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      float v[16];
+      ld_col16(lane_addr + C_WORK + c0 + 16 * hh, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        v[q] = leaky(v[q] + bias_c[16 * hh + q], a.slope);
+        m |= (v[q] > 0.f ? 1u : 0u) << (16 * hh + q);
+      }
+      st_bf16x8(sm + xbuf(k), row, c0 + 16 * hh, v);
+      st_bf16x8(sm + xbuf(k), row, c0 + 16 * hh + 8, v + 8);
+    }
+    return m;
+  };
+  // WORK x act'(h) (from the mask) of this thread's 32 columns into tile k
+  auto bwd_epi = [&](uint32_t msk, int k) {
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      float v[16];
+      ld_col16(lane_addr + C_WORK + c0 + 16 * hh, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] *= ((msk >> (16 * hh + q)) & 1u) ? 1.f : a.slope;
+      st_bf16x8(sm + xbuf(k), row, c0 + 16 * hh, v);
+      st_bf16x8(sm + xbuf(k), row, c0 + 16 * hh + 8, v + 8);
+    }
   };
   auto row_valid = [&](int i0_, int t0_) { return i0_ + il < a.N && t0_ + tl < a.T; };
 
@@ -281,17 +310,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
     }
     if (next < ntiles) stage_issue(0, ni0, nt0);
     tc_wait(bar, phase, ok);
-    uint32_t m2 = 0u, m3 = 0u;
-    {
-      float v[32];
-      ld_col32(lane_addr + C_WORK + c0, v);
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        v[k] = leaky(v[k] + b2[k], a.slope);
-        m2 |= (v[k] > 0.f ? 1u : 0u) << k;
-      }
-      st_row32h(sm + xbuf(xb), row, c0, v);
-    }
+    const uint32_t m2 = fwd_epi(b2, xb);
     // ---- 3: h3
     if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
@@ -299,16 +318,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
       tc::mma_commit(bar);
     }
     tc_wait(bar, phase, ok);
-    {
-      float v[32];
-      ld_col32(lane_addr + C_WORK + c0, v);
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        v[k] = leaky(v[k] + b3[k], a.slope);
-        m3 |= (v[k] > 0.f ? 1u : 0u) << k;
-      }
-      st_row32h(sm + xbuf(xc), row, c0, v);
-    }
+    const uint32_t m3 = fwd_epi(b3, xc);
     // ---- 4: o; dL/do (half 0); y and the previous tile's dL/dz (half 1)
     if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
@@ -357,13 +367,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
     }
     if (next < ntiles) stage_issue(1, ni0, nt0);
     tc_wait(bar, phase, ok);
-    {
-      float v[32];
-      ld_col32(lane_addr + C_WORK + c0, v);
-#pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] *= ((m3 >> k) & 1u) ? 1.f : a.slope;
-      st_row32h(sm + xbuf(xc), row, c0, v);  // dpre3
-    }
+    bwd_epi(m3, xc);  // dpre3
     // ---- 6: dh2 = dpre3 W3; ACC_3 += dpre3^T [h2 | y]
     if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
@@ -373,13 +377,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
       tc::mma_commit(bar);
     }
     tc_wait(bar, phase, ok);
-    {
-      float v[32];
-      ld_col32(lane_addr + C_WORK + c0, v);
-#pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] *= ((m2 >> k) & 1u) ? 1.f : a.slope;
-      st_row32h(sm + xbuf(xb), row, c0, v);  // dpre2
-    }
+    bwd_epi(m2, xb);  // dpre2
     // ---- 7: dh1 = dpre2 W2; ACC_2 += dpre2^T [h1 | y]
     if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
@@ -389,13 +387,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
       tc::mma_commit(bar);
     }
     tc_wait(bar, phase, ok);
-    {
-      float v[32];
-      ld_col32(lane_addr + C_WORK + c0, v);
-#pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] *= ((m1 >> k) & 1u) ? 1.f : a.slope;
-      st_row32h(sm + xbuf(xa), row, c0, v);  // dpre1
-    }
+    bwd_epi(m1, xa);  // dpre1
     if (next < ntiles) {
       stage_wait(0);
       m1 = put_h1(xb, row_valid(ni0, nt0));

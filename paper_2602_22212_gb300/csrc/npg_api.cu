@@ -187,8 +187,10 @@ static int validate(const npg_config* c, char* why, size_t n) {
     return snprintf(why, n, "depth=%d out of 1..8", c->depth), 0;
   if (c->n_freq < 1 || c->n_freq > NPG_MAX_FREQ)
     return snprintf(why, n, "n_freq=%d out of 1..8", c->n_freq), 0;
-  if (c->time_enc < NPG_TIME_FOURIER || c->time_enc > NPG_TIME_GAUSS)
+  if (c->time_enc < NPG_TIME_FOURIER || c->time_enc > NPG_TIME_LEARNED)
     return snprintf(why, n, "time_enc=%d", c->time_enc), 0;
+  if (c->time_enc == NPG_TIME_LEARNED && (c->time_hidden < 1 || c->time_hidden > 256))
+    return snprintf(why, n, "time_hidden=%d out of 1..256", c->time_hidden), 0;
   if (c->conf_delta < NPG_DELTA_SQRT || c->conf_delta > NPG_DELTA_INTERP)
     return snprintf(why, n, "conf_delta=%d", c->conf_delta), 0;
   if (c->conf_omega < NPG_OMEGA_CUMULATIVE || c->conf_omega > NPG_OMEGA_SINGLE)
@@ -211,6 +213,14 @@ static int validate(const npg_config* c, char* why, size_t n) {
 }
 
 // ----------------------------------------------------------------- create
+
+// Largest bucket resolution the autotuner may try for a set of T frames whose
+// default is G: 1.25 G, at most 256, with T G^3 below 32M cell starts.
+static int tune_cap(int G, int T) {
+  int g = std::min(256, (G * 5 + 3) / 4);
+  while (g > G && (double)g * g * g * T > 32.0e6) --g;
+  return std::max(g, G);
+}
 
 static int copy_in(npg_ctx* c, void* dst, const void* src, size_t bytes, int on_device) {
   if (bytes == 0) return NPG_OK;
@@ -325,8 +335,10 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
   md.K = md.Z + 2 * md.M;
   md.NO = cfg->rot_mode == NPG_ROT_QUAT ? 7 : 6;
   md.slope = cfg->leaky_slope;
-  c->mlp_len = (long long)md.H * md.K + md.H + (long long)(md.D - 1) * (md.H * md.H + md.H) +
+  md.Ht = cfg->time_enc == NPG_TIME_LEARNED ? cfg->time_hidden : 0;
+  md.dec_len = (long long)md.H * md.K + md.H + (long long)(md.D - 1) * (md.H * md.H + md.H) +
                (long long)md.NO * md.H + md.NO;
+  c->mlp_len = md.dec_len + (md.Ht > 0 ? 2LL * md.Ht + 2LL * md.M * md.Ht + 2 * md.M : 0);
   if ((long long)mlp_len != c->mlp_len)
     return fail(set_err(c, NPG_EINVAL, "mlp_len %zu != expected %lld", mlp_len, c->mlp_len));
   if (cfg->precision == NPG_FP32) {
@@ -338,6 +350,8 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
       return fail(set_err(c, NPG_ENOTIMPL, "FP32 backward needs %zu B shared memory (H=%d depth=%d)",
                           mlp_bwd_fp32_smem(md), md.H, md.D));
   } else if (cfg->precision == NPG_BF16_MLP) {
+    if (md.Ht > 0)
+      return fail(set_err(c, NPG_ENOTIMPL, "the learned time embedding needs precision NPG_FP32"));
     if (!decode_bf16_supported(md.H, md.D) || !backward_bf16_supported(md.K, md.Z))
       return fail(set_err(c, NPG_ENOTIMPL,
                           "BF16 path supports H in {64, 128}, depth 3, F_n + F_p + 2 n_freq <= 15; "
@@ -417,8 +431,12 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
   c->pb.G = cfg->nn_cells > 0 ? cfg->nn_cells : auto_cells(Mavg, T);
   c->xb.G = cfg->nn_cells > 0 ? cfg->nn_cells : auto_cells(N, T);
   c->pb.nsets = c->xb.nsets = T;
-  const long long Gp3 = (long long)c->pb.G * c->pb.G * c->pb.G;
-  const long long Gx3 = (long long)c->xb.G * c->xb.G * c->xb.G;
+  // room for the autotuner's finer candidates (up to 1.25 x, within the cap of
+  // 32M cell starts over all frames)
+  c->G_cap_p = tune_cap(c->pb.G, T);
+  c->G_cap_x = tune_cap(c->xb.G, T);
+  const long long Gp3 = (long long)c->G_cap_p * c->G_cap_p * c->G_cap_p;
+  const long long Gx3 = (long long)c->G_cap_x * c->G_cap_x * c->G_cap_x;
   const long long NT = (long long)N * T;
 
   bool ok = true;
@@ -439,6 +457,7 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
         alloc_n(c, c->dxhat, NT) && alloc_n(c, c->nn_x, NT) && alloc_n(c, c->d_x, NT) &&
         alloc_n(c, c->nn_p, c->MT_cap) && alloc_n(c, c->d_p, c->MT_cap) &&
         alloc_n(c, c->dz, (long long)N * md.Z);
+  if (md.Ht > 0) ok &= alloc_n(c, c->dV, (long long)T * md.H);
   ok &= alloc_n(c, c->cd, T) && alloc_n(c, c->wconf, T) && alloc_n(c, c->iso_t, T) &&
         alloc_n(c, c->loss_part, (long long)T * 8 * 3) &&
         alloc_n(c, c->loss, 4) && alloc_n(c, c->d_epoch, 1) && alloc_n(c, c->d_adam_c, 2) &&
@@ -578,6 +597,10 @@ static int forward_launch(npg_ctx* c) {
   begin_iteration_timing(c);
   mark(c, 0);
   CK(c, launch_encode(c));
+  if (c->md.Ht > 0) {
+    CK(c, launch_learned_time(c));
+    c->launches += 1;
+  }
   CK(c, launch_time_mod(c));
   mark(c, 1);
   if (c->cfg.precision == NPG_BF16_MLP)
@@ -630,6 +653,8 @@ static int loss_launch(npg_ctx* c) {
 static int backprop_launch(npg_ctx* c) {
   CK(c, cudaMemsetAsync(c->g_mlp, 0, sizeof(float) * c->mlp_len, c->stream));
   CK(c, cudaMemsetAsync(c->dz, 0, sizeof(float) * (size_t)c->N * c->md.Z, c->stream));
+  if (c->dV)
+    CK(c, cudaMemsetAsync(c->dV, 0, sizeof(float) * (size_t)c->T * c->md.H, c->stream));
   // the grid gradient (every level; 0.6 GB at the paper's sizes) is cleared on
   // lane 1 while the MLP backward, which neither reads nor writes it, runs
   CK(c, lanes_fork(c, 2));
@@ -639,6 +664,10 @@ static int backprop_launch(npg_ctx* c) {
   else
     CK(c, launch_mlp_backward_fp32(c));
   CK(c, lanes_join(c, 2));
+  if (c->md.Ht > 0) {
+    CK(c, launch_learned_time_backward(c));
+    c->launches += 1;
+  }
   mark(c, 8);
   CK(c, launch_scatter(c));
   mark(c, 9);
@@ -1074,6 +1103,109 @@ extern "C" int npg_timing_read(npg_ctx* c, int stage, double* total_ms, int* n_i
 }
 
 extern "C" long long npg_launch_count(const npg_ctx* c) { return c ? c->launches : 0; }
+
+// ----------------------------------------------------------------- autotuner
+// Milliseconds per pass of `reps` forward passes (plus the loss when with_loss)
+// at the current launch shapes, on the context's stream. Parameters, Adam
+// state and e are untouched; the nearest-neighbour results (which are also
+// the next search's seeds) are recomputed.
+static int time_passes(npg_ctx* c, int reps, bool with_loss, float* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(c, cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(c, ce, "cudaEventCreate");
+  }
+  int rc = forward_launch(c);  // warm-up at these shapes
+  if (!rc && with_loss) rc = loss_launch(c);
+  if (!rc) {
+    cudaEventRecord(e0, c->stream);
+    for (int k = 0; k < reps && !rc; ++k) {
+      rc = forward_launch(c);
+      if (!rc && with_loss) rc = loss_launch(c);
+    }
+    cudaEventRecord(e1, c->stream);
+    ce = cudaEventSynchronize(e1);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(ms, e0, e1);
+    if (ce != cudaSuccess) rc = cuda_fail(c, ce, "autotune timing");
+    *ms /= (float)reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+extern "C" int npg_autotune(npg_ctx* c, int reps, int* chosen) {
+  int rc = guard(c);
+  if (rc) return rc;
+  if (reps < 1 || reps > 100) return set_err(c, NPG_EINVAL, "reps out of 1..100");
+  if (c->cfg.nn_cells > 0) return set_err(c, NPG_EINVAL, "nn_cells is fixed by the configuration");
+  CK(c, cudaStreamSynchronize(c->stream));
+  // search grids: the default resolution G scaled by 0.7 .. 1.25 (the search
+  // stays exact at every resolution); the point side is rebuilt per candidate
+  const int gx0 = c->xb.G, gp0 = c->pb.G;
+  const double scale[4] = {0.7, 0.85, 1.0, 1.25};
+  auto cand = [](int g0, double f, int cap) {
+    return std::max(1, std::min(cap, (int)lround(g0 * f)));
+  };
+  float best = 0.f, ms = 0.f;
+  int bx = gx0, bp = gp0;
+  bool first = true;
+  for (int k = 0; k < 4; ++k) {  // vertex side, point side at its default
+    c->xb.G = cand(gx0, scale[k], c->G_cap_x);
+    if ((rc = time_passes(c, reps, true, &ms))) return rc;
+    if (first || ms < best) {
+      best = ms;
+      bx = c->xb.G;
+      first = false;
+    }
+  }
+  c->xb.G = bx;
+  first = true;
+  for (int k = 0; k < 4; ++k) {  // point side at the chosen vertex side
+    c->pb.G = cand(gp0, scale[k], c->G_cap_p);
+    if ((rc = build_point_buckets(c))) return rc;
+    if ((rc = time_passes(c, reps, true, &ms))) return rc;
+    if (first || ms < best) {
+      best = ms;
+      bp = c->pb.G;
+      first = false;
+    }
+  }
+  c->pb.G = bp;
+  if ((rc = build_point_buckets(c))) return rc;
+  // CTAs per SM of the BF16 decode (timed on the forward pass alone)
+  if (c->cfg.precision == NPG_BF16_MLP && c->md.H == 64) {
+    const int opts[4] = {3, 4, 6, 8};
+    int bd = c->dec_per_sm;
+    first = true;
+    for (int k = 0; k < 4; ++k) {
+      c->dec_per_sm = opts[k];
+      if ((rc = time_passes(c, reps, false, &ms))) return rc;
+      if (first || ms < best) {
+        best = ms;
+        bd = opts[k];
+        first = false;
+      }
+    }
+    c->dec_per_sm = bd;
+  }
+  // the shapes are baked into a captured iteration: capture it again
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+  }
+  c->phase = 0;
+  if (chosen) {
+    chosen[0] = c->xb.G;
+    chosen[1] = c->pb.G;
+    chosen[2] = c->dec_per_sm;
+  }
+  return NPG_OK;
+}
 
 // ----------------------------------------------------------------- evaluation
 extern "C" int npg_evaluate(npg_ctx* c, const float* gt_xyz, int on_device, float tau_rel,

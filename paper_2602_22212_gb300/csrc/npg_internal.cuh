@@ -49,12 +49,18 @@ struct NnQueue {
 struct MlpDims {
   int H, D, K, Z, NO, M;  // hidden width, hidden layers, first-layer inputs, latent, outputs, freqs
   float slope;
+  int Ht;                 // hidden width of the learned time embedding (0: a fixed encoding)
+  long long dec_len;      // decoder parameters; psi_t's follow them
 };
 
 }  // namespace npg
 
 struct npg_ctx {
   npg_config cfg;
+  // tunable launch shapes (npg_autotune): bucket cells per axis of the two
+  // search grids are pb.G / xb.G below; CTAs per SM of the BF16 decode
+  int dec_per_sm = 6;
+  int G_cap_p = 0, G_cap_x = 0;  // the bucket arrays hold up to this many cells per axis
   cudaStream_t stream = nullptr;
   int dev = 0;
   int N = 0, T = 0, t_key = 0, E = 0;
@@ -112,6 +118,8 @@ struct npg_ctx {
   float* m_mlp = nullptr;
   float* v_mlp = nullptr;
   float* mlp_bf16 = nullptr;  // packed tensor-core weights (BF16 path)
+  float* dV = nullptr;        // T x H: sum over vertices of dL/d(first-layer pre-activation)
+                              // (learned time embedding)
   float* wide = nullptr;      // FP32 path with H > 64: per-chunk activations and gradients
   long long wide_rows = 0;    // rows per chunk of that path
 
@@ -169,6 +177,9 @@ namespace npg {
 cudaError_t launch_encode(npg_ctx* c);
 cudaError_t launch_time_table(npg_ctx* c);
 cudaError_t launch_time_mod(npg_ctx* c);
+// learned time embedding: gamma from psi_t's parameters; the reverse pass from dV
+cudaError_t launch_learned_time(npg_ctx* c);
+cudaError_t launch_learned_time_backward(npg_ctx* c);
 cudaError_t launch_decode_fp32(npg_ctx* c);
 cudaError_t launch_decode_bf16(npg_ctx* c);
 cudaError_t launch_decode_bf16_h128(npg_ctx* c);

@@ -25,7 +25,7 @@ _lib = C.CDLL(LIB_PATH)
 
 MAX_LEVELS = 16
 MAX_FREQ = 8
-TIME_FOURIER, TIME_POLY, TIME_GAUSS = 0, 1, 2
+TIME_FOURIER, TIME_POLY, TIME_GAUSS, TIME_LEARNED = 0, 1, 2, 3
 DELTA_SQRT, DELTA_CONST, DELTA_LINEAR, DELTA_EXP, DELTA_INTERP = 0, 1, 2, 3, 4
 OMEGA_CUMULATIVE, OMEGA_CONST, OMEGA_HALF, OMEGA_SINGLE = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
@@ -78,6 +78,7 @@ class npg_config(C.Structure):
         ("time_B", C.c_float * MAX_FREQ),
         ("conf_delta", C.c_int),
         ("conf_omega", C.c_int),
+        ("time_hidden", C.c_int),
     ]
 
 
@@ -117,6 +118,7 @@ _SIG = {
     "npg_batch_iteration": (_i, [_vp, _vp]),
     "npg_batch_destroy": (_i, [_vp]),
     "npg_fp32_fma_rate": (_i, [C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
+    "npg_autotune": (_i, [_vp, _i, C.POINTER(C.c_int)]),
 }
 for _name, (_res, _args) in _SIG.items():
     _f = getattr(_lib, _name)
@@ -359,6 +361,14 @@ def npg_precondition_static(g, out, r, F, lam, stream=None):
                                         _stream_handle(stream)))
 
 
+def npg_autotune(ctx, reps=3):
+    """Tune the context's launch shapes; returns (vertex-side cells, point-side
+    cells, decode CTAs per SM)."""
+    out = (C.c_int * 3)()
+    _check(_lib.npg_autotune(ctx, int(reps), out), ctx)
+    return tuple(int(v) for v in out)
+
+
 def npg_fp32_fma_rate(stream=None):
     """(TFLOP/s, ms) of the FP32 FMA probe on the current device."""
     t, ms = C.c_double(0), C.c_double(0)
@@ -372,7 +382,7 @@ def make_config(L, res, F_p, H, depth, *, F_n=2, res_n=4, slope=0.01, rot_mode=R
                 precision=FP32, e_max=1000, w_iso=100.0, lr_mlp=1e-3, lr_grid=None,
                 lam=None, n_freq=4, alpha=0.1, nn_cells=0, use_graph=False, stream=None,
                 precond_mode=PRECOND_FP32, time_enc=TIME_FOURIER, time_B=None,
-                conf_delta=DELTA_SQRT, conf_omega=OMEGA_CUMULATIVE):
+                conf_delta=DELTA_SQRT, conf_omega=OMEGA_CUMULATIVE, time_hidden=0):
     """npg_config with the paper's defaults (Sec. 3.2-3.5) and explicit resolutions."""
     cfg = npg_config_default(L, 2, 2, F_p, H, depth)
     for k, r in enumerate(res):
@@ -385,6 +395,7 @@ def make_config(L, res, F_p, H, depth, *, F_n=2, res_n=4, slope=0.01, rot_mode=R
         nn_cells), int(bool(use_graph))
     cfg.precond_mode = int(precond_mode)
     cfg.time_enc, cfg.conf_delta, cfg.conf_omega = int(time_enc), int(conf_delta), int(conf_omega)
+    cfg.time_hidden = int(time_hidden)
     for j, b in enumerate(time_B if time_B is not None else []):
         cfg.time_B[j] = float(b)
     if lr_grid is not None:
@@ -401,7 +412,11 @@ def mlp_len(cfg) -> int:
     H, D = cfg.H, cfg.depth
     K = cfg.F_n + cfg.F_p + 2 * cfg.n_freq
     NO = 7 if cfg.rot_mode == ROT_QUAT else 6
-    return H * K + H + (D - 1) * (H * H + H) + NO * H + NO
+    n = H * K + H + (D - 1) * (H * H + H) + NO * H + NO
+    if cfg.time_enc == TIME_LEARNED:
+        Ht, G2 = cfg.time_hidden, 2 * cfg.n_freq
+        n += 2 * Ht + G2 * Ht + G2
+    return n
 
 
 def grid_len(cfg) -> int:

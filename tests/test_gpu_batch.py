@@ -141,3 +141,33 @@ def test_batch_throughput_reported(npg):
         npg.npg_batch_destroy(batch)
         for c in cb + ones:
             c.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotune_keeps_results_exact(npg, precision):
+    """npg_autotune picks each sequence's search-grid resolutions (and, for the
+    BF16 form, the decode's CTAs per SM) among its candidates; the searches are
+    exact at every resolution, so the first loss after tuning equals the loss
+    before it bit for bit, and the tuned contexts then run as a batch."""
+    import torch
+    seqs = [make_seq(*s) for s in SPECS[:3]]
+    streams = [torch.cuda.Stream() for _ in seqs]
+    ctxs = contexts(npg, seqs, precision, streams, use_graph=bool(precision))
+    for ctx in ctxs:
+        ctx.forward()
+        before, _ = ctx.loss()
+        chosen = npg.npg_autotune(ctx.h, 2)
+        assert chosen[0] >= 1 and chosen[1] >= 1
+        if precision:
+            assert chosen[2] in (3, 4, 6, 8)
+        ctx.forward()
+        after, _ = ctx.loss()
+        np.testing.assert_array_equal(after, before)
+    batch = npg.npg_batch_create([c.h for c in ctxs], torch.cuda.Stream())
+    out = np.zeros((len(ctxs), 3))
+    for _ in range(3):
+        npg.npg_batch_iteration(batch, out)
+        assert np.all(np.isfinite(out))
+    npg.npg_batch_destroy(batch)
+    for c in ctxs:
+        c.close()

@@ -580,3 +580,60 @@ def test_ablation_variants_parity(npg, variant):
         check_grad_block(name, (gg if name.startswith("grid") else gm)[sl],
                          (want_g if name.startswith("grid") else want_m)[sl], rng)
     ctx.close()
+
+
+@pytest.mark.parametrize("H,slope", [(64, 1.0), (64, 0.01), (128, 1.0)])
+def test_learned_time_embedding_parity(npg, H, slope):
+    """The learned time embedding of the time-encoding ablation (Sec. 4),
+    gamma(t) = psi_t(t~) with 16 hidden units, on the FP32 paths (H = 64 fused,
+    H = 128 layered): x-hat, loss, cd_t and the gradient of every parameter
+    block, psi_t's included, from the same dL/dx-hat as the oracle; then one
+    full iteration through npg_iteration."""
+    import torch
+    seq = I.sphere_blob(subdiv=4, T=8, M=4096, noise=0.005, seed=2)
+    res = (8, 27, 45, 64)
+    ocfg = O.make_cfg(L=4, res=res, F=2, H=H, D=2, slope=slope, time_enc=3, time_hidden=16)
+    prob = O.Problem(ocfg, seq.x, seq.n, seq.faces, seq.points, seq.offsets, seq.t_key)
+    rng = np.random.default_rng(31)
+    grid = rng.normal(scale=0.3, size=O.grid_len(ocfg)).astype(np.float32)
+    nt = O.time_params(ocfg)
+    dec = I.mlp_init(O.k_in(ocfg), H, 2, O.n_out(ocfg), seed=32, zero_last=False)
+    dec[-(O.n_out(ocfg) * H + O.n_out(ocfg)):] *= 0.5
+    mlp = np.concatenate([dec, rng.normal(scale=0.7, size=nt)]).astype(np.float32)
+    assert len(mlp) == O.mlp_len(ocfg)
+    ref = O.loss_full(prob, f32(grid), f32(mlp), 3, 10, decide_f32=True)
+    cfg = npg.make_config(4, res, 2, H, 2, slope=slope, e_max=10, time_enc=npg.TIME_LEARNED,
+                          time_hidden=16)
+    assert npg.mlp_len(cfg) == len(mlp)
+    ctx = npg.Context(cfg, seq, mlp)
+    ctx.set(npg.BUF_GRID, grid)
+    npg.npg_set_epoch(ctx.h, 3)
+    ctx.forward()
+    xh = ctx.get(npg.BUF_XHAT).reshape(prob.T, prob.N, 3)
+    assert np.abs(xh - ref["xhat"]).max() <= 1e-5
+    loss, cd = ctx.loss()
+    np.testing.assert_allclose(cd, ref["cd"], rtol=LOSS_RTOL)
+    assert abs(loss[0] - ref["loss"]) <= LOSS_RTOL * ref["loss"]
+    gx32 = ref["g_xhat"].astype(np.float32)
+    want_g, want_m = O.backprop(prob, f32(grid), f32(mlp), f32(gx32))
+    npg.npg_backprop(ctx.h, torch.from_numpy(gx32.reshape(-1)).cuda())
+    gg = ctx.get(npg.BUF_GRID_GRAD).astype(np.float64)
+    gm = ctx.get(npg.BUF_MLP_GRAD).astype(np.float64)
+    rng = np.random.default_rng(10)
+    gb, mb = blocks_of(ocfg)
+    for name, sl in gb + mb + [("psi_t", slice(len(mlp) - nt, len(mlp)))]:
+        check_grad_block(name, (gg if name.startswith("grid") else gm)[sl],
+                         (want_g if name.startswith("grid") else want_m)[sl], rng)
+    it = ctx.iteration()
+    assert np.all(np.isfinite(it))
+    ctx.close()
+
+
+def test_learned_time_embedding_needs_fp32(npg):
+    seq = I.sphere_blob(subdiv=2, T=3, M=200, seed=0)
+    cfg = npg.make_config(2, [8, 17], 4, 64, 3, precision=npg.BF16_MLP,
+                          time_enc=npg.TIME_LEARNED, time_hidden=8)
+    mlp = np.zeros(npg.mlp_len(cfg), np.float32)
+    with pytest.raises(npg.NpgError) as ei:
+        npg.Context(cfg, seq, mlp)
+    assert ei.value.code == npg.ENOTIMPL
