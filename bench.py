@@ -202,9 +202,8 @@ def stage_work(p, N, T, MT, mlp_dims, precond="fp32", precision="fp32", mlp_len=
         "decode": (mlp_kind, fwd_row * rows, "FLOP"),
         "mlp_bwd": (mlp_kind, bwd_row * rows, "FLOP"),
         # the grid levels' Adam steps run inside the preconditioner stage (each
-        # level's DCT passes and Adam on one of four concurrent stream lanes,
-        # Adam in the last pass's epilogue on the tensor-core levels); the adam
-        # stage is the MLP's. Algorithmic bytes per grid parameter: read and
+        # level's DCT passes and Adam on one of four concurrent stream lanes);
+        # the adam stage is the MLP's. Algorithmic bytes per grid parameter: read and
         # write of the gradient for Eq. 9 (8 B) and Adam's read of p, g~, m, v
         # and write of p, m, v (28 B). The six DCT passes move 48 B per value
         # (implementation traffic, `dct_bytes`).
@@ -468,7 +467,7 @@ def main():
                     help="time that many uneven sequences as one batch (npg_batch_*) against "
                          "running them one by one, instead of the single-sequence step")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="--batch: keep every sequence's default launch shapes")
+                    help="keep the default launch shapes (no npg_autotune) in the BF16 form")
     ap.add_argument("--micro", default=None, choices=["precond_tc", "precond_fp32"],
                     help="time one kernel family alone on a standalone grid instead of the step")
     ap.add_argument("--micro-res", type=int, default=256)
@@ -505,6 +504,13 @@ def main():
     cfg = make_cfg(npg, p, args.precision, graph, stream, e_max, precond)
     ctx = npg.Context(cfg, seq, mlp, device_inputs=True)
     N, T, MT = seq.N, seq.T, int(seq.offsets[-1])
+    # the batched form's launch shapes come from the project's autotuner
+    # (search-grid resolutions, decode CTAs per SM); the plain form keeps the
+    # defaults. Tuning runs forward and loss passes only: the optimisation
+    # state is unchanged.
+    tuned = None
+    if args.precision == "bf16" and not args.no_autotune:
+        tuned = npg.npg_autotune(ctx.h, 3)
 
     def barrier():
         if dist is not None:
@@ -541,6 +547,8 @@ def main():
     if graph:
         cfg2 = make_cfg(npg, p, args.precision, False, stream, e_max, precond)
         sctx = npg.Context(cfg2, seq, mlp, device_inputs=True)
+        if tuned is not None:
+            npg.npg_autotune(sctx.h, 3)
         for _ in range(args.warmup):
             sctx.iteration()
     npg.npg_timing(sctx.h, args.steps)
@@ -690,7 +698,9 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16" if args.precision == "bf16" else "f32",
             "data": "synthetic (seeded capsule-figure sequence; no dataset)",
-            "config": config_dict(p, seq, form, graph),
+            "config": dict(config_dict(p, seq, form, graph), autotuned=(
+                dict(vertex_cells=tuned[0], point_cells=tuned[1], decode_ctas_per_sm=tuned[2])
+                if tuned else None)),
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(seq.points.nbytes + seq.offsets.nbytes),
                     "d2h_bytes_per_step": 24},

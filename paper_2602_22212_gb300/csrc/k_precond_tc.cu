@@ -95,15 +95,6 @@ __device__ __forceinline__ void split4(float4 x, uint2& hi, uint2& lo) {
   lo = make_uint2(l[0], l[1]);
 }
 
-// Adam on one value (the same arithmetic as adam4_kernel), c1 = 1 - beta1^s,
-// c2 = 1 - beta2^s.
-__device__ __forceinline__ void adam_update(const PcAdam& ad, float c1, float c2, float g,
-                                            float& m, float& v, float& p) {
-  m = fmaf(ad.b1, m, (1.f - ad.b1) * g);
-  v = fmaf(ad.b2, v, (1.f - ad.b2) * g * g);
-  p -= ad.lr * (m / c1) / (sqrtf(v / c2) + ad.eps);
-}
-
 // Bounded wait shared by every role; gives up (and flags the CTA) once any
 // thread of the CTA has timed out.
 __device__ __forceinline__ bool pc_wait(uint64_t* bar, uint32_t phase, volatile int* abort,
@@ -132,8 +123,7 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
     const float* __restrict__ in, float* __restrict__ out, const uint8_t* __restrict__ tabs,
     const float* __restrict__ mu, int r, int F, float lambda, int* err,
     const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
-    __nv_bfloat16* __restrict__ ohi, __nv_bfloat16* __restrict__ olo, long long pitch,
-    PcAdam ad) {
+    __nv_bfloat16* __restrict__ ohi, __nv_bfloat16* __restrict__ olo, long long pitch) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + PcSmem::BAR);
@@ -296,7 +286,6 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
     const int cg_hi = RL::EW == 8 ? cg_lo + 64 : 128;
     const uint32_t qlane = (uint32_t)((warp & 3) * 32) << 16;
     const long long rF = (long long)r * F;
-    const float c1 = ad.p ? ad.cc[0] : 1.f, c2 = ad.p ? ad.cc[1] : 1.f;
     uint32_t lt = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
       const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
@@ -348,18 +337,6 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
               } else {
                 const long long o = ((long long)pa * r + pb) * rF + (long long)k * 4;
                 __stcs(reinterpret_cast<float4*>(out + o), make_float4(x0, x1, x2, x3));
-                if (ad.p) {
-                  float4 p4 = __ldcs(reinterpret_cast<const float4*>(ad.p + o));
-                  float4 m4 = __ldcs(reinterpret_cast<const float4*>(ad.m + o));
-                  float4 v4 = __ldcs(reinterpret_cast<const float4*>(ad.v + o));
-                  adam_update(ad, c1, c2, x0, m4.x, v4.x, p4.x);
-                  adam_update(ad, c1, c2, x1, m4.y, v4.y, p4.y);
-                  adam_update(ad, c1, c2, x2, m4.z, v4.z, p4.z);
-                  adam_update(ad, c1, c2, x3, m4.w, v4.w, p4.w);
-                  __stcs(reinterpret_cast<float4*>(ad.m + o), m4);
-                  __stcs(reinterpret_cast<float4*>(ad.v + o), v4);
-                  __stcs(reinterpret_cast<float4*>(ad.p + o), p4);
-                }
               }
             }
           } else {
@@ -383,9 +360,7 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
                 ohi[o] = h;
                 olo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
               } else {
-                const long long o = (long long)pi * rF + (long long)k * F + c;
-                out[o] = x;
-                if (ad.p) adam_update(ad, c1, c2, x, ad.m[o], ad.v[o], ad.p[o]);
+                out[(long long)pi * rF + (long long)k * F + c] = x;
               }
             }
           }
@@ -499,8 +474,7 @@ static bool split_map(CUtensorMap* m, const __nv_bfloat16* base, int rows, long 
 // intermediates (hi then lo BF16 arrays).
 cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float* t1,
                                    const uint16_t* tabC, const uint16_t* tabCt, const float* mu,
-                                   int r, int F, float lambda, int* err, cudaStream_t s,
-                                   const PcAdam* adam) {
+                                   int r, int F, float lambda, int* err, cudaStream_t s) {
   const size_t smem = PcSmem::TOTAL + 1024;
   static bool attr = false;
   int dev = 0, sms = 148;
@@ -535,23 +509,20 @@ cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float*
   if (!split_map(&mh0, h0, r, ncol, pitch) || !split_map(&ml0, l0, r, ncol, pitch) ||
       !split_map(&mh1, h1, r, ncol, pitch) || !split_map(&ml1, l1, r, ncol, pitch))
     return cudaErrorInvalidValue;
-  // g -> t0 (split) -> t1 -> t0 (scaled) -> t1 -> t0 -> out (FP32), the last
-  // pass with the Adam step of the level fused into its epilogue when asked
+  // g -> t0 (split) -> t1 -> t0 (scaled) -> t1 -> t0 -> out (FP32)
   constexpr int T0 = Roles<false>::THREADS, T1 = Roles<true>::THREADS;
-  const PcAdam none{};
-  const PcAdam last = adam ? *adam : none;
   dct_pass_tc_kernel<false, false, true><<<grid, T0, smem, s>>>(
-      g, nullptr, C, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch, none);
+      g, nullptr, C, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch);
   dct_pass_tc_kernel<false, true, true><<<grid, T1, smem, s>>>(
-      nullptr, nullptr, C, mu, r, F, lambda, err, mh0, ml0, h1, l1, pitch, none);
+      nullptr, nullptr, C, mu, r, F, lambda, err, mh0, ml0, h1, l1, pitch);
   dct_pass_tc_kernel<true, true, true><<<grid, T1, smem, s>>>(
-      nullptr, nullptr, C, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch, none);
+      nullptr, nullptr, C, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch);
   dct_pass_tc_kernel<false, true, true><<<grid, T1, smem, s>>>(
-      nullptr, nullptr, Ct, mu, r, F, lambda, err, mh0, ml0, h1, l1, pitch, none);
+      nullptr, nullptr, Ct, mu, r, F, lambda, err, mh0, ml0, h1, l1, pitch);
   dct_pass_tc_kernel<false, true, true><<<grid, T1, smem, s>>>(
-      nullptr, nullptr, Ct, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch, none);
+      nullptr, nullptr, Ct, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch);
   dct_pass_tc_kernel<false, true, false><<<grid, T1, smem, s>>>(
-      nullptr, out, Ct, mu, r, F, lambda, err, mh0, ml0, nullptr, nullptr, pitch, last);
+      nullptr, out, Ct, mu, r, F, lambda, err, mh0, ml0, nullptr, nullptr, pitch);
   return cudaGetLastError();
 }
 

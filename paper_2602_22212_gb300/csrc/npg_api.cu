@@ -694,29 +694,18 @@ static int step_launch(npg_ctx* c) {
     cudaStream_t ls = c->lane[j];
     const float* tab = c->dct + c->dct_off[l];
     const long long rr = (long long)lv.r * lv.r;
-    if (c->cfg.precond_mode == NPG_PRECOND_TC && lv.r >= PRECOND_TC_MIN_R) {
-      // Adam of the level in the epilogue of its last pass
-      PcAdam ad;
-      ad.p = c->grid + lv.off;
-      ad.m = c->m_grid + lv.off;
-      ad.v = c->v_grid + lv.off;
-      ad.cc = c->d_adam_c;
-      ad.lr = lv.lr;
-      ad.b1 = f.adam_beta1;
-      ad.b2 = f.adam_beta2;
-      ad.eps = f.adam_eps;
+    if (c->cfg.precond_mode == NPG_PRECOND_TC && lv.r >= PRECOND_TC_MIN_R)
       CK(c, launch_precondition_tc(c->g_grid + lv.off, c->g_pc + lv.off, c->lane_tmp[j][0],
                                    c->lane_tmp[j][1], c->dct_tc + c->dct_tc_off[l][0],
                                    c->dct_tc + c->dct_tc_off[l][1], tab + 2 * rr, lv.r, lv.F,
-                                   lv.lambda, c->d_err, ls, &ad));
-    } else {
+                                   lv.lambda, c->d_err, ls));
+    else
       CK(c, launch_precondition(c->g_grid + lv.off, c->g_pc + lv.off, c->lane_tmp[j][0],
                                 c->lane_tmp[j][1], tab, tab + rr, tab + 2 * rr, lv.r, lv.F,
                                 lv.lambda, ls));
-      CK(c, launch_adam(c->grid + lv.off, c->g_pc + lv.off, c->m_grid + lv.off,
-                        c->v_grid + lv.off, lv.n, lv.lr, f.adam_beta1, f.adam_beta2, f.adam_eps,
-                        c->d_adam_c, ls));
-    }
+    CK(c, launch_adam(c->grid + lv.off, c->g_pc + lv.off, c->m_grid + lv.off,
+                      c->v_grid + lv.off, lv.n, lv.lr, f.adam_beta1, f.adam_beta2, f.adam_eps,
+                      c->d_adam_c, ls));
   }
   CK(c, lanes_join(c, npg_ctx::NLANE));
   mark(c, 10);
@@ -725,10 +714,7 @@ static int step_launch(npg_ctx* c) {
   CK(c, launch_step_finish(c->d_epoch, c->stream));
   mark(c, 11);
   end_iteration_timing(c);
-  int fused = 0;  // levels whose Adam step runs inside their last pass
-  for (int l = 0; l < c->nlev; ++l)
-    fused += c->cfg.precond_mode == NPG_PRECOND_TC && c->lev[l].r >= PRECOND_TC_MIN_R;
-  c->launches += 1 + 6LL * c->nlev + (c->nlev - fused) + 1 + 1;
+  c->launches += 1 + 6LL * c->nlev + c->nlev + 1 + 1;
   return NPG_OK;
 }
 

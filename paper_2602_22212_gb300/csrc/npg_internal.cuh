@@ -219,20 +219,9 @@ size_t dct_tc_table_elems(int r);
 // r^3 x F level: its split hi / lo intermediates with padded rows.
 size_t dct_tc_scratch_elems(int r, int F);
 void dct_tc_tables(int r, const float* Mx, uint16_t* dst);
-// Adam applied in the last preconditioner pass (p == nullptr: none): the level's
-// parameters p, moments m, v (same layout as the gradient), its rate and the
-// device pair cc = {1 - beta1^s, 1 - beta2^s} of the current step.
-struct PcAdam {
-  float* p = nullptr;
-  float* m = nullptr;
-  float* v = nullptr;
-  const float* cc = nullptr;
-  float lr = 0.f, b1 = 0.f, b2 = 0.f, eps = 0.f;
-};
 cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float* t1,
                                    const uint16_t* tabC, const uint16_t* tabCt, const float* mu,
-                                   int r, int F, float lambda, int* err, cudaStream_t s,
-                                   const PcAdam* adam = nullptr);
+                                   int r, int F, float lambda, int* err, cudaStream_t s);
 constexpr int PRECOND_TC_MIN_R = 24;
 cudaError_t launch_points_to_float4(const float* src, float4* dst, long long n, cudaStream_t s);
 cudaError_t launch_xhat_out(const float4* xhat, float* out, long long n, cudaStream_t s);
