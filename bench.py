@@ -61,7 +61,8 @@ KERNEL_SOURCES = {
                            "npg_device.cuh"),
 }
 MEASURED_TRAFFIC = {
-    ("mlp_bwd_tc2_kernel", "paper"): {"bytes": None, "sha256": None},
+    ("mlp_bwd_tc2_kernel", "paper"): {"bytes": 78.875136e6 + 1.362944e6,
+                                      "sha256": "2cc64b65795ab87505786cb2af8984336681ab90a9c9c8495e067ecf11c035bb"},
 }
 
 
@@ -426,8 +427,9 @@ def run_batch(args):
                    "sequences": sizes},
         "one_by_one": {"value": vf / (ms1 * 1e-3), "unit": UNIT, "ms_per_step": ms1,
                        "timing": "host clock, each sequence's graph synchronised"},
-        "autotuned": ([dict(vertex_cells=t[0], point_cells=t[1], decode_ctas_per_sm=t[2])
-                       for t in tuned] if tuned else None),
+        "autotuned": ([dict(vertex_cells=t[0], point_cells=t[1], decode_ctas_per_sm=t[2],
+                            ball_rows_x=t[3], ball_rows_p=t[4]) for t in tuned]
+                      if tuned else None),
         "gpu_launches": int(launches), "clocks": clocks}))
     for c in ctxs:
         c.close()
@@ -604,6 +606,15 @@ def main():
                   "derived_at_probe_clock": (fp32_peak_tflops(sms, probe_clk["sm_mhz"])
                                              if probe_clk else None)}
     work = stage_work(p, N, T, MT, (H, D, K, Z, NO), precond, args.precision, mlp.size)
+    # the searches against brute force: 2 N M_t pair evaluations per frame
+    # (both directions) would be needed without the grid; delivered per
+    # second of the two search stages, at 8 FLOP per pair
+    t_search = (stages["nn_x"] + stages["nn_p"]) * 1e-3
+    bf_pairs = 2.0 * N * MT
+    search["brute_force_equivalent"] = {
+        "pairs": bf_pairs, "pairs_per_s": bf_pairs / t_search,
+        "tflops_equivalent": 8.0 * bf_pairs / t_search / 1e12,
+        "x_fp32_peak": 8.0 * bf_pairs / t_search / 1e12 / fp32_peak}
     # search work: 8 FLOP per candidate pair (3 sub, 1 mul, 2 fma, compare)
     work["nn_x"] = ("alu", 8 * search["cand_per_query_x"] * N * T, "FLOP")
     work["nn_p"] = ("alu", 8 * search["cand_per_query_p"] * MT, "FLOP")
@@ -699,8 +710,8 @@ def main():
             "dtype": "bf16" if args.precision == "bf16" else "f32",
             "data": "synthetic (seeded capsule-figure sequence; no dataset)",
             "config": dict(config_dict(p, seq, form, graph), autotuned=(
-                dict(vertex_cells=tuned[0], point_cells=tuned[1], decode_ctas_per_sm=tuned[2])
-                if tuned else None)),
+                dict(vertex_cells=tuned[0], point_cells=tuned[1], decode_ctas_per_sm=tuned[2],
+                     ball_rows_x=tuned[3], ball_rows_p=tuned[4]) if tuned else None)),
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(seq.points.nbytes + seq.offsets.nbytes),
                     "d2h_bytes_per_step": 24},
@@ -708,7 +719,8 @@ def main():
             "roofline": roof,
             "stage_rooflines": stage_roofs,
             "stages_ms": {k: round(v, 4) for k, v in stages.items()},
-            "search": {k: round(v, 2) for k, v in search.items()},
+            "search": {k: (round(v, 2) if isinstance(v, float) else v)
+                       for k, v in search.items()},
             "plain_fp32": plain,
             "fp32_fma_probe": fp32_probe,
             "cpu_baseline": cpu,

@@ -370,13 +370,16 @@ NPG_API long long npg_launch_count(const npg_ctx* ctx);
  * forward (+ loss) passes, after one warm-up, for each candidate and keeps the
  * fastest: the bucket cells per axis of the vertex-side and then of the
  * point-side search grid (the default resolution times 0.7, 0.85, 1, 1.25;
- * the search is exact at every resolution), then, for the BF16 form with
- * H = 64, the decode's CTAs per SM (3, 4, 6 or 8). Parameters, Adam state and
+ * the search is exact at every resolution), the widest seed ball (6, 12, 24
+ * or 48 cell rows) that one thread covers before a query of each search
+ * direction goes to the lane-group pass, then, for the BF16 form with H = 64,
+ * the decode's CTAs per SM (3, 4, 6 or 8). Parameters, Adam state and
  * e are unchanged; the nearest-neighbour buffers hold the last search's
  * (exact) results; the call order restarts before forward, and a captured
  * iteration graph is captured again at the next npg_iteration.
- * chosen (host, nullable): 3 ints {vertex-side cells, point-side cells,
- * decode CTAs per SM}. NPG_EINVAL if cfg.nn_cells fixes the cells. Synchronizes.
+ * chosen (host, nullable): 5 ints {vertex-side cells, point-side cells,
+ * decode CTAs per SM, ball rows per thread for vertex -> point, and for point
+ * -> vertex}. NPG_EINVAL if cfg.nn_cells fixes the cells. Synchronizes.
  */
 NPG_API int npg_autotune(npg_ctx* ctx, int reps, int* chosen);
 

@@ -186,11 +186,10 @@ int auto_cells(long long points_per_set, int nsets) {
 // ball that can hold the nearest neighbour. The ball is then covered directly,
 // one row segment per (z, y) cell row within reach, instead of ring by ring:
 // every cell row costs two loads of cell starts, however many cells its
-// segment spans. Balls of up to NN_NEAR_BALL_ROWS rows are covered in pass 1,
-// wider ones in pass 2. The result is the same exact nearest neighbour; the
+// segment spans. Balls of up to `near_rows` rows (12 unless tuned) are covered
+// in pass 1, wider ones in pass 2. The result is the same exact nearest neighbour; the
 // seed only changes how much of the grid is visited.
 constexpr int NN_NEAR_RINGS = 1;
-constexpr int NN_NEAR_BALL_ROWS = 12;  // ball scans up to this many cell rows stay in pass 1
 
 struct NnGeom {
   const float4* qs;
@@ -210,6 +209,7 @@ struct NnGeom {
   int4* qitems;
   const float4* csrc;  // candidates in their own order (seed lookups)
   bool seeded;         // out_idx holds a starting candidate per query (or an invalid index)
+  int near_rows;       // widest seed ball (cell rows) that pass 1 covers
 };
 
 __device__ __forceinline__ void scan_range(const float4* __restrict__ cs, long long cb, int lo,
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(128) nn_near_kernel(NnGeom g) {
       int za, zb, ya, yb;
       ball_axis(q.z, best, G, za, zb);
       ball_axis(q.y, best, G, ya, yb);
-      if ((zb - za + 1) * (yb - ya + 1) <= NN_NEAR_BALL_ROWS) {
+      if ((zb - za + 1) * (yb - ya + 1) <= g.near_rows) {
         for (int z = za; z <= zb; ++z)
           for (int y = ya; y <= yb; ++y)
             n_rows += ball_row(g, st, cb, z, y, q, h, best, bi, n_cand) ? 1 : 0;
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(128) nn_near_kernel(NnGeom g) {
 }
 
 // ----------------------------------------------------------------- far queries, lane groups
-// The queued queries (a seed ball wider than NN_NEAR_BALL_ROWS cell rows, or
+// The queued queries (a seed ball wider than `near_rows` cell rows, or
 // no seed and still open after rings 0..1) are served by groups of NN_GROUP
 // lanes: a group takes the next item of the queue and deals the cell rows of
 // the seed's ball (nearest rows first: the query's own row, then rows
@@ -506,7 +506,7 @@ cudaError_t launch_nn(const float4* queries_sorted, long long q_uniform, const l
   if (q_total == 0) return cudaSuccess;
   NnGeom g{queries_sorted, q_uniform, q_off, nsets, q_total, cand.sorted, cand.cell_start,
            cand.G, c_off, c_uniform, out_idx, out_d, stats, queue.counters, queue.items,
-           cand.src, seeded && cand.src != nullptr};
+           cand.src, seeded && cand.src != nullptr, queue.near_rows};
   cudaError_t e = cudaMemsetAsync(queue.counters, 0, 2 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   nn_near_kernel<<<grid_blocks(q_total, 128), 128, 0, s>>>(g);

@@ -1161,6 +1161,24 @@ extern "C" int npg_autotune(npg_ctx* c, int reps, int* chosen) {
   }
   c->pb.G = bp;
   if ((rc = build_point_buckets(c))) return rc;
+  // the widest seed ball that one thread covers before a query goes to the
+  // lane-group pass, per search direction
+  const int rows_opt[4] = {6, 12, 24, 48};
+  for (int dir = 0; dir < 2; ++dir) {
+    NnQueue& qd = dir == 0 ? c->nnq : c->nnq_p;
+    int brow = qd.near_rows;
+    first = true;
+    for (int k = 0; k < 4; ++k) {
+      qd.near_rows = rows_opt[k];
+      if ((rc = time_passes(c, reps, true, &ms))) return rc;
+      if (first || ms < best) {
+        best = ms;
+        brow = rows_opt[k];
+        first = false;
+      }
+    }
+    qd.near_rows = brow;
+  }
   // CTAs per SM of the BF16 decode (timed on the forward pass alone)
   if (c->cfg.precision == NPG_BF16_MLP && c->md.H == 64) {
     const int opts[4] = {3, 4, 6, 8};
@@ -1189,6 +1207,8 @@ extern "C" int npg_autotune(npg_ctx* c, int reps, int* chosen) {
     chosen[0] = c->xb.G;
     chosen[1] = c->pb.G;
     chosen[2] = c->dec_per_sm;
+    chosen[3] = c->nnq.near_rows;
+    chosen[4] = c->nnq_p.near_rows;
   }
   return NPG_OK;
 }

@@ -44,6 +44,7 @@ struct NnQueue {
   int* counters = nullptr;  // 2 ints: pushed, popped
   int4* items = nullptr;    // capacity >= number of queries
   int far_blocks = 1;
+  int near_rows = 12;       // seed balls of up to this many cell rows stay in pass 1
 };
 
 struct MlpDims {

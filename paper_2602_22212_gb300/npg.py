@@ -363,8 +363,8 @@ def npg_precondition_static(g, out, r, F, lam, stream=None):
 
 def npg_autotune(ctx, reps=3):
     """Tune the context's launch shapes; returns (vertex-side cells, point-side
-    cells, decode CTAs per SM)."""
-    out = (C.c_int * 3)()
+    cells, decode CTAs per SM, ball rows per thread x -> P, P -> x)."""
+    out = (C.c_int * 5)()
     _check(_lib.npg_autotune(ctx, int(reps), out), ctx)
     return tuple(int(v) for v in out)
 
