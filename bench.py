@@ -61,8 +61,7 @@ KERNEL_SOURCES = {
                            "npg_device.cuh"),
 }
 MEASURED_TRAFFIC = {
-    ("mlp_bwd_tc2_kernel", "paper"): {"bytes": 78.875136e6 + 1.362944e6,
-                                      "sha256": "2cc64b65795ab87505786cb2af8984336681ab90a9c9c8495e067ecf11c035bb"},
+    ("mlp_bwd_tc2_kernel", "paper"): {"bytes": None, "sha256": None},
 }
 
 

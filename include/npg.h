@@ -125,7 +125,7 @@ typedef struct npg_ctx npg_ctx; /* opaque; owns all device memory it allocates *
  *                    decoder's LeakyReLU, trained with the decoder: its
  *                    parameters a, b (time_hidden each; h = act(a t~ + b)), W
  *                    (2M x time_hidden), c (2M; gamma = W h + c) follow the
- *                    decoder's in the MLP vector; NPG_FP32 only).
+ *                    decoder's in the MLP vector).
  *   time_hidden      hidden width of psi_t (NPG_TIME_LEARNED; 1..256).
  *   conf_delta       catch-up variable of the confidence weights (Eq. 11-12 and
  *                    the stability ablation): NPG_DELTA_SQRT (1 - sqrt(e~), the

@@ -313,7 +313,8 @@ __device__ void bwd128_stage(const TcArgs& a, int i0, int t0, uint8_t* stg, uint
   }
 }
 
-template <int ROT>
+// TSUM: also the per-frame sums of dpre1 into a.dV (learned time embedding).
+template <int ROT, bool TSUM>
 __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -578,6 +579,7 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
 #pragma unroll
       for (int k = 0; k < 32; ++k) v[k] *= ((m1 >> k) & 1u) ? 1.f : a.slope;
       st_row32(sm + xbuf(xa), row, c0, v);  // dpre1 (h1 is used up)
+      if (TSUM) frame_sums<32>(v, a.dV, t0, tl, a.T, H, c0);
     }
     // the next tile's h1 into X[b] (dpre2 is used up)
     if (next < ntiles) {
@@ -682,9 +684,12 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
 
 cudaError_t launch_mlp_backward_bf16_h128(npg_ctx* c) {
   const size_t smem = Bwd128Smem::TOTAL + 1024;
-  auto k = c->cfg.rot_mode == NPG_ROT_QUAT     ? mlp_bwd_tc128_kernel<0>
-           : c->cfg.rot_mode == NPG_ROT_EXPMAP ? mlp_bwd_tc128_kernel<1>
-                                               : mlp_bwd_tc128_kernel<2>;
+  const bool ts = c->dV != nullptr;
+  auto k = c->cfg.rot_mode == NPG_ROT_QUAT
+               ? (ts ? mlp_bwd_tc128_kernel<0, true> : mlp_bwd_tc128_kernel<0, false>)
+           : c->cfg.rot_mode == NPG_ROT_EXPMAP
+               ? (ts ? mlp_bwd_tc128_kernel<1, true> : mlp_bwd_tc128_kernel<1, false>)
+               : (ts ? mlp_bwd_tc128_kernel<2, true> : mlp_bwd_tc128_kernel<2, false>);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long tiles = (long long)((c->N + 15) / 16) * ((c->T + 7) / 8);

@@ -134,7 +134,8 @@ __device__ void bwd64_stage(const TcArgs& a, int i0, int t0, uint8_t* stg, uint6
 }
 }  // namespace
 
-template <int ROT>
+// TSUM: also the per-frame sums of dpre1 into a.dV (learned time embedding).
+template <int ROT, bool TSUM>
 __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -262,8 +263,9 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
     }
     return m;
   };
-  // WORK x act'(h) (from the mask) of this thread's 32 columns into tile k
-  auto bwd_epi = [&](uint32_t msk, int k) {
+  // WORK x act'(h) (from the mask) of this thread's 32 columns into tile k;
+  // with `sums` (dpre1 of a learned time embedding) also its per-frame sums
+  auto bwd_epi = [&](uint32_t msk, int k, bool sums) {
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
       float v[16];
@@ -272,6 +274,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
       for (int q = 0; q < 16; ++q) v[q] *= ((msk >> (16 * hh + q)) & 1u) ? 1.f : a.slope;
       st_bf16x8(sm + xbuf(k), row, c0 + 16 * hh, v);
       st_bf16x8(sm + xbuf(k), row, c0 + 16 * hh + 8, v + 8);
+      if (sums) frame_sums<16>(v, a.dV, t0, tl, a.T, H, c0 + 16 * hh);
     }
   };
   auto row_valid = [&](int i0_, int t0_) { return i0_ + il < a.N && t0_ + tl < a.T; };
@@ -367,7 +370,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
     }
     if (next < ntiles) stage_issue(1, ni0, nt0);
     tc_wait(bar, phase, ok);
-    bwd_epi(m3, xc);  // dpre3
+    bwd_epi(m3, xc, false);  // dpre3
     // ---- 6: dh2 = dpre3 W3; ACC_3 += dpre3^T [h2 | y]
     if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
       tc::mma_commit(bar);
     }
     tc_wait(bar, phase, ok);
-    bwd_epi(m2, xb);  // dpre2
+    bwd_epi(m2, xb, false);  // dpre2
     // ---- 7: dh1 = dpre2 W2; ACC_2 += dpre2^T [h1 | y]
     if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (tid == 0) {
@@ -387,7 +390,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
       tc::mma_commit(bar);
     }
     tc_wait(bar, phase, ok);
-    bwd_epi(m1, xa);  // dpre1
+    bwd_epi(m1, xa, TSUM);  // dpre1
     if (next < ntiles) {
       stage_wait(0);
       m1 = put_h1(xb, row_valid(ni0, nt0));
@@ -493,9 +496,12 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
 
 cudaError_t launch_mlp_backward_bf16_h64(npg_ctx* c) {
   const size_t smem = Bwd64Smem::TOTAL + 1024;
-  auto k = c->cfg.rot_mode == NPG_ROT_QUAT     ? mlp_bwd_tc2_kernel<0>
-           : c->cfg.rot_mode == NPG_ROT_EXPMAP ? mlp_bwd_tc2_kernel<1>
-                                               : mlp_bwd_tc2_kernel<2>;
+  const bool ts = c->dV != nullptr;
+  auto k = c->cfg.rot_mode == NPG_ROT_QUAT
+               ? (ts ? mlp_bwd_tc2_kernel<0, true> : mlp_bwd_tc2_kernel<0, false>)
+           : c->cfg.rot_mode == NPG_ROT_EXPMAP
+               ? (ts ? mlp_bwd_tc2_kernel<1, true> : mlp_bwd_tc2_kernel<1, false>)
+               : (ts ? mlp_bwd_tc2_kernel<2, true> : mlp_bwd_tc2_kernel<2, false>);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long tiles = (long long)((c->N + 15) / 16) * ((c->T + 7) / 8);

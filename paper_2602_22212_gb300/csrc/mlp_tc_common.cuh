@@ -28,6 +28,7 @@ struct TcArgs {
   const float* gamma;  // T x 2M time encoding
   float* g_mlp;
   float* dz;
+  float* dV;  // T x H, nullable: per-frame sums of dpre1 (learned time embedding)
   int* err;
   int N, T, K, Z, M, NO;
   float slope, alpha;
@@ -45,6 +46,7 @@ inline TcArgs make_tc_args(npg_ctx* c) {
   a.z = c->z;
   a.g_mlp = c->g_mlp;
   a.dz = c->dz;
+  a.dV = c->dV;
   a.err = c->d_err;
   a.N = c->N;
   a.T = c->T;
@@ -107,6 +109,23 @@ __device__ __forceinline__ void ld_col16(uint32_t taddr, float* v) {
   tc::tmem_ld_wait();
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Per-frame sums of n values per thread over the 16 lanes of each half-warp
+// (the 16 vertices of one frame in a 16 x 8 tile whose row = 16 frame +
+// vertex sits in TMEM lane row % 32 of warp row / 32), added to
+// dV[t0 + frame][col0 + j]. Every lane of the warp takes part.
+template <int NV>
+__device__ __forceinline__ void frame_sums(const float* v, float* dV, int t0, int frame, int T,
+                                           int H, int col0) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    float s = v[j];
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((lane & 15) == 0 && t0 + frame < T) atomicAdd(dV + (long long)(t0 + frame) * H + col0 + j, s);
+  }
 }
 
 // 32 consecutive FP32 columns of this thread's TMEM lane.

@@ -350,8 +350,6 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
       return fail(set_err(c, NPG_ENOTIMPL, "FP32 backward needs %zu B shared memory (H=%d depth=%d)",
                           mlp_bwd_fp32_smem(md), md.H, md.D));
   } else if (cfg->precision == NPG_BF16_MLP) {
-    if (md.Ht > 0)
-      return fail(set_err(c, NPG_ENOTIMPL, "the learned time embedding needs precision NPG_FP32"));
     if (!decode_bf16_supported(md.H, md.D) || !backward_bf16_supported(md.K, md.Z))
       return fail(set_err(c, NPG_ENOTIMPL,
                           "BF16 path supports H in {64, 128}, depth 3, F_n + F_p + 2 n_freq <= 15; "

@@ -629,11 +629,43 @@ def test_learned_time_embedding_parity(npg, H, slope):
     ctx.close()
 
 
-def test_learned_time_embedding_needs_fp32(npg):
-    seq = I.sphere_blob(subdiv=2, T=3, M=200, seed=0)
-    cfg = npg.make_config(2, [8, 17], 4, 64, 3, precision=npg.BF16_MLP,
-                          time_enc=npg.TIME_LEARNED, time_hidden=8)
-    mlp = np.zeros(npg.mlp_len(cfg), np.float32)
-    with pytest.raises(npg.NpgError) as ei:
-        npg.Context(cfg, seq, mlp)
-    assert ei.value.code == npg.ENOTIMPL
+@pytest.mark.parametrize("H", [64, 128])
+def test_learned_time_embedding_bf16(npg, H):
+    """The learned time embedding in the BF16 form (tcgen05 decode and
+    backward, which then also sum dpre1 per frame for psi_t's gradient): every
+    parameter block, psi_t's included, within the BF16 rounding bound of
+    tests/bf16_model.py of the oracle's gradient from the same dL/dx-hat."""
+    import torch
+    from bf16_model import bf16_block_bound
+    seq = I.sphere_blob(subdiv=3, T=8, M=2048, noise=0.005, seed=3)
+    res = (8, 27, 45, 64)
+    ocfg = O.make_cfg(L=4, res=res, F=4, H=H, D=3, slope=0.01, time_enc=3, time_hidden=16)
+    prob = O.Problem(ocfg, seq.x, seq.n, seq.faces, seq.points, seq.offsets, seq.t_key)
+    rng = np.random.default_rng(33)
+    grid = rng.normal(scale=0.3, size=O.grid_len(ocfg)).astype(np.float32)
+    nt = O.time_params(ocfg)
+    dec = I.mlp_init(O.k_in(ocfg), H, 3, O.n_out(ocfg), seed=34, zero_last=False)
+    dec[-(O.n_out(ocfg) * H + O.n_out(ocfg)):] *= 0.5
+    mlp = np.concatenate([dec, rng.normal(scale=0.7, size=nt)]).astype(np.float32)
+    ref = O.loss_full(prob, f32(grid), f32(mlp), 3, 10, decide_f32=True)
+    gx32 = ref["g_xhat"].astype(np.float32)
+    want_g, want_m = O.backprop(prob, f32(grid), f32(mlp), f32(gx32))
+    mag_g, mag_m = O.backprop(prob, f32(grid), f32(mlp), f32(gx32), magnitude=True)
+    cfg = npg.make_config(4, res, 4, H, 3, slope=0.01, e_max=10, precision=npg.BF16_MLP,
+                          time_enc=npg.TIME_LEARNED, time_hidden=16)
+    ctx = npg.Context(cfg, seq, mlp)
+    ctx.set(npg.BUF_GRID, grid)
+    npg.npg_set_epoch(ctx.h, 3)
+    ctx.forward()
+    xh = ctx.get(npg.BUF_XHAT).reshape(prob.T, prob.N, 3)
+    assert np.abs(xh - ref["xhat"]).max() <= 5e-3
+    npg.npg_backprop(ctx.h, torch.from_numpy(gx32.reshape(-1)).cuda())
+    gg = ctx.get(npg.BUF_GRID_GRAD).astype(np.float64)
+    gm = ctx.get(npg.BUF_MLP_GRAD).astype(np.float64)
+    gb, mb = blocks_of(ocfg)
+    for name, sl in gb + mb + [("psi_t", slice(len(mlp) - nt, len(mlp)))]:
+        g, w, m = ((gg, want_g, mag_g) if name.startswith("grid") else (gm, want_m, mag_m))
+        err, bound = np.linalg.norm(g[sl] - w[sl]), bf16_block_bound(m[sl])
+        assert err <= bound, (name, err, bound)
+    assert np.all(np.isfinite(ctx.iteration()))
+    ctx.close()
