@@ -459,7 +459,7 @@ def main():
                     help="skip timing the plain FP32 form beside the BF16 form")
     ap.add_argument("--graph", dest="graph", action="store_true", default=None)
     ap.add_argument("--no-graph", dest="graph", action="store_false")
-    ap.add_argument("--workload", default="paper", choices=["paper", "long", "tiny", "profile"])
+    ap.add_argument("--workload", default="paper", choices=["paper", "long", "stress", "tiny", "profile"])
     ap.add_argument("--precond", default=None, choices=["fp32", "tc"],
                     help="preconditioner DCT arithmetic (default: tc with bf16, fp32 with fp32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

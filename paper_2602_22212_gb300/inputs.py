@@ -344,6 +344,10 @@ def preset(name):
         return dict(gen="figure", n_vertices=20000, T=1000, M=10000, noise_rel=0.003, L=8,
                     res=linear_resolutions(8, 16, 256), F=4, H=128, D=3, slope=0.01, iters=300,
                     w_iso=1.0)
+    if name == "stress":    # 100000 vertices, 200 frames, 100000 points per frame
+        return dict(gen="figure", n_vertices=100000, T=200, M=100000, noise_rel=0.003, L=8,
+                    res=linear_resolutions(8, 16, 256), F=4, H=64, D=3, slope=0.01, iters=500,
+                    w_iso=1.0)
     if name == "profile":   # 10242 vertices, 10 frames, 20000 points: search kernels at moderate size
         return dict(gen="figure", subdiv=5, T=10, M=20000, noise_rel=0.003, L=4,
                     res=linear_resolutions(4, 16, 64), F=4, H=64, D=3, slope=0.01, iters=500,
