@@ -356,8 +356,9 @@ def run_micro(args):
 def run_batch(args):
     """Uneven sequences (sizes from inputs.batch_specs: N 5k-50k, T 50-500, M
     5k-30k, sphere blobs and capsule figures) optimised as one batch: every
-    iteration of all of them is one CUDA-graph launch with a branch per
-    sequence. value = total vertex-frames / batched iteration time; the same
+    iteration of all of them is one CUDA-graph launch, the sequences in
+    chains (npg_batch_set_width; the chain count is swept unless given).
+    value = total vertex-frames / batched iteration time; the same
     contexts run one after the other (each its own graph, synchronised in
     between) for `one_by_one`. Sequences are generated in worker processes
     (spawned before any CUDA use); generation is outside the timed region."""
@@ -384,8 +385,34 @@ def run_batch(args):
     # SM) tuned to its sizes before the batch is captured
     tuned = [npg.npg_autotune(c.h, 2) for c in ctxs] if not args.no_autotune else None
     main = torch.cuda.Stream()
-    batch = npg.npg_batch_create([c.h for c in ctxs], main)
     vf = sum(s.N * s.T for s in seqs)
+
+    def time_batch(batch, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        for _ in range(steps):
+            npg.npg_batch_iteration(batch)
+        e1.record(main)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    # the graph's concurrency: sequences in `width` chains (1: one after the
+    # other; 0: every sequence its own branch), the fastest of a short sweep
+    # (its iterations are part of the warm-up)
+    sweep = {}
+    if args.batch_width is None:
+        for w in (1, 2, 4, 0):
+            b = npg.npg_batch_create([c.h for c in ctxs], main)
+            npg.npg_batch_set_width(b, w)
+            for _ in range(2):
+                npg.npg_batch_iteration(b)
+            sweep[w] = time_batch(b, 3)
+            npg.npg_batch_destroy(b)
+        width = min(sweep, key=sweep.get)
+    else:
+        width = args.batch_width
+    batch = npg.npg_batch_create([c.h for c in ctxs], main)
+    npg.npg_batch_set_width(batch, width)
     for _ in range(args.warmup):
         npg.npg_batch_iteration(batch)
     torch.cuda.synchronize()
@@ -422,7 +449,12 @@ def run_batch(args):
         "capsule figures of uneven sizes; no dataset)",
         "config": {"workload": f"{len(seqs)} uneven sequences, {vf} vertex-frames per "
                                "iteration, 8-level grid 16->256 x F=4, MLP 3x64, w_iso=1",
-                   "form": "one CUDA graph per batch iteration, a branch per sequence",
+                   "form": "one CUDA graph per batch iteration, the sequences in "
+                           + ("one chain" if width == 1 else
+                              "a branch each" if width == 0 or width >= len(seqs) else
+                              f"{width} concurrent chains"),
+                   "chains": width,
+                   "chain_sweep_ms": {str(k): round(v, 3) for k, v in sweep.items()} or None,
                    "sequences": sizes},
         "one_by_one": {"value": vf / (ms1 * 1e-3), "unit": UNIT, "ms_per_step": ms1,
                        "timing": "host clock, each sequence's graph synchronised"},
@@ -459,6 +491,9 @@ def main():
                     help="skip timing the plain FP32 form beside the BF16 form")
     ap.add_argument("--graph", dest="graph", action="store_true", default=None)
     ap.add_argument("--no-graph", dest="graph", action="store_false")
+    ap.add_argument("--batch-width", type=int, default=None,
+                    help="with --batch: chains of sequences in the batch graph (0: one branch "
+                         "per sequence); default: the fastest of 1, 2, 4 and 0")
     ap.add_argument("--workload", default="paper", choices=["paper", "long", "stress", "tiny", "profile"])
     ap.add_argument("--precond", default=None, choices=["fp32", "tc"],
                     help="preconditioner DCT arithmetic (default: tc with bf16, fp32 with fp32)")

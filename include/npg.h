@@ -276,6 +276,14 @@ NPG_API int npg_evaluate(npg_ctx* ctx, const float* gt_xyz, int on_device, float
 typedef struct npg_batch npg_batch;
 NPG_API int npg_batch_create(npg_batch** out, int S, npg_ctx* const* ctxs, void* stream);
 NPG_API int npg_batch_iteration(npg_batch* batch, double* loss_out);
+/* Concurrency of the batch graph: the sequences form `width` chains, the
+ * sequences of one chain run one after the other, the chains concurrently.
+ * Sequences go largest first (work N T + M T) onto the chain with the least
+ * work so far. width 0 (the default) or >= S: every sequence its own branch;
+ * width 1: all of them in sequence (no contention for the GPU between
+ * sequences that each fill it). Call before the first npg_batch_iteration
+ * (NPG_EINVAL once the graph is captured); negative values count as 0. */
+NPG_API int npg_batch_set_width(npg_batch* batch, int width);
 /* NULL is allowed. Leaves the contexts alive. */
 NPG_API int npg_batch_destroy(npg_batch* batch);
 

@@ -4,8 +4,8 @@
 // rotation/translation mapping and its Jacobian) on the CUDA cores.
 //
 // A CTA of 128 threads owns tiles of 128 consecutive rows (row = t N + i);
-// thread t owns row t of the tile and TMEM lane t. One elected thread issues
-// the MMAs; completion is tracked by an mbarrier whose waits are bounded: a
+// thread t owns row t of the tile and TMEM lane t. One elected lane of warp 0
+// issues the MMAs; completion is tracked by an mbarrier whose waits are bounded: a
 // wait that gives up sets *err and the CTA frees its TMEM and exits.
 #include "mlp_tc_common.cuh"
 
@@ -29,13 +29,11 @@ __device__ __forceinline__ void st_row64(uint8_t* tile, int row, const float* v)
   }
 }
 
-// Issue D = A * B^T with K = 64 (4 steps of 16), K-major operands.
-__device__ __forceinline__ void mma_k64(uint32_t d, uint32_t a_smem, uint32_t b_smem,
-                                        uint32_t idesc) {
+// Issue D = A * B^T with K = 64 (4 steps of 16), K-major operand descriptors
+// (a K step of 16 advances the start address by 32 B, 2 in its 16 B units).
+__device__ __forceinline__ void mma_k64(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc) {
 #pragma unroll
-  for (int ks = 0; ks < 4; ++ks)
-    tc::mma_bf16(d, tc::kmajor_sw128(a_smem + 32 * ks), tc::kmajor_sw128(b_smem + 32 * ks),
-                 idesc, ks > 0);
+  for (int ks = 0; ks < 4; ++ks) tc::mma_bf16(d, a + 2 * ks, b + 2 * ks, idesc, ks > 0);
 }
 
 // Shared layout of the decode kernel (offsets from a 1024-byte aligned base).
@@ -141,12 +139,14 @@ __global__ void __launch_bounds__(128) decode_tc_kernel(TcArgs a) {
       run = __syncthreads_and(ok) != 0;
       tc::fence_after_sync();
       if (!run) break;
-      if (tid == 0) {
-        if (layer < 2)
-          mma_k64(tmem, s_act, layer == 0 ? s_w2 : s_w3, ID64);
-        else
-          mma_k64(tmem, s_act, s_wo, ID16);
-        tc::mma_commit(bar);
+      if (warp == 0) {  // descriptors from the whole warp, one elected lane issues
+        const uint64_t da = tc::kmajor_sw128(s_act);
+        const uint64_t db = tc::kmajor_sw128(layer == 0 ? s_w2 : layer == 1 ? s_w3 : s_wo);
+        if (tc::elect_one()) {
+          mma_k64(tmem, da, db, layer < 2 ? ID64 : ID16);
+          tc::mma_commit(bar);
+        }
+        __syncwarp();
       }
       if (!tc::mbar_wait(bar, phase, WAIT_TRIES)) {
         ok = false;

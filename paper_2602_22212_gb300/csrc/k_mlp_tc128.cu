@@ -34,40 +34,47 @@ __device__ void load_weight128(uint8_t* tile, uint32_t blk, const float* W, int 
   }
 }
 
+// The MMA helpers take descriptors that warp 0 computed as a whole (one
+// elected lane issues): a K step of 16 advances a K-major descriptor's start
+// address by 32 B (2 in its 16-byte units), an MN-major one by 2048 B (128);
+// the start field cannot carry out of its 14 bits below 256 KB.
+__device__ __forceinline__ uint64_t kdesc(uint32_t saddr) { return tc::kmajor_sw128(saddr); }
+// MN-major operand whose 64-wide feature halves are one [128][64] tile apart
+__device__ __forceinline__ uint64_t mdesc2(uint32_t saddr, uint32_t lbo = TC_TILE) {
+  return tc::mnmajor_sw128(saddr, lbo, 1024);
+}
+
 // D (M 128 x N) = A B^T over K = 128 features, K-major A (a [128][128] tile)
 // and B (rows of `bblk` bytes per 64-K block).
-__device__ __forceinline__ void mma_feat(uint32_t d, uint32_t a, uint32_t b, uint32_t bblk,
+__device__ __forceinline__ void mma_feat(uint32_t d, uint64_t a, uint64_t b, uint32_t bblk,
                                          uint32_t idesc) {
 #pragma unroll
   for (int kb = 0; kb < 2; ++kb)
 #pragma unroll
     for (int ks = 0; ks < 4; ++ks)
-      tc::mma_bf16(d, tc::kmajor_sw128(a + kb * TC_TILE + 32 * ks),
-                   tc::kmajor_sw128(b + kb * bblk + 32 * ks), idesc, (kb | ks) ? 1u : 0u);
+      tc::mma_bf16(d, a + kb * (TC_TILE >> 4) + 2 * ks, b + kb * (bblk >> 4) + 2 * ks, idesc,
+                   (kb | ks) ? 1u : 0u);
 }
 
 // D (M 128 x N 128) = A W over K = 128 (the weight's output rows): K-major A
-// (a [128][128] tile, K = its features), W a K-major [128 out][128 in] tile
-// read as the MN-major operand (K = out rows, N = in features).
-__device__ __forceinline__ void mma_wT(uint32_t d, uint32_t a, uint32_t w, uint32_t idesc) {
+// (a [128][128] tile, K = its features), w the MN-major descriptor of a
+// K-major [128 out][128 in] weight tile (K = out rows, N = in features).
+__device__ __forceinline__ void mma_wT(uint32_t d, uint64_t a, uint64_t w, uint32_t idesc) {
 #pragma unroll
   for (int kb = 0; kb < 2; ++kb)
 #pragma unroll
     for (int ks = 0; ks < 4; ++ks)
-      tc::mma_bf16(d, tc::kmajor_sw128(a + kb * TC_TILE + 32 * ks),
-                   tc::mnmajor_sw128(w + 2048 * (4 * kb + ks), TC_TILE, 1024), idesc,
+      tc::mma_bf16(d, a + kb * (TC_TILE >> 4) + 2 * ks, w + 128 * (4 * kb + ks), idesc,
                    (kb | ks) ? 1u : 0u);
 }
 
 // D (M 128 x N) (+)= A^T B over K = the 128 rows of a tile: A and B MN-major
-// tiles whose 64-wide feature halves are 16 KB apart.
-__device__ __forceinline__ void mma_rows128(uint32_t d, uint32_t a, uint32_t b, uint32_t idesc,
+// descriptors (feature halves 16 KB apart).
+__device__ __forceinline__ void mma_rows128(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
                                             bool first) {
 #pragma unroll
   for (int ks = 0; ks < 8; ++ks)
-    tc::mma_bf16(d, tc::mnmajor_sw128(a + 2048 * ks, TC_TILE, 1024),
-                 tc::mnmajor_sw128(b + 2048 * ks, TC_TILE, 1024), idesc,
-                 (first && ks == 0) ? 0u : 1u);
+    tc::mma_bf16(d, a + 128 * ks, b + 128 * ks, idesc, (first && ks == 0) ? 0u : 1u);
 }
 }  // namespace
 
@@ -159,12 +166,17 @@ __global__ void __launch_bounds__(DEC128_THREADS, 2) decode_tc128_kernel(TcArgs 
 #pragma unroll 1
     for (int layer = 0; layer < 3; ++layer) {
       if (!(ok = tc_sync_ok(ok, a.err))) break;
-      if (tid == 0) {
-        if (layer < 2)
-          mma_feat(tmem, s_x, layer == 0 ? s_w2 : s_w3, TC_TILE, ID128);
-        else
-          mma_feat(tmem, s_x, s_wo, 2048, ID16);
-        tc::mma_commit(bar);
+      if (warp == 0) {
+        const uint64_t da = kdesc(s_x);
+        const uint64_t db = kdesc(layer == 0 ? s_w2 : layer == 1 ? s_w3 : s_wo);
+        if (tc::elect_one()) {
+          if (layer < 2)
+            mma_feat(tmem, da, db, TC_TILE, ID128);
+          else
+            mma_feat(tmem, da, db, 2048, ID16);
+          tc::mma_commit(bar);
+        }
+        __syncwarp();
       }
       tc_wait(bar, phase, ok);
       if (layer < 2) {
@@ -255,9 +267,10 @@ struct Bwd128Smem {
   static constexpr uint32_t BIAS = STG + Bwd128Stage::BYTES;   // b2, b3, bo
   static constexpr uint32_t DZP = BIAS + (128 + 128 + 16) * 4;  // [8 qz][4 q4][16 vertices]
   static constexpr uint32_t DBO = DZP + 8 * 64 * 4;
-  // mbarriers: chain MMAs, final drain, dL/dz MMA, staged U/V, staged rest
+  // mbarriers: chain MMAs, final drain, dL/dz MMA, staged U/V, staged rest,
+  // weight-gradient MMAs
   static constexpr uint32_t BAR = DBO + 8 * 4;
-  static constexpr uint32_t TMEMP = BAR + 5 * 8;
+  static constexpr uint32_t TMEMP = BAR + 6 * 8;
   static constexpr uint32_t TOTAL = TMEMP + 8;
 };
 static_assert(Bwd128Smem::TOTAL + 1024 <= 227 * 1024, "backward H = 128 shared memory");
@@ -355,7 +368,7 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
   }
   if (tid < 16) bias[256 + tid] = tid < NO ? po[NO * H + tid] : 0.f;
   if (tid == 0) {
-    for (int b = 0; b < 5; ++b) tc::mbar_init(bar + b, 1);
+    for (int b = 0; b < 6; ++b) tc::mbar_init(bar + b, 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -396,11 +409,22 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
   constexpr uint32_t IDW = tc::idesc_bf16(128, 128, false, true);   // A K-major, B MN-major
   constexpr uint32_t IDR = tc::idesc_bf16(128, 128, true, true);    // A^T B over rows
   constexpr uint32_t IDR16 = tc::idesc_bf16(128, 16, true, true);
-  uint32_t phase = 0, phase_dz = 0;
-  bool first = true;
+  // bar + 5: the weight-gradient MMAs of a step, committed after its chain
+  // MMA: the epilogue loads and scales its values meanwhile and waits for
+  // them only before it overwrites the tile they read.
+  // Phase parities from the tile count lt: per tile the chain barrier
+  // completes 6 phases (steps 2-7: parities 0, 1, 0, 1, 0, 1), the weight
+  // barrier 3 (steps 5-7: lt, lt + 1, lt), the dL/dz barrier 1 (lt).
+  int lt = 0;  // tiles done (0: the weight gradients' first MMAs overwrite)
   const float* b2 = bias + c0;
   const float* b3 = bias + 128 + c0;
   auto xbuf = [&](int k) { return Bwd128Smem::XB + (uint32_t)k * ACT; };
+  // descriptors of the fixed operands (the weights, dL/do and y tiles)
+  const uint64_t d_w2k = kdesc(sa(Bwd128Smem::W2)), d_w3k = kdesc(sa(Bwd128Smem::W3));
+  const uint64_t d_w2m = mdesc2(sa(Bwd128Smem::W2)), d_w3m = mdesc2(sa(Bwd128Smem::W3));
+  const uint64_t d_wok = kdesc(sa(Bwd128Smem::WO)), d_wom = mdesc2(sa(Bwd128Smem::WO), 2048);
+  const uint64_t d_gok = kdesc(sa(Bwd128Smem::GO)), d_gom = mdesc2(sa(Bwd128Smem::GO));
+  const uint64_t d_ym = mdesc2(sa(Bwd128Smem::Y)), d_w1z = kdesc(sa(Bwd128Smem::W1Z));
 
   // h1 of the tile staged in `stg` into X[k]: act' mask of this thread's columns
   auto put_h1 = [&](int k, bool valid) {
@@ -452,13 +476,17 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
     }
     // ---- 2: h2
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      mma_feat(tmem + C_WORK, sa(xbuf(xa)), sa(Bwd128Smem::W2), TC_TILE, ID128);
-      tc::mma_commit(bar);
+    if (warp == 0) {
+      const uint64_t da = kdesc(sa(xbuf(xa)));
+      if (tc::elect_one()) {
+        mma_feat(tmem + C_WORK, da, d_w2k, TC_TILE, ID128);
+        tc::mma_commit(bar);
+      }
+      __syncwarp();
     }
     // the U/V rows of this tile were read (step 7 of the previous tile)
     if (next < ntiles) stage_issue(0, ni0, nt0);
-    tc_wait(bar, phase, ok);
+    tc_wait_parity(bar, 0u, ok);
     uint32_t m2 = 0u, m3 = 0u;
     {
       float v[32];
@@ -472,11 +500,15 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
     }
     // ---- 3: h3
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      mma_feat(tmem + C_WORK, sa(xbuf(xb)), sa(Bwd128Smem::W3), TC_TILE, ID128);
-      tc::mma_commit(bar);
+    if (warp == 0) {
+      const uint64_t da = kdesc(sa(xbuf(xb)));
+      if (tc::elect_one()) {
+        mma_feat(tmem + C_WORK, da, d_w3k, TC_TILE, ID128);
+        tc::mma_commit(bar);
+      }
+      __syncwarp();
     }
-    tc_wait(bar, phase, ok);
+    tc_wait_parity(bar, 1u, ok);
     {
       float v[32];
       ld_col32(lane_addr + C_WORK + c0, v);
@@ -489,12 +521,16 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
     }
     // ---- 4: o, dL/do (quarter 0), y (quarter 1), previous dL/dz (quarters 2, 3)
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      mma_feat(tmem + C_WORK, sa(xbuf(xc)), sa(Bwd128Smem::WO), 2048, ID16);
-      tc::mma_commit(bar);
+    if (warp == 0) {
+      const uint64_t da = kdesc(sa(xbuf(xc)));
+      if (tc::elect_one()) {
+        mma_feat(tmem + C_WORK, da, d_wok, 2048, ID16);
+        tc::mma_commit(bar);
+      }
+      __syncwarp();
     }
     stage_wait(1);
-    tc_wait(bar, phase, ok);
+    tc_wait_parity(bar, 0u, ok);
     if (c == 0) {
       float r[16];
       ld_col16(lane_addr + C_WORK, r);
@@ -532,54 +568,73 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
     }
     // ---- 5: dh3 = gO Wo, ACC_O += h3^T gO
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      tc::mma_bf16(tmem + C_WORK, tc::kmajor_sw128(sa(Bwd128Smem::GO)),
-                   tc::mnmajor_sw128(sa(Bwd128Smem::WO), 2048, 1024), IDW, 0u);
-      mma_rows128(tmem + C_ACCO, sa(xbuf(xc)), sa(Bwd128Smem::GO), IDR16, first);
-      tc::mma_commit(bar);
+    if (warp == 0) {
+      const uint64_t dc = mdesc2(sa(xbuf(xc)));
+      if (tc::elect_one()) {
+        tc::mma_bf16(tmem + C_WORK, d_gok, d_wom, IDW, 0u);
+        tc::mma_commit(bar);
+        mma_rows128(tmem + C_ACCO, dc, d_gom, IDR16, lt == 0);
+        tc::mma_commit(bar + 5);
+      }
+      __syncwarp();
     }
     // x, dL/dx-hat, z and gamma of this tile were read in step 4
     if (next < ntiles) stage_issue(1, ni0, nt0);
-    tc_wait(bar, phase, ok);
+    tc_wait_parity(bar, 1u, ok);
     {
       float v[32];
       ld_col32(lane_addr + C_WORK + c0, v);
 #pragma unroll
       for (int k = 0; k < 32; ++k) v[k] *= ((m3 >> k) & 1u) ? 1.f : a.slope;
+      tc_wait_parity(bar + 5, (uint32_t)(lt & 1), ok);         // ACC_O has read h3
       st_row32(sm + xbuf(xc), row, c0, v);  // dpre3
     }
     // ---- 6: dh2 = dpre3 W3, ACC_3 += dpre3^T h2, ACC_B3 += dpre3^T y
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      mma_wT(tmem + C_WORK, sa(xbuf(xc)), sa(Bwd128Smem::W3), IDW);
-      mma_rows128(tmem + C_ACC3, sa(xbuf(xc)), sa(xbuf(xb)), IDR, first);
-      mma_rows128(tmem + C_ACCB, sa(xbuf(xc)), sa(Bwd128Smem::Y), IDR16, first);
-      tc::mma_commit(bar);
+    if (warp == 0) {
+      const uint64_t dck = kdesc(sa(xbuf(xc))), dc = mdesc2(sa(xbuf(xc)));
+      const uint64_t db = mdesc2(sa(xbuf(xb)));
+      if (tc::elect_one()) {
+        mma_wT(tmem + C_WORK, dck, d_w3m, IDW);
+        tc::mma_commit(bar);
+        mma_rows128(tmem + C_ACC3, dc, db, IDR, lt == 0);
+        mma_rows128(tmem + C_ACCB, dc, d_ym, IDR16, lt == 0);
+        tc::mma_commit(bar + 5);
+      }
+      __syncwarp();
     }
-    tc_wait(bar, phase, ok);
+    tc_wait_parity(bar, 0u, ok);
     {
       float v[32];
       ld_col32(lane_addr + C_WORK + c0, v);
 #pragma unroll
       for (int k = 0; k < 32; ++k) v[k] *= ((m2 >> k) & 1u) ? 1.f : a.slope;
+      tc_wait_parity(bar + 5, (uint32_t)((lt + 1) & 1), ok);         // ACC_3 has read h2
       st_row32(sm + xbuf(xb), row, c0, v);  // dpre2
     }
     // ---- 7: dh1 = dpre2 W2, ACC_2 += dpre2^T h1, ACC_B2 += dpre2^T y
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      mma_wT(tmem + C_WORK, sa(xbuf(xb)), sa(Bwd128Smem::W2), IDW);
-      mma_rows128(tmem + C_ACC2, sa(xbuf(xb)), sa(xbuf(xa)), IDR, first);
-      mma_rows128(tmem + C_ACCB + 16, sa(xbuf(xb)), sa(Bwd128Smem::Y), IDR16, first);
-      tc::mma_commit(bar);
+    if (warp == 0) {
+      const uint64_t dbk = kdesc(sa(xbuf(xb))), db = mdesc2(sa(xbuf(xb)));
+      const uint64_t da = mdesc2(sa(xbuf(xa)));
+      if (tc::elect_one()) {
+        mma_wT(tmem + C_WORK, dbk, d_w2m, IDW);
+        tc::mma_commit(bar);
+        mma_rows128(tmem + C_ACC2, db, da, IDR, lt == 0);
+        mma_rows128(tmem + C_ACCB + 16, db, d_ym, IDR16, lt == 0);
+        tc::mma_commit(bar + 5);
+      }
+      __syncwarp();
     }
-    tc_wait(bar, phase, ok);
+    tc_wait_parity(bar, 1u, ok);
     {
       float v[32];
       ld_col32(lane_addr + C_WORK + c0, v);
 #pragma unroll
       for (int k = 0; k < 32; ++k) v[k] *= ((m1 >> k) & 1u) ? 1.f : a.slope;
-      st_row32(sm + xbuf(xa), row, c0, v);  // dpre1 (h1 is used up)
       if (TSUM) frame_sums<32>(v, a.dV, t0, tl, a.T, H, c0);
+      tc_wait_parity(bar + 5, (uint32_t)(lt & 1), ok);         // ACC_2 has read h1 (and dpre2)
+      st_row32(sm + xbuf(xa), row, c0, v);  // dpre1
     }
     // the next tile's h1 into X[b] (dpre2 is used up)
     if (next < ntiles) {
@@ -589,15 +644,18 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
     // ---- 8: dL/dz rows = dpre1 W1[:, :Z]; ACC_B1 += dpre1^T y
     if (!(ok = tc_sync_ok(ok, a.err))) break;
     // ACC_B1 is not waited for here: the next tile's first commit covers it
-    if (tid == 0) {
-      mma_feat(tmem + C_DZ, sa(xbuf(xa)), sa(Bwd128Smem::W1Z), 2048, ID16);
-      tc::mma_commit(bar + 2);
-      mma_rows128(tmem + C_ACCB + 32, sa(xbuf(xa)), sa(Bwd128Smem::Y), IDR16, first);
+    if (warp == 0) {
+      const uint64_t dak = kdesc(sa(xbuf(xa))), da = mdesc2(sa(xbuf(xa)));
+      if (tc::elect_one()) {
+        mma_feat(tmem + C_DZ, dak, d_w1z, 2048, ID16);
+        tc::mma_commit(bar + 2);
+        mma_rows128(tmem + C_ACCB + 32, da, d_ym, IDR16, lt == 0);
+      }
+      __syncwarp();
     }
-    first = false;
     dz_i0 = i0;
     if (c == 1) {
-      tc_wait(bar + 2, phase_dz, ok);
+      tc_wait_parity(bar + 2, (uint32_t)(lt & 1), ok);
       float r[16];
       ld_col16(lane_addr + C_DZ, r);
 #pragma unroll
@@ -608,6 +666,7 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
         }
       }
     }
+    ++lt;
     const int t_ = xa;
     xa = xb;
     xb = xc;
@@ -615,9 +674,12 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
     i0 = ni0;
     t0 = nt0;
   }
-  if (!first) {
-    if (tid == 0) tc::mma_commit(bar);
-    tc_wait(bar, phase, ok);
+  if (lt > 0) {  // drain: every MMA issued (by warp 0's elected lane) has completed
+    if (warp == 0) {
+      if (tc::elect_one()) tc::mma_commit(bar);
+      __syncwarp();
+    }
+    tc_wait_parity(bar, 0u, ok);
   }
   ok = tc_sync_ok(ok, a.err);
   if (ok && dz_i0 >= 0) flush_dz(tid, BWD128_THREADS);
@@ -631,7 +693,7 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
     }
   }
   ok = tc_sync_ok(ok, a.err);
-  if (ok && !first) {
+  if (ok && lt > 0) {
     // accumulators (TMEM lane = output feature j or m) -> the gradient, once per CTA
     float* g = a.g_mlp;
     float* gW1 = g;
@@ -672,9 +734,12 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
   }
   for (int b = 0; b < 2; ++b)
     if (pending & (1u << b)) tc::mbar_wait(sbar + b, (sphase >> b) & 1u, WAIT_TRIES);
-  if (tid == 0) {
-    tc::mma_commit(bar + 1);
-    tc::mbar_wait(bar + 1, 0, WAIT_TRIES);
+  if (warp == 0) {
+    if (tc::elect_one()) {
+      tc::mma_commit(bar + 1);
+      tc::mbar_wait(bar + 1, 0, WAIT_TRIES);
+    }
+    __syncwarp();
   }
   tc::fence_before_sync();
   __syncthreads();

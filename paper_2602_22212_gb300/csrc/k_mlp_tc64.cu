@@ -2,22 +2,26 @@
 // and 3 hidden layers, sized so that two CTAs share an SM: while one waits on
 // its MMAs or its barriers the other runs its epilogues, which is what the
 // chain of dependent MMA -> TMEM -> CUDA-core steps of one tile cannot do by
-// itself. Each CTA takes 97 KB of shared memory and 256 TMEM columns.
+// itself. Each CTA takes 112 KB of shared memory and 256 TMEM columns.
 //
 // Tile = 16 vertices x 8 frames = 128 rows (row r = tl 16 + il); 256 threads:
 // warp w serves TMEM lanes 32 (w % 4) .. + 31 (its rows) and the 32-column
-// half c = w / 4 of every 64-wide activation. Three [128][64] activation
-// tiles X[a], X[b], X[c] rotate roles from tile to tile (see k_mlp_tc128.cu
-// for the step list); a fourth tile YG holds y = (z_i, gamma_t, 0.., 1) in
-// columns 0..15 and dL/do in columns 16..22. The weight gradients accumulate
-// in TMEM over all of a CTA's tiles as M = 64 MMAs whose 64 accumulator rows
-// sit in lanes 16 q .. 16 q + 15 of each 32-lane quarter q:
-//   ACC_3 = dpre3^T [h2 | y]   dW3 in columns 0..63, db3 in column 79 (y's 1)
-//   ACC_2 = dpre2^T [h1 | y]   dW2, db2 likewise
-//   ACC_O = h3^T dL/do         dWo^T
-//   ACC_1 = dpre1^T y          dW1 in columns 0..K-1, db1 in column 15
-// ([h | y] is one MN-major operand whose second 64-column block is YG: the
-// descriptor's leading-byte offset is the distance from the h tile to YG).
+// half c = w / 4 of every 64-wide activation. Four [128][64] activation
+// tiles P, Q, R, S hold, per tile: h1 (P), h2 (Q), h3 (R), then dpre3 (S),
+// dpre2 (R), dpre1 (Q) and the next tile's h1 (S); the next tile's roles are
+// (P, Q, R, S) <- (S, P, Q, R). No epilogue writes a tile that a weight-
+// gradient MMA still reads, so those MMAs are not waited for in their own
+// step: each is covered by the next step's commit. A fifth tile YG holds
+// y = (z_i, gamma_t, 0.., 1) in columns 0..15 and dL/do in columns 16..22.
+// The weight gradients accumulate in TMEM over all of a CTA's tiles:
+//   ACC_3 = [h2 | y]^T dpre3   M = 128: lanes 0..63 dW3^T, lane 79 db3
+//   ACC_2 = [h1 | y]^T dpre2   likewise ([h | y] is one MN-major operand
+//                              whose second 64-row block is YG: the
+//                              descriptor's leading-byte offset is YG - h)
+//   ACC_O = h3^T dL/do         M = 64 (rows 16 q .. 16 q + 15 of TMEM
+//   ACC_1 = dpre1^T y          quarter q): dWo^T; dW1 in columns 0..K-1, db1
+//                              in column 15
+// Warp 0 computes every MMA's descriptors and one elected lane issues them.
 #include "mlp_tc_common.cuh"
 
 namespace npg {
@@ -37,20 +41,19 @@ struct Bwd64Stage {  // inputs of one tile, FP32
 };
 struct Bwd64Smem {
   static constexpr uint32_t W2 = 0, W3 = W2 + TC_TILE / 2;  // [64][64] K-major, 8 KB each
-  static constexpr uint32_t XB = W3 + TC_TILE / 2;          // X[0..2], 16 KB each
-  static constexpr uint32_t YG = XB + 3 * TC_TILE;          // y | dL/do
+  static constexpr uint32_t XB = W3 + TC_TILE / 2;          // four activation tiles, 16 KB each
+  static constexpr uint32_t YG = XB + 4 * TC_TILE;          // y | dL/do (after every X tile)
   static constexpr uint32_t WO = YG + TC_TILE;              // [16][64] K-major
   static constexpr uint32_t W1Z = WO + 2048;                // [16][64]: W1[:, :Z]^T
   static constexpr uint32_t STG = W1Z + 2048;
-  static constexpr uint32_t BIAS = STG + Bwd64Stage::BYTES;    // b2, b3 (64 each), bo (16)
-  static constexpr uint32_t DZP = BIAS + (64 + 64 + 16) * 4;   // [8 qz][4 q4][16 vertices]
+  static constexpr uint32_t DZP = STG + Bwd64Stage::BYTES;  // [8 qz][4 q4][16 vertices]
   static constexpr uint32_t DBO = DZP + 8 * 64 * 4;
   static constexpr uint32_t BAR = DBO + 8 * 4;  // chain, drain, dL/dz, staged U/V, staged rest
   static constexpr uint32_t TMEMP = BAR + 5 * 8;
   static constexpr uint32_t TOTAL = TMEMP + 8;
 };
 static_assert(2 * (Bwd64Smem::TOTAL + 1024) <= 226 * 1024, "two CTAs per SM");
-constexpr uint32_t C_WORK = 0, C_ACC3 = 64, C_ACC2 = 144, C_ACCO = 224, C_ACC1 = 240;
+constexpr uint32_t C_WORK = 0, C_ACC3 = 64, C_ACC2 = 128, C_ACCO = 192, C_ACC1 = 208;
 constexpr int BWD64_THREADS = 256;
 
 __device__ void load_weight64(uint8_t* tile, const float* W, int rows, int valid_rows) {
@@ -60,31 +63,36 @@ __device__ void load_weight64(uint8_t* tile, const float* W, int rows, int valid
   }
 }
 
+// The MMA helpers take descriptors that warp 0 computed as a whole (one
+// elected lane issues). A K step of 16 advances a K-major descriptor's start
+// address by 32 B (2 in its 16-byte units) and an MN-major one by 2048 B
+// (128); the start field cannot carry out of its 14 bits below 256 KB.
+
 // M 128 x N (= idesc) over K = 64 features: K-major A and B ([rows][64]).
-__device__ __forceinline__ void mma_f64(uint32_t d, uint32_t a, uint32_t b, uint32_t idesc) {
+__device__ __forceinline__ void mma_f64(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc) {
 #pragma unroll
-  for (int ks = 0; ks < 4; ++ks)
-    tc::mma_bf16(d, tc::kmajor_sw128(a + 32 * ks), tc::kmajor_sw128(b + 32 * ks), idesc, ks > 0);
+  for (int ks = 0; ks < 4; ++ks) tc::mma_bf16(d, a + 2 * ks, b + 2 * ks, idesc, ks > 0);
 }
 
-// M 128 x N 64 = A W over K = 64 (the weight's output rows): W a K-major
-// [64 out][64 in] tile read as the MN-major operand.
-__device__ __forceinline__ void mma_w64T(uint32_t d, uint32_t a, uint32_t w, uint32_t idesc) {
+// M 128 x N 64 = A W over K = 64 (the weight's output rows): A K-major, w the
+// MN-major descriptor of a K-major [64 out][64 in] weight tile.
+__device__ __forceinline__ void mma_w64T(uint32_t d, uint64_t a, uint64_t w, uint32_t idesc) {
 #pragma unroll
-  for (int ks = 0; ks < 4; ++ks)
-    tc::mma_bf16(d, tc::kmajor_sw128(a + 32 * ks), tc::mnmajor_sw128(w + 2048 * ks, 0, 1024),
-                 idesc, ks > 0);
+  for (int ks = 0; ks < 4; ++ks) tc::mma_bf16(d, a + 2 * ks, w + 128 * ks, idesc, ks > 0);
 }
 
-// M 64 x N (+)= A^T B over K = the 128 rows of a tile, A and B MN-major; B's
-// second 64-column block lies lbo bytes after its first.
-__device__ __forceinline__ void mma_rows64(uint32_t d, uint32_t a, uint32_t b, uint32_t lbo,
-                                           uint32_t idesc, bool first) {
+// M x N (+)= A^T B over K = the 128 rows of a tile, A and B MN-major
+// descriptors (a second 64-wide block at their leading-byte offsets).
+__device__ __forceinline__ void mma_rows(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         bool first) {
 #pragma unroll
   for (int ks = 0; ks < 8; ++ks)
-    tc::mma_bf16(d, tc::mnmajor_sw128(a + 2048 * ks, 0, 1024),
-                 tc::mnmajor_sw128(b + 2048 * ks, lbo, 1024), idesc,
-                 (first && ks == 0) ? 0u : 1u);
+    tc::mma_bf16(d, a + 128 * ks, b + 128 * ks, idesc, (first && ks == 0) ? 0u : 1u);
+}
+
+__device__ __forceinline__ uint64_t kdesc(uint32_t saddr) { return tc::kmajor_sw128(saddr); }
+__device__ __forceinline__ uint64_t mdesc(uint32_t saddr, uint32_t lbo = 0) {
+  return tc::mnmajor_sw128(saddr, lbo, 1024);
 }
 
 // One of the two staged groups of a tile (part 0: the U rows and V, 17
@@ -141,7 +149,6 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
   uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + Bwd64Smem::BAR);
   uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + Bwd64Smem::TMEMP);
-  float* bias = reinterpret_cast<float*>(sm + Bwd64Smem::BIAS);
   float* dzp = reinterpret_cast<float*>(sm + Bwd64Smem::DZP);
   float* dbo = reinterpret_cast<float*>(sm + Bwd64Smem::DBO);
   uint64_t* sbar = bar + 3;
@@ -168,11 +175,6 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
     for (int e = tid; e < TC_TILE / 16; e += BWD64_THREADS)
       *reinterpret_cast<uint4*>(sm + Bwd64Smem::YG + (uint32_t)e * 16u) = zero;
   }
-  for (int k = tid; k < 64; k += BWD64_THREADS) {
-    bias[k] = p2[H * H + k];
-    bias[64 + k] = p3[H * H + k];
-  }
-  if (tid < 16) bias[128 + tid] = tid < NO ? po[NO * H + tid] : 0.f;
   if (tid == 0) {
     for (int b = 0; b < 5; ++b) tc::mbar_init(bar + b, 1);
     tc::fence_mbar_init();
@@ -212,14 +214,23 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
   constexpr uint32_t ID64 = tc::idesc_bf16(128, 64, false, false);
   constexpr uint32_t ID16 = tc::idesc_bf16(128, 16, false, false);
   constexpr uint32_t IDW = tc::idesc_bf16(128, 64, false, true);    // A K-major, B MN-major
-  constexpr uint32_t IDR80 = tc::idesc_bf16(64, 80, true, true);    // A^T B over rows
+  constexpr uint32_t IDR128 = tc::idesc_bf16(128, 64, true, true);  // A^T B over rows
   constexpr uint32_t IDR16 = tc::idesc_bf16(64, 16, true, true);
-  uint32_t phase = 0, phase_dz = 0;
-  bool first = true;
-  const float* b2 = bias + c0;
-  const float* b3 = bias + 64 + c0;
+  // phase parities from the tile count lt (below): per tile the chain barrier
+  // completes 6 phases (steps 2-7: parities 0, 1, 0, 1, 0, 1), the dL/dz
+  // barrier one (lt)
+  // biases from global memory (read-only, L1-resident)
+  const float* b2 = p2 + H * H + c0;
+  const float* b3 = p3 + H * H + c0;
   auto xbuf = [&](int k) { return Bwd64Smem::XB + (uint32_t)k * TC_TILE; };
   const uint32_t s_yg = sa(Bwd64Smem::YG);
+  const uint64_t d_w2k = kdesc(sa(Bwd64Smem::W2)), d_w3k = kdesc(sa(Bwd64Smem::W3));
+  const uint64_t d_w2m = mdesc(sa(Bwd64Smem::W2)), d_w3m = mdesc(sa(Bwd64Smem::W3));
+  const uint64_t d_wok = kdesc(sa(Bwd64Smem::WO)), d_wom = mdesc(sa(Bwd64Smem::WO));
+  const uint64_t d_w1z = kdesc(sa(Bwd64Smem::W1Z));
+  const uint64_t d_ygk32 = kdesc(s_yg + 32), d_ygm = mdesc(s_yg), d_ygm32 = mdesc(s_yg + 32);
+  // [h | y]: the activation tile and YG as one MN-major operand of 128
+  auto d_hy = [&](int k) { return mdesc(sa(xbuf(k)), Bwd64Smem::YG - xbuf(k)); };
 
   // (every epilogue below works on 16 columns at a time: fewer live registers)
   auto put_h1 = [&](int k, bool valid) {
@@ -255,7 +266,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
       ld_col16(lane_addr + C_WORK + c0 + 16 * hh, v);
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        v[q] = leaky(v[q] + bias_c[16 * hh + q], a.slope);
+        v[q] = leaky(v[q] + __ldg(bias_c + 16 * hh + q), a.slope);
         m |= (v[q] > 0.f ? 1u : 0u) << (16 * hh + q);
       }
       st_bf16x8(sm + xbuf(k), row, c0 + 16 * hh, v);
@@ -279,23 +290,26 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
   };
   auto row_valid = [&](int i0_, int t0_) { return i0_ + il < a.N && t0_ + tl < a.T; };
 
-  int xa = 0, xb = 1, xc = 2;
+  int xp = 0, xq = 1, xr = 2, xs = 3;  // tiles P, Q, R, S
   uint32_t m1 = 0u;
-  int dz_i0 = -1;
+  // dL/dz of a tile's 16 vertices: per-quarter partial sums over its frames
+  // (step 8), added to global memory in step 4 of the next tile
+  int dz_prev = -1, lt = 0;  // i0 of the previous tile; tiles done (0: the weight
+                             // gradients' first MMAs overwrite their accumulators)
   float dbo_acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   auto flush_dz = [&](int e0, int stride) {
     for (int e = e0; e < 16 * Z; e += stride) {
       const int vi = e & 15, qz = e >> 4;
-      if (dz_i0 + vi >= a.N) continue;
+      if (dz_prev + vi >= a.N) continue;
       float s = 0.f;
 #pragma unroll
       for (int q = 0; q < 4; ++q) s += dzp[(qz * 4 + q) * 16 + vi];
-      atomicAdd(a.dz + (long long)(dz_i0 + vi) * Z + qz, s);
+      atomicAdd(a.dz + (long long)(dz_prev + vi) * Z + qz, s);
     }
   };
   if (tile < ntiles) {
     stage_wait(0);
-    m1 = put_h1(xa, row_valid(i0, t0));
+    m1 = put_h1(xp, row_valid(i0, t0));
   }
   for (; tile < ntiles; tile += gridDim.x) {
     const bool valid = row_valid(i0, t0);
@@ -305,38 +319,50 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
       ni0 = next / n_tb * 16;
       nt0 = (next - ni0 / 16 * n_tb) * 8;
     }
-    // ---- 2: h2
+    // ---- 2: h2 (P W2^T) -> Q
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      mma_f64(tmem + C_WORK, sa(xbuf(xa)), sa(Bwd64Smem::W2), ID64);
-      tc::mma_commit(bar);
+    if (warp == 0) {
+      const uint64_t da = kdesc(sa(xbuf(xp)));
+      if (tc::elect_one()) {
+        mma_f64(tmem + C_WORK, da, d_w2k, ID64);
+        tc::mma_commit(bar);
+      }
+      __syncwarp();
     }
     if (next < ntiles) stage_issue(0, ni0, nt0);
-    tc_wait(bar, phase, ok);
-    const uint32_t m2 = fwd_epi(b2, xb);
-    // ---- 3: h3
+    tc_wait_parity(bar, 0u, ok);
+    const uint32_t m2 = fwd_epi(b2, xq);
+    // ---- 3: h3 (Q W3^T) -> R
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      mma_f64(tmem + C_WORK, sa(xbuf(xb)), sa(Bwd64Smem::W3), ID64);
-      tc::mma_commit(bar);
+    if (warp == 0) {
+      const uint64_t da = kdesc(sa(xbuf(xq)));
+      if (tc::elect_one()) {
+        mma_f64(tmem + C_WORK, da, d_w3k, ID64);
+        tc::mma_commit(bar);
+      }
+      __syncwarp();
     }
-    tc_wait(bar, phase, ok);
-    const uint32_t m3 = fwd_epi(b3, xc);
+    tc_wait_parity(bar, 1u, ok);
+    const uint32_t m3 = fwd_epi(b3, xr);
     // ---- 4: o; dL/do (half 0); y and the previous tile's dL/dz (half 1)
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      mma_f64(tmem + C_WORK, sa(xbuf(xc)), sa(Bwd64Smem::WO), ID16);
-      tc::mma_commit(bar);
+    if (warp == 0) {
+      const uint64_t da = kdesc(sa(xbuf(xr)));
+      if (tc::elect_one()) {
+        mma_f64(tmem + C_WORK, da, d_wok, ID16);
+        tc::mma_commit(bar);
+      }
+      __syncwarp();
     }
     stage_wait(1);
-    tc_wait(bar, phase, ok);
+    tc_wait_parity(bar, 0u, ok);
     if (c == 0) {
       float r[16];
       ld_col16(lane_addr + C_WORK, r);
       float o[7], go[8];
 #pragma unroll
       for (int j = 0; j < 7; ++j) {
-        o[j] = r[j] + bias[128 + j];
+        o[j] = r[j] + (j < NO ? __ldg(po + NO * H + j) : 0.f);
         go[j] = 0.f;
       }
       go[7] = 0.f;
@@ -358,54 +384,65 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
         y[k] = k == 15 ? 1.f : !valid ? 0.f : k < Z ? zs[k] : k < K ? gt[k - Z] : 0.f;
       st_bf16x8(sm + Bwd64Smem::YG, row, 0, y);
       st_bf16x8(sm + Bwd64Smem::YG, row, 8, y + 8);
-      if (dz_i0 >= 0) flush_dz(tid - 128, 128);
+      if (dz_prev >= 0) flush_dz(tid - 128, 128);
     }
-    // ---- 5: dh3 = dL/do Wo, ACC_O += h3^T dL/do
+    // ---- 5: dh3 = dL/do Wo (waited); ACC_O += h3^T dL/do (covered by step 6)
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      tc::mma_bf16(tmem + C_WORK, tc::kmajor_sw128(s_yg + 32),
-                   tc::mnmajor_sw128(sa(Bwd64Smem::WO), 0, 1024), IDW, 0u);
-      mma_rows64(tmem + C_ACCO, sa(xbuf(xc)), s_yg + 32, 0, IDR16, first);
-      tc::mma_commit(bar);
+    if (warp == 0) {
+      const uint64_t dh3 = mdesc(sa(xbuf(xr)));
+      if (tc::elect_one()) {
+        tc::mma_bf16(tmem + C_WORK, d_ygk32, d_wom, IDW, 0u);
+        tc::mma_commit(bar);
+        mma_rows(tmem + C_ACCO, dh3, d_ygm32, IDR16, lt == 0);
+      }
+      __syncwarp();
     }
     if (next < ntiles) stage_issue(1, ni0, nt0);
-    tc_wait(bar, phase, ok);
-    bwd_epi(m3, xc, false);  // dpre3
-    // ---- 6: dh2 = dpre3 W3; ACC_3 += dpre3^T [h2 | y]
+    tc_wait_parity(bar, 1u, ok);
+    bwd_epi(m3, xs, false);  // dpre3 -> S
+    // ---- 6: dh2 = dpre3 W3; ACC_3 += [h2 | y]^T dpre3
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      mma_w64T(tmem + C_WORK, sa(xbuf(xc)), sa(Bwd64Smem::W3), IDW);
-      mma_rows64(tmem + C_ACC3, sa(xbuf(xc)), sa(xbuf(xb)), Bwd64Smem::YG - xbuf(xb), IDR80,
-                 first);
-      tc::mma_commit(bar);
+    if (warp == 0) {
+      const uint64_t dsk = kdesc(sa(xbuf(xs))), dsm = mdesc(sa(xbuf(xs))), dhy = d_hy(xq);
+      if (tc::elect_one()) {
+        mma_w64T(tmem + C_WORK, dsk, d_w3m, IDW);
+        tc::mma_commit(bar);
+        mma_rows(tmem + C_ACC3, dhy, dsm, IDR128, lt == 0);
+      }
+      __syncwarp();
     }
-    tc_wait(bar, phase, ok);
-    bwd_epi(m2, xb, false);  // dpre2
-    // ---- 7: dh1 = dpre2 W2; ACC_2 += dpre2^T [h1 | y]
+    tc_wait_parity(bar, 0u, ok);
+    bwd_epi(m2, xr, false);  // dpre2 -> R (h3's last reader, ACC_O, came before)
+    // ---- 7: dh1 = dpre2 W2; ACC_2 += [h1 | y]^T dpre2
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      mma_w64T(tmem + C_WORK, sa(xbuf(xb)), sa(Bwd64Smem::W2), IDW);
-      mma_rows64(tmem + C_ACC2, sa(xbuf(xb)), sa(xbuf(xa)), Bwd64Smem::YG - xbuf(xa), IDR80,
-                 first);
-      tc::mma_commit(bar);
+    if (warp == 0) {
+      const uint64_t drk = kdesc(sa(xbuf(xr))), drm = mdesc(sa(xbuf(xr))), dhy = d_hy(xp);
+      if (tc::elect_one()) {
+        mma_w64T(tmem + C_WORK, drk, d_w2m, IDW);
+        tc::mma_commit(bar);
+        mma_rows(tmem + C_ACC2, dhy, drm, IDR128, lt == 0);
+      }
+      __syncwarp();
     }
-    tc_wait(bar, phase, ok);
-    bwd_epi(m1, xa, TSUM);  // dpre1
+    tc_wait_parity(bar, 1u, ok);
+    bwd_epi(m1, xq, TSUM);  // dpre1 -> Q (h2's last reader, ACC_3, came before)
     if (next < ntiles) {
       stage_wait(0);
-      m1 = put_h1(xb, row_valid(ni0, nt0));
+      m1 = put_h1(xs, row_valid(ni0, nt0));  // the next h1 -> S (dpre3 is done)
     }
     // ---- 8: dL/dz rows = dpre1 W1[:, :Z] (into WORK); ACC_1 += dpre1^T y
     if (!(ok = tc_sync_ok(ok, a.err))) break;
-    if (tid == 0) {
-      mma_f64(tmem + C_WORK, sa(xbuf(xa)), sa(Bwd64Smem::W1Z), ID16);
-      tc::mma_commit(bar + 2);
-      mma_rows64(tmem + C_ACC1, sa(xbuf(xa)), s_yg, 0, IDR16, first);
+    if (warp == 0) {
+      const uint64_t dqk = kdesc(sa(xbuf(xq))), dqm = mdesc(sa(xbuf(xq)));
+      if (tc::elect_one()) {
+        mma_f64(tmem + C_WORK, dqk, d_w1z, ID16);
+        tc::mma_commit(bar + 2);
+        mma_rows(tmem + C_ACC1, dqm, d_ygm, IDR16, lt == 0);
+      }
+      __syncwarp();
     }
-    first = false;
-    dz_i0 = i0;
     if (c == 1) {
-      tc_wait(bar + 2, phase_dz, ok);
+      tc_wait_parity(bar + 2, (uint32_t)(lt & 1), ok);
       float r[16];
       ld_col16(lane_addr + C_WORK, r);
 #pragma unroll
@@ -416,19 +453,25 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
         }
       }
     }
-    const int t_ = xa;
-    xa = xb;
-    xb = xc;
-    xc = t_;
+    dz_prev = i0;
+    ++lt;
+    const int t_ = xs;
+    xs = xr;
+    xr = xq;
+    xq = xp;
+    xp = t_;
     i0 = ni0;
     t0 = nt0;
   }
-  if (!first) {
-    if (tid == 0) tc::mma_commit(bar);
-    tc_wait(bar, phase, ok);
+  if (lt > 0) {  // drain: every MMA issued (by warp 0's elected lane) has completed
+    if (warp == 0) {
+      if (tc::elect_one()) tc::mma_commit(bar);
+      __syncwarp();
+    }
+    tc_wait_parity(bar, 0u, ok);
   }
   ok = tc_sync_ok(ok, a.err);
-  if (ok && dz_i0 >= 0) flush_dz(tid, BWD64_THREADS);
+  if (ok && dz_prev >= 0) flush_dz(tid, BWD64_THREADS);
   if (c == 0) {
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
@@ -439,8 +482,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
     }
   }
   ok = tc_sync_ok(ok, a.err);
-  if (ok && !first) {
-    // M = 64 accumulators: feature j = 16 q4 + lane in lanes 0..15 of each quarter
+  if (ok && lt > 0) {
     float* g = a.g_mlp;
     float* gW1 = g;
     float* gb1 = g + H * K;
@@ -450,22 +492,31 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
     float* gb3 = gW3 + H * H;
     float* gWo = gb3 + H;
     float* gbo = gWo + NO * H;
+    float v[32];
+    // M = 128 accumulators ACC_3, ACC_2: lane m < 64 is input feature m of
+    // the layer, lane 79 the bias (y's constant column); column n is output
+    // feature n (this thread's half: c0 .. c0 + 31)
+    // (the TMEM loads are warp-collective: every lane loads)
+    ld_col32(lane_addr + C_ACC3 + c0, v);
+    if (row < 64) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) atomicAdd(gW3 + (c0 + k) * H + row, v[k]);
+    } else if (row == 79) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) atomicAdd(gb3 + c0 + k, v[k]);
+    }
+    ld_col32(lane_addr + C_ACC2 + c0, v);
+    if (row < 64) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) atomicAdd(gW2 + (c0 + k) * H + row, v[k]);
+    } else if (row == 79) {
+#pragma unroll
+      for (int k = 0; k < 32; ++k) atomicAdd(gb2 + c0 + k, v[k]);
+    }
+    // M = 64 accumulators: feature j = 16 q4 + lane in lanes 0..15 of each quarter
     const int j = 16 * q4 + lane;
     const bool has = lane < 16;
-    float v[32];
-    ld_col32(lane_addr + C_ACC3 + c0, v);
-    if (has)
-#pragma unroll
-      for (int k = 0; k < 32; ++k) atomicAdd(gW3 + j * H + c0 + k, v[k]);
-    ld_col32(lane_addr + C_ACC2 + c0, v);
-    if (has)
-#pragma unroll
-      for (int k = 0; k < 32; ++k) atomicAdd(gW2 + j * H + c0 + k, v[k]);
     if (c == 0) {
-      ld_col16(lane_addr + C_ACC3 + 64, v);
-      if (has) atomicAdd(gb3 + j, v[15]);
-      ld_col16(lane_addr + C_ACC2 + 64, v);
-      if (has) atomicAdd(gb2 + j, v[15]);
       ld_col16(lane_addr + C_ACCO, v);  // row m = j of dWo^T
       if (has)
 #pragma unroll
@@ -484,9 +535,12 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
   }
   for (int b = 0; b < 2; ++b)
     if (pending & (1u << b)) tc::mbar_wait(sbar + b, (sphase >> b) & 1u, WAIT_TRIES);
-  if (tid == 0) {
-    tc::mma_commit(bar + 1);
-    tc::mbar_wait(bar + 1, 0, WAIT_TRIES);
+  if (warp == 0) {
+    if (tc::elect_one()) {
+      tc::mma_commit(bar + 1);
+      tc::mbar_wait(bar + 1, 0, WAIT_TRIES);
+    }
+    __syncwarp();
   }
   tc::fence_before_sync();
   __syncthreads();

@@ -92,6 +92,13 @@ __device__ __forceinline__ void tc_wait(uint64_t* bar, uint32_t& phase, bool& ok
   tc::fence_after_sync();
 }
 
+// The same wait for a phase parity the caller derives (a barrier committed a
+// fixed number of times per tile completes a fixed parity pattern).
+__device__ __forceinline__ void tc_wait_parity(uint64_t* bar, uint32_t parity, bool& ok) {
+  ok = ok && tc::mbar_wait(bar, parity, WAIT_TRIES);
+  tc::fence_after_sync();
+}
+
 // Shared-memory writes -> async proxy, TMEM reads complete, then a CTA
 // barrier that also agrees on `ok`.
 __device__ __forceinline__ bool tc_sync_ok(bool ok, int* err) {

@@ -1330,6 +1330,7 @@ struct npg_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<long long> graph_launches;
+  int width = 0;  // chains in the graph; 0: every sequence its own branch
 };
 
 extern "C" int npg_batch_destroy(npg_batch* b) {
@@ -1381,6 +1382,43 @@ extern "C" int npg_batch_create(npg_batch** out, int S, npg_ctx* const* ctxs, vo
   return NPG_OK;
 }
 
+extern "C" int npg_batch_set_width(npg_batch* b, int width) {
+  if (!b) return set_err(nullptr, NPG_EINVAL, "batch is NULL");
+  if (b->exec)
+    return set_err(nullptr, NPG_EINVAL, "npg_batch_set_width: the batch graph is already captured");
+  b->width = width < 0 ? 0 : width;
+  return NPG_OK;
+}
+
+// Chains of the batch graph: with `width` chains (0 or >= S: S chains of one
+// sequence), the sequences go largest first (work N T + M T) onto the chain
+// with the least work so far. Returns, per sequence, the index of the
+// sequence it follows in its chain (-1: it starts its chain).
+static std::vector<int> batch_chains(const npg_batch* b) {
+  const int S = (int)b->ctx.size();
+  std::vector<int> prev(S, -1);
+  const int W = (b->width <= 0 || b->width >= S) ? S : b->width;
+  if (W == S) return prev;
+  std::vector<int> order(S);
+  for (int i = 0; i < S; ++i) order[i] = i;
+  auto work = [&](int i) {
+    const npg_ctx* c = b->ctx[i];
+    return (double)c->N * c->T + (double)c->MT;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+  std::vector<double> load(W, 0.0);
+  std::vector<int> tail(W, -1);
+  for (int i : order) {
+    int best = 0;
+    for (int w = 1; w < W; ++w)
+      if (load[w] < load[best]) best = w;
+    prev[i] = tail[best];
+    tail[best] = i;
+    load[best] += work(i);
+  }
+  return prev;
+}
+
 // The batch stream waits for every context's stream (prior single-sequence work).
 static cudaError_t batch_after_contexts(npg_batch* b) {
   for (size_t i = 0; i < b->ctx.size(); ++i) {
@@ -1420,13 +1458,25 @@ extern "C" int npg_batch_iteration(npg_batch* b, double* loss_out) {
       c->phase = 0;
     }
     for (npg_ctx* c : b->ctx) CK(c, cudaStreamSynchronize(c->stream));
-    // capture: the batch stream forks to every context's stream and joins them
+    // capture: the batch stream forks to the first context of every chain;
+    // a later context of a chain waits for the one before it; every context
+    // joins back into the batch stream
+    const std::vector<int> prev = batch_chains(b);
+    std::vector<int> seq_order;
+    std::vector<char> placed(S, 0);
+    while ((int)seq_order.size() < S)  // each context after the one it follows
+      for (int i = 0; i < S; ++i)
+        if (!placed[i] && (prev[i] < 0 || placed[prev[i]])) {
+          placed[i] = 1;
+          seq_order.push_back(i);
+        }
     CK(nullptr, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     int rc = NPG_OK;
     cudaError_t ce = cudaEventRecord(b->fork, b->stream);
-    for (int i = 0; i < S && ce == cudaSuccess && rc == NPG_OK; ++i) {
+    for (int n = 0; n < S && ce == cudaSuccess && rc == NPG_OK; ++n) {
+      const int i = seq_order[n];
       npg_ctx* c = b->ctx[i];
-      ce = cudaStreamWaitEvent(c->stream, b->fork, 0);
+      ce = cudaStreamWaitEvent(c->stream, prev[i] < 0 ? b->fork : b->join[prev[i]], 0);
       if (ce != cudaSuccess) break;
       c->capturing = 1;
       const long long before = c->launches;

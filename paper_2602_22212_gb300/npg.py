@@ -117,6 +117,7 @@ _SIG = {
     "npg_batch_create": (_i, [C.POINTER(_vp), _i, C.POINTER(_vp), _vp]),
     "npg_batch_iteration": (_i, [_vp, _vp]),
     "npg_batch_destroy": (_i, [_vp]),
+    "npg_batch_set_width": (_i, [_vp, _i]),
     "npg_fp32_fma_rate": (_i, [C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
     "npg_autotune": (_i, [_vp, _i, C.POINTER(C.c_int)]),
 }
@@ -242,6 +243,10 @@ def npg_batch_create(ctxs, stream):
 def npg_batch_iteration(batch, loss_out=None):
     """loss_out: host float64 array of S x 3, or None."""
     _check(_lib.npg_batch_iteration(batch, _ptr(loss_out)))
+
+
+def npg_batch_set_width(batch, width):
+    _check(_lib.npg_batch_set_width(batch, int(width)))
 
 
 def npg_batch_destroy(batch):

@@ -50,8 +50,10 @@ def contexts(npg, seqs, precision, streams, use_graph=False):
     return out
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_batch_matches_separate_runs(npg, precision):
+@pytest.mark.parametrize("precision, width", [(0, 0), (1, 0), (1, 1), (1, 2)])
+def test_batch_matches_separate_runs(npg, precision, width):
+    """Every chain width (0: a branch per sequence; 1: all in one chain; 2:
+    two chains of sequences assigned largest first) gives the same results."""
     import torch
     seqs = [make_seq(*s) for s in SPECS]
     S = len(seqs)
@@ -61,6 +63,7 @@ def test_batch_matches_separate_runs(npg, precision):
     cb = contexts(npg, seqs, precision, bstreams)
     cs = contexts(npg, seqs, precision, sstreams)
     batch = npg.npg_batch_create([c.h for c in cb], main)
+    npg.npg_batch_set_width(batch, width)
     try:
         for it in range(4):
             lb = np.zeros((S, 3))
@@ -73,6 +76,8 @@ def test_batch_matches_separate_runs(npg, precision):
         for c in cb:
             assert npg.npg_get_epoch(c.h) == 4
             assert npg.npg_launch_count(c.h) > 0
+        with pytest.raises(npg.NpgError):  # the graph is captured
+            npg.npg_batch_set_width(batch, 3)
         # the contexts stay usable on their own streams after the batch
         for c in cb:
             c.forward()
