@@ -59,7 +59,7 @@ __device__ void load_weight_tile(uint8_t* tile, const float* W, int rows, int va
 template <int ROT>
 __global__ void __launch_bounds__(128) decode_tc_kernel(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sm = tc::align1024(smem_raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + DecodeSmem::BAR);
   uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + DecodeSmem::TMEMP);
   float* bias = reinterpret_cast<float*>(sm + DecodeSmem::BIAS);

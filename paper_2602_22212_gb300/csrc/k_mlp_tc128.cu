@@ -96,7 +96,7 @@ constexpr int DEC128_THREADS = 256;
 template <int ROT>
 __global__ void __launch_bounds__(DEC128_THREADS, 2) decode_tc128_kernel(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sm = tc::align1024(smem_raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + Dec128Smem::BAR);
   uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + Dec128Smem::TMEMP);
   float* bias = reinterpret_cast<float*>(sm + Dec128Smem::BIAS);
@@ -330,7 +330,7 @@ __device__ void bwd128_stage(const TcArgs& a, int i0, int t0, uint8_t* stg, uint
 template <int ROT, bool TSUM>
 __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sm = tc::align1024(smem_raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + Bwd128Smem::BAR);
   uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + Bwd128Smem::TMEMP);
   float* bias = reinterpret_cast<float*>(sm + Bwd128Smem::BIAS);

@@ -146,7 +146,7 @@ __device__ void bwd64_stage(const TcArgs& a, int i0, int t0, uint8_t* stg, uint6
 template <int ROT, bool TSUM>
 __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sm = tc::align1024(smem_raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + Bwd64Smem::BAR);
   uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + Bwd64Smem::TMEMP);
   float* dzp = reinterpret_cast<float*>(sm + Bwd64Smem::DZP);

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
     const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
     __nv_bfloat16* __restrict__ ohi, __nv_bfloat16* __restrict__ olo, long long pitch) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sm = tc::align1024(smem_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + PcSmem::BAR);
   uint64_t* full = bars;
   uint64_t* empty = bars + 2;

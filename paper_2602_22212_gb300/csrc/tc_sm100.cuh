@@ -29,6 +29,15 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// The first 1024-byte aligned byte (in the shared window) of a dynamic
+// shared-memory array. Offsetting the array itself, rather than rounding its
+// generic address through an integer, keeps the shared address space known
+// to the compiler, so accesses through the result compile to shared-memory
+// instructions instead of generic ones.
+__device__ __forceinline__ uint8_t* align1024(uint8_t* smem) {
+  return smem + ((1024u - (smem_u32(smem) & 1023u)) & 1023u);
+}
+
 // ----------------------------------------------------------------- mbarrier
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
