@@ -212,6 +212,10 @@ struct NnGeom {
   int near_rows;       // widest seed ball (cell rows) that pass 1 covers
 };
 
+// Candidates [lo, hi) of one cell row against the best (distance, index)
+// pair, the lowest index winning ties. (Loading them four at a time measured
+// slower: a row's candidates are contiguous and mostly hit L1 after the
+// first, and short rows paid for the padding.)
 __device__ __forceinline__ void scan_range(const float4* __restrict__ cs, long long cb, int lo,
                                            int hi, float4 q, float& best, int& bi) {
   for (int j = lo; j < hi; ++j) {

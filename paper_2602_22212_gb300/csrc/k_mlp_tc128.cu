@@ -555,12 +555,20 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
       q0.w = tc::pack_bf16(NO > 6 ? go[6] : 0.f, 0.f);
       *reinterpret_cast<uint4*>(sm + Bwd128Smem::GO + tc::sw128_off(row, 0)) = q0;
     } else if (c == 1) {
+      // y = (z_i, gamma_t, 0.., 1): both sources read at fixed offsets from
+      // per-thread bases (zs[k], and gamma through gz = gt - Z), unconditionally
+      // and then selected, every read inside the staging area (Z <= 8 floats
+      // per vertex, K - Z <= 12 per frame, 128 floats each)
       const float* zs = reinterpret_cast<const float*>(stg + Bwd128Stage::Z) + il * Z;
-      const float* gt = reinterpret_cast<const float*>(stg + Bwd128Stage::GAM) + tl * (K - Z);
+      const float* gz = reinterpret_cast<const float*>(stg + Bwd128Stage::GAM) + tl * (K - Z) - Z;
       float y[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k)
-        y[k] = k == 15 ? 1.f : !valid ? 0.f : k < Z ? zs[k] : k < K ? gt[k - Z] : 0.f;
+      for (int k = 0; k < 15; ++k) {
+        const float zk = k < 8 ? zs[k] : 0.f;
+        const float gk = k >= 1 ? gz[k] : 0.f;
+        y[k] = !valid ? 0.f : k < Z ? zk : k < K ? gk : 0.f;
+      }
+      y[15] = 1.f;
       st_bf16x8(sm + Bwd128Smem::Y, row, 0, y);
       st_bf16x8(sm + Bwd128Smem::Y, row, 8, y + 8);
     } else if (dz_i0 >= 0) {

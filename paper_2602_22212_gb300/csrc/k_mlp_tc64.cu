@@ -376,12 +376,20 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
       for (int j = 0; j < 7; ++j) dbo_acc[j] += go[j];
       st_bf16x8(sm + Bwd64Smem::YG, row, 16, go);
     } else {
+      // y = (z_i, gamma_t, 0.., 1): both sources read at fixed offsets from
+      // per-thread bases (zs[k], and gamma through gz = gt - Z), unconditionally
+      // and then selected, every read inside the staging area (Z <= 8 floats
+      // per vertex, K - Z <= 12 per frame, 128 floats each)
       const float* zs = reinterpret_cast<const float*>(stg + Bwd64Stage::Z) + il * Z;
-      const float* gt = reinterpret_cast<const float*>(stg + Bwd64Stage::GAM) + tl * (K - Z);
+      const float* gz = reinterpret_cast<const float*>(stg + Bwd64Stage::GAM) + tl * (K - Z) - Z;
       float y[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k)
-        y[k] = k == 15 ? 1.f : !valid ? 0.f : k < Z ? zs[k] : k < K ? gt[k - Z] : 0.f;
+      for (int k = 0; k < 15; ++k) {
+        const float zk = k < 8 ? zs[k] : 0.f;
+        const float gk = k >= 1 ? gz[k] : 0.f;
+        y[k] = !valid ? 0.f : k < Z ? zk : k < K ? gk : 0.f;
+      }
+      y[15] = 1.f;
       st_bf16x8(sm + Bwd64Smem::YG, row, 0, y);
       st_bf16x8(sm + Bwd64Smem::YG, row, 8, y + 8);
       if (dz_prev >= 0) flush_dz(tid - 128, 128);
