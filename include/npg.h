@@ -378,8 +378,8 @@ NPG_API long long npg_launch_count(const npg_ctx* ctx);
  * forward (+ loss) passes, after one warm-up, for each candidate and keeps the
  * fastest: the bucket cells per axis of the vertex-side and then of the
  * point-side search grid (the default resolution times 0.7, 0.85, 1, 1.25;
- * the search is exact at every resolution), the widest seed ball (6, 12, 24
- * or 48 cell rows) that one thread covers before a query of each search
+ * the search is exact at every resolution), the widest seed ball (6, 12, 24,
+ * 48, 96, 192 or 384 cell rows) that one thread covers before a query of each search
  * direction goes to the lane-group pass, then, for the BF16 form with H = 64,
  * the decode's CTAs per SM (3, 4, 6 or 8). Parameters, Adam state and
  * e are unchanged; the nearest-neighbour buffers hold the last search's

@@ -1161,12 +1161,12 @@ extern "C" int npg_autotune(npg_ctx* c, int reps, int* chosen) {
   if ((rc = build_point_buckets(c))) return rc;
   // the widest seed ball that one thread covers before a query goes to the
   // lane-group pass, per search direction
-  const int rows_opt[4] = {6, 12, 24, 48};
+  const int rows_opt[7] = {6, 12, 24, 48, 96, 192, 384};
   for (int dir = 0; dir < 2; ++dir) {
     NnQueue& qd = dir == 0 ? c->nnq : c->nnq_p;
     int brow = qd.near_rows;
     first = true;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 7; ++k) {
       qd.near_rows = rows_opt[k];
       if ((rc = time_passes(c, reps, true, &ms))) return rc;
       if (first || ms < best) {

@@ -165,7 +165,7 @@ def test_autotune_keeps_results_exact(npg, precision):
         assert chosen[0] >= 1 and chosen[1] >= 1
         if precision:
             assert chosen[2] in (3, 4, 6, 8)
-        assert chosen[3] in (6, 12, 24, 48) and chosen[4] in (6, 12, 24, 48)
+        assert chosen[3] in (6, 12, 24, 48, 96, 192, 384) and chosen[4] in (6, 12, 24, 48, 96, 192, 384)
         ctx.forward()
         after, _ = ctx.loss()
         np.testing.assert_array_equal(after, before)
