@@ -674,22 +674,35 @@ cudaError_t launch_loss(npg_ctx* c) {
 // Vertex side of the Chamfer term plus the isometry term (vertex-centric over
 // the edge adjacency, no atomics); writes dxhat. The sign of |e_t| - |e_key|
 // is 0 at the keyframe (stop-grad reference, d|u|/du at 0 taken as 0).
+// The per-frame coefficients of the Chamfer terms of dL/dx-hat, formed once in
+// FP64 and rounded to FP32 (the FP64 divisions per row would cost more than
+// the rest of the dL/dx-hat kernels: FP64 runs at a small fraction of FP32
+// here): coef[t] = w_t / T * 2 / N (vertex side), coef[T + t] = w_t / T * 2 /
+// M_t (point side).
+__global__ void dx_coef_kernel(const double* __restrict__ w, const long long* __restrict__ off,
+                               int N, int T, float* __restrict__ coef) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+    coef[t] = (float)(w[t] / (double)T * 2.0 / (double)N);
+    coef[T + t] = (float)(w[t] / (double)T * 2.0 / (double)(off[t + 1] - off[t]));
+  }
+}
+
+// ci: the isometry coefficient w_iso / (T E), rounded to FP32.
 __global__ void __launch_bounds__(256) dxhat_vertex_kernel(
     const float4* __restrict__ xr, const float4* __restrict__ disp, const int* __restrict__ nn_x,
     const long long* __restrict__ off, const float4* __restrict__ praw,
-    const double* __restrict__ w, const int* __restrict__ adj_off, const int* __restrict__ adj,
-    int N, int T, int E, int t_key, double w_iso, float4* __restrict__ dxhat) {
+    const float* __restrict__ coef, const int* __restrict__ adj_off, const int* __restrict__ adj,
+    int N, int T, int E, int t_key, float ci, float4* __restrict__ dxhat) {
   const long long total = (long long)N * T;
   for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < total;
        row += (long long)gridDim.x * blockDim.x) {
     const int t = (int)(row / N), i = (int)(row - (long long)t * N);
     const float4 xi = xr[i], di = disp[row];
     const float4 p = praw[off[t] + nn_x[row]];
-    const float cx = (float)(w[t] / (double)T * 2.0 / (double)N);
+    const float cx = coef[t];
     float gx = cx * ((xi.x - p.x) + di.x), gy = cx * ((xi.y - p.y) + di.y),
           gz = cx * ((xi.z - p.z) + di.z);
     if (E > 0 && t != t_key) {
-      const float ci = (float)(w_iso / ((double)T * (double)E));
       const float4* Dl = disp + (long long)t * N;
       const float4* Dk = disp + (long long)t_key * N;
       const float4 ki = Dk[i];
@@ -721,12 +734,11 @@ __global__ void __launch_bounds__(256) dxhat_vertex_kernel(
 __global__ void __launch_bounds__(256) dxhat_point_kernel(
     const float4* __restrict__ praw, const long long* __restrict__ off, int T, long long MT,
     const int* __restrict__ nn_p, const float4* __restrict__ xr, const float4* __restrict__ disp,
-    const double* __restrict__ w, int N, float4* __restrict__ dxhat) {
+    const float* __restrict__ coef, int N, float4* __restrict__ dxhat) {
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < MT;
        k += (long long)gridDim.x * blockDim.x) {
     const int t = set_of(k, 0, off, T);
-    const long long M = off[t + 1] - off[t];
-    const float cp = (float)(w[t] / (double)T * 2.0 / (double)M);
+    const float cp = coef[T + t];
     const int i = nn_p[k];
     const float4 p = praw[k];
     const long long row = (long long)t * N + i;
@@ -740,11 +752,15 @@ __global__ void __launch_bounds__(256) dxhat_point_kernel(
 
 cudaError_t launch_dxhat(npg_ctx* c) {
   const long long rows = (long long)c->N * c->T;
+  dx_coef_kernel<<<(c->T + 255) / 256, 256, 0, c->stream>>>(c->wconf, c->p_off, c->N, c->T,
+                                                            c->dx_coef);
+  const float ci =
+      c->E > 0 ? (float)((double)c->cfg.w_iso / ((double)c->T * (double)c->E)) : 0.f;
   dxhat_vertex_kernel<<<grid_blocks(rows, 256), 256, 0, c->stream>>>(
-      c->xr, c->disp, c->nn_x, c->p_off, c->praw, c->wconf, c->adj_off, c->adj, c->N, c->T,
-      c->E, c->t_key, (double)c->cfg.w_iso, c->dxhat);
+      c->xr, c->disp, c->nn_x, c->p_off, c->praw, c->dx_coef, c->adj_off, c->adj, c->N, c->T,
+      c->E, c->t_key, ci, c->dxhat);
   dxhat_point_kernel<<<grid_blocks(c->MT, 256), 256, 0, c->stream>>>(
-      c->praw, c->p_off, c->T, c->MT, c->nn_p, c->xr, c->disp, c->wconf, c->N, c->dxhat);
+      c->praw, c->p_off, c->T, c->MT, c->nn_p, c->xr, c->disp, c->dx_coef, c->N, c->dxhat);
   return cudaGetLastError();
 }
 

@@ -457,7 +457,7 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
         alloc_n(c, c->dz, (long long)N * md.Z);
   if (md.Ht > 0) ok &= alloc_n(c, c->dV, (long long)T * md.H);
   ok &= alloc_n(c, c->cd, T) && alloc_n(c, c->wconf, T) && alloc_n(c, c->iso_t, T) &&
-        alloc_n(c, c->loss_part, (long long)T * 8 * 3) &&
+        alloc_n(c, c->loss_part, (long long)T * 8 * 3) && alloc_n(c, c->dx_coef, 2LL * T) &&
         alloc_n(c, c->loss, 4) && alloc_n(c, c->d_epoch, 1) && alloc_n(c, c->d_adam_c, 2) &&
         alloc_n(c, c->d_err, 1) && alloc_n(c, c->d_nnstats, 4) &&
         alloc_n(c, c->nnq.counters, 4) && alloc_n(c, c->nnq.items, std::max(NT, c->MT_cap));
@@ -676,7 +676,7 @@ static int backprop_launch(npg_ctx* c) {
 static int backward_launch(npg_ctx* c) {
   CK(c, launch_dxhat(c));
   mark(c, 7);
-  c->launches += 2;
+  c->launches += 3;
   return backprop_launch(c);
 }
 

@@ -105,6 +105,7 @@ struct npg_ctx {
   double* wconf = nullptr; // T
   double* iso_t = nullptr; // T
   double* loss_part = nullptr;  // T x 8 x 3 partial sums
+  float* dx_coef = nullptr;  // 2 T: per-frame Chamfer coefficients of dL/dx-hat (vertex, point)
   double* loss = nullptr;  // 3: L, L_def, L_iso
   double* h_loss = nullptr;  // pinned host mirror (3 + T)
 
