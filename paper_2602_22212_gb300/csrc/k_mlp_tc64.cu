@@ -18,9 +18,9 @@
 //   ACC_2 = [h1 | y]^T dpre2   likewise ([h | y] is one MN-major operand
 //                              whose second 64-row block is YG: the
 //                              descriptor's leading-byte offset is YG - h)
-//   ACC_O = h3^T dL/do         M = 64 (rows 16 q .. 16 q + 15 of TMEM
-//   ACC_1 = dpre1^T y          quarter q): dWo^T; dW1 in columns 0..K-1, db1
-//                              in column 15
+//   ACC_O = [h3 | y]^T dL/do   M = 128 (lanes 0..63; y's block only pads
+//   ACC_1 = [dpre1 | y]^T y    M up to the faster 128): dWo^T; dW1 in
+//                              columns 0..K-1, db1 in column 15
 // Warp 0 computes every MMA's descriptors and one elected lane issues them.
 #include "mlp_tc_common.cuh"
 
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
   constexpr uint32_t ID16 = tc::idesc_bf16(128, 16, false, false);
   constexpr uint32_t IDW = tc::idesc_bf16(128, 64, false, true);    // A K-major, B MN-major
   constexpr uint32_t IDR128 = tc::idesc_bf16(128, 64, true, true);  // A^T B over rows
-  constexpr uint32_t IDR16 = tc::idesc_bf16(64, 16, true, true);
+  constexpr uint32_t IDR16 = tc::idesc_bf16(128, 16, true, true);
   // phase parities from the tile count lt (below): per tile the chain barrier
   // completes 6 phases (steps 2-7: parities 0, 1, 0, 1, 0, 1), the dL/dz
   // barrier one (lt)
@@ -397,11 +397,11 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
     // ---- 5: dh3 = dL/do Wo (waited); ACC_O += h3^T dL/do (covered by step 6)
     if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (warp == 0) {
-      const uint64_t dh3 = mdesc(sa(xbuf(xr)));
+      const uint64_t dhy = d_hy(xr);
       if (tc::elect_one()) {
         tc::mma_bf16(tmem + C_WORK, d_ygk32, d_wom, IDW, 0u);
         tc::mma_commit(bar);
-        mma_rows(tmem + C_ACCO, dh3, d_ygm32, IDR16, lt == 0);
+        mma_rows(tmem + C_ACCO, dhy, d_ygm32, IDR16, lt == 0);
       }
       __syncwarp();
     }
@@ -441,11 +441,11 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
     // ---- 8: dL/dz rows = dpre1 W1[:, :Z] (into WORK); ACC_1 += dpre1^T y
     if (!(ok = tc_sync_ok(ok, a.err))) break;
     if (warp == 0) {
-      const uint64_t dqk = kdesc(sa(xbuf(xq))), dqm = mdesc(sa(xbuf(xq)));
+      const uint64_t dqk = kdesc(sa(xbuf(xq))), dqy = d_hy(xq);
       if (tc::elect_one()) {
         mma_f64(tmem + C_WORK, dqk, d_w1z, ID16);
         tc::mma_commit(bar + 2);
-        mma_rows(tmem + C_ACC1, dqm, d_ygm, IDR16, lt == 0);
+        mma_rows(tmem + C_ACC1, dqy, d_ygm, IDR16, lt == 0);
       }
       __syncwarp();
     }
@@ -521,22 +521,21 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
 #pragma unroll
       for (int k = 0; k < 32; ++k) atomicAdd(gb2 + c0 + k, v[k]);
     }
-    // M = 64 accumulators: feature j = 16 q4 + lane in lanes 0..15 of each quarter
-    const int j = 16 * q4 + lane;
-    const bool has = lane < 16;
+    // ACC_O, ACC_1 (M = 128 over [h | y]): lane m < 64 is feature m of h3 or
+    // of dpre1 (the lanes of y's block are not used)
     if (c == 0) {
-      ld_col16(lane_addr + C_ACCO, v);  // row m = j of dWo^T
-      if (has)
+      ld_col16(lane_addr + C_ACCO, v);  // row m of dWo^T
+      if (row < 64)
 #pragma unroll
         for (int q = 0; q < 7; ++q)
-          if (q < NO) atomicAdd(gWo + q * H + j, v[q]);
+          if (q < NO) atomicAdd(gWo + q * H + row, v[q]);
     } else {
       ld_col16(lane_addr + C_ACC1, v);
-      if (has) {
+      if (row < 64) {
 #pragma unroll
         for (int k = 0; k < 15; ++k)
-          if (k < K) atomicAdd(gW1 + j * K + k, v[k]);
-        atomicAdd(gb1 + j, v[15]);
+          if (k < K) atomicAdd(gW1 + row * K + k, v[k]);
+        atomicAdd(gb1 + row, v[15]);
       }
       if (q4 == 0 && lane < NO) atomicAdd(gbo + lane, dbo[lane]);
     }
