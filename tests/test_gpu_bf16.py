@@ -75,6 +75,24 @@ def test_bf16_decode_tracks_fp32(npg, rot_mode):
     assert rel(out[npg.BF16_MLP] - seq.x[None], disp) <= 2e-2
 
 
+@pytest.mark.parametrize("subdiv", [1, 2, 3])
+def test_bf16_decode_small_and_ragged_meshes(npg, subdiv):
+    """Meshes of 42 vertices (fewer than a 128-row tile: every thread loads
+    its own U and V rows), 162 and 642 (tiles across frame boundaries, a
+    ragged last tile: the staged rows of two frames)."""
+    seq = I.sphere_blob(subdiv=subdiv, T=5, M=500, noise=0.005, seed=3)
+    ocfg = O.make_cfg(L=4, res=(8, 27, 45, 64), F=4, Fn=2, H=64, D=3, slope=0.01, n_freq=4)
+    grid, mlp = rand_params(ocfg)
+    out = {}
+    for prec in (npg.FP32, npg.BF16_MLP):
+        ctx = npg.Context(cfg_of(npg, ocfg, prec), seq, mlp)
+        ctx.set(npg.BUF_GRID, grid)
+        ctx.forward()
+        out[prec] = ctx.get(npg.BUF_XHAT).reshape(seq.T, seq.N, 3)
+        ctx.close()
+    assert np.abs(out[npg.BF16_MLP] - out[npg.FP32]).max() <= 5e-3
+
+
 def test_bf16_identity_initialisation_exact(npg):
     seq, ocfg, prob = setup(T=3, M=500)
     mlp = I.mlp_init(O.k_in(ocfg), ocfg.H, ocfg.D, O.n_out(ocfg), seed=0)
