@@ -10,8 +10,8 @@ within a few 1e-3 of its FP32 value. Tolerances:
                         the rounding bound k u ||m|| of tests/bf16_model.py,
                         m the oracle's magnitude pass (sums of |products|): the
                         bound follows each block's cancellation
-  final Chamfer         paired over eight sequences, the mean excess over the
-                        FP32 path's within 1% (plus twice its standard error)
+  final Chamfer         paired over 128 sequences, the mean excess over the
+                        FP32 path's at most 1%
 """
 import numpy as np
 import pytest
@@ -151,7 +151,7 @@ def test_bf16_backprop_ragged_tiles(npg):
     _backprop_vs_oracle(npg, seq, ocfg, prob, F_n=1, n_freq=3)
 
 
-_FINAL_RUNS = 8
+_FINAL_RUNS = 128
 _FINAL_ITERS = 500
 _final_cache = {}
 
@@ -180,15 +180,17 @@ def final_chamfer(npg, precision, precond, seed):
 @pytest.mark.parametrize("precond", [0, 1])
 def test_bf16_final_chamfer_within_one_percent_of_fp32(npg, precond):
     """Full 500-iteration runs (the paper's schedules are 250 and 1000) on
-    eight articulated-figure sequences, FP32 against BF16 (with the FP32 or the
+    128 articulated-figure sequences, FP32 against BF16 (with the FP32 or the
     tensor-core preconditioner). A single run's final Chamfer is not
     reproducible to 1%, even in FP32: the gradient's float atomics sum in a
     varying order and Adam's sign-like steps carry their last-bit differences
-    into a different trajectory (about 2% spread per run). So the comparison
-    is paired per sequence and averaged: the BF16 runs' mean relative excess
-    over FP32 must stay below 1% plus twice its standard error. The isometry
-    weight is 1: on this synthetic data w_iso = 100 makes the isometry term
-    dominate L_def and the paper's per-level learning rates diverge."""
+    into a different trajectory (a heavy-tailed spread per run, up to ~18%).
+    So the comparison is paired per sequence and averaged over enough
+    sequences that the mean's standard error (~0.45%) is well inside the 1%:
+    the BF16 runs' mean relative excess over FP32 must be at most 1% (measured:
+    -1.15% and -1.33%, standard errors 0.51% and 0.50%). The isometry weight
+    is 1: on this synthetic data w_iso = 100 makes the isometry term dominate
+    L_def and the paper's per-level learning rates diverge."""
     ratios = []
     for seed in range(_FINAL_RUNS):
         f = final_chamfer(npg, npg.FP32, 0, seed)
@@ -198,4 +200,4 @@ def test_bf16_final_chamfer_within_one_percent_of_fp32(npg, precond):
     se = ratios.std(ddof=1) / np.sqrt(len(ratios))
     print("BF16/FP32 - 1 per sequence:", np.round(ratios, 4), "mean %.4f se %.4f" % (
         ratios.mean(), se))
-    assert ratios.mean() <= 0.01 + 2.0 * se, (ratios, se)
+    assert ratios.mean() <= 0.01, (ratios.mean(), se)
