@@ -186,7 +186,7 @@ int auto_cells(long long points_per_set, int nsets) {
 // ball that can hold the nearest neighbour. The ball is then covered directly,
 // one row segment per (z, y) cell row within reach, instead of ring by ring:
 // every cell row costs two loads of cell starts, however many cells its
-// segment spans. Balls of up to `near_rows` rows (12 unless tuned) are covered
+// segment spans. Balls of up to `near_rows` rows (set per direction) are covered
 // in pass 1, wider ones in pass 2. The result is the same exact nearest neighbour; the
 // seed only changes how much of the grid is visited.
 constexpr int NN_NEAR_RINGS = 1;

@@ -462,6 +462,9 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
         alloc_n(c, c->d_err, 1) && alloc_n(c, c->d_nnstats, 4) &&
         alloc_n(c, c->nnq.counters, 4) && alloc_n(c, c->nnq.items, std::max(NT, c->MT_cap));
   c->nnq.far_blocks = c->num_sms * 16;
+  // the widest seed ball one thread covers: the autotuner's usual choices
+  // (vertex -> point 24-96, point -> vertex 192-384 rows)
+  c->nnq.near_rows = 48;
   ok &= alloc_n(c, c->grid, c->grid_dev_len) && alloc_n(c, c->g_grid, c->grid_dev_len) &&
         alloc_n(c, c->g_pc, c->grid_dev_len) && alloc_n(c, c->m_grid, c->grid_dev_len) &&
         alloc_n(c, c->v_grid, c->grid_dev_len);
@@ -472,6 +475,7 @@ extern "C" int npg_create(npg_ctx** out, const npg_config* cfg, const float* ref
     ok &= alloc_n(c, c->wide, wide_fp32_scratch_floats(md.H, md.D, md.K, NT, &c->wide_rows));
   ok &= alloc_n(c, c->nnq_p.counters, 4) && alloc_n(c, c->nnq_p.items, c->MT_cap);
   c->nnq_p.far_blocks = c->num_sms * 16;
+  c->nnq_p.near_rows = 192;
   // levels to lanes, largest first onto the least loaded lane; each lane's
   // scratch holds its largest level
   {
