@@ -242,7 +242,10 @@ cudaError_t launch_decode_bf16_h128(npg_ctx* c) {
 // ACC_O dWo^T, the ACC_B blocks the bias gradients (the column of ones in y)
 // and dW1 | db1; all accumulate in TMEM over the CTA's tiles. Every MMA
 // issued before a commit is complete when that commit's wait returns, so a
-// buffer read by step 8 is free after the next tile's step 2.
+// buffer read by step 8 is free after the next tile's step 2. Warp 0 computes
+// every MMA's descriptors and one elected lane issues them; the weight-
+// gradient MMAs of steps 5-7 commit to their own barrier, which the epilogue
+// waits for only before it overwrites the tile they read.
 // The staged inputs of the next tile arrive by bulk copies into one staging
 // buffer: U and V rows (read in step 7 of the current tile) are issued in
 // step 2, the rest (x, dL/dx-hat, z, gamma; read in step 4) in step 5.
