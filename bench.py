@@ -61,8 +61,7 @@ KERNEL_SOURCES = {
                            "npg_device.cuh"),
 }
 MEASURED_TRAFFIC = {
-    ("mlp_bwd_tc2_kernel", "paper"): {"bytes": 78831872 + 1103872,
-                                      "sha256": "3f67845189e47808aca0c700b5a63ad3ddb78e0f37a1955d9aad419efbdc1e6f"},
+    ("mlp_bwd_tc2_kernel", "paper"): {"bytes": None, "sha256": None},
 }
 
 

@@ -95,33 +95,40 @@ __device__ __forceinline__ uint64_t mdesc(uint32_t saddr, uint32_t lbo = 0) {
   return tc::mnmajor_sw128(saddr, lbo, 1024);
 }
 
-// One of the two staged groups of a tile (part 0: the U rows and V, 17
-// pieces; part 1: dL/dx-hat rows, x, z, gamma, 11 pieces), issued by the
-// lanes of one warp; lane 0 announces the group's bytes (one arrival).
-__device__ void bwd64_stage(const TcArgs& a, int i0, int t0, uint8_t* stg, uint64_t* sbar,
-                            int part, int lane) {
+// The two staged groups of a tile (part 0: the U rows and V, 17 pieces;
+// part 1: dL/dx-hat rows, x, z, gamma, 11 pieces). One thread announces a
+// group's bytes on its barrier before a CTA barrier (bwd64_stage_expect);
+// after that barrier warps 1..7 issue the pieces, at most three lanes each
+// (bwd64_stage_issue): a bulk copy costs its issuing lane tens of cycles, and
+// a group issued by one warp made that warp the straggler of the next barrier.
+constexpr int STAGE_PIECES = 17, STAGE_WARPS = 7;
+
+__device__ __forceinline__ uint32_t bwd64_piece_bytes(const TcArgs& a, int i0, int t0, int part,
+                                                      int k) {
   const int nv = min(16, a.N - i0), nf = min(8, a.T - t0);
-  const uint32_t zb = ((uint32_t)(nv * a.Z * 4) + 15u) & ~15u;
-  const uint32_t gb = ((uint32_t)(nf * 2 * a.M * 4) + 15u) & ~15u;
-  auto bytes = [&](int k) -> uint32_t {
-    if (part == 0) {
-      if (k < 16) return k < nv ? 256u : 0u;
-      return k == 16 ? (uint32_t)nf * 256u : 0u;
-    }
-    if (k < 8) return k < nf ? (uint32_t)nv * 16u : 0u;
-    if (k == 8) return (uint32_t)nv * 16u;
-    if (k == 9) return zb;
-    return k == 10 ? gb : 0u;
-  };
-  if (lane == 0) {
-    uint32_t total = 0u;
-    for (int k = 0; k < 17; ++k) total += bytes(k);
-    tc::mbar_arrive_expect_tx(sbar, total);
+  if (part == 0) {
+    if (k < 16) return k < nv ? 256u : 0u;
+    return k == 16 ? (uint32_t)nf * 256u : 0u;
   }
-  __syncwarp();
-  const uint32_t n = lane < 17 ? bytes(lane) : 0u;
+  if (k < 8) return k < nf ? (uint32_t)nv * 16u : 0u;
+  if (k == 8) return (uint32_t)nv * 16u;
+  if (k == 9) return ((uint32_t)(nv * a.Z * 4) + 15u) & ~15u;
+  return k == 10 ? ((uint32_t)(nf * 2 * a.M * 4) + 15u) & ~15u : 0u;
+}
+
+__device__ void bwd64_stage_expect(const TcArgs& a, int i0, int t0, uint64_t* sbar, int part) {
+  uint32_t total = 0u;
+  for (int k = 0; k < STAGE_PIECES; ++k) total += bwd64_piece_bytes(a, i0, t0, part, k);
+  tc::mbar_arrive_expect_tx(sbar, total);
+}
+
+__device__ void bwd64_stage_issue(const TcArgs& a, int i0, int t0, uint8_t* stg, uint64_t* sbar,
+                                  int part, int warp, int lane) {
+  if (warp < 1) return;
+  const int k = lane * STAGE_WARPS + (warp - 1);
+  if (k >= STAGE_PIECES) return;
+  const uint32_t n = bwd64_piece_bytes(a, i0, t0, part, k);
   if (n == 0u) return;
-  const int k = lane;
   if (part == 0) {
     if (k < 16)
       tc::bulk_g2s(stg + Bwd64Stage::U + k * Bwd64Stage::U_PITCH, a.U + (long long)(i0 + k) * H64,
@@ -179,6 +186,12 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
     for (int b = 0; b < 5; ++b) tc::mbar_init(bar + b, 1);
     tc::fence_mbar_init();
   }
+  const int n_tb0 = (a.T + 7) / 8;
+  if (tid == 0 && (int)blockIdx.x < ((a.N + 15) / 16) * n_tb0) {  // the first tile's groups
+    const int fi0 = (int)blockIdx.x / n_tb0 * 16, ft0 = ((int)blockIdx.x - fi0 / 16 * n_tb0) * 8;
+    bwd64_stage_expect(a, fi0, ft0, bar + 3, 0);
+    bwd64_stage_expect(a, fi0, ft0, bar + 4, 1);
+  }
   if (warp == 0) {
     tc::tmem_alloc(tmem_ptr, 256);
     tc::tmem_relinquish();
@@ -195,8 +208,13 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
   if (c == 1) st_bf16(sm + Bwd64Smem::YG, row, 15, 1.f);
   bool ok = tc_sync_ok(true, a.err);
   uint32_t sphase = 0u, pending = 0u;
+  // a group's bytes are announced (thread 0) before the CTA barrier that
+  // precedes its issue
+  auto stage_expect = [&](int part, int i0_, int t0_) {
+    if (tid == 0) bwd64_stage_expect(a, i0_, t0_, sbar + part, part);
+  };
   auto stage_issue = [&](int part, int i0_, int t0_) {
-    if (warp == 1 + part) bwd64_stage(a, i0_, t0_, stg, sbar + part, part, lane);
+    bwd64_stage_issue(a, i0_, t0_, stg, sbar + part, part, warp, lane);
     pending |= 1u << part;
   };
   auto stage_wait = [&](int part) {
@@ -318,6 +336,9 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
     if (next < ntiles) {
       ni0 = next / n_tb * 16;
       nt0 = (next - ni0 / 16 * n_tb) * 8;
+      // the U/V group of this tile has been waited for (before its h1): the
+      // next tile's is announced before step 2's barrier and issued after it
+      stage_expect(0, ni0, nt0);
     }
     // ---- 2: h2 (P W2^T) -> Q
     if (!(ok = tc_sync_ok(ok, a.err))) break;
@@ -355,6 +376,7 @@ __global__ void __launch_bounds__(BWD64_THREADS, 2) mlp_bwd_tc2_kernel(TcArgs a)
       __syncwarp();
     }
     stage_wait(1);
+    if (next < ntiles) stage_expect(1, ni0, nt0);  // issued after step 5's barrier
     tc_wait_parity(bar, 0u, ok);
     if (c == 0) {
       float r[16];
