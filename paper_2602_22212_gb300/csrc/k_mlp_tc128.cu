@@ -282,34 +282,40 @@ constexpr uint32_t C_WORK = 0, C_ACC3 = 128, C_ACC2 = 256, C_ACCB = 384, C_ACCO 
 constexpr int BWD128_THREADS = 512;
 
 // The two staged groups of one tile: U and V rows (part 0, 17 pieces) or x,
-// dL/dx-hat, z and gamma (part 1, 11 pieces), issued by the 32 lanes of one
-// warp; lane 0 announces the group's bytes on *sbar (one arrival). Rows past
-// N or T are not copied: the readers replace their stale values by zero.
-// The z and gamma copies round up to 16 B (those arrays carry 16 B of padding).
-__device__ void bwd128_stage(const TcArgs& a, int i0, int t0, uint8_t* stg, uint64_t* sbar,
-                             int part, int lane) {
+// dL/dx-hat, z and gamma (part 1, 11 pieces). One thread announces a group's
+// bytes on its barrier before a CTA barrier; after it warps 1..15 issue the
+// pieces, at most two lanes each (one warp issuing a whole group became the
+// next barrier's straggler). Rows past N or T are not copied: the readers
+// replace their stale values by zero. The z and gamma copies round up to 16 B
+// (those arrays carry 16 B of padding).
+constexpr int STAGE_PIECES = 17, STAGE_WARPS128 = 15;
+
+__device__ __forceinline__ uint32_t bwd128_piece_bytes(const TcArgs& a, int i0, int t0,
+                                                       int part, int k) {
   const int nv = min(16, a.N - i0), nf = min(8, a.T - t0);
-  const uint32_t zb = ((uint32_t)(nv * a.Z * 4) + 15u) & ~15u;
-  const uint32_t gb = ((uint32_t)(nf * 2 * a.M * 4) + 15u) & ~15u;
-  auto bytes = [&](int k) -> uint32_t {
-    if (part == 0) {
-      if (k < 16) return k < nv ? 512u : 0u;
-      return k == 16 ? (uint32_t)nf * 512u : 0u;
-    }
-    if (k < 8) return k < nf ? (uint32_t)nv * 16u : 0u;
-    if (k == 8) return (uint32_t)nv * 16u;
-    if (k == 9) return zb;
-    return k == 10 ? gb : 0u;
-  };
-  if (lane == 0) {
-    uint32_t total = 0u;
-    for (int k = 0; k < 17; ++k) total += bytes(k);
-    tc::mbar_arrive_expect_tx(sbar, total);
+  if (part == 0) {
+    if (k < 16) return k < nv ? 512u : 0u;
+    return k == 16 ? (uint32_t)nf * 512u : 0u;
   }
-  __syncwarp();
-  const uint32_t n = lane < 17 ? bytes(lane) : 0u;
+  if (k < 8) return k < nf ? (uint32_t)nv * 16u : 0u;
+  if (k == 8) return (uint32_t)nv * 16u;
+  if (k == 9) return ((uint32_t)(nv * a.Z * 4) + 15u) & ~15u;
+  return k == 10 ? ((uint32_t)(nf * 2 * a.M * 4) + 15u) & ~15u : 0u;
+}
+
+__device__ void bwd128_stage_expect(const TcArgs& a, int i0, int t0, uint64_t* sbar, int part) {
+  uint32_t total = 0u;
+  for (int k = 0; k < STAGE_PIECES; ++k) total += bwd128_piece_bytes(a, i0, t0, part, k);
+  tc::mbar_arrive_expect_tx(sbar, total);
+}
+
+__device__ void bwd128_stage_issue(const TcArgs& a, int i0, int t0, uint8_t* stg,
+                                   uint64_t* sbar, int part, int warp, int lane) {
+  if (warp < 1) return;
+  const int k = lane * STAGE_WARPS128 + (warp - 1);
+  if (k >= STAGE_PIECES) return;
+  const uint32_t n = bwd128_piece_bytes(a, i0, t0, part, k);
   if (n == 0u) return;
-  const int k = lane;
   if (part == 0) {
     if (k < 16)
       tc::bulk_g2s(stg + Bwd128Stage::U + k * Bwd128Stage::U_PITCH,
@@ -374,6 +380,12 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
     for (int b = 0; b < 6; ++b) tc::mbar_init(bar + b, 1);
     tc::fence_mbar_init();
   }
+  const int n_tb0 = (a.T + 7) / 8;
+  if (tid == 0 && (int)blockIdx.x < ((a.N + 15) / 16) * n_tb0) {  // the first tile's groups
+    const int fi0 = (int)blockIdx.x / n_tb0 * 16, ft0 = ((int)blockIdx.x - fi0 / 16 * n_tb0) * 8;
+    bwd128_stage_expect(a, fi0, ft0, bar + 3, 0);
+    bwd128_stage_expect(a, fi0, ft0, bar + 4, 1);
+  }
   if (warp == 0) {
     tc::tmem_alloc(tmem_ptr, 512);
     tc::tmem_relinquish();
@@ -391,8 +403,13 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
   bool ok = tc_sync_ok(true, a.err);
   uint32_t sphase = 0u, pending = 0u;
   // warps 1 and 2 issue the U/V and the other copies of a tile
+  // a group's bytes are announced (thread 0) before the CTA barrier that
+  // precedes its issue
+  auto stage_expect = [&](int part, int i0_, int t0_) {
+    if (tid == 0) bwd128_stage_expect(a, i0_, t0_, sbar + part, part);
+  };
   auto stage_issue = [&](int part, int i0_, int t0_) {
-    if (warp == 1 + part) bwd128_stage(a, i0_, t0_, stg, sbar + part, part, lane);
+    bwd128_stage_issue(a, i0_, t0_, stg, sbar + part, part, warp, lane);
     pending |= 1u << part;
   };
   auto stage_wait = [&](int part) {
@@ -476,6 +493,9 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
     if (next < ntiles) {
       ni0 = next / n_tb * 16;
       nt0 = (next - ni0 / 16 * n_tb) * 8;
+      // the U/V group of this tile has been waited for (before its h1): the
+      // next tile's is announced before step 2's barrier and issued after it
+      stage_expect(0, ni0, nt0);
     }
     // ---- 2: h2
     if (!(ok = tc_sync_ok(ok, a.err))) break;
@@ -533,6 +553,7 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
       __syncwarp();
     }
     stage_wait(1);
+    if (next < ntiles) stage_expect(1, ni0, nt0);  // issued after step 5's barrier
     tc_wait_parity(bar, 0u, ok);
     if (c == 0) {
       float r[16];
