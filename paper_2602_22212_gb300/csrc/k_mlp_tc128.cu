@@ -402,9 +402,9 @@ __global__ void __launch_bounds__(BWD128_THREADS, 1) mlp_bwd_tc128_kernel(TcArgs
   if (c == 1) st_bf16(sm + Bwd128Smem::Y, row, 15, 1.f);
   bool ok = tc_sync_ok(true, a.err);
   uint32_t sphase = 0u, pending = 0u;
-  // warps 1 and 2 issue the U/V and the other copies of a tile
   // a group's bytes are announced (thread 0) before the CTA barrier that
-  // precedes its issue
+  // precedes its issue; after it warps 1-15 issue the group's pieces, at most
+  // two each
   auto stage_expect = [&](int part, int i0_, int t0_) {
     if (tid == 0) bwd128_stage_expect(a, i0_, t0_, sbar + part, part);
   };
