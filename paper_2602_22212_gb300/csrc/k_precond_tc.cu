@@ -9,14 +9,16 @@
 // (the dropped lo.lo term is below 2^-16 relative), accumulated in FP32 in
 // TMEM: about 1e-5 relative per pass.
 //
-// Persistent, warp-specialised CTA of 288 threads, one per SM, looping over
-// column tiles of 128: the tile covers all r output rows (one or two 128-row
-// MMA blocks); K (the transformed axis n) is streamed in chunks of 64 through
-// a two-stage shared-memory ring. Per chunk, a bulk copy brings the tables'
-// pre-swizzled hi/lo rows, the producer warps load, split and store the input
-// columns as MN-major tiles, and one thread issues 12 MMAs per 128-row block
-// into one of two TMEM accumulators while the epilogue warps drain the other
-// with coalesced rotated stores (float4 for F = 4).
+// Persistent, warp-specialised CTA, one per SM, looping over column tiles of
+// 128: the tile covers all r output rows (one or two 128-row MMA blocks); K
+// (the transformed axis n) is streamed in chunks of 64. The table blocks (one
+// 128-row block of C's hi and lo rows per K chunk, 32 KB, pre-swizzled, from
+// L2) and the input chunks (64 rows x 128 columns, hi and lo, 32 KB, from HBM)
+// come through two separate shared-memory rings of four and three slots, so
+// that the input of the next two chunks and the table of the next one are in
+// flight while one chunk is multiplied. One thread issues 12 MMAs per table
+// block into one of two TMEM accumulators while the epilogue warps drain the
+// other with coalesced rotated stores (8-byte hi / lo pieces for F = 4).
 //
 // Between the passes of one preconditioner call the data stays split: a pass
 // may store its output as the hi and lo BF16 arrays (the same bytes as FP32,
@@ -37,6 +39,9 @@ namespace npg {
 namespace {
 constexpr uint32_t TILE_A = 128 * 128;  // [128][64] BF16, 128B-swizzled
 constexpr uint32_t ATOM_B = 64 * 128;   // MN-major atom: 64 K-rows x 64 columns BF16
+constexpr uint32_t A_SLOT = 2 * TILE_A;  // hi and lo of one 128-row table block
+constexpr uint32_t B_SLOT = 4 * ATOM_B;  // hi (2 atoms) and lo (2 atoms) of one input chunk
+constexpr int NA = 4, NB = 3;            // ring depths (table blocks, input chunks)
 constexpr uint32_t WAIT = 1u << 22;
 // Warp roles: producers [0, PW), epilogue [PW, PW + EW), the MMA warp PW + EW.
 // A pass that splits FP32 input needs 4 producer warps; one whose input comes
@@ -49,16 +54,20 @@ template <bool IN_SPLIT> struct Roles {
 };
 constexpr int PRODUCERS = Roles<false>::PRODUCERS;
 
-// Per stage: A chunk [hi m0, hi m1, lo m0, lo m1] (a straight copy of the
-// pre-swizzled table chunk), B chunk [hi (2 atoms), lo (2 atoms)].
+// Table ring (NA blocks [hi, lo] of 128 rows x 64 K), input ring (NB chunks
+// [hi atom 0, hi atom 1, lo atom 0, lo atom 1]), the spectral weights mu (r <=
+// 256) and the barriers.
 struct PcSmem {
-  static constexpr uint32_t STAGE = 4 * TILE_A + 4 * ATOM_B;  // 96 KB
-  static constexpr uint32_t MU = 2 * STAGE;
-  // full[2], empty[2], acc_full[2], acc_empty[2], fin
-  static constexpr uint32_t BAR = MU + 1024 * 4;
-  static constexpr uint32_t FLAGS = BAR + 9 * 8;
+  static constexpr uint32_t A = 0;
+  static constexpr uint32_t B = A + NA * A_SLOT;
+  static constexpr uint32_t MU = B + NB * B_SLOT;
+  // a_full[NA], a_empty[NA], b_full[NB], b_empty[NB], acc_full[2], acc_empty[2], fin
+  static constexpr uint32_t BAR = MU + 256 * 4;
+  static constexpr uint32_t NBAR = 2 * NA + 2 * NB + 5;
+  static constexpr uint32_t FLAGS = BAR + NBAR * 8;
   static constexpr uint32_t TOTAL = FLAGS + 16;
 };
+static_assert(PcSmem::TOTAL + 1024 <= 232448, "shared memory of one CTA");
 
 __device__ __forceinline__ uint32_t mn_off(uint32_t m, uint32_t k) {
   return (m >> 6) * ATOM_B + (k >> 3) * 1024u + (k & 7u) * 128u +
@@ -109,11 +118,12 @@ __device__ __forceinline__ bool pc_wait(uint64_t* bar, uint32_t phase, volatile 
 }
 }  // namespace
 
-// One pass, persistent and warp-specialised: warps 0-3 produce (bulk copy of
-// the table chunk, load + split of the input chunk) into a two-stage ring,
-// warp 8 issues the MMAs into one of two TMEM accumulators, warps 4-7 drain
-// the other accumulator to global memory. CTAs loop over column tiles of 128.
-// tabs: pre-swizzled chunks [kc][hi m0, hi m1, lo m0, lo m1] of 16 KB each.
+// One pass, persistent and warp-specialised: the producer warps (bulk copies
+// of the table blocks into the table ring; TMA loads, or load + split, of the
+// input chunks into the input ring), the epilogue warps draining one TMEM
+// accumulator to global memory and the MMA warp filling the other. CTAs loop
+// over column tiles of 128.
+// tabs: pre-swizzled 32 KB slots [kc][mt][hi, lo] (dct_tc_tables).
 // IN_SPLIT: the input is hi / lo BF16 rows loaded by TMA (tm_hi, tm_lo, boxes
 // of 64 rows x 64 columns, 128B swizzle); else FP32 `in`, split by the
 // producers. OUT_SPLIT: the output goes to hi / lo BF16 arrays `ohi`, `olo`
@@ -127,17 +137,18 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = tc::align1024(smem_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + PcSmem::BAR);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + 2;
-  uint64_t* acc_full = bars + 4;
-  uint64_t* acc_empty = bars + 6;
-  uint64_t* fin = bars + 8;
+  uint64_t* a_full = bars;
+  uint64_t* a_empty = a_full + NA;
+  uint64_t* b_full = a_empty + NA;
+  uint64_t* b_empty = b_full + NB;
+  uint64_t* acc_full = b_empty + NB;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* fin = acc_empty + 2;
   volatile int* abort = reinterpret_cast<volatile int*>(sm + PcSmem::FLAGS);
   uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + PcSmem::FLAGS + 4);
   float* smu = reinterpret_cast<float*>(sm + PcSmem::MU);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nM = (r + 127) >> 7, nK = (r + 63) >> 6;
-  const uint32_t a_bytes = (uint32_t)nM * 2u * TILE_A;
   const uint32_t acc_cols = (uint32_t)nM * 128u;
   const uint32_t tm_cols = nM == 2 ? 512u : 256u;
   const long long ncol = (long long)r * r * F;
@@ -145,9 +156,17 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
   using RL = Roles<IN_SPLIT>;
   for (int k = tid; k < r; k += RL::THREADS) smu[k] = mu[k];
   if (tid == 0) {
+    for (int b = 0; b < NA; ++b) {
+      tc::mbar_init(a_full + b, 1);
+      tc::mbar_init(a_empty + b, 1);
+    }
+    for (int b = 0; b < NB; ++b) {
+      // TMA input: thread 0 arrives with the transaction count; split input:
+      // every producer arrives once its share of the chunk is stored
+      tc::mbar_init(b_full + b, IN_SPLIT ? 1 : RL::PRODUCERS);
+      tc::mbar_init(b_empty + b, 1);
+    }
     for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(full + b, RL::PRODUCERS + 1);
-      tc::mbar_init(empty + b, 1);
       tc::mbar_init(acc_full + b, 1);
       tc::mbar_init(acc_empty + b, RL::EPILOGUE);
     }
@@ -166,33 +185,38 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
 
   if (warp < RL::PW) {
     // ------------------------------------------------------------ producers
-    // Thread 0 arrives with the table copy's transaction count when it issues
-    // it; every producer arrives once its share of the input chunk is stored.
-    uint32_t u = 0, last_copy = 0;
-    bool copied = false;
+    // Thread 0 issues the input chunk's TMA loads (split input), then the
+    // chunk's table blocks; with FP32 input every producer loads, splits and
+    // stores its share of the chunk, and thread 0 issues the table blocks
+    // while its loads are in flight.
+    uint32_t ua = 0, ub = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       const long long col0 = tile * 128;
-      for (int kc = 0; kc < nK; ++kc, ++u) {
-        const uint32_t s = u & 1u, ph = (u >> 1) & 1u;
-        if (!pc_wait(empty + s, ph ^ 1u, abort, err)) goto producers_done;
-        uint8_t* st = sm + s * PcSmem::STAGE;
-        uint8_t* sb = st + 4 * TILE_A;
-        if (tid == 0) {
-          tc::mbar_arrive_expect_tx(full + s, a_bytes + (IN_SPLIT ? 4 * ATOM_B : 0u));
-          tc::bulk_g2s(st, tabs + (size_t)kc * a_bytes, a_bytes, full + s);
-          if (IN_SPLIT) {
+      for (int kc = 0; kc < nK; ++kc, ++ub) {
+        const uint32_t sbi = ub % NB, bph = (ub / NB) & 1u;
+        if (!pc_wait(b_empty + sbi, bph ^ 1u, abort, err)) goto producers_done;
+        uint8_t* sb = sm + PcSmem::B + sbi * B_SLOT;
+        if (IN_SPLIT) {
+          if (tid == 0) {
+            tc::mbar_arrive_expect_tx(b_full + sbi, B_SLOT);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              tc::tma_load_2d(sb + h * ATOM_B, &tm_hi, (int)(col0 + 64 * h), kc * 64, full + s);
+              tc::tma_load_2d(sb + h * ATOM_B, &tm_hi, (int)(col0 + 64 * h), kc * 64,
+                              b_full + sbi);
               tc::tma_load_2d(sb + (2 + h) * ATOM_B, &tm_lo, (int)(col0 + 64 * h), kc * 64,
-                              full + s);
+                              b_full + sbi);
+            }
+            for (int mt = 0; mt < nM; ++mt, ++ua) {
+              const uint32_t sai = ua % NA, aph = (ua / NA) & 1u;
+              if (!pc_wait(a_empty + sai, aph ^ 1u, abort, err)) {
+                ++ub;  // this chunk's input copy is in flight
+                goto producers_done;
+              }
+              tc::mbar_arrive_expect_tx(a_full + sai, A_SLOT);
+              tc::bulk_g2s(sm + PcSmem::A + sai * A_SLOT,
+                           tabs + ((size_t)kc * nM + mt) * A_SLOT, A_SLOT, a_full + sai);
             }
           }
-          last_copy = u;
-          copied = true;
-        }
-        if (IN_SPLIT) {
-          tc::mbar_arrive(full + s);
           continue;
         }
         // 64 K-rows x 16 groups of 8 columns; all loads issued before any store.
@@ -214,6 +238,15 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
               x[i][j] = (n < r && c0 + j < ncol) ? in[(long long)n * ncol + c0 + j] : 0.f;
           }
         }
+        if (tid == 0) {
+          for (int mt = 0; mt < nM; ++mt, ++ua) {
+            const uint32_t sai = ua % NA, aph = (ua / NA) & 1u;
+            if (!pc_wait(a_empty + sai, aph ^ 1u, abort, err)) goto producers_done;
+            tc::mbar_arrive_expect_tx(a_full + sai, A_SLOT);
+            tc::bulk_g2s(sm + PcSmem::A + sai * A_SLOT, tabs + ((size_t)kc * nM + mt) * A_SLOT,
+                         A_SLOT, a_full + sai);
+          }
+        }
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
           const int e = tid + i * PRODUCERS;
@@ -224,49 +257,68 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
           *reinterpret_cast<uint4*>(sb + 2 * ATOM_B + o) = lo;
         }
         tc::fence_async_smem();
-        tc::mbar_arrive(full + s);
+        tc::mbar_arrive(b_full + sbi);
       }
     }
   producers_done:
-    // Do not leave with a table copy in flight (bounded).
-    if (tid == 0 && copied) tc::mbar_wait(full + (last_copy & 1u), (last_copy >> 1) & 1u, WAIT);
+    // Do not leave with a copy in flight: wait (bounded) for the last copy
+    // issued into every slot of both rings. A slot whose copies were all
+    // consumed has completed that phase, and the wait returns at once.
+    if (tid == 0) {
+      for (uint32_t i = 0; i < NA && i < ua; ++i) {
+        const uint32_t last = ua - 1 - ((ua - 1 - i) % NA);  // latest u < ua with u % NA == i
+        tc::mbar_wait(a_full + i, (last / NA) & 1u, WAIT);
+      }
+      if (IN_SPLIT)
+        for (uint32_t i = 0; i < NB && i < ub; ++i) {
+          const uint32_t last = ub - 1 - ((ub - 1 - i) % NB);
+          tc::mbar_wait(b_full + i, (last / NB) & 1u, WAIT);
+        }
+    }
   } else if (warp == RL::MMA_WARP) {
     // ------------------------------------------------------------ MMA issuer
     // The whole warp follows the barriers; lane 0 issues.
     const bool leader = (tid & 31) == 0;
     constexpr uint32_t IDESC = tc::idesc_bf16(128, 128, false, true);
-    uint32_t u = 0, lt = 0;
+    uint32_t ua = 0, ub = 0, lt = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
       const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
       if (!pc_wait(acc_empty + acc, aph ^ 1u, abort, err)) break;
       tc::fence_after_sync();
       const uint32_t d0 = tmem + acc * acc_cols;
       bool ok = true;
-      for (int kc = 0; kc < nK; ++kc, ++u) {
-        const uint32_t s = u & 1u, ph = (u >> 1) & 1u;
-        if (!pc_wait(full + s, ph, abort, err)) {
+      for (int kc = 0; kc < nK && ok; ++kc, ++ub) {
+        const uint32_t sbi = ub % NB;
+        if (!pc_wait(b_full + sbi, (ub / NB) & 1u, abort, err)) {
           ok = false;
           break;
         }
-        tc::fence_after_sync();
-        if (leader) {
-          const uint32_t sA = tc::smem_u32(sm + s * PcSmem::STAGE);
-          const uint32_t sB = sA + 4 * TILE_A;
-          for (int mt = 0; mt < nM; ++mt) {
+        const uint32_t sB = tc::smem_u32(sm + PcSmem::B + sbi * B_SLOT);
+        for (int mt = 0; mt < nM; ++mt, ++ua) {
+          const uint32_t sai = ua % NA;
+          if (!pc_wait(a_full + sai, (ua / NA) & 1u, abort, err)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          if (leader) {
+            const uint32_t sA = tc::smem_u32(sm + PcSmem::A + sai * A_SLOT);
+            const uint32_t d = d0 + mt * 128;
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
-              const uint64_t ah = tc::kmajor_sw128(sA + mt * TILE_A + 32 * ks);
-              const uint64_t al = tc::kmajor_sw128(sA + (nM + mt) * TILE_A + 32 * ks);
+              const uint64_t ah = tc::kmajor_sw128(sA + 32 * ks);
+              const uint64_t al = tc::kmajor_sw128(sA + TILE_A + 32 * ks);
               const uint64_t bh = tc::mnmajor_sw128(sB + 2048 * ks, ATOM_B, 1024);
               const uint64_t bl = tc::mnmajor_sw128(sB + 2 * ATOM_B + 2048 * ks, ATOM_B, 1024);
-              const uint32_t d = d0 + mt * 128;
               tc::mma_bf16(d, ah, bh, IDESC, (kc > 0 || ks > 0) ? 1u : 0u);
               tc::mma_bf16(d, ah, bl, IDESC, 1u);
               tc::mma_bf16(d, al, bh, IDESC, 1u);
             }
+            tc::mma_commit(a_empty + sai);
           }
-          tc::mma_commit(empty + s);
+          __syncwarp();
         }
+        if (ok && leader) tc::mma_commit(b_empty + sbi);
         __syncwarp();
       }
       if (!ok) break;
@@ -401,8 +453,8 @@ static float bf16_to_float(uint16_t b) {
 }
 
 // Split BF16 hi / lo tables of an FP32 r x r matrix (row-major), stored as the
-// shared-memory image the kernel copies per K chunk: for chunk kc, the blocks
-// [hi m0, hi m1, lo m0, lo m1], each [128 rows][64 columns] 128B-swizzled.
+// shared-memory images the kernel copies: for K chunk kc and row block mt, the
+// 32 KB slot [hi, lo], each [128 rows][64 columns] 128B-swizzled.
 void dct_tc_tables(int r, const float* Mx, uint16_t* dst) {
   const int nM = (r + 127) / 128, nK = (r + 63) / 64;
   uint8_t* base = reinterpret_cast<uint8_t*>(dst);
@@ -410,7 +462,7 @@ void dct_tc_tables(int r, const float* Mx, uint16_t* dst) {
   for (int kc = 0; kc < nK; ++kc)
     for (int part = 0; part < 2; ++part)
       for (int mt = 0; mt < nM; ++mt) {
-        uint8_t* blk = base + ((size_t)kc * nM * 2 + part * nM + mt) * TILE_A;
+        uint8_t* blk = base + ((size_t)kc * nM + mt) * A_SLOT + part * TILE_A;
         for (int rr = 0; rr < 128; ++rr)
           for (int k = 0; k < 64; ++k) {
             const int i = mt * 128 + rr, j = kc * 64 + k;
