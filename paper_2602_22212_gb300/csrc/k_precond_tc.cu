@@ -43,16 +43,19 @@ constexpr uint32_t A_SLOT = 2 * TILE_A;  // hi and lo of one 128-row table block
 constexpr uint32_t B_SLOT = 4 * ATOM_B;  // hi (2 atoms) and lo (2 atoms) of one input chunk
 constexpr int NA = 4, NB = 3;            // ring depths (table blocks, input chunks)
 constexpr uint32_t WAIT = 1u << 22;
-// Warp roles: producers [0, PW), epilogue [PW, PW + EW), the MMA warp PW + EW.
-// A pass that splits FP32 input needs 4 producer warps; one whose input comes
-// by TMA needs one thread to issue it, and gives the warps to the epilogue
-// (two per TMEM lane quarter, each draining half of the tile's columns).
+// Warp roles: input producers [0, BW), the table warp BW, epilogue [PW, PW +
+// EW), the MMA warp PW + EW. A pass that splits FP32 input needs 4 input
+// warps; one whose input comes by TMA needs one thread to issue it, and gives
+// the warps to the epilogue (two per TMEM lane quarter, each draining half of
+// the tile's columns). The table blocks have a warp of their own so that the
+// input copies run ahead of them, as far as the input ring allows.
 template <bool IN_SPLIT> struct Roles {
-  static constexpr int PW = IN_SPLIT ? 1 : 4, EW = IN_SPLIT ? 8 : 4;
-  static constexpr int PRODUCERS = PW * 32, EPILOGUE = EW * 32, MMA_WARP = PW + EW;
+  static constexpr int BW = IN_SPLIT ? 1 : 4, PW = BW + 1, EW = IN_SPLIT ? 8 : 4;
+  static constexpr int PRODUCERS = BW * 32, EPILOGUE = EW * 32, MMA_WARP = PW + EW;
   static constexpr int THREADS = (PW + EW + 1) * 32;
 };
 constexpr int PRODUCERS = Roles<false>::PRODUCERS;
+
 
 // Table ring (NA blocks [hi, lo] of 128 rows x 64 K), input ring (NB chunks
 // [hi atom 0, hi atom 1, lo atom 0, lo atom 1]), the spectral weights mu (r <=
@@ -183,18 +186,16 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_ptr;
 
-  if (warp < RL::PW) {
-    // ------------------------------------------------------------ producers
-    // Thread 0 issues the input chunk's TMA loads (split input), then the
-    // chunk's table blocks; with FP32 input every producer loads, splits and
-    // stores its share of the chunk, and thread 0 issues the table blocks
-    // while its loads are in flight.
-    uint32_t ua = 0, ub = 0;
+  if (warp < RL::BW) {
+    // ------------------------------------------------------------ input producers
+    // TMA input: thread 0 issues the chunk's four loads. FP32 input: every
+    // producer loads, splits and stores its share of the chunk.
+    uint32_t ub = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       const long long col0 = tile * 128;
       for (int kc = 0; kc < nK; ++kc, ++ub) {
         const uint32_t sbi = ub % NB, bph = (ub / NB) & 1u;
-        if (!pc_wait(b_empty + sbi, bph ^ 1u, abort, err)) goto producers_done;
+        if (!pc_wait(b_empty + sbi, bph ^ 1u, abort, err)) goto inputs_done;
         uint8_t* sb = sm + PcSmem::B + sbi * B_SLOT;
         if (IN_SPLIT) {
           if (tid == 0) {
@@ -205,16 +206,6 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
                               b_full + sbi);
               tc::tma_load_2d(sb + (2 + h) * ATOM_B, &tm_lo, (int)(col0 + 64 * h), kc * 64,
                               b_full + sbi);
-            }
-            for (int mt = 0; mt < nM; ++mt, ++ua) {
-              const uint32_t sai = ua % NA, aph = (ua / NA) & 1u;
-              if (!pc_wait(a_empty + sai, aph ^ 1u, abort, err)) {
-                ++ub;  // this chunk's input copy is in flight
-                goto producers_done;
-              }
-              tc::mbar_arrive_expect_tx(a_full + sai, A_SLOT);
-              tc::bulk_g2s(sm + PcSmem::A + sai * A_SLOT,
-                           tabs + ((size_t)kc * nM + mt) * A_SLOT, A_SLOT, a_full + sai);
             }
           }
           continue;
@@ -238,15 +229,6 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
               x[i][j] = (n < r && c0 + j < ncol) ? in[(long long)n * ncol + c0 + j] : 0.f;
           }
         }
-        if (tid == 0) {
-          for (int mt = 0; mt < nM; ++mt, ++ua) {
-            const uint32_t sai = ua % NA, aph = (ua / NA) & 1u;
-            if (!pc_wait(a_empty + sai, aph ^ 1u, abort, err)) goto producers_done;
-            tc::mbar_arrive_expect_tx(a_full + sai, A_SLOT);
-            tc::bulk_g2s(sm + PcSmem::A + sai * A_SLOT, tabs + ((size_t)kc * nM + mt) * A_SLOT,
-                         A_SLOT, a_full + sai);
-          }
-        }
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
           const int e = tid + i * PRODUCERS;
@@ -260,20 +242,33 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
         tc::mbar_arrive(b_full + sbi);
       }
     }
-  producers_done:
+  inputs_done:
     // Do not leave with a copy in flight: wait (bounded) for the last copy
-    // issued into every slot of both rings. A slot whose copies were all
-    // consumed has completed that phase, and the wait returns at once.
-    if (tid == 0) {
+    // issued into every slot. A slot whose copies were all consumed has
+    // completed that phase, and the wait returns at once.
+    if (IN_SPLIT && tid == 0)
+      for (uint32_t i = 0; i < NB && i < ub; ++i) {
+        const uint32_t last = ub - 1 - ((ub - 1 - i) % NB);  // latest u < ub with u % NB == i
+        tc::mbar_wait(b_full + i, (last / NB) & 1u, WAIT);
+      }
+  } else if (warp == RL::BW) {
+    // ------------------------------------------------------------ table blocks
+    if ((tid & 31) == 0) {
+      uint32_t ua = 0;
+      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        for (int kc = 0; kc < nK; ++kc)
+          for (int mt = 0; mt < nM; ++mt, ++ua) {
+            const uint32_t sai = ua % NA, aph = (ua / NA) & 1u;
+            if (!pc_wait(a_empty + sai, aph ^ 1u, abort, err)) goto tables_done;
+            tc::mbar_arrive_expect_tx(a_full + sai, A_SLOT);
+            tc::bulk_g2s(sm + PcSmem::A + sai * A_SLOT, tabs + ((size_t)kc * nM + mt) * A_SLOT,
+                         A_SLOT, a_full + sai);
+          }
+    tables_done:
       for (uint32_t i = 0; i < NA && i < ua; ++i) {
-        const uint32_t last = ua - 1 - ((ua - 1 - i) % NA);  // latest u < ua with u % NA == i
+        const uint32_t last = ua - 1 - ((ua - 1 - i) % NA);
         tc::mbar_wait(a_full + i, (last / NA) & 1u, WAIT);
       }
-      if (IN_SPLIT)
-        for (uint32_t i = 0; i < NB && i < ub; ++i) {
-          const uint32_t last = ub - 1 - ((ub - 1 - i) % NB);
-          tc::mbar_wait(b_full + i, (last / NB) & 1u, WAIT);
-        }
     }
   } else if (warp == RL::MMA_WARP) {
     // ------------------------------------------------------------ MMA issuer
@@ -374,7 +369,7 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
               float sc = 1.f;
               if (SCALE) {
                 const float dd = 1.f + lambda * (smu[pa] + smu[pb] + smu[k]);
-                sc = 1.f / (dd * dd);
+                sc = __frcp_rn(dd * dd);  // = 1 / dd^2, correctly rounded
               }
               const float x0 = __uint_as_float(v[4 * q]) * sc;
               const float x1 = __uint_as_float(v[4 * q + 1]) * sc;
@@ -402,7 +397,7 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
               float sc = 1.f;
               if (SCALE) {
                 const float dd = 1.f + lambda * (smu[pa] + smu[pb] + smu[k]);
-                sc = 1.f / (dd * dd);
+                sc = __frcp_rn(dd * dd);  // = 1 / dd^2, correctly rounded
               }
               const float x = __uint_as_float(v[j]) * sc;
               if (OUT_SPLIT) {
