@@ -125,12 +125,11 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g,
   const float c1 = cc[0], c2 = cc[1];
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
-    const float gk = g[k];
-    const float mk = fmaf(b1, m[k], (1.f - b1) * gk);
-    const float vk = fmaf(b2, v[k], (1.f - b2) * gk * gk);
+    float mk = m[k], vk = v[k], pk = p[k];
+    adam_update(g[k], mk, vk, pk, lr, b1, b2, eps, c1, c2);
     m[k] = mk;
     v[k] = vk;
-    p[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+    p[k] = pk;
   }
 }
 
@@ -146,15 +145,10 @@ __global__ void adam4_kernel(float4* __restrict__ p, const float4* __restrict__ 
   const float c1 = cc[0], c2 = cc[1];
   const float4 gk = __ldcs(g + k);
   float4 mk = __ldcs(m + k), vk = __ldcs(v + k), pk = __ldcs(p + k);
-  auto upd = [&](float gg, float& mm, float& vv, float& pp) {
-    mm = fmaf(b1, mm, (1.f - b1) * gg);
-    vv = fmaf(b2, vv, (1.f - b2) * gg * gg);
-    pp -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
-  };
-  upd(gk.x, mk.x, vk.x, pk.x);
-  upd(gk.y, mk.y, vk.y, pk.y);
-  upd(gk.z, mk.z, vk.z, pk.z);
-  upd(gk.w, mk.w, vk.w, pk.w);
+  adam_update(gk.x, mk.x, vk.x, pk.x, lr, b1, b2, eps, c1, c2);
+  adam_update(gk.y, mk.y, vk.y, pk.y, lr, b1, b2, eps, c1, c2);
+  adam_update(gk.z, mk.z, vk.z, pk.z, lr, b1, b2, eps, c1, c2);
+  adam_update(gk.w, mk.w, vk.w, pk.w, lr, b1, b2, eps, c1, c2);
   __stcs(m + k, mk);
   __stcs(v + k, vk);
   __stcs(p + k, pk);

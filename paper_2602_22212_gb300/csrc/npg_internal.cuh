@@ -221,6 +221,16 @@ size_t dct_tc_table_elems(int r);
 // r^3 x F level: its split hi / lo intermediates with padded rows.
 size_t dct_tc_scratch_elems(int r, int F);
 void dct_tc_tables(int r, const float* Mx, uint16_t* dst);
+// One Adam step of one parameter (Sec. 3.5: Adam on the preconditioned
+// gradient), bias corrections c1 = 1 - b1^s, c2 = 1 - b2^s of step s; shared
+// by the scalar and the float4 Adam kernels.
+__device__ __forceinline__ void adam_update(float g, float& m, float& v, float& p, float lr,
+                                            float b1, float b2, float eps, float c1, float c2) {
+  m = fmaf(b1, m, (1.f - b1) * g);
+  v = fmaf(b2, v, (1.f - b2) * g * g);
+  p -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
 cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float* t1,
                                    const uint16_t* tabC, const uint16_t* tabCt, const float* mu,
                                    int r, int F, float lambda, int* err, cudaStream_t s);
