@@ -43,14 +43,17 @@ constexpr uint32_t A_SLOT = 2 * TILE_A;  // hi and lo of one 128-row table block
 constexpr uint32_t B_SLOT = 4 * ATOM_B;  // hi (2 atoms) and lo (2 atoms) of one input chunk
 constexpr int NA = 4, NB = 3;            // ring depths (table blocks, input chunks)
 constexpr uint32_t WAIT = 1u << 22;
-// Warp roles: input producers [0, BW), the table warp BW, epilogue [PW, PW +
-// EW), the MMA warp PW + EW. A pass that splits FP32 input needs 4 input
-// warps; one whose input comes by TMA needs one thread to issue it, and gives
-// the warps to the epilogue (two per TMEM lane quarter, each draining half of
-// the tile's columns). The table blocks have a warp of their own so that the
-// input copies run ahead of them, as far as the input ring allows.
+// Warp roles: input producers [0, BW), the table warp BW, (FP32 input) the raw
+// warp BW + 1, epilogue [PW, PW + EW), the MMA warp PW + EW. A pass that splits
+// FP32 input needs 4 input warps, which split the raw chunks that the raw warp
+// brings by TMA (or load them themselves); one whose input comes split by TMA
+// needs one thread to issue it, and gives the warps to the epilogue (two per
+// TMEM lane quarter, each draining half of the tile's columns). The table
+// blocks have a warp of their own so that the input copies run ahead of them,
+// as far as the input ring allows.
 template <bool IN_SPLIT> struct Roles {
-  static constexpr int BW = IN_SPLIT ? 1 : 4, PW = BW + 1, EW = IN_SPLIT ? 8 : 4;
+  static constexpr int BW = IN_SPLIT ? 1 : 4, PW = IN_SPLIT ? BW + 1 : BW + 2;
+  static constexpr int EW = IN_SPLIT ? 8 : 4;
   static constexpr int PRODUCERS = BW * 32, EPILOGUE = EW * 32, MMA_WARP = PW + EW;
   static constexpr int THREADS = (PW + EW + 1) * 32;
 };
@@ -64,9 +67,10 @@ struct PcSmem {
   static constexpr uint32_t A = 0;
   static constexpr uint32_t B = A + NA * A_SLOT;
   static constexpr uint32_t MU = B + NB * B_SLOT;
-  // a_full[NA], a_empty[NA], b_full[NB], b_empty[NB], acc_full[2], acc_empty[2], fin
+  // a_full[NA], a_empty[NA], b_full[NB], b_empty[NB], acc_full[2], acc_empty[2], fin,
+  // raw_full[NB], raw_read[NB]
   static constexpr uint32_t BAR = MU + 256 * 4;
-  static constexpr uint32_t NBAR = 2 * NA + 2 * NB + 5;
+  static constexpr uint32_t NBAR = 2 * NA + 4 * NB + 5;
   static constexpr uint32_t FLAGS = BAR + NBAR * 8;
   static constexpr uint32_t TOTAL = FLAGS + 16;
 };
@@ -136,7 +140,8 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
     const float* __restrict__ in, float* __restrict__ out, const uint8_t* __restrict__ tabs,
     const float* __restrict__ mu, int r, int F, float lambda, int* err,
     const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
-    __nv_bfloat16* __restrict__ ohi, __nv_bfloat16* __restrict__ olo, long long pitch) {
+    __nv_bfloat16* __restrict__ ohi, __nv_bfloat16* __restrict__ olo, long long pitch,
+    const __grid_constant__ CUtensorMap tm_raw, int raw_tma) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = tc::align1024(smem_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + PcSmem::BAR);
@@ -147,6 +152,8 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
   uint64_t* acc_full = b_empty + NB;
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* fin = acc_empty + 2;
+  uint64_t* raw_full = fin + 1;
+  uint64_t* raw_read = raw_full + NB;
   volatile int* abort = reinterpret_cast<volatile int*>(sm + PcSmem::FLAGS);
   uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(sm + PcSmem::FLAGS + 4);
   float* smu = reinterpret_cast<float*>(sm + PcSmem::MU);
@@ -174,6 +181,10 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
       tc::mbar_init(acc_empty + b, RL::EPILOGUE);
     }
     tc::mbar_init(fin, 1);
+    for (int b = 0; b < NB; ++b) {
+      tc::mbar_init(raw_full + b, 1);
+      tc::mbar_init(raw_read + b, RL::PRODUCERS);
+    }
     *abort = 0;
     tc::fence_mbar_init();
   }
@@ -213,6 +224,25 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
         // 64 K-rows x 16 groups of 8 columns; all loads issued before any store.
         constexpr int PER = 64 * 16 / PRODUCERS;
         float x[PER][8];
+        if (raw_tma) {
+          // The raw FP32 chunk is in this slot (four 128B-swizzled boxes of 64
+          // rows x 32 columns); every producer reads its values before any of
+          // them overwrites the slot with the split operand.
+          if (!pc_wait(raw_full + sbi, bph, abort, err)) goto inputs_done;
+#pragma unroll
+          for (int i = 0; i < PER; ++i) {
+            const int e = tid + i * PRODUCERS;
+            const uint32_t n = (uint32_t)(e >> 4), g = (uint32_t)(e & 15);
+            const uint8_t* row = sb + (g >> 2) * 8192u + n * 128u;
+            const uint32_t c0 = (g & 3u) * 2u;
+            const float4 a = *reinterpret_cast<const float4*>(row + ((c0 ^ (n & 7u)) << 4));
+            const float4 b = *reinterpret_cast<const float4*>(row + (((c0 + 1u) ^ (n & 7u)) << 4));
+            x[i][0] = a.x; x[i][1] = a.y; x[i][2] = a.z; x[i][3] = a.w;
+            x[i][4] = b.x; x[i][5] = b.y; x[i][6] = b.z; x[i][7] = b.w;
+          }
+          tc::mbar_arrive(raw_read + sbi);
+          if (!pc_wait(raw_read + sbi, bph, abort, err)) goto inputs_done;
+        } else
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
           const int e = tid + i * PRODUCERS;
@@ -268,6 +298,30 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
       for (uint32_t i = 0; i < NA && i < ua; ++i) {
         const uint32_t last = ua - 1 - ((ua - 1 - i) % NA);
         tc::mbar_wait(a_full + i, (last / NA) & 1u, WAIT);
+      }
+    }
+  } else if (!IN_SPLIT && warp == RL::BW + 1) {
+    // ------------------------------------------------------------ raw FP32 chunks
+    // Lane 0 brings each input chunk as FP32 into its slot of the input ring
+    // (four 128B-swizzled TMA boxes of 64 rows x 32 columns; rows and columns
+    // outside the level read as 0), as far ahead as the ring allows.
+    if (raw_tma && (tid & 31) == 0) {
+      uint32_t ub = 0;
+      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        for (int kc = 0; kc < nK; ++kc, ++ub) {
+          const uint32_t sbi = ub % NB, bph = (ub / NB) & 1u;
+          if (!pc_wait(b_empty + sbi, bph ^ 1u, abort, err)) goto raw_done;
+          uint8_t* sb = sm + PcSmem::B + sbi * B_SLOT;
+          tc::mbar_arrive_expect_tx(raw_full + sbi, B_SLOT);
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            tc::tma_load_2d(sb + b * 8192, &tm_raw, (int)(tile * 128 + 32 * b), kc * 64,
+                            raw_full + sbi);
+        }
+    raw_done:
+      for (uint32_t i = 0; i < NB && i < ub; ++i) {
+        const uint32_t last = ub - 1 - ((ub - 1 - i) % NB);
+        tc::mbar_wait(raw_full + i, (last / NB) & 1u, WAIT);
       }
     }
   } else if (warp == RL::MMA_WARP) {
@@ -517,6 +571,21 @@ static bool split_map(CUtensorMap* m, const __nv_bfloat16* base, int rows, long 
          CUDA_SUCCESS;
 }
 
+// Tensor map of the FP32 input: r rows of `cols` floats; boxes of 64 rows x 32
+// columns, 128-byte swizzle, zero fill outside. Needs 16-byte aligned rows.
+static bool raw_map(CUtensorMap* m, const float* base, int rows, long long cols) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc || (cols & 3) != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
+  const cuuint32_t box[2] = {32, 64};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 // t0, t1: scratch of dct_tc_scratch_elems(r, F) floats each, holding the split
 // intermediates (hi then lo BF16 arrays).
 cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float* t1,
@@ -558,18 +627,23 @@ cudaError_t launch_precondition_tc(const float* g, float* out, float* t0, float*
     return cudaErrorInvalidValue;
   // g -> t0 (split) -> t1 -> t0 (scaled) -> t1 -> t0 -> out (FP32)
   constexpr int T0 = Roles<false>::THREADS, T1 = Roles<true>::THREADS;
+  // the first pass reads its FP32 input by TMA where the rows allow it (else
+  // its producers load it)
+  CUtensorMap mraw;
+  const int raw = raw_map(&mraw, g, r, ncol) ? 1 : 0;
+  if (!raw) mraw = mh0;  // not read
   dct_pass_tc_kernel<false, false, true><<<grid, T0, smem, s>>>(
-      g, nullptr, C, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch);
+      g, nullptr, C, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch, mraw, raw);
   dct_pass_tc_kernel<false, true, true><<<grid, T1, smem, s>>>(
-      nullptr, nullptr, C, mu, r, F, lambda, err, mh0, ml0, h1, l1, pitch);
+      nullptr, nullptr, C, mu, r, F, lambda, err, mh0, ml0, h1, l1, pitch, mh0, 0);
   dct_pass_tc_kernel<true, true, true><<<grid, T1, smem, s>>>(
-      nullptr, nullptr, C, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch);
+      nullptr, nullptr, C, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch, mh0, 0);
   dct_pass_tc_kernel<false, true, true><<<grid, T1, smem, s>>>(
-      nullptr, nullptr, Ct, mu, r, F, lambda, err, mh0, ml0, h1, l1, pitch);
+      nullptr, nullptr, Ct, mu, r, F, lambda, err, mh0, ml0, h1, l1, pitch, mh0, 0);
   dct_pass_tc_kernel<false, true, true><<<grid, T1, smem, s>>>(
-      nullptr, nullptr, Ct, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch);
+      nullptr, nullptr, Ct, mu, r, F, lambda, err, mh1, ml1, h0, l0, pitch, mh0, 0);
   dct_pass_tc_kernel<false, true, false><<<grid, T1, smem, s>>>(
-      nullptr, out, Ct, mu, r, F, lambda, err, mh0, ml0, nullptr, nullptr, pitch);
+      nullptr, out, Ct, mu, r, F, lambda, err, mh0, ml0, nullptr, nullptr, pitch, mh0, 0);
   return cudaGetLastError();
 }
 
