@@ -25,7 +25,8 @@
 // rows padded to a multiple of 8 elements), and the next pass then loads its
 // input tiles with TMA straight into the swizzled operand layout, so that its
 // producer warps move no data through registers. Only the first pass reads
-// (and splits) FP32 and only the last one writes FP32.
+// FP32 (by TMA into the input slot, where its producers split it in place) and
+// only the last one writes FP32.
 #include <cuda.h>  // CUtensorMap and its encoder's types (the encoder is fetched at run time)
 #include <cuda_bf16.h>
 
