@@ -413,23 +413,36 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
               pb -= r;
               ++pa;
             }
+            int pq[4], bq[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               if (q > 0 && ++pb == r) {
                 pb = 0;
                 ++pa;
               }
+              pq[q] = pa;
+              bq[q] = pb;
+            }
+            // the four scale factors first (independent of the stores; pa runs
+            // past r - 1 only for columns beyond the level, never stored)
+            float sc[4] = {1.f, 1.f, 1.f, 1.f};
+            if (SCALE) {
+              const float mk = smu[k];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float dd = 1.f + lambda * (smu[min(pq[q], r - 1)] + smu[bq[q]] + mk);
+                sc[q] = __frcp_rn(dd * dd);  // = 1 / dd^2, correctly rounded
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int pa = pq[q], pb = bq[q];
               const long long col = col0 + cg + 4 * q;
               if (col >= ncol) break;
-              float sc = 1.f;
-              if (SCALE) {
-                const float dd = 1.f + lambda * (smu[pa] + smu[pb] + smu[k]);
-                sc = __frcp_rn(dd * dd);  // = 1 / dd^2, correctly rounded
-              }
-              const float x0 = __uint_as_float(v[4 * q]) * sc;
-              const float x1 = __uint_as_float(v[4 * q + 1]) * sc;
-              const float x2 = __uint_as_float(v[4 * q + 2]) * sc;
-              const float x3 = __uint_as_float(v[4 * q + 3]) * sc;
+              const float x0 = __uint_as_float(v[4 * q]) * sc[q];
+              const float x1 = __uint_as_float(v[4 * q + 1]) * sc[q];
+              const float x2 = __uint_as_float(v[4 * q + 2]) * sc[q];
+              const float x3 = __uint_as_float(v[4 * q + 3]) * sc[q];
               if (OUT_SPLIT) {
                 const long long o = (long long)pa * pitch + (long long)pb * rF + (long long)k * 4;
                 uint2 hi, lo;
