@@ -48,13 +48,13 @@ constexpr uint32_t WAIT = 1u << 22;
 // warp BW + 1, epilogue [PW, PW + EW), the MMA warp PW + EW. A pass that splits
 // FP32 input needs 4 input warps, which split the raw chunks that the raw warp
 // brings by TMA (or load them themselves); one whose input comes split by TMA
-// needs one thread to issue it, and gives the warps to the epilogue (two per
-// TMEM lane quarter, each draining half of the tile's columns). The table
-// blocks have a warp of their own so that the input copies run ahead of them,
-// as far as the input ring allows.
+// needs one thread to issue it. Both have 8 epilogue warps, two per TMEM lane
+// quarter, each draining half of the tile's columns. The table blocks have a
+// warp of their own so that the input copies run ahead of them, as far as the
+// input ring allows.
 template <bool IN_SPLIT> struct Roles {
   static constexpr int BW = IN_SPLIT ? 1 : 4, PW = IN_SPLIT ? BW + 1 : BW + 2;
-  static constexpr int EW = IN_SPLIT ? 8 : 4;
+  static constexpr int EW = 8;
   static constexpr int PRODUCERS = BW * 32, EPILOGUE = EW * 32, MMA_WARP = PW + EW;
   static constexpr int THREADS = (PW + EW + 1) * 32;
 };
@@ -222,52 +222,62 @@ __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kerne
           }
           continue;
         }
-        // 64 K-rows x 16 groups of 8 columns; all loads issued before any store.
-        constexpr int PER = 64 * 16 / PRODUCERS;
-        float x[PER][8];
-        if (raw_tma) {
-          // The raw FP32 chunk is in this slot (four 128B-swizzled boxes of 64
-          // rows x 32 columns); every producer reads its values before any of
-          // them overwrites the slot with the split operand.
-          if (!pc_wait(raw_full + sbi, bph, abort, err)) goto inputs_done;
+        // 64 K-rows x 16 groups of 8 columns, in two halves of 32 rows; each
+        // half's loads are issued before its stores. The raw rows 0-31 and the
+        // split rows 0-31 both lie in the first 4 KB of each 8 KB box / atom of
+        // the slot, rows 32-63 in the second: a half's stores overwrite only
+        // raw values of the same half.
+        constexpr int PER = 32 * 16 / PRODUCERS;
+        if (raw_tma && !pc_wait(raw_full + sbi, bph, abort, err)) goto inputs_done;
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+          float x[PER][8];
+          if (raw_tma) {
+            // the raw FP32 chunk is in this slot (four 128B-swizzled boxes of
+            // 64 rows x 32 columns); every producer reads its values of the
+            // half before any of them overwrites it with the split operand
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+              const int e = tid + i * PRODUCERS;
+              const uint32_t n = (uint32_t)(32 * half + (e >> 4)), g = (uint32_t)(e & 15);
+              const uint8_t* row = sb + (g >> 2) * 8192u + n * 128u;
+              const uint32_t c0 = (g & 3u) * 2u;
+              const float4 a = *reinterpret_cast<const float4*>(row + ((c0 ^ (n & 7u)) << 4));
+              const float4 b =
+                  *reinterpret_cast<const float4*>(row + (((c0 + 1u) ^ (n & 7u)) << 4));
+              x[i][0] = a.x; x[i][1] = a.y; x[i][2] = a.z; x[i][3] = a.w;
+              x[i][4] = b.x; x[i][5] = b.y; x[i][6] = b.z; x[i][7] = b.w;
+            }
+            // one phase per half: the phase of half h has parity h
+            tc::mbar_arrive(raw_read + sbi);
+            if (!pc_wait(raw_read + sbi, (uint32_t)half, abort, err)) goto inputs_done;
+          } else
 #pragma unroll
           for (int i = 0; i < PER; ++i) {
             const int e = tid + i * PRODUCERS;
-            const uint32_t n = (uint32_t)(e >> 4), g = (uint32_t)(e & 15);
-            const uint8_t* row = sb + (g >> 2) * 8192u + n * 128u;
-            const uint32_t c0 = (g & 3u) * 2u;
-            const float4 a = *reinterpret_cast<const float4*>(row + ((c0 ^ (n & 7u)) << 4));
-            const float4 b = *reinterpret_cast<const float4*>(row + (((c0 + 1u) ^ (n & 7u)) << 4));
-            x[i][0] = a.x; x[i][1] = a.y; x[i][2] = a.z; x[i][3] = a.w;
-            x[i][4] = b.x; x[i][5] = b.y; x[i][6] = b.z; x[i][7] = b.w;
+            const int n = kc * 64 + 32 * half + (e >> 4);
+            const long long c0 = col0 + (e & 15) * 8;
+            if (n < r && (ncol & 3) == 0 && c0 + 8 <= ncol) {
+              const float4* p = reinterpret_cast<const float4*>(in + (long long)n * ncol + c0);
+              const float4 a = __ldcs(p), b = __ldcs(p + 1);
+              x[i][0] = a.x; x[i][1] = a.y; x[i][2] = a.z; x[i][3] = a.w;
+              x[i][4] = b.x; x[i][5] = b.y; x[i][6] = b.z; x[i][7] = b.w;
+            } else {
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                x[i][j] = (n < r && c0 + j < ncol) ? in[(long long)n * ncol + c0 + j] : 0.f;
+            }
           }
-          tc::mbar_arrive(raw_read + sbi);
-          if (!pc_wait(raw_read + sbi, bph, abort, err)) goto inputs_done;
-        } else
 #pragma unroll
-        for (int i = 0; i < PER; ++i) {
-          const int e = tid + i * PRODUCERS;
-          const int n = kc * 64 + (e >> 4);
-          const long long c0 = col0 + (e & 15) * 8;
-          if (n < r && (ncol & 3) == 0 && c0 + 8 <= ncol) {
-            const float4* p = reinterpret_cast<const float4*>(in + (long long)n * ncol + c0);
-            const float4 a = __ldcs(p), b = __ldcs(p + 1);
-            x[i][0] = a.x; x[i][1] = a.y; x[i][2] = a.z; x[i][3] = a.w;
-            x[i][4] = b.x; x[i][5] = b.y; x[i][6] = b.z; x[i][7] = b.w;
-          } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              x[i][j] = (n < r && c0 + j < ncol) ? in[(long long)n * ncol + c0 + j] : 0.f;
+          for (int i = 0; i < PER; ++i) {
+            const int e = tid + i * PRODUCERS;
+            uint4 hi, lo;
+            split8(x[i], hi, lo);
+            const uint32_t o =
+                mn_off((uint32_t)((e & 15) * 8), (uint32_t)(32 * half + (e >> 4)));
+            *reinterpret_cast<uint4*>(sb + o) = hi;
+            *reinterpret_cast<uint4*>(sb + 2 * ATOM_B + o) = lo;
           }
-        }
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-          const int e = tid + i * PRODUCERS;
-          uint4 hi, lo;
-          split8(x[i], hi, lo);
-          const uint32_t o = mn_off((uint32_t)((e & 15) * 8), (uint32_t)(e >> 4));
-          *reinterpret_cast<uint4*>(sb + o) = hi;
-          *reinterpret_cast<uint4*>(sb + 2 * ATOM_B + o) = lo;
         }
         tc::fence_async_smem();
         tc::mbar_arrive(b_full + sbi);
