@@ -134,8 +134,11 @@ __device__ __forceinline__ bool pc_wait(uint64_t* bar, uint32_t phase, volatile 
 // tabs: pre-swizzled 32 KB slots [kc][mt][hi, lo] (dct_tc_tables).
 // IN_SPLIT: the input is hi / lo BF16 rows loaded by TMA (tm_hi, tm_lo, boxes
 // of 64 rows x 64 columns, 128B swizzle); else FP32 `in`, split by the
-// producers. OUT_SPLIT: the output goes to hi / lo BF16 arrays `ohi`, `olo`
-// with row pitch `pitch`; else FP32 `out`.
+// producers after the raw warp brought it by TMA (tm_raw, boxes of 64 rows x
+// 32 columns, 128B swizzle; raw_tma != 0) or loaded by themselves (raw_tma ==
+// 0: rows that are not 16-byte multiples or an unaligned base). OUT_SPLIT: the
+// output goes to hi / lo BF16 arrays `ohi`, `olo` with row pitch `pitch`; else
+// FP32 `out`.
 template <bool SCALE, bool IN_SPLIT, bool OUT_SPLIT>
 __global__ void __launch_bounds__(Roles<IN_SPLIT>::THREADS, 1) dct_pass_tc_kernel(
     const float* __restrict__ in, float* __restrict__ out, const uint8_t* __restrict__ tabs,
